@@ -1,0 +1,708 @@
+"""FP64 CPU oracle for the standardized Fourier-coefficient PTA posterior.
+
+TEST INFRASTRUCTURE ONLY.  Only the test-suite, the package's smoke check and
+the benchmark's CPU-baseline leg may import this module.  It shares no code
+with the CUDA path and imports nothing from it.
+
+Every function is the plain definition of the quantity it returns, written in
+FP64 with numpy, following the paper (Gundersen, van Haasteren, Cornish,
+Vallisneri, Meyers, "A new framework for lightning-fast gravitational wave
+analysis of pulsar timing data"):
+
+  * white-noise covariance N            Eq. (WN_cov), Sec. "White noise"
+  * Fourier basis F, DM basis F_DM      Eq. (Fourier_series) and the text after
+                                        it, Sec. "Red and chromatic noise"
+  * prior covariance phi, HD ORF        Eqs. (prior_cov), (HD), Sec. "Priors"
+  * power-law spectrum                  Eq. (power_law)
+  * timing-model marginalisation N~^-1  Eq. (Gmatrix_proj) and its QR form
+  * standardizing transform a = L z     Eqs. (standardizing_transform),
+                                        (standardized_density) with mu = 0 and
+                                        Sigma = phi (prior-whitened reading)
+  * posterior with deterministic signal Eq. (raw_det_posterior)
+  * CW phase / frequency evolution      Eqs. (phase_evolve), (CW_evolve),
+                                        (phase_evolve_Taylor)
+  * HMC leapfrog + Metropolis accept    Eqs. (Hamiltonian), (Hamilton's_eq),
+                                        (Gaussian_momentum), (HMC_acceptance)
+
+Units: residuals, uncertainties and covariances in ns / ns^2 (Sec. "Single
+precision"), times in s.  The canonical log-posterior ``logp`` drops the
+data-only constants that the paper drops (det 2 pi N, det M^T N^-1 M); the
+function ``logp_full`` adds them back (and the (2 pi)^(-D_z/2) of the z
+prior) so that it is a normalised density in z.
+
+Pins (tests/test_oracle_*.py): HD closed-form values; power-law spectral ratios
+and a hand value; three routes to N~^-1 agree; logp_full integrated over z in
+closed form equals the dense time-domain Gaussian marginal likelihood with
+C = N + F phi F^T; the log-det cancellation of the prior-whitened transform;
+the Gram-form (Eq. stochastic_posterior) equivalence; central finite
+differences of every gradient block; CW invariants (h -> 0, L -> 0 with equal
+phases, psi -> psi + pi/2, dPhi/dt = omega(t), antenna-pattern identity);
+Philox4x32-10 known-answer vectors; HMC reversibility and Gaussian moments.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.linalg as sla
+
+YEAR_S = 365.25 * 86400.0
+F_YR = 1.0 / YEAR_S
+NU_REF_MHZ = 1400.0
+TSUN_S = 4.925490947641267e-06       # G Msun / c^3 in s
+KPC_S = 1.0292712503e11              # 1 kpc / c in s
+LN10 = math.log(10.0)
+
+# uniform hyper-prior boxes (Sec. "Priors": log10 A ~ U(-20, -10), gamma ~ U(0, 7),
+# identical for intrinsic red noise; the same box is used for DM)
+PRIOR_LOG10A = (-20.0, -10.0)
+PRIOR_GAMMA = (0.0, 7.0)
+# CW prior boxes (order: log10 Mc, log10 f, log10 h, cos iota, psi, cos theta, phi, Phi0)
+PRIOR_CW = [(7.0, 10.5), (-9.0, -7.0), (-18.0, -11.0), (-1.0, 1.0), (0.0, math.pi),
+            (-1.0, 1.0), (0.0, 2.0 * math.pi), (0.0, 2.0 * math.pi)]
+PRIOR_PPHASE = (0.0, 2.0 * math.pi)
+DIST_SIGMA_KPC = 0.2                 # pulsar-distance prior width (Sec. "Analyses")
+
+
+# --------------------------------------------------------------------------- #
+# Building blocks, each the definition printed in the paper.
+# --------------------------------------------------------------------------- #
+def hellings_downs(pos: np.ndarray) -> np.ndarray:
+    """Eq. (HD): alpha_IJ = 3/2 b ln b - b/4 + 1/2 + delta_IJ/2, b = (1 - cos Theta_IJ)/2."""
+    npsr = pos.shape[0]
+    G = np.empty((npsr, npsr))
+    for I in range(npsr):
+        for J in range(npsr):
+            cos_t = float(np.clip(np.dot(pos[I], pos[J]), -1.0, 1.0))
+            b = 0.5 * (1.0 - cos_t)
+            blnb = b * math.log(b) if b > 0.0 else 0.0
+            G[I, J] = 1.5 * blnb - 0.25 * b + 0.5 + (0.5 if I == J else 0.0)
+    return G
+
+
+def power_law(log10A: float, gamma: float, k: np.ndarray, T: float) -> np.ndarray:
+    """Eq. (power_law) in ns^2: rho_k = A^2/(12 pi^2) (1/T) (f_k / f_yr)^(-gamma) yr^3 / yr,
+    i.e. A^2/(12 pi^2) f_yr^(gamma-3) f_k^(-gamma) / T with f_k = k/T, T in s."""
+    A = 10.0 ** log10A
+    f = np.asarray(k, dtype=float) / T
+    rho_s2 = A * A / (12.0 * math.pi ** 2) * F_YR ** (gamma - 3.0) * f ** (-gamma) / T
+    return rho_s2 * 1e18
+
+
+def white_noise_var(psr) -> np.ndarray:
+    """Eq. (WN_cov): N_ii = EFAC_mu^2 sigma_i^2 + EQUAD_mu^2, in ns^2."""
+    s = psr.sigma_s * 1e9
+    b = psr.backend
+    return psr.efac[b] ** 2 * s * s + (psr.equad_s[b] * 1e9) ** 2
+
+
+def fourier_basis(t_rel: np.ndarray, T: float, nf: int) -> np.ndarray:
+    """Eq. (Fourier_series): columns [sin(2 pi k t/T), cos(2 pi k t/T)] for k = 1..nf,
+    ordered so that F a = sum_k a_k sin + b_k cos with a = [a1, b1, a2, b2, ...]."""
+    F = np.zeros((t_rel.shape[0], 2 * nf))
+    for k in range(1, nf + 1):
+        arg = 2.0 * math.pi * k * t_rel / T
+        F[:, 2 * (k - 1)] = np.sin(arg)
+        F[:, 2 * (k - 1) + 1] = np.cos(arg)
+    return F
+
+
+def chromatic_weight(freqs_mhz: np.ndarray) -> np.ndarray:
+    """DM basis weight: F_DM = F / (K nu^2), with the constant absorbed into the DM
+    amplitude and referenced to 1400 MHz: (nu_ref / nu)^2."""
+    return (NU_REF_MHZ / freqs_mhz) ** 2
+
+
+def ntilde_inv_woodbury(Nvar: np.ndarray, M: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """N~^-1 v with N~^-1 = N^-1 - N^-1 M (M^T N^-1 M)^-1 M^T N^-1 (the flat-prior
+    timing-model marginalisation; equal to Eq. (Gmatrix_proj), see ntilde_inv_G)."""
+    w = v / Nvar[:, None] if v.ndim == 2 else v / Nvar
+    K = M.T @ (M / Nvar[:, None])
+    b = M.T @ w
+    c = np.linalg.solve(K, b)
+    corr = M @ c
+    return w - (corr / Nvar[:, None] if v.ndim == 2 else corr / Nvar)
+
+
+def ntilde_inv_G(Nvar: np.ndarray, M: np.ndarray) -> np.ndarray:
+    """Eq. (Gmatrix_proj) with G = Q_2 from the (column-pivoted) QR decomposition of
+    M (the text after Eq. (Gmatrix_proj)): N~^-1 = G (G^T N G)^-1 G^T.  Dense n x n."""
+    n, m = M.shape
+    Q, _R, _P = sla.qr(M, pivoting=True)
+    G = Q[:, m:]
+    GNG = G.T @ (Nvar[:, None] * G)
+    return G @ np.linalg.solve(GNG, G.T)
+
+
+def ntilde_inv_svd(Nvar: np.ndarray, M: np.ndarray) -> np.ndarray:
+    """The same projector with G from the SVD of M (G = left singular vectors
+    orthogonal to the column space of M)."""
+    n, m = M.shape
+    U, _s, _vt = np.linalg.svd(M, full_matrices=True)
+    G = U[:, m:]
+    return G @ np.linalg.solve(G.T @ (Nvar[:, None] * G), G.T)
+
+
+def chol_tangent(L: np.ndarray, dPhi: np.ndarray) -> np.ndarray:
+    """Forward-mode derivative of the Cholesky factor: for Phi = L L^T,
+    dL = L tril_half(L^-1 dPhi L^-T), where tril_half keeps the strict lower
+    triangle and half the diagonal (follows from dPhi = dL L^T + L dL^T with
+    L^-1 dL lower triangular)."""
+    X = sla.solve_triangular(L, dPhi, lower=True)
+    Y = sla.solve_triangular(L, X.T, lower=True).T
+    P = np.tril(Y, -1) + 0.5 * np.diag(np.diag(Y))
+    return L @ P
+
+
+# --------------------------------------------------------------------------- #
+# CW: circular super-massive black-hole binary (Sec. "Deterministic signals and
+# continuous waves", Eqs. (phase_evolve), (CW_evolve)).  The antenna pattern,
+# polarisation amplitudes and pulsar term follow the published circular-binary
+# model of Ellis, Siemens & Creighton (2012), restated from the physics.
+# --------------------------------------------------------------------------- #
+def cw_geometry(cos_gwtheta, gwphi, pos):
+    """Propagation direction Omega, polarisation basis (m, n) and antenna patterns
+    F+ = ((m.p)^2 - (n.p)^2) / (2 (1 + Omega.p)), Fx = (m.p)(n.p) / (1 + Omega.p)."""
+    ct = cos_gwtheta
+    st = np.sqrt(1.0 - ct * ct)
+    sp, cp = np.sin(gwphi), np.cos(gwphi)
+    omhat = -np.array([st * cp, st * sp, ct])
+    mhat = np.array([sp, -cp, 0.0 * sp])
+    nhat = np.array([-ct * cp, -ct * sp, st])
+    mp = mhat @ pos
+    np_ = nhat @ pos
+    op = omhat @ pos
+    fplus = 0.5 * (mp * mp - np_ * np_) / (1.0 + op)
+    fcross = mp * np_ / (1.0 + op)
+    return fplus, fcross, op
+
+
+def cw_phase(t, mc_s, omega0):
+    """Phase advance and frequency of the Earth term from Eqs. (phase_evolve) and
+    (CW_evolve): omega = omega0 (1 - x)^(-3/8), x = (256/5) Mc^(5/3) omega0^(8/3) t,
+    Phi - Phi0 = [omega0^(-5/3) - omega^(-5/3)] / (32 Mc^(5/3))."""
+    x = 256.0 / 5.0 * mc_s ** (5.0 / 3.0) * omega0 ** (8.0 / 3.0) * t
+    omega = omega0 * (1.0 - x) ** (-3.0 / 8.0)
+    dphi = (omega0 ** (-5.0 / 3.0) - omega ** (-5.0 / 3.0)) / (32.0 * mc_s ** (5.0 / 3.0))
+    return dphi, omega
+
+
+def cw_phase_taylor(t, mc_s, omega0):
+    """First-order form of Eq. (phase_evolve_Taylor): Phi - Phi0 ~ omega0 t."""
+    xp = mc_s ** (5.0 / 3.0) * omega0 ** (8.0 / 3.0) * t
+    return xp / (mc_s * omega0) ** (5.0 / 3.0)
+
+
+def cw_signal(t_rel, pos, th, dist_kpc, pphase):
+    """Deterministic CW delay h(theta) in ns at times t_rel (s from the array's first
+    TOA) for one pulsar.  th = (log10 Mc[Msun], log10 f_gw[Hz], log10 h, cos iota, psi,
+    cos theta, phi, Phi0).  Earth term r(t) and pulsar term r(t_p) with
+    t_p = t - L (1 + Omega.p); the pulsar-term phase at t = 0 is the free parameter
+    Phi_I (the paper treats pulsar phases as independent parameters).  Residual
+    s = F+ (r+(t_p) - r+(t)) + Fx (rx(t_p) - rx(t))."""
+    log10mc, log10f, log10h, cosi, psi, cos_gt, gwphi, phi0 = th
+    mc = 10.0 ** log10mc * TSUN_S
+    omega0 = np.pi * 10.0 ** log10f
+    h = 10.0 ** log10h
+    L = dist_kpc * KPC_S
+    fplus, fcross, op = cw_geometry(cos_gt, gwphi, pos)
+    tp = t_rel - L * (1.0 + op)
+    # Earth term
+    dphi_e, om_e = cw_phase(t_rel, mc, omega0)
+    ph_e = phi0 + dphi_e
+    # pulsar term: same evolution law, referenced so its phase at t = 0 is Phi_I
+    dphi_p0, _ = cw_phase(-L * (1.0 + op), mc, omega0)
+    dphi_p, om_p = cw_phase(tp, mc, omega0)
+    ph_p = pphase + (dphi_p - dphi_p0)
+    c2psi, s2psi = np.cos(2 * psi), np.sin(2 * psi)
+    inc_p = 1.0 + cosi * cosi
+    inc_x = 2.0 * cosi
+
+    def pols(phase, om):
+        alpha = h / (2.0 * omega0 ** (2.0 / 3.0) * om ** (1.0 / 3.0))
+        s2, c2 = np.sin(2 * phase), np.cos(2 * phase)
+        rp = alpha * (-s2 * inc_p * c2psi - c2 * inc_x * s2psi)
+        rx = alpha * (-s2 * inc_p * s2psi + c2 * inc_x * c2psi)
+        return rp, rx
+
+    rp_e, rx_e = pols(ph_e, om_e)
+    rp_p, rx_p = pols(ph_p, om_p)
+    return (fplus * (rp_p - rp_e) + fcross * (rx_p - rx_e)) * 1e9
+
+
+# --------------------------------------------------------------------------- #
+# The posterior.
+# --------------------------------------------------------------------------- #
+class Oracle:
+    """Plain FP64 posterior and gradient for one synthetic array.
+
+    ``arr`` exposes ``pulsars`` (each with toas_s, freqs_mhz, resid_s, sigma_s,
+    backend, efac, equad_s, M, pos, dist_kpc), ``n_gwb``, ``n_rn``, ``n_dm``, ``cw``.
+    """
+
+    def __init__(self, arr, store_basis: bool = True):
+        self.arr = arr
+        self.psrs = arr.pulsars
+        self.npsr = len(self.psrs)
+        self.n_gwb, self.n_rn, self.n_dm = arr.n_gwb, arr.n_rn, arr.n_dm
+        self.cw = bool(arr.cw)
+        self.na = max(self.n_gwb, self.n_rn)
+        self.P = 2 * self.na + 2 * self.n_dm
+        tmin = min(p.toas_s.min() for p in self.psrs)
+        tmax = max(p.toas_s.max() for p in self.psrs)
+        self.t0, self.T = tmin, tmax - tmin               # Sec. "Red and chromatic noise"
+        self.Gamma = hellings_downs(np.array([p.pos for p in self.psrs]))
+        self.Nvar = [white_noise_var(p) for p in self.psrs]
+        self.dt_ns = [p.resid_s * 1e9 for p in self.psrs]
+        self.t_rel = [p.toas_s - self.t0 for p in self.psrs]
+        self.F = [self.basis(I) for I in range(self.npsr)] if store_basis else None
+        # parameter layout (same convention as the C ABI)
+        o = {}
+        o["z_dm"] = self.na * 2 * self.npsr
+        o["dz"] = o["z_dm"] + self.npsr * self.n_dm * 2
+        o["th_rn"] = o["dz"]
+        o["th_dm"] = o["th_rn"] + 2 * self.npsr
+        o["th_gwb"] = o["th_dm"] + (2 * self.npsr if self.n_dm else 0)
+        o["th_cw"] = o["th_gwb"] + 2
+        o["d"] = o["th_cw"] + ((8 + 2 * self.npsr) if self.cw else 0)
+        self.lay = o
+        self.D = o["d"]
+        self.Dz = o["dz"]
+
+    # -- basis ------------------------------------------------------------------
+    def basis(self, I: int) -> np.ndarray:
+        p = self.psrs[I]
+        t = p.toas_s - self.t0
+        F = fourier_basis(t, self.T, self.na)
+        if self.n_dm:
+            Fd = fourier_basis(t, self.T, self.n_dm) * chromatic_weight(p.freqs_mhz)[:, None]
+            F = np.concatenate([F, Fd], axis=1)
+        return F
+
+    def get_F(self, I):
+        return self.F[I] if self.F is not None else self.basis(I)
+
+    # -- parameter unpacking ----------------------------------------------------
+    def unpack(self, x):
+        x = np.asarray(x, dtype=np.float64)
+        o, npsr, na, nd = self.lay, self.npsr, self.na, self.n_dm
+        z_ach = x[: o["z_dm"]].reshape(na, 2, npsr)            # [k][c][I]
+        z_dm = x[o["z_dm"]: o["dz"]].reshape(npsr, nd, 2)        # [I][k][c]
+        th_rn = x[o["th_rn"]: o["th_rn"] + 2 * npsr].reshape(npsr, 2)
+        th_dm = x[o["th_dm"]: o["th_dm"] + 2 * npsr].reshape(npsr, 2) if nd else np.zeros((npsr, 2))
+        th_gwb = x[o["th_gwb"]: o["th_gwb"] + 2]
+        th_cw = x[o["th_cw"]: o["d"]] if self.cw else None
+        return z_ach, z_dm, th_rn, th_dm, th_gwb, th_cw
+
+    def in_prior(self, x) -> bool:
+        _, _, th_rn, th_dm, th_gwb, th_cw = self.unpack(x)
+        def box(v, lo_hi):
+            return bool(np.all((v > lo_hi[0]) & (v < lo_hi[1])))
+        ok = box(th_rn[:, 0], PRIOR_LOG10A) and box(th_rn[:, 1], PRIOR_GAMMA)
+        ok = ok and box(th_gwb[0:1], PRIOR_LOG10A) and box(th_gwb[1:2], PRIOR_GAMMA)
+        if self.n_dm:
+            ok = ok and box(th_dm[:, 0], PRIOR_LOG10A) and box(th_dm[:, 1], PRIOR_GAMMA)
+        if self.cw:
+            for j in range(8):
+                ok = ok and box(th_cw[j:j + 1], PRIOR_CW[j])
+            dist = th_cw[8::2]
+            ok = ok and bool(np.all(dist > 0.0)) and box(th_cw[9::2], PRIOR_PPHASE)
+        return ok
+
+    # -- spectra and prior covariance (Eqs. prior_cov, power_law) -----------------
+    def spectra(self, th_rn, th_dm, th_gwb):
+        ks = np.arange(1, self.na + 1)
+        rho = np.zeros(self.na)
+        rho[: self.n_gwb] = power_law(th_gwb[0], th_gwb[1], ks[: self.n_gwb], self.T)
+        kappa = np.zeros((self.npsr, self.na))
+        for I in range(self.npsr):
+            kappa[I, : self.n_rn] = power_law(th_rn[I, 0], th_rn[I, 1], ks[: self.n_rn], self.T)
+        kdm = np.zeros((self.npsr, self.n_dm))
+        if self.n_dm:
+            kd = np.arange(1, self.n_dm + 1)
+            for I in range(self.npsr):
+                kdm[I] = power_law(th_dm[I, 0], th_dm[I, 1], kd, self.T)
+        return rho, kappa, kdm
+
+    def phi_bin(self, rho_k, kappa_k):
+        """Eq. (prior_cov) restricted to one frequency bin: Phi_k = rho_k Gamma + diag(kappa_.k)."""
+        return rho_k * self.Gamma + np.diag(kappa_k)
+
+    # -- standardizing transform a = L z (prior-whitened) -------------------------
+    def transform(self, z_ach, z_dm, rho, kappa, kdm):
+        """a_{.,k,c} = L_k z_{.,k,c} with Phi_k = L_k L_k^T (Eq. standardizing_transform
+        with mu = 0, Sigma = phi, batched over frequency bins); DM: a = sqrt(kappa) z.
+        Returns per-pulsar coefficient vectors a_I[P] and the factors L_k."""
+        a = np.zeros((self.npsr, self.P))
+        Ls = []
+        for k in range(self.na):
+            Lk = np.linalg.cholesky(self.phi_bin(rho[k], kappa[:, k]))
+            Ls.append(Lk)
+            for c in range(2):
+                a[:, 2 * k + c] = Lk @ z_ach[k, c]
+        if self.n_dm:
+            off = 2 * self.na
+            for I in range(self.npsr):
+                for k in range(self.n_dm):
+                    for c in range(2):
+                        a[I, off + 2 * k + c] = math.sqrt(kdm[I, k]) * z_dm[I, k, c]
+        return a, Ls
+
+    # -- deterministic signal ---------------------------------------------------
+    def cw_th(self, th_cw, I):
+        return th_cw[:8], th_cw[8 + 2 * I], th_cw[9 + 2 * I]
+
+    def signal(self, th_cw, I):
+        if not self.cw:
+            return 0.0
+        th8, dist, pph = self.cw_th(th_cw, I)
+        return cw_signal(self.t_rel[I], self.psrs[I].pos, th8, dist, pph)
+
+    # -- log posterior ----------------------------------------------------------
+    def residuals(self, x):
+        z_ach, z_dm, th_rn, th_dm, th_gwb, th_cw = self.unpack(x)
+        rho, kappa, kdm = self.spectra(th_rn, th_dm, th_gwb)
+        a, Ls = self.transform(z_ach, z_dm, rho, kappa, kdm)
+        rs = [self.dt_ns[I] - self.get_F(I) @ a[I] - self.signal(th_cw, I) for I in range(self.npsr)]
+        return rs, a, Ls, (rho, kappa, kdm)
+
+    def chi2_terms(self, x):
+        """Per-pulsar r_I^T N~_I^-1 r_I with r_I = dt_I - F_I a_I - h_I(theta)."""
+        rs, *_ = self.residuals(x)
+        out = np.zeros(self.npsr)
+        for I in range(self.npsr):
+            wt = ntilde_inv_woodbury(self.Nvar[I], self.psrs[I].M, rs[I])
+            out[I] = rs[I] @ wt
+        return out
+
+    def log_prior_theta(self, x) -> float:
+        if not self.in_prior(x):
+            return -math.inf
+        lp = 0.0
+        if self.cw:
+            th_cw = self.unpack(x)[5]
+            for I in range(self.npsr):
+                d = (th_cw[8 + 2 * I] - self.psrs[I].dist_kpc) / DIST_SIGMA_KPC
+                lp += -0.5 * d * d
+        return lp
+
+    def logp(self, x) -> float:
+        """Canonical log posterior (the quantity the GPU path computes):
+        -1/2 sum_I chi2_I - 1/2 |z|^2 + log p(theta), data-only constants dropped.
+        Under the prior-whitened transform the Gaussian prior on a and the Jacobian
+        det L combine to -1/2 |z|^2 - (D_z/2) log 2 pi (constant dropped here)."""
+        lpt = self.log_prior_theta(x)
+        if not math.isfinite(lpt):
+            return -math.inf
+        x = np.asarray(x, dtype=np.float64)
+        z = x[: self.Dz]
+        return -0.5 * float(self.chi2_terms(x).sum()) - 0.5 * float(z @ z) + lpt
+
+    def data_constant(self) -> float:
+        """-1/2 sum_I [log det(2 pi N_I) + log det(M_I^T N_I^-1 M_I) - m_I log 2 pi]
+        (the flat-prior integral over the timing-model offsets of Eq. likelihood)."""
+        c = 0.0
+        for I, p in enumerate(self.psrs):
+            Nv = self.Nvar[I]
+            M = p.M
+            K = M.T @ (M / Nv[:, None])
+            sign, ld = np.linalg.slogdet(K)
+            c += -0.5 * (np.sum(np.log(2 * math.pi * Nv)) + ld - M.shape[1] * math.log(2 * math.pi))
+        return c
+
+    def logp_full(self, x) -> float:
+        """Normalised log density in (z, theta) at fixed theta: logp + data_constant
+        - (D_z/2) log 2 pi, with the prior on a and the Jacobian written out literally:
+        log N(a; 0, phi) + log det L (Eqs. a_prior, standardized_density)."""
+        x = np.asarray(x, dtype=np.float64)
+        z_ach, z_dm, th_rn, th_dm, th_gwb, th_cw = self.unpack(x)
+        rho, kappa, kdm = self.spectra(th_rn, th_dm, th_gwb)
+        a, Ls = self.transform(z_ach, z_dm, rho, kappa, kdm)
+        lp_a = 0.0
+        logdetL = 0.0
+        for k in range(self.na):
+            Phi = self.phi_bin(rho[k], kappa[:, k])
+            sign, ld = np.linalg.slogdet(2 * math.pi * Phi)
+            for c in range(2):
+                ak = a[:, 2 * k + c]
+                lp_a += -0.5 * ak @ np.linalg.solve(Phi, ak) - 0.5 * ld
+                logdetL += np.sum(np.log(np.diag(Ls[k])))
+        off = 2 * self.na
+        for I in range(self.npsr):
+            for k in range(self.n_dm):
+                for c in range(2):
+                    v = kdm[I, k]
+                    ak = a[I, off + 2 * k + c]
+                    lp_a += -0.5 * ak * ak / v - 0.5 * math.log(2 * math.pi * v)
+                    logdetL += 0.5 * math.log(v)
+        chi2 = self.chi2_terms(x).sum()
+        return -0.5 * chi2 + self.data_constant() + lp_a + logdetL + self.log_prior_theta(x)
+
+    # -- gradient (analytic chain, pinned by central differences) -----------------
+    def grad(self, x, theta_only_idx=None) -> np.ndarray:
+        """d logp / dx.  z-block: g_z = L_k^T F^T N~^-1 r - z.  Hyper-parameters: the
+        chain rule through a = L(phi(eta)) z with the forward-mode Cholesky tangent for
+        each spectral parameter.  CW parameters: (N~^-1 r)^T dh/dtheta with dh/dtheta
+        from complex-step differentiation of ``cw_signal`` (exact to rounding)."""
+        x = np.asarray(x, dtype=np.float64)
+        g = np.zeros(self.D)
+        if not math.isfinite(self.log_prior_theta(x)):
+            return g
+        z_ach, z_dm, th_rn, th_dm, th_gwb, th_cw = self.unpack(x)
+        rs, a, Ls, (rho, kappa, kdm) = self.residuals(x)
+        npsr, na, nd = self.npsr, self.na, self.n_dm
+        ghat = np.zeros((npsr, self.P))
+        wts = []
+        for I in range(npsr):
+            wt = ntilde_inv_woodbury(self.Nvar[I], self.psrs[I].M, rs[I])
+            wts.append(wt)
+            ghat[I] = self.get_F(I).T @ wt                       # d logp / d a_I
+        o = self.lay
+        gz = np.zeros((na, 2, npsr))
+        for k in range(na):
+            for c in range(2):
+                gz[k, c] = Ls[k].T @ ghat[:, 2 * k + c] - z_ach[k, c]
+        g[: o["z_dm"]] = gz.reshape(-1)
+        if nd:
+            gzd = np.zeros((npsr, nd, 2))
+            for I in range(npsr):
+                for k in range(nd):
+                    for c in range(2):
+                        gzd[I, k, c] = (math.sqrt(kdm[I, k]) * ghat[I, 2 * na + 2 * k + c]
+                                        - z_dm[I, k, c])
+            g[o["z_dm"]: o["dz"]] = gzd.reshape(-1)
+        # d logp / d rho_k and d logp / d kappa_Ik via dL = chol_tangent(L, dPhi)
+        d_rho = np.zeros(na)
+        d_kap = np.zeros((npsr, na))
+        for k in range(na):
+            Lk = Ls[k]
+            def dir_deriv(dPhi):
+                dL = chol_tangent(Lk, dPhi)
+                return sum(ghat[:, 2 * k + c] @ (dL @ z_ach[k, c]) for c in range(2))
+            if k < self.n_gwb:
+                d_rho[k] = dir_deriv(self.Gamma)
+            if k < self.n_rn:
+                for I in range(npsr):
+                    E = np.zeros((npsr, npsr))
+                    E[I, I] = 1.0
+                    d_kap[I, k] = dir_deriv(E)
+        ks = np.arange(1, na + 1)
+        lnf = np.log(ks / self.T / F_YR)
+        # rho = A^2 ... f^-gamma: d rho/d log10A = 2 ln10 rho, d rho/d gamma = -ln(f/f_yr) rho
+        g[o["th_gwb"]] = np.sum(d_rho * 2 * LN10 * rho)
+        g[o["th_gwb"] + 1] = np.sum(d_rho * (-lnf) * rho)
+        for I in range(npsr):
+            g[o["th_rn"] + 2 * I] = np.sum(d_kap[I] * 2 * LN10 * kappa[I])
+            g[o["th_rn"] + 2 * I + 1] = np.sum(d_kap[I] * (-lnf) * kappa[I])
+        if nd:
+            kd = np.arange(1, nd + 1)
+            lnfd = np.log(kd / self.T / F_YR)
+            for I in range(npsr):
+                # a = sqrt(kdm) z  =>  d logp / d kdm = ghat z / (2 sqrt(kdm))
+                gz_dm = ghat[I, 2 * na:].reshape(nd, 2)
+                dk = (gz_dm * z_dm[I]).sum(1) / (2.0 * np.sqrt(kdm[I]))
+                g[o["th_dm"] + 2 * I] = np.sum(dk * 2 * LN10 * kdm[I])
+                g[o["th_dm"] + 2 * I + 1] = np.sum(dk * (-lnfd) * kdm[I])
+        if self.cw:
+            h = 1e-30
+            for j in range(8 + 2 * npsr):
+                pulsars = range(npsr) if j < 8 else [(j - 8) // 2]
+                acc = 0.0
+                for I in pulsars:
+                    th8, dist, pph = self.cw_th(th_cw, I)
+                    th8c = np.array(th8, dtype=complex)
+                    dist_c, pph_c = complex(dist), complex(pph)
+                    if j < 8:
+                        th8c[j] += 1j * h
+                    elif (j - 8) % 2 == 0:
+                        dist_c += 1j * h
+                    else:
+                        pph_c += 1j * h
+                    ds = np.imag(cw_signal(self.t_rel[I], self.psrs[I].pos, th8c, dist_c, pph_c)) / h
+                    acc += wts[I] @ ds        # r = dt - F a - h  =>  d(-chi2/2) = +w~ . dh
+                g[o["th_cw"] + j] = acc
+            for I in range(npsr):
+                g[o["th_cw"] + 8 + 2 * I] += -(th_cw[8 + 2 * I] - self.psrs[I].dist_kpc) / DIST_SIGMA_KPC ** 2
+        return g
+
+    # -- brute-force and alternative forms for pins -------------------------------
+    def dense_marginal(self, x) -> float:
+        """Time-domain Gaussian marginal likelihood with the Fourier coefficients and
+        the timing-model offsets integrated out (flat prior on the offsets):
+        log N(dt; 0, C) with C = N + F phi F^T and the standard TM marginal,
+        -1/2 dt^T (C^-1 - C^-1 M (M^T C^-1 M)^-1 M^T C^-1) dt - 1/2 log det 2 pi C
+        - 1/2 log det(M^T C^-1 M) + (m/2) log 2 pi.  Dense over all TOAs."""
+        z_ach, z_dm, th_rn, th_dm, th_gwb, th_cw = self.unpack(x)
+        rho, kappa, kdm = self.spectra(th_rn, th_dm, th_gwb)
+        npsr, na, nd = self.npsr, self.na, self.n_dm
+        ns = [p.n for p in self.psrs]
+        offs = np.concatenate([[0], np.cumsum(ns)])
+        ntot = offs[-1]
+        Ptot = npsr * self.P
+        Fbig = np.zeros((ntot, Ptot))
+        for I in range(npsr):
+            Fbig[offs[I]: offs[I + 1], I * self.P:(I + 1) * self.P] = self.get_F(I)
+        phi = np.zeros((Ptot, Ptot))
+        for I in range(npsr):
+            for J in range(npsr):
+                for k in range(na):
+                    v = rho[k] * self.Gamma[I, J] + (kappa[I, k] if I == J else 0.0)
+                    for c in range(2):
+                        phi[I * self.P + 2 * k + c, J * self.P + 2 * k + c] = v
+            for k in range(nd):
+                for c in range(2):
+                    q = I * self.P + 2 * na + 2 * k + c
+                    phi[q, q] = kdm[I, k]
+        C = Fbig @ phi @ Fbig.T + np.diag(np.concatenate(self.Nvar))
+        mtot = sum(p.M.shape[1] for p in self.psrs)
+        Mbig = np.zeros((ntot, mtot))
+        mo = 0
+        for I, p in enumerate(self.psrs):
+            Mbig[offs[I]: offs[I + 1], mo: mo + p.M.shape[1]] = p.M
+            mo += p.M.shape[1]
+        dt = np.concatenate([self.dt_ns[I] - (self.signal(th_cw, I) if self.cw else 0.0)
+                             for I in range(npsr)])
+        cf = sla.cho_factor(C, lower=True)
+        Ci_dt = sla.cho_solve(cf, dt)
+        Ci_M = sla.cho_solve(cf, Mbig)
+        MCM = Mbig.T @ Ci_M
+        quad = dt @ Ci_dt - (Mbig.T @ Ci_dt) @ np.linalg.solve(MCM, Mbig.T @ Ci_dt)
+        logdetC = 2.0 * np.sum(np.log(np.diag(cf[0])))
+        s2, ldM = np.linalg.slogdet(MCM)
+        return (-0.5 * quad - 0.5 * (ntot * math.log(2 * math.pi) + logdetC) - 0.5 * ldM
+                + 0.5 * mtot * math.log(2 * math.pi))
+
+    def raw_posterior_exponent(self, a_all, x):
+        """Exponent of Eq. (raw_posterior) at coefficients a_all[I][P] (theta from x):
+        -1/2 (dt - F a)^T N~^-1 (dt - F a) - 1/2 a^T phi^-1 a."""
+        _, _, th_rn, th_dm, th_gwb, _ = self.unpack(x)
+        rho, kappa, kdm = self.spectra(th_rn, th_dm, th_gwb)
+        q = 0.0
+        for I in range(self.npsr):
+            r = self.dt_ns[I] - self.get_F(I) @ a_all[I]
+            q += r @ ntilde_inv_woodbury(self.Nvar[I], self.psrs[I].M, r)
+        q += self._a_phi_a(a_all, rho, kappa, kdm)
+        return -0.5 * q
+
+    def _a_phi_a(self, a_all, rho, kappa, kdm):
+        q = 0.0
+        for k in range(self.na):
+            Phi = self.phi_bin(rho[k], kappa[:, k])
+            for c in range(2):
+                ak = a_all[:, 2 * k + c]
+                q += ak @ np.linalg.solve(Phi, ak)
+        for I in range(self.npsr):
+            for k in range(self.n_dm):
+                for c in range(2):
+                    q += a_all[I, 2 * self.na + 2 * k + c] ** 2 / kdm[I, k]
+        return q
+
+    def gram_posterior_exponent(self, a_all, x):
+        """Exponent of Eq. (stochastic_posterior): -1/2 (a - ahat)^T Sigma^-1 (a - ahat)
+        + 1/2 ahat^T Sigma^-1 ahat with Sigma^-1 = F^T N~^-1 F + phi^-1 and
+        ahat = Sigma F^T N~^-1 dt (the dt^T N~^-1 dt term dropped)."""
+        _, _, th_rn, th_dm, th_gwb, _ = self.unpack(x)
+        rho, kappa, kdm = self.spectra(th_rn, th_dm, th_gwb)
+        npsr, P = self.npsr, self.P
+        Ptot = npsr * P
+        FNF = np.zeros((Ptot, Ptot))
+        FNd = np.zeros(Ptot)
+        for I in range(npsr):
+            F = self.get_F(I)
+            NF = ntilde_inv_woodbury(self.Nvar[I], self.psrs[I].M, F)
+            FNF[I * P:(I + 1) * P, I * P:(I + 1) * P] = F.T @ NF
+            FNd[I * P:(I + 1) * P] = NF.T @ self.dt_ns[I]
+        phi = np.zeros((Ptot, Ptot))
+        for I in range(npsr):
+            for J in range(npsr):
+                for k in range(self.na):
+                    v = rho[k] * self.Gamma[I, J] + (kappa[I, k] if I == J else 0.0)
+                    for c in range(2):
+                        phi[I * P + 2 * k + c, J * P + 2 * k + c] = v
+            for k in range(self.n_dm):
+                for c in range(2):
+                    q = I * P + 2 * self.na + 2 * k + c
+                    phi[q, q] = kdm[I, k]
+        Sinv = FNF + np.linalg.inv(phi)
+        ahat = np.linalg.solve(Sinv, FNd)
+        av = a_all.reshape(-1)
+        d = av - ahat
+        return -0.5 * d @ Sinv @ d + 0.5 * ahat @ Sinv @ ahat
+
+
+# --------------------------------------------------------------------------- #
+# Counter-based random numbers (Salmon, Moraes, Dror, Shaw, "Parallel random
+# numbers: as easy as 1, 2, 3", SC'11): Philox4x32 with 10 rounds.
+# --------------------------------------------------------------------------- #
+PHILOX_M0, PHILOX_M1 = 0xD2511F53, 0xCD9E8D57
+PHILOX_W0, PHILOX_W1 = 0x9E3779B9, 0xBB67AE85
+MASK32 = 0xFFFFFFFF
+
+
+def philox4x32_10(ctr, key):
+    c0, c1, c2, c3 = (int(v) & MASK32 for v in ctr)
+    k0, k1 = (int(v) & MASK32 for v in key)
+    for r in range(10):
+        p0 = PHILOX_M0 * c0
+        p1 = PHILOX_M1 * c2
+        hi0, lo0 = p0 >> 32, p0 & MASK32
+        hi1, lo1 = p1 >> 32, p1 & MASK32
+        c0, c1, c2, c3 = (hi1 ^ c1 ^ k0) & MASK32, lo1, (hi0 ^ c3 ^ k1) & MASK32, lo0
+        if r < 9:
+            k0 = (k0 + PHILOX_W0) & MASK32
+            k1 = (k1 + PHILOX_W1) & MASK32
+    return (c0, c1, c2, c3)
+
+
+def u01(w: int) -> float:
+    """uint32 -> (0, 1): (w + 1/2) 2^-32."""
+    return (w + 0.5) * 2.0 ** -32
+
+
+def hmc_normals(seed: int, iteration: int, chain: int, D: int) -> np.ndarray:
+    """Momentum draw for one chain: Philox block j has counter (j, chain, it_lo, it_hi),
+    key (seed_lo, seed_hi); each block's words (w0, w1, w2, w3) give two Box-Muller
+    pairs (w0, w1) and (w2, w3): n = sqrt(-2 ln u_a) (cos 2 pi u_b, sin 2 pi u_b)."""
+    out = np.zeros(D)
+    nblk = (D + 3) // 4
+    key = (seed & MASK32, (seed >> 32) & MASK32)
+    for j in range(nblk):
+        w = philox4x32_10((j, chain, iteration & MASK32, (iteration >> 32) & MASK32), key)
+        for q in range(2):
+            ua, ub = u01(w[2 * q]), u01(w[2 * q + 1])
+            rad = math.sqrt(-2.0 * math.log(ua))
+            for s, v in enumerate((rad * math.cos(2 * math.pi * ub), rad * math.sin(2 * math.pi * ub))):
+                idx = 4 * j + 2 * q + s
+                if idx < D:
+                    out[idx] = v
+    return out
+
+
+def hmc_uniform(seed: int, iteration: int, chain: int) -> float:
+    """Metropolis uniform: word 0 of the Philox block with counter (0xFFFFFFFF, chain, it)."""
+    key = (seed & MASK32, (seed >> 32) & MASK32)
+    w = philox4x32_10((MASK32, chain, iteration & MASK32, (iteration >> 32) & MASK32), key)
+    return u01(w[0])
+
+
+def hmc_trajectory(logp_grad, x0, logp0, grad0, step, n_leapfrog, p0, u, inv_mass=None):
+    """One HMC transition (App. "Hamiltonian Monte Carlo"): Euclidean-Gaussian kinetic
+    energy 1/2 p^T M^-1 p (Eq. Gaussian_momentum), H = -logp + K (Eq. Hamiltonian),
+    n_leapfrog leapfrog steps of Hamilton's equations (Eq. Hamilton's_eq), accepted
+    with probability min(1, exp(H0 - H1)) (Eq. HMC_acceptance) if u < that.
+    Returns (x, logp, grad, accepted)."""
+    im = np.ones_like(x0) if inv_mass is None else inv_mass
+    x = x0.copy()
+    p = p0.copy()
+    lp, g = logp0, grad0.copy()
+    H0 = -logp0 + 0.5 * np.sum(p0 * p0 * im)
+    for _ in range(n_leapfrog):
+        p = p + 0.5 * step * g
+        x = x + step * im * p
+        lp, g = logp_grad(x)
+        p = p + 0.5 * step * g
+    H1 = -lp + 0.5 * np.sum(p * p * im) if math.isfinite(lp) else math.inf
+    acc = math.log(u) < (H0 - H1)
+    if acc:
+        return x, lp, g, True
+    return x0.copy(), logp0, grad0.copy(), False
