@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Throughput of the batched log posterior + gradient (the HMC hot path).
+
+One step = one pta_logp_and_grad call over all chains of the workload: prior
+spectra + FP64 per-frequency Cholesky + transform, TOA-domain contractions, FP64
+timing-model solve, adjoint and final sum.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): chains are independent, so every rank runs its own batch of
+chains on its own GPU (weak scaling, no data-path collective); a barrier and a
+max-over-ranks of the timed duration use the process group.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "ng15_b256"
+WORKLOAD_DESC = "NANOGrav-15-yr-like: 67 pulsars, 3.0e5 TOAs, RN 30 / DM 100 / HD-GWB 14 bins, 256 chains"
+METRIC = "logp+grad evals/s (all chains) at 67-psr size vs FP64 plain path; % roofline"
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
+FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12     # SMs x 2 FP64 FMA/clk x 2 flop x max SM clock
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p))
+        except Exception:
+            return None
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [l.strip().split(", ") for l in open(self.f.name) if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def toa_flops_per_launch(arr, B):
+    """Algorithmic flops of the TOA contractions per launch: F a (2 n P), F^T w (2 n P)
+    and M^T w (2 n m) per chain and pulsar, unpadded TOA counts."""
+    na = max(arr.n_gwb, arr.n_rn)
+    P = 2 * na + 2 * arr.n_dm
+    return float(B * sum(2 * p.n * (2 * P + p.m) for p in arr.pulsars))
+
+
+def chol_flops_per_launch(arr, B):
+    """FP64 flops of the dense-bin prior forward per launch: Cholesky (np^3/3),
+    triangular inverse (np^3/3) and the transform (2 x np^2) per (chain, bin)."""
+    npsr = arr.npsr
+    nb = min(arr.n_gwb, arr.n_rn)
+    return float(B * nb * (2 * npsr ** 3 / 3 + 2 * npsr ** 2))
+
+
+def cpu_baseline(arr, n_eval: int):
+    """The FP64 oracle, as it stands, on the host cores: logp + grad of n_eval chains."""
+    from oracle import pta_oracle as O
+    from paper_2607_06834_b300 import synth
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([t.get("num_threads", 1) for t in threadpool_info()] or [1])
+    except Exception:
+        cores = os.cpu_count()
+    orc = O.Oracle(arr)
+    X = synth.make_points(arr, n_eval, seed=6834 + 2).astype(np.float64)
+    orc.logp(X[0])
+    t0 = time.perf_counter()
+    for x in X:
+        orc.logp(x)
+        orc.grad(x)
+    dt = time.perf_counter() - t0
+    return {"value": n_eval / dt, "unit": "evals/s", "cores": int(cores), "kind": "oracle",
+            "sample": f"{n_eval} single-chain logp+grad evaluations of the {WORKLOAD} workload "
+                      f"({dt:.1f} s, numpy FP64)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2607_06834_b300 import synth
+    from oracle import pta_oracle as O
+    arr = synth.make_array(WORKLOAD)
+    orc = O.Oracle(arr)
+    X = synth.make_points(arr, args.steps + args.warmup, seed=6834 + 2).astype(np.float64)
+    for i in range(args.warmup):
+        orc.logp(X[i])
+        orc.grad(X[i])
+    t0 = time.perf_counter()
+    for i in range(args.warmup, args.warmup + args.steps):
+        orc.logp(X[i])
+        orc.grad(X[i])
+    dt = time.perf_counter() - t0
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([t.get("num_threads", 1) for t in threadpool_info()] or [1])
+    except Exception:
+        cores = os.cpu_count()
+    value = args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "chains_per_step": 1},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": int(cores), "kind": "oracle",
+                             "sample": "one single-chain logp+grad evaluation per step"},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    from paper_2607_06834_b300 import abi, synth
+    from paper_2607_06834_b300.engine import Engine
+    arr = synth.make_array(WORKLOAD)
+    B = synth.WORKLOADS[WORKLOAD]["chains"]
+    X = synth.make_points(arr, B, seed=6834 + 2 + 1000 * rank)
+    eng = Engine(arr, precision=args.precision)
+    D = eng.D
+    dev = torch.device("cuda", local)
+    x = torch.tensor(X, device=dev)
+    logp = torch.empty(B, dtype=torch.float64, device=dev)
+    grad = torch.empty_like(x)
+    status = torch.empty(B, dtype=torch.int32, device=dev)
+    out = (logp, grad, status)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 126 MB L2
+    for _ in range(args.warmup):
+        eng.logp_and_grad(x, out=out)
+    torch.cuda.synchronize()
+    assert int((status != 0).sum()) == 0, "non-finite or out-of-prior chains in the bench batch"
+
+    def barrier():
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    abi.lib.pta_profile_enable(eng._h, 1)
+    abi.lib.pta_profile_read(eng._h, None, None, 1)
+    clocks = Clocks(local) if rank == 0 or True else None
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record()
+        eng.logp_and_grad(x, out=out)
+        ends[i].record()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    ck = clocks.stop() if clocks else None
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = float(np.sum(step_ms)) / args.steps
+    stage_ms = (C.c_double * abi.NSTAGES)()
+    stage_n = (C.c_longlong * abi.NSTAGES)()
+    abi.lib.pta_profile_read(eng._h, stage_ms, stage_n, 1)
+    abi.lib.pta_profile_enable(eng._h, 0)
+    stage_ms = [v / args.steps for v in stage_ms]
+    launches = int(sum(stage_n))
+    if pg:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    if rank != 0:
+        pg.destroy_process_group()
+        return
+    value = world * B / (ms * 1e-3)
+    # roofline of the dominant stage's kernel
+    dom = int(np.argmax(stage_ms))
+    peaks = measured_peaks()
+    if abi.STAGES[dom] == "toa":
+        flops = toa_flops_per_launch(arr, B)
+        roof = {"kernel": "k_toa_simt (TOA contractions)", "bound": "alu", "unit": "TFLOP/s",
+                "achieved": flops / (stage_ms[dom] * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
+                "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 flop x 2.032 GHz"}
+    else:
+        flops = chol_flops_per_launch(arr, B)
+        roof = {"kernel": "k_chol_forward (FP64 Cholesky + inverse + transform)", "bound": "alu",
+                "unit": "TFLOP/s", "achieved": flops / (stage_ms[dom] * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "peak_source": "derived: 148 SM x 2 FP64 FMA/clk x 2 flop x 2.032 GHz"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["stage_ms"] = dict(zip(abi.STAGES, [round(v, 4) for v in stage_ms]))
+    # end to end through the public call with host buffers (pinned), copies inside the timed region
+    xh = torch.tensor(X).pin_memory()
+    lh = torch.empty(B, dtype=torch.float64).pin_memory()
+    gh = torch.empty((B, D), dtype=torch.float32).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_e2e = max(3, args.steps // 2)
+    e2e_ms = 0.0
+    for i in range(n_e2e):
+        flush.zero_()
+        e0.record()
+        x.copy_(xh, non_blocking=True)
+        eng.logp_and_grad(x, out=out)
+        lh.copy_(logp, non_blocking=True)
+        gh.copy_(grad, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    e2e_ms /= n_e2e
+    # the plain FP64 GPU path on the same workload (the metric's comparison)
+    fp64 = None
+    if not args.skip_fp64:
+        eng.set_precision("fp64")
+        eng.logp_and_grad(x, out=out)
+        torch.cuda.synchronize()
+        n64 = 2
+        e0.record()
+        for _ in range(n64):
+            eng.logp_and_grad(x, out=out)
+        e1.record()
+        e1.synchronize()
+        ms64 = e0.elapsed_time(e1) / n64
+        x1 = x[:1].contiguous()
+        eng.logp_and_grad(x1)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(5):
+            eng.logp_and_grad(x1)
+        e1.record()
+        e1.synchronize()
+        ms64_1 = e0.elapsed_time(e1) / 5
+        fp64 = {"value": B / (ms64 * 1e-3), "unit": "evals/s", "ms_per_step": ms64, "chains": B,
+                "single_chain_ms": ms64_1, "speedup_of_value": (B / (ms * 1e-3)) / (B / (ms64 * 1e-3))}
+        eng.set_precision(args.precision)
+    cpu = None if args.skip_cpu else cpu_baseline(arr, args.cpu_evals)
+    line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32",
+            "dtype_detail": "FP32 TOA contractions; FP64 Cholesky, log-det, timing-model solve and sums",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "chains_per_gpu": B, "ntoa": arr.ntoa, "npsr": arr.npsr,
+                       "precision": args.precision, "l2": "flushed between timed steps (512 MB write)"},
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": world * B / (e2e_ms * 1e-3), "unit": "evals/s",
+                    "h2d_bytes_per_step": int(B * D * 4), "d2h_bytes_per_step": int(B * 8 + B * D * 4)},
+            "gpu_launches": launches, "fp64_plain_path": fp64, "clocks": ck,
+            "wall_s_timed": t_wall, "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None}
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--cpu-evals", type=int, default=16)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,159 @@
+/*
+ * ptahmc.h -- C ABI of the B300 engine for the standardized Fourier-coefficient
+ * pulsar-timing-array posterior (Gundersen, van Haasteren, Cornish, Vallisneri,
+ * Meyers, "A new framework for lightning-fast gravitational wave analysis of
+ * pulsar timing data").
+ *
+ * The library evaluates, for a batch of B HMC chains, the log posterior of
+ * Eq. (raw_det_posterior) with the timing model marginalised by Eq.
+ * (Gmatrix_proj), sampled in prior-whitened coordinates a = L z
+ * (Eqs. standardizing_transform, standardized_density with mu = 0 and
+ * Sigma = phi of Eq. prior_cov), and its gradient; and it runs fixed-length HMC
+ * trajectories (App. "Hamiltonian Monte Carlo").
+ *
+ * Conventions shared by every call:
+ *  - Return value: PTA_OK (0) or a negative PTA_E* code; pta_last_error() then
+ *    holds a one-line message.  No call aborts the process.
+ *  - Host arrays passed to pta_add_pulsar are copied; the caller keeps them.
+ *  - Pointers named *_dev are device pointers owned by the caller (for example
+ *    torch tensors).  The library never frees or reallocates them and never
+ *    synchronises the stream it is given, except in pta_finalize.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy stream.
+ *  - The context owns every device buffer it allocates; pta_destroy frees them.
+ *  - Units inside: residuals and covariances in ns / ns^2 (Sec. "Single
+ *    precision"), time in s.  Inputs are in seconds and MHz.
+ */
+#ifndef PTAHMC_H
+#define PTAHMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PTA_OK 0
+#define PTA_EINVAL (-1)   /* bad argument (NULL, size, NaN, sigma <= 0, m >= n, ...) */
+#define PTA_ESTATE (-2)   /* call out of order (add after finalize, eval before) */
+#define PTA_ECUDA (-3)    /* a CUDA runtime call failed */
+#define PTA_ENOMEM (-4)   /* device or host allocation failed */
+#define PTA_ETIMEOUT (-5) /* a bounded device wait gave up */
+
+/* Precision of the TOA-length contractions F a, F^T w, M^T w (Sec. "Single
+ * precision").  The per-frequency Cholesky, its log-det, the timing-model solve
+ * and the final sums are FP64 in every mode. */
+#define PTA_PREC_FP64 0   /* plain path: stored FP64 basis, SIMT FP64 */
+#define PTA_PREC_FP32 1   /* basis generated on the fly, SIMT FP32 */
+#define PTA_PREC_TF32X3 2 /* tcgen05 tensor cores, 3-term split TF32 */
+#define PTA_PREC_TF32 3   /* tcgen05, single TF32 product (reported only) */
+#define PTA_PREC_BF16X3 4 /* tcgen05, 3-term split BF16 (reported only) */
+
+typedef struct pta_ctx pta_ctx;
+
+/* Model sizes.  n_gwb / n_rn / n_dm are the numbers of Fourier frequencies
+ * k/T (k = 1..n) of the GWB, intrinsic red noise and DM processes (Eq.
+ * Fourier_series; the DM basis is F (nu_ref/nu)^2, text after Eq. RN=Fa).
+ * Achromatic processes share one basis of max(n_gwb, n_rn) bins. */
+typedef struct {
+  int n_gwb;
+  int n_rn;
+  int n_dm;
+  int cw;             /* 1: add the circular-binary deterministic signal */
+  int precision;      /* PTA_PREC_* */
+  double nu_ref_mhz;  /* DM reference frequency; 0 selects 1400 MHz */
+} pta_model_desc;
+
+/* One pulsar.  All arrays have n entries except efac/equad (n_backend) and M
+ * (n x m, row-major).  White noise N_ii = efac[b_i]^2 sigma_i^2 + equad[b_i]^2
+ * (Eq. WN_cov); M is the timing design matrix of Eq. (TM=Me). */
+typedef struct {
+  int n, m, n_backend;
+  const double* toas_s;
+  const double* freqs_mhz;
+  const double* resid_s;
+  const double* sigma_s;
+  const int32_t* backend;
+  const double* efac;
+  const double* equad_s;
+  const double* M;
+  double pos[3];      /* unit vector to the pulsar */
+  double dist_kpc;    /* distance prior mean (CW pulsar term) */
+} pta_pulsar_desc;
+
+/* Offsets into the parameter vector x[D] of one chain:
+ *   z_ach[k][c][I]  k < max(n_gwb, n_rn), c = 0 sin / 1 cos, I < npsr
+ *   z_dm [I][k][c]  k < n_dm
+ *   th_rn[I][2]     (log10 A, gamma) intrinsic red noise, Eq. (power_law)
+ *   th_dm[I][2]     (log10 A, gamma) DM            (absent if n_dm == 0)
+ *   th_gwb[2]       (log10 A, gamma) GWB
+ *   th_cw[8]        log10 Mc[Msun], log10 f_gw[Hz], log10 h, cos iota, psi,
+ *                   cos theta, phi, Phi0; then per pulsar (L_I[kpc], Phi_I)
+ *                   (absent unless cw) */
+typedef struct {
+  int npsr, n_ach, n_dm, P;   /* P = 2 n_ach + 2 n_dm coefficients per pulsar */
+  int d_z, d;                 /* standardized block size, total size */
+  int z_ach, z_dm, th_rn, th_dm, th_gwb, th_cw;
+  long long ntoa;             /* total TOAs */
+  double tspan_s, t0_s;       /* basis span T and origin t0 */
+} pta_layout_t;
+
+int pta_create(pta_ctx** out, const pta_model_desc* desc);
+int pta_add_pulsar(pta_ctx* ctx, const pta_pulsar_desc* psr);
+/* Precompute (noise weights, normalised timing model, its FP64 Cholesky, the
+ * Hellings-Downs matrix of Eq. HD, tile table) and upload.  Synchronises. */
+int pta_finalize(pta_ctx* ctx, void* stream);
+int pta_layout(const pta_ctx* ctx, pta_layout_t* out);
+/* Select the contraction precision (PTA_PREC_*) for later calls. */
+int pta_set_precision(pta_ctx* ctx, int precision);
+/* Hyper-prior box for (log10 A, gamma) of the GWB, red noise and DM (Sec.
+ * "Priors": log10 A ~ U(-20,-10), gamma ~ U(0,7) by default). */
+int pta_set_hyperprior(pta_ctx* ctx, double log10a_lo, double log10a_hi,
+                       double gamma_lo, double gamma_hi);
+
+/* Log posterior and gradient for B chains (the hot path).
+ *   x_dev      [B x D] float32, row per chain (layout above)
+ *   logp_dev   [B] float64: -1/2 sum_I r_I^T N~_I^-1 r_I - 1/2 |z|^2 + log p(theta),
+ *              data-only constants dropped (see pta_logp_constant)
+ *   grad_dev   [B x D] float32 d logp / d x, or NULL
+ *   status_dev [B] int32, or NULL: 0 ok; 1 theta outside the prior box;
+ *              2 per-frequency covariance not positive definite; 3 non-finite.
+ *              Any nonzero status sets logp = -inf and grad = 0 for that chain.
+ * Asynchronous on `stream`. */
+int pta_logp_and_grad(pta_ctx* ctx, int B, const float* x_dev, double* logp_dev,
+                      float* grad_dev, int32_t* status_dev, void* stream);
+
+/* One HMC transition per chain (Eqs. Hamiltonian, Hamilton's_eq,
+ * Gaussian_momentum, HMC_acceptance): momentum p ~ N(0, M) from Philox4x32-10
+ * (counter (j, chain, iteration), key seed), n_leapfrog leapfrog steps of size
+ * step_dev[b] with inverse mass inv_mass_dev[D] (NULL = identity), Metropolis
+ * accept.  x/logp/grad are read as the current state and overwritten with the
+ * next state; logp/grad must hold the values at x on entry.
+ * accepted_dev[B] receives 1/0.  The leapfrog loop runs as a CUDA graph that is
+ * captured on first use for each (B, n_leapfrog) and replayed after. */
+int pta_hmc_trajectory(pta_ctx* ctx, int B, float* x_dev, double* logp_dev, float* grad_dev,
+                       const float* step_dev, const float* inv_mass_dev, int n_leapfrog,
+                       uint64_t seed, uint64_t iteration, int32_t* accepted_dev, void* stream);
+
+/* The data-only constant dropped from logp:
+ * -1/2 sum_I [log det(2 pi N_I) + log det(M_I^T N_I^-1 M_I) - m_I log 2 pi]
+ * in ns units, minus (D_z/2) log 2 pi (host value, available after finalize). */
+int pta_logp_constant(const pta_ctx* ctx, double* c);
+
+/* Stage timing for measurement.  While enabled, pta_logp_and_grad records CUDA
+ * events on the caller's stream around each of its stages and counts the kernels
+ * it launches per stage.  pta_profile_read waits for the recorded events, writes
+ * the accumulated milliseconds and launch counts per stage (arrays of
+ * PTA_NSTAGES entries, either may be NULL) and, if reset != 0, clears them.
+ * Stages: 0 prior forward (spectra, Cholesky, transform), 1 TOA contractions,
+ * 2 FP64 epilogue (timing-model solve), 3 adjoint, 4 final sum. */
+#define PTA_NSTAGES 5
+int pta_profile_enable(pta_ctx* ctx, int enable);
+int pta_profile_read(pta_ctx* ctx, double* ms, long long* launches, int reset);
+
+const char* pta_last_error(const pta_ctx* ctx);
+void pta_destroy(pta_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -706,3 +706,47 @@ def hmc_trajectory(logp_grad, x0, logp0, grad0, step, n_leapfrog, p0, u, inv_mas
     if acc:
         return x, lp, g, True
     return x0.copy(), logp0, grad0.copy(), False
+
+
+# --------------------------------------------------------------------------- #
+# Near-posterior evaluation points (Eq. PTA_standard_transform_curn): per pulsar,
+# Sigma_CURN^-1 = F^T N~^-1 F + phi_CURN^-1 with phi_CURN the prior covariance
+# without inter-pulsar correlations, a_hat = Sigma_CURN F^T N~^-1 (dt - h), and
+# a = a_hat + L_CURN eps.  Returned in the z coordinates of the prior-whitened
+# transform, z = L_k^-1 a per frequency bin.
+# --------------------------------------------------------------------------- #
+def curn_point(orc: Oracle, x, eps_scale: float = 1.0, seed: int = 0):
+    x = np.asarray(x, dtype=np.float64).copy()
+    rng = np.random.default_rng(seed)
+    z_ach, z_dm, th_rn, th_dm, th_gwb, th_cw = orc.unpack(x)
+    rho, kappa, kdm = orc.spectra(th_rn, th_dm, th_gwb)
+    a = np.zeros((orc.npsr, orc.P))
+    for I in range(orc.npsr):
+        F = orc.get_F(I)
+        NF = ntilde_inv_woodbury(orc.Nvar[I], orc.psrs[I].M, F)
+        phi = np.zeros(orc.P)
+        for k in range(orc.na):
+            phi[2 * k: 2 * k + 2] = rho[k] + kappa[I, k]
+        for k in range(orc.n_dm):
+            phi[2 * orc.na + 2 * k: 2 * orc.na + 2 * k + 2] = kdm[I, k]
+        Sinv = F.T @ NF + np.diag(1.0 / phi)
+        d = orc.dt_ns[I] - (orc.signal(th_cw, I) if orc.cw else 0.0)
+        Lc = np.linalg.cholesky(Sinv)                 # Sinv = Lc Lc^T
+        ahat = sla.cho_solve((Lc, True), NF.T @ d)
+        # L_CURN eps with L_CURN L_CURN^T = Sinv^-1: solve Lc^T v = eps
+        a[I] = ahat + eps_scale * sla.solve_triangular(Lc.T, rng.normal(size=orc.P), lower=False)
+    Ls = [np.linalg.cholesky(orc.phi_bin(rho[k], kappa[:, k])) for k in range(orc.na)]
+    z = np.zeros(orc.Dz)
+    za = np.zeros((orc.na, 2, orc.npsr))
+    for k in range(orc.na):
+        for c in range(2):
+            za[k, c] = sla.solve_triangular(Ls[k], a[:, 2 * k + c], lower=True)
+    z[: orc.lay["z_dm"]] = za.reshape(-1)
+    if orc.n_dm:
+        zd = np.zeros((orc.npsr, orc.n_dm, 2))
+        for I in range(orc.npsr):
+            for k in range(orc.n_dm):
+                zd[I, k] = a[I, 2 * orc.na + 2 * k: 2 * orc.na + 2 * k + 2] / math.sqrt(kdm[I, k])
+        z[orc.lay["z_dm"]: orc.Dz] = zd.reshape(-1)
+    x[: orc.Dz] = z
+    return x

@@ -1,0 +1,423 @@
+// Prior side of the evaluation, FP64: spectra (Eq. power_law), the per-frequency
+// prior covariance Phi_k = rho_k Gamma + diag(kappa_.k) (Eq. prior_cov), its
+// Cholesky factor and inverse, the standardizing transform a = L z
+// (Eq. standardizing_transform with mu = 0), the adjoint of that transform and
+// the final per-chain sum.
+//
+// Work decomposition: one CTA per (frequency bin, chain) for bins whose Phi_k is
+// dense; the triangular updates walk a flat index over the active triangle or
+// rectangle so that every FP64 warp instruction runs with full lanes (FP64
+// issue is the scarce resource on this part).
+#include <cmath>
+
+#include "pta_internal.cuh"
+
+namespace pta {
+namespace {
+
+__device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+
+// Row index of packed-lower element idx (idx = i(i+1)/2 + j, 0 <= j <= i).
+__device__ __forceinline__ int tri_row(int idx) {
+  int i = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+  while (tri(i + 1, 0) <= idx) ++i;
+  while (tri(i, 0) > idx) --i;
+  return i;
+}
+
+__device__ __forceinline__ double pl_rho(const DevModel& m, const float* xb, int off, int k) {
+  return exp(ln_pl(m.ln_rho0, m.ln_Tfyr, (double)xb[off], (double)xb[off + 1], k));
+}
+
+// ---------------------------------------------------------------------------
+// Dense bins k < n_chol: Phi_k = rho_k Gamma + diag(kappa_.k).
+// ---------------------------------------------------------------------------
+__global__ void k_chol_forward(DevModel m, const float* __restrict__ x, float* a32, double* a64,
+                               double* Lpk, double* Lipk, int32_t* stat, int fp64) {
+  extern __shared__ double sm[];
+  const int np = m.npsr, ntri = np * (np + 1) / 2;
+  double* A = sm;              // packed lower, becomes L
+  double* X = sm + ntri;       // packed lower, becomes L^-1
+  double* zs = X + ntri;       // [2][np]
+  __shared__ double s_rho, s_piv;
+  __shared__ int s_bad;
+  const int k = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, nt = blockDim.x;
+  const float* xb = x + (size_t)b * m.d;
+  if (tid == 0) {
+    s_rho = pl_rho(m, xb, m.th_gwb, k + 1);
+    s_bad = 0;
+  }
+  __syncthreads();
+  const double rho = s_rho;
+  for (int idx = tid; idx < ntri; idx += nt) {
+    const int i = tri_row(idx), j = idx - tri(i, 0);
+    double v = rho * m.Gamma[i * np + j];
+    if (i == j) v += exp(ln_pl(m.ln_rho0, m.ln_Tfyr, (double)xb[m.th_rn + 2 * i], (double)xb[m.th_rn + 2 * i + 1], k + 1));
+    A[idx] = v;
+    X[idx] = (i == j) ? 1.0 : 0.0;
+  }
+  for (int i = tid; i < 2 * np; i += nt) zs[i] = (double)xb[m.z_ach + (2 * k) * np + i];
+  __syncthreads();
+  // right-looking Cholesky
+  for (int j = 0; j < np; ++j) {
+    if (tid == 0) {
+      double d = A[tri(j, j)];
+      if (!(d > 0.0)) {
+        s_bad = 1;
+        d = 1.0;
+      }
+      s_piv = sqrt(d);
+      A[tri(j, j)] = s_piv;
+    }
+    __syncthreads();
+    const double inv = 1.0 / s_piv;
+    for (int i = j + 1 + tid; i < np; i += nt) A[tri(i, j)] *= inv;
+    __syncthreads();
+    const int s = np - j - 1, cnt = s * (s + 1) / 2;
+    for (int idx = tid; idx < cnt; idx += nt) {
+      const int ip = tri_row(idx), lp = idx - tri(ip, 0);
+      const int i = ip + j + 1, l = lp + j + 1;
+      A[tri(i, l)] = fma(-A[tri(i, j)], A[tri(l, j)], A[tri(i, l)]);
+    }
+    __syncthreads();
+  }
+  // L^-1 by right-looking forward substitution on all right-hand sides at once
+  for (int j = 0; j < np; ++j) {
+    const double inv = 1.0 / A[tri(j, j)];
+    for (int c = tid; c <= j; c += nt) X[tri(j, c)] *= inv;
+    __syncthreads();
+    const int w = j + 1, cnt = (np - j - 1) * w;
+    for (int idx = tid; idx < cnt; idx += nt) {
+      const int i = j + 1 + idx / w, c = idx % w;
+      X[tri(i, c)] = fma(-A[tri(i, j)], X[tri(j, c)], X[tri(i, c)]);
+    }
+    __syncthreads();
+  }
+  if (s_bad && tid == 0) atomicOr(&stat[b], 2);
+  // a_{I,k,c} = sum_J L[I][J] z_{J,k,c}
+  for (int I = tid; I < np; I += nt) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int J = 0; J <= I; ++J) {
+      const double l = A[tri(I, J)];
+      s0 = fma(l, zs[J], s0);
+      s1 = fma(l, zs[np + J], s1);
+    }
+    const size_t o = ((size_t)I * gridDim.y + b) * m.PM + 2 * k;
+    a64[o] = s0;
+    a64[o + 1] = s1;
+  }
+  double* Lg = Lpk + ((size_t)b * m.n_chol + k) * ntri;
+  double* Xg = Lipk + ((size_t)b * m.n_chol + k) * ntri;
+  for (int idx = tid; idx < ntri; idx += nt) {
+    Lg[idx] = A[idx];
+    Xg[idx] = X[idx];
+  }
+}
+
+// Adjoint of a = L z for the dense bins.  With ghat = d logp / d a and
+// gt = L^T ghat:  d logp / d z = gt - z (the -z from -|z|^2/2);
+// kappa_I d logp/d kappa_I = kappa_I sum_c sum_{a>=I} gt_a u_a (sum_{I<=b<a} u_b z_b + u_a z_a / 2)
+// with u = column I of L^-1 (from dL = L tril_half(L^-1 dPhi L^-T), dPhi = e_I e_I^T); and
+// rho d logp / d rho = 1/2 sum_c gt.z - sum_I kappa_I d logp/d kappa_I (scaling identity:
+// Phi -> s Phi gives a -> sqrt(s) a).
+__global__ void k_chol_adjoint(DevModel m, const float* __restrict__ x, const double* __restrict__ ghat,
+                               const double* __restrict__ Lpk, const double* __restrict__ Lipk, float* grad,
+                               double* dlnk, double* dlnr, int B) {
+  extern __shared__ double sm[];
+  const int np = m.npsr, ntri = np * (np + 1) / 2;
+  double* Ls = sm;
+  double* Xs = sm + ntri;
+  double* zs = Xs + ntri;     // [2][np]
+  double* gs = zs + 2 * np;   // [2][np] ghat
+  double* gt = gs + 2 * np;   // [2][np]
+  double* red = gt + 2 * np;  // [np] kappa dlogp/dkappa
+  const int k = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, nt = blockDim.x;
+  const float* xb = x + (size_t)b * m.d;
+  const double* Lg = Lpk + ((size_t)b * m.n_chol + k) * ntri;
+  const double* Xg = Lipk + ((size_t)b * m.n_chol + k) * ntri;
+  for (int idx = tid; idx < ntri; idx += nt) {
+    Ls[idx] = Lg[idx];
+    Xs[idx] = Xg[idx];
+  }
+  for (int i = tid; i < 2 * np; i += nt) {
+    const int c = i / np, I = i % np;
+    zs[i] = (double)xb[m.z_ach + (2 * k) * np + i];
+    gs[i] = ghat[((size_t)I * B + b) * m.P + 2 * k + c];
+  }
+  __syncthreads();
+  for (int i = tid; i < 2 * np; i += nt) {
+    const int c = i / np, J = i % np;
+    double s = 0.0;
+    for (int I = J; I < np; ++I) s = fma(Ls[tri(I, J)], gs[c * np + I], s);
+    gt[i] = s;
+    grad[(size_t)b * m.d + m.z_ach + (2 * k) * np + i] = (float)(s - zs[i]);
+  }
+  __syncthreads();
+  for (int I = tid; I < np; I += nt) {
+    double p0 = 0.0, p1 = 0.0, acc = 0.0;
+    for (int a = I; a < np; ++a) {
+      const double u = Xs[tri(a, I)];
+      const double h0 = fma(0.5 * u, zs[a], p0), h1 = fma(0.5 * u, zs[np + a], p1);
+      acc = fma(gt[a] * u, h0, acc);
+      acc = fma(gt[np + a] * u, h1, acc);
+      p0 = fma(u, zs[a], p0);
+      p1 = fma(u, zs[np + a], p1);
+    }
+    const double kap = exp(ln_pl(m.ln_rho0, m.ln_Tfyr, (double)xb[m.th_rn + 2 * I], (double)xb[m.th_rn + 2 * I + 1], k + 1));
+    const double v = kap * acc;
+    red[I] = v;
+    dlnk[((size_t)b * np + I) * m.na + k] = v;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    double s = 0.0;
+    for (int i = tid; i < np; i += 32) s += 0.5 * (gt[i] * zs[i] + gt[np + i] * zs[np + i]) - red[i];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (tid == 0) dlnr[(size_t)b * m.na + k] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// GWB-only bins (no intrinsic red noise): Phi_k = rho_k Gamma, L_k = sqrt(rho_k) chol(Gamma).
+// ---------------------------------------------------------------------------
+__global__ void k_gwbonly_forward(DevModel m, const float* __restrict__ x, float* a32, double* a64, int fp64) {
+  const int k = m.n_chol + blockIdx.x, b = blockIdx.y, np = m.npsr;
+  const float* xb = x + (size_t)b * m.d;
+  const double sr = sqrt(pl_rho(m, xb, m.th_gwb, k + 1));
+  for (int I = threadIdx.x; I < np; I += blockDim.x) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int J = 0; J <= I; ++J) {
+      const double l = m.LGamma[I * np + J];
+      s0 = fma(l, (double)xb[m.z_ach + (2 * k) * np + J], s0);
+      s1 = fma(l, (double)xb[m.z_ach + (2 * k + 1) * np + J], s1);
+    }
+    const size_t o = ((size_t)I * gridDim.y + b) * m.PM + 2 * k;
+    a64[o] = sr * s0;
+    a64[o + 1] = sr * s1;
+  }
+}
+
+__global__ void k_gwbonly_adjoint(DevModel m, const float* __restrict__ x, const double* __restrict__ ghat,
+                                  float* grad, double* dlnr, int B) {
+  const int k = m.n_chol + blockIdx.x, b = blockIdx.y, np = m.npsr;
+  const float* xb = x + (size_t)b * m.d;
+  const double sr = sqrt(pl_rho(m, xb, m.th_gwb, k + 1));
+  double part = 0.0;
+  for (int i = threadIdx.x; i < 2 * np; i += blockDim.x) {
+    const int c = i / np, J = i % np;
+    double s = 0.0;
+    for (int I = J; I < np; ++I) s = fma(m.LGamma[I * np + J], ghat[((size_t)I * B + b) * m.P + 2 * k + c], s);
+    s *= sr;
+    const double z = (double)xb[m.z_ach + (2 * k) * np + i];
+    grad[(size_t)b * m.d + m.z_ach + (2 * k) * np + i] = (float)(s - z);
+    part += 0.5 * s * z;
+  }
+  __shared__ double red[32];
+  for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    dlnr[(size_t)b * m.na + k] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal bins: red-noise-only achromatic bins (n_gwb <= k < n_rn) and DM bins.
+// a = sqrt(kappa) z; d logp/d z = sqrt(kappa) ghat - z;
+// kappa d logp / d kappa = 1/2 sqrt(kappa) sum_c ghat_c z_c.
+// One thread per (chain, pulsar, bin).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void diag_index(const DevModel& m, int r, int& I, int& k, bool& dm) {
+  const int nrn_only = m.na - m.n_chol - m.n_gwbonly;  // achromatic diagonal bins
+  const int per = nrn_only + m.nd;
+  I = r / per;
+  const int q = r % per;
+  dm = q >= nrn_only;
+  k = dm ? q - nrn_only : m.n_chol + m.n_gwbonly + q;
+}
+
+__global__ void k_diag_forward(DevModel m, const float* __restrict__ x, float* a32, double* a64, int fp64,
+                               int B, int per_chain) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+  if (r >= per_chain) return;
+  int I, k;
+  bool dm;
+  diag_index(m, r, I, k, dm);
+  const float* xb = x + (size_t)b * m.d;
+  const int th = dm ? m.th_dm : m.th_rn;
+  const double sk = exp(0.5 * ln_pl(m.ln_rho0, m.ln_Tfyr, (double)xb[th + 2 * I], (double)xb[th + 2 * I + 1], k + 1));
+  const int zo = dm ? m.z_dm + (I * m.nd + k) * 2 : 0;
+  const double z0 = dm ? xb[zo] : xb[m.z_ach + (2 * k) * m.npsr + I];
+  const double z1 = dm ? xb[zo + 1] : xb[m.z_ach + (2 * k + 1) * m.npsr + I];
+  const size_t o = ((size_t)I * B + b) * m.PM + (dm ? 2 * m.na : 0) + 2 * k;
+  a64[o] = sk * z0;
+  a64[o + 1] = sk * z1;
+}
+
+__global__ void k_diag_adjoint(DevModel m, const float* __restrict__ x, const double* __restrict__ ghat,
+                               float* grad, double* dlnk, double* dlnkd, int B, int per_chain) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+  if (r >= per_chain) return;
+  int I, k;
+  bool dm;
+  diag_index(m, r, I, k, dm);
+  const float* xb = x + (size_t)b * m.d;
+  const int th = dm ? m.th_dm : m.th_rn;
+  const double sk = exp(0.5 * ln_pl(m.ln_rho0, m.ln_Tfyr, (double)xb[th + 2 * I], (double)xb[th + 2 * I + 1], k + 1));
+  const int z0i = dm ? m.z_dm + (I * m.nd + k) * 2 : m.z_ach + (2 * k) * m.npsr + I;
+  const int z1i = dm ? z0i + 1 : z0i + m.npsr;
+  const size_t o = ((size_t)I * B + b) * m.P + (dm ? 2 * m.na : 0) + 2 * k;
+  const double g0 = ghat[o], g1 = ghat[o + 1];
+  const double z0 = xb[z0i], z1 = xb[z1i];
+  grad[(size_t)b * m.d + z0i] = (float)(sk * g0 - z0);
+  grad[(size_t)b * m.d + z1i] = (float)(sk * g1 - z1);
+  const double v = 0.5 * sk * (g0 * z0 + g1 * z1);
+  if (dm)
+    dlnkd[((size_t)b * m.npsr + I) * m.nd + k] = v;
+  else
+    dlnk[((size_t)b * m.npsr + I) * m.na + k] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Final per-chain assembly: logp = -1/2 sum_I chi2_I - 1/2 |z|^2 (FP64), prior box,
+// status, and the hyper-parameter gradient by the chain rule through the power law:
+// d/d log10A = 2 ln10 sum_k kappa_k dlogp/dkappa_k, d/d gamma = -sum_k ln(f_k/f_yr) (...).
+// ---------------------------------------------------------------------------
+__global__ void k_final(DevModel m, const float* __restrict__ x, const double* __restrict__ chi2,
+                        const double* __restrict__ dlnk, const double* __restrict__ dlnkd,
+                        const double* __restrict__ dlnr, const int32_t* __restrict__ stat, double* logp,
+                        float* grad, int32_t* status, int B) {
+  const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x, np = m.npsr;
+  const float* xb = x + (size_t)b * m.d;
+  __shared__ double red[32];
+  __shared__ int s_flag;
+  if (tid == 0) s_flag = stat[b];
+  __syncthreads();
+  double acc = 0.0;
+  for (int j = tid; j < m.d_z; j += nt) acc = fma((double)xb[j], (double)xb[j], acc);
+  acc *= -0.5;
+  for (int I = tid; I < np; I += nt) acc -= 0.5 * chi2[(size_t)I * B + b];
+  int outside = 0;
+  for (int I = tid; I < np; I += nt) {
+    const float la = xb[m.th_rn + 2 * I], ga = xb[m.th_rn + 2 * I + 1];
+    outside |= !(la > m.la_lo && la < m.la_hi && ga > m.g_lo && ga < m.g_hi);
+    if (m.nd) {
+      const float ld = xb[m.th_dm + 2 * I], gd = xb[m.th_dm + 2 * I + 1];
+      outside |= !(ld > m.la_lo && ld < m.la_hi && gd > m.g_lo && gd < m.g_hi);
+    }
+  }
+  if (tid == 0) {
+    const float la = xb[m.th_gwb], ga = xb[m.th_gwb + 1];
+    outside |= !(la > m.la_lo && la < m.la_hi && ga > m.g_lo && ga < m.g_hi);
+  }
+  if (outside) atomicOr(&s_flag, 1);
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((tid & 31) == 0) red[tid >> 5] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (nt >> 5); ++w) s += red[w];
+    int fl = s_flag;
+    if (!isfinite(s) && fl == 0) fl = 3;
+    if (fl) {
+      if (fl & 1) fl = 1;
+      else if (fl & 2) fl = 2;
+      s = -INFINITY;
+    }
+    logp[b] = s;
+    if (status) status[b] = fl;
+    s_flag = fl;
+  }
+  __syncthreads();
+  if (!grad) return;
+  float* gb = grad + (size_t)b * m.d;
+  if (s_flag) {
+    for (int j = tid; j < m.d; j += nt) gb[j] = 0.f;
+    return;
+  }
+  for (int I = tid; I < np; I += nt) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int k = 0; k < m.n_rn; ++k) {
+      const double v = dlnk[((size_t)b * np + I) * m.na + k];
+      s1 += v;
+      s2 -= (log((double)(k + 1)) - m.ln_Tfyr) * v;
+    }
+    gb[m.th_rn + 2 * I] = (float)(2.0 * kLn10 * s1);
+    gb[m.th_rn + 2 * I + 1] = (float)s2;
+    if (m.nd) {
+      double d1 = 0.0, d2 = 0.0;
+      for (int k = 0; k < m.nd; ++k) {
+        const double v = dlnkd[((size_t)b * np + I) * m.nd + k];
+        d1 += v;
+        d2 -= (log((double)(k + 1)) - m.ln_Tfyr) * v;
+      }
+      gb[m.th_dm + 2 * I] = (float)(2.0 * kLn10 * d1);
+      gb[m.th_dm + 2 * I + 1] = (float)d2;
+    }
+  }
+  if (tid == 0) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int k = 0; k < m.n_gwb; ++k) {
+      const double v = dlnr[(size_t)b * m.na + k];
+      s1 += v;
+      s2 -= (log((double)(k + 1)) - m.ln_Tfyr) * v;
+    }
+    gb[m.th_gwb] = (float)(2.0 * kLn10 * s1);
+    gb[m.th_gwb + 1] = (float)s2;
+  }
+}
+
+}  // namespace
+
+static size_t chol_smem(const DevModel& m) {
+  const size_t np = m.npsr, ntri = np * (np + 1) / 2;
+  return (2 * ntri + 2 * np) * sizeof(double);
+}
+static size_t adj_smem(const DevModel& m) {
+  const size_t np = m.npsr, ntri = np * (np + 1) / 2;
+  return (2 * ntri + 7 * np) * sizeof(double);
+}
+
+cudaError_t launch_prior_forward(const DevModel& m, const Scratch& s, int B, const float* x, int fp64,
+                                 cudaStream_t st) {
+  if (m.n_chol > 0) {
+    const size_t sm = chol_smem(m);
+    cudaError_t e = cudaFuncSetAttribute(k_chol_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_chol_forward<<<dim3(m.n_chol, B), 128, sm, st>>>(m, x, s.a32, s.a64, s.Lpk, s.Lipk, s.stat, fp64);
+  }
+  if (m.n_gwbonly > 0) k_gwbonly_forward<<<dim3(m.n_gwbonly, B), 128, 0, st>>>(m, x, s.a32, s.a64, fp64);
+  const int per = m.npsr * ((m.na - m.n_chol - m.n_gwbonly) + m.nd);
+  if (per > 0) k_diag_forward<<<dim3((per + 127) / 128, B), 128, 0, st>>>(m, x, s.a32, s.a64, fp64, B, per);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prior_adjoint(const DevModel& m, const Scratch& s, int B, const float* x, float* grad,
+                                 cudaStream_t st) {
+  if (m.n_chol > 0) {
+    const size_t sm = adj_smem(m);
+    cudaError_t e = cudaFuncSetAttribute(k_chol_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_chol_adjoint<<<dim3(m.n_chol, B), 128, sm, st>>>(m, x, s.ghat, s.Lpk, s.Lipk, grad, s.dlnk, s.dlnr, B);
+  }
+  if (m.n_gwbonly > 0) k_gwbonly_adjoint<<<dim3(m.n_gwbonly, B), 128, 0, st>>>(m, x, s.ghat, grad, s.dlnr, B);
+  const int per = m.npsr * ((m.na - m.n_chol - m.n_gwbonly) + m.nd);
+  if (per > 0)
+    k_diag_adjoint<<<dim3((per + 127) / 128, B), 128, 0, st>>>(m, x, s.ghat, grad, s.dlnk, s.dlnkd, B, per);
+  return cudaGetLastError();
+}
+
+int count_prior_forward(const DevModel& m) {
+  return (m.n_chol > 0) + (m.n_gwbonly > 0) + (m.npsr * ((m.na - m.n_chol - m.n_gwbonly) + m.nd) > 0);
+}
+int count_prior_adjoint(const DevModel& m) { return count_prior_forward(m); }
+
+cudaError_t launch_final(const DevModel& m, const Scratch& s, int B, const float* x, double* logp, float* grad,
+                         int32_t* status, cudaStream_t st) {
+  k_final<<<B, 256, 0, st>>>(m, x, s.chi2, s.dlnk, s.dlnkd, s.dlnr, s.stat, logp, grad, status, B);
+  return cudaGetLastError();
+}
+
+}  // namespace pta

@@ -1,0 +1,421 @@
+// TOA-domain part of the evaluation: the timing-model-marginalised likelihood of
+// Eq. (raw_det_posterior) with N~^-1 of Eq. (Gmatrix_proj) in its projected form,
+//   c  = (M^T N^-1 M)^-1 M^T N^-1 (dt - F a)          (FP64, per pulsar and chain)
+//   r~ = dt - F a - M c,   w~ = N^-1 r~ = N~^-1 (dt - F a)
+//   chi2 = r~ . w~,        ghat = F^T w~ = d logp / d a
+// The projection is applied before the TOA-length sums, so neither chi2 nor ghat
+// is a small difference of large terms (the unprojected residual can be orders
+// of magnitude above the noise where F a carries timing-model-like power).
+//
+// Work unit = (pulsar, chunk of <= 2048 TOAs) x block of chains; each unit writes
+// its partial sums to its own slot and the FP64 reduction sums them in a fixed
+// order, so results do not depend on scheduling.
+//
+// FP32 variant: the Fourier basis of Eq. (Fourier_series) and its DM copy weighted
+// by (nu_ref/nu)^2 are generated in shared memory from a 64-bit fixed-point phase
+// k * U_i mod 2^64 (exact argument reduction); with the timing-model rows they
+// form one transposed tile X^T[q][t] used by both contractions.
+// FP64 variant (plain path): stored FP64 basis, one CTA per (unit, chain).
+#include "pta_internal.cuh"
+
+namespace pta {
+namespace {
+
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------
+// Timing-model prologue, one CTA (128 threads) per (pulsar, chain).
+// With the reference coefficients a_ref (the projected reference residual dt''
+// satisfies M^T N^-1 dt'' = 0) and da = a - a_ref, the projected residual is
+//   r~ = dt'' - F da - M c,  c = -(M^T N^-1 M)^-1 H^T da,  H = F^T N^-1 M.
+// FP64 path: c from the full H in FP64; row = [da, c].
+// FP32 path: the lowest-frequency columns (nla achromatic, nld DM bins) use the
+// stored projected basis F~_lo = F_lo - M K^-1 H_lo^T, so c only carries the other
+// columns: c_hi = -K^-1 H_hi^T da_hi.  H_hi^T da_hi is a compensated FP32 dot
+// product (error-free FMA products and sums, Ogita-Rump-Oishi "Dot2") on hi/lo
+// splits of H and da; the K solve is FP64.  Row = [da with zeros on the low
+// columns, c_hi, da_lo] matching the tile rows [F, M, F~_lo].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool is_low_col(const DevModel& m, int p) {
+  return p < 2 * m.nla || (p >= 2 * m.na && p < 2 * m.na + 2 * m.nld);
+}
+__device__ __forceinline__ int low_col(const DevModel& m, int q) {
+  return q < 2 * m.nla ? q : 2 * m.na + (q - 2 * m.nla);
+}
+
+__global__ void __launch_bounds__(128)
+    k_tm_prologue(DevModel m, double* __restrict__ a64, float* __restrict__ a32, int B, int fp64) {
+  extern __shared__ double smp[];
+  const int I = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int P = m.P, mI = m.m[I];
+  double* da = smp;             // [P]
+  double* part = da + P;        // [4][mI]
+  double* cv = part + 4 * mI;   // [mI]
+  double* row = a64 + ((size_t)I * B + b) * m.PM;
+  const double* ar = m.aref + (size_t)I * P;
+  for (int p = tid; p < P; p += 128) da[p] = row[p] - ar[p];
+  __syncthreads();
+  for (int j0 = 0; j0 < mI; j0 += 32) {
+    const int j = j0 + lane;
+    if (j < mI) {
+      if (fp64) {
+        const double* H = m.H + m.h_off[I];
+        double s = 0.0;
+        for (int p = warp; p < P; p += 4) s = fma(H[(size_t)p * mI + j], da[p], s);
+        part[warp * mI + j] = s;
+      } else {
+        const float* Hh = m.Hhi + m.h_off[I];
+        const float* Hl = m.Hlo + m.h_off[I];
+        float s = 0.f, comp = 0.f;
+        for (int p = warp; p < P; p += 4) {
+          if (is_low_col(m, p)) continue;
+          const float xh = (float)da[p], xl = (float)(da[p] - (double)xh);
+          const float hh = Hh[(size_t)p * mI + j], hl = Hl[(size_t)p * mI + j];
+          const float pr = hh * xh;
+          const float pe = fmaf(hh, xh, -pr);          // exact product error
+          const float t = s + pr;
+          const float z = t - s;
+          const float se = (s - (t - z)) + (pr - z);   // exact sum error
+          s = t;
+          comp += se + pe + fmaf(hh, xl, hl * xh);
+        }
+        part[warp * mI + j] = (double)s + (double)comp;
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int j = lane; j < mI; j += 32)
+      cv[j] = -(part[j] + part[mI + j] + part[2 * mI + j] + part[3 * mI + j]);
+    __syncwarp();
+    const double* Lk = m.LK + m.lk_off[I];
+    for (int i = 0; i < mI; ++i) {  // Lk y = rhs
+      double s = 0.0;
+      for (int l = lane; l < i; l += 32) s = fma(Lk[i * mI + l], cv[l], s);
+      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) cv[i] = (cv[i] - s) / Lk[i * mI + i];
+      __syncwarp();
+    }
+    for (int i = mI - 1; i >= 0; --i) {  // Lk^T c = y
+      double s = 0.0;
+      for (int l = i + 1 + lane; l < mI; l += 32) s = fma(Lk[l * mI + i], cv[l], s);
+      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) cv[i] = (cv[i] - s) / Lk[i * mI + i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (fp64) {
+    for (int p = tid; p < P; p += 128) row[p] = da[p];
+    for (int j = tid; j < mI; j += 128) row[P + j] = cv[j];
+  } else {
+    float* r32 = a32 + ((size_t)I * B + b) * m.PM;
+    for (int q = tid; q < m.PM; q += 128) {
+      float v = 0.f;
+      if (q < P)
+        v = is_low_col(m, q) ? 0.f : (float)da[q];
+      else if (q < P + mI)
+        v = (float)cv[q - P];
+      else if (q < P + mI + m.NL)
+        v = (float)da[low_col(m, q - P - mI)];
+      r32[q] = v;
+    }
+  }
+}
+
+template <int BC, int TT, int QPT>
+struct SimtCfg {
+  static constexpr int CG = BC / 4;            // chain groups of 4
+  static constexpr int RG = kThreads / CG;     // row groups (GEMM1) == q lanes (GEMM2)
+  static constexpr int RPT = TT / RG;          // TOA rows per thread in GEMM1
+  static constexpr int QPAD = RG * QPT;        // rows of ghat covered by GEMM2
+  static constexpr int XS = TT + 4;            // X^T row stride (floats)
+  static constexpr int AS = BC + 4;            // A row stride
+  static constexpr int WS = BC + 4;            // W row stride
+  static_assert(RPT >= 1 && RG * RPT == TT, "tile shape");
+};
+
+template <int BC, int TT, int QPT>
+int simt_xrows(const DevModel& m) {
+  using C = SimtCfg<BC, TT, QPT>;
+  return C::QPAD > m.PM ? C::QPAD : m.PM;
+}
+
+template <int BC, int TT, int QPT>
+size_t simt_smem(const DevModel& m) {
+  using C = SimtCfg<BC, TT, QPT>;
+  return sizeof(float) * ((size_t)simt_xrows<BC, TT, QPT>(m) * C::XS + (size_t)m.PM * C::AS +
+                          (size_t)TT * C::WS + (size_t)C::RG * BC + 2 * TT);
+}
+
+template <int BC, int TT, int QPT>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_toa_simt(DevModel m, const float* __restrict__ a32, float* __restrict__ gpart, double* __restrict__ c2part,
+               int B, int XR) {
+  using C = SimtCfg<BC, TT, QPT>;
+  extern __shared__ float4 sm4[];
+  float* Xs = reinterpret_cast<float*>(sm4);            // [XR][XS]  rows: F (P), M (m_I), F~_lo (NL), zero
+  float* As = Xs + XR * C::XS;                          // [PM][AS]  coefficient rows in the same order
+  float* Ws = As + m.PM * C::AS;                        // [TT][WS]
+  float* C2 = Ws + TT * C::WS;                          // [RG][BC]
+  float* dts = C2 + C::RG * BC;                         // [TT]
+  float* nis = dts + TT;                                // [TT]
+  const int u = blockIdx.x, b0 = blockIdx.y * BC, tid = threadIdx.x;
+  const int I = m.unit_psr[u], start = m.unit_start[u], len = m.unit_len[u];
+  const int P = m.P, mI = m.m[I], NL = m.NL, KA = P + mI + NL, na = m.na, nd = m.nd;
+  const int kmax = na > nd ? na : nd;
+  const float* Mg = m.M32 + m.m_off[I] + (long long)(start - m.toa_off[I]) * mI;
+  const float* Lg = m.Flo + m.flo_off[I] + (long long)(start - m.toa_off[I]) * NL;
+  for (int e = tid; e < KA * BC; e += kThreads) {
+    const int c = e / KA, p = e % KA;
+    As[p * C::AS + c] = (b0 + c < B) ? a32[((size_t)I * B + b0 + c) * m.PM + p] : 0.f;
+  }
+  const int cg = tid % C::CG, rg = tid / C::CG;
+  float acc[QPT][4];
+#pragma unroll
+  for (int i = 0; i < QPT; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  double c2acc = 0.0;
+
+  for (int t0 = 0; t0 < len; t0 += TT) {
+    __syncthreads();  // previous tile fully consumed
+    {
+      const int t = tid % TT;
+      const int lane_k = tid / TT, kstride = kThreads / TT;
+      const uint64_t U = m.phase[start + t0 + t];
+      const float wch = m.chrom[start + t0 + t];
+      uint64_t ph = U * (uint64_t)(lane_k + 1);
+      const uint64_t dph = U * (uint64_t)kstride;
+      for (int k = lane_k + 1; k <= kmax; k += kstride, ph += dph) {
+        float s, c;
+        sincos_turns64(ph, &s, &c);
+        if (k <= na) {
+          Xs[(2 * (k - 1)) * C::XS + t] = s;
+          Xs[(2 * (k - 1) + 1) * C::XS + t] = c;
+        }
+        if (k <= nd) {
+          Xs[(2 * na + 2 * (k - 1)) * C::XS + t] = s * wch;
+          Xs[(2 * na + 2 * (k - 1) + 1) * C::XS + t] = c * wch;
+        }
+      }
+      for (int e = tid; e < TT * mI; e += kThreads) {
+        const int tt = e / mI, j = e % mI;
+        Xs[(P + j) * C::XS + tt] = Mg[(long long)(t0 + tt) * mI + j];
+      }
+      for (int e = tid; e < TT * NL; e += kThreads) {
+        const int tt = e / NL, j = e % NL;
+        Xs[(P + mI + j) * C::XS + tt] = Lg[(long long)(t0 + tt) * NL + j];
+      }
+      for (int e = tid; e < (XR - KA) * TT; e += kThreads) {
+        const int q = KA + e / TT, tt = e % TT;
+        Xs[q * C::XS + tt] = 0.f;
+      }
+      if (tid < TT) {
+        dts[tid] = m.dt[start + t0 + tid];
+        nis[tid] = m.ninv[start + t0 + tid];
+      }
+    }
+    __syncthreads();
+    // --- y[t][c] = sum_p [F | M | F~_lo][t][p] coef[p][c]
+    float y[C::RPT][4];
+#pragma unroll
+    for (int r = 0; r < C::RPT; ++r)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) y[r][j] = 0.f;
+    const float* xrow = Xs + rg * C::RPT;
+    const float* arow = As + 4 * cg;
+#pragma unroll 2
+    for (int p = 0; p < KA; ++p) {
+      const float4 av = *reinterpret_cast<const float4*>(arow + p * C::AS);
+      float fv[C::RPT];
+      if constexpr (C::RPT % 4 == 0) {
+#pragma unroll
+        for (int r = 0; r < C::RPT; r += 4) {
+          const float4 f4 = *reinterpret_cast<const float4*>(xrow + p * C::XS + r);
+          fv[r] = f4.x;
+          fv[r + 1] = f4.y;
+          fv[r + 2] = f4.z;
+          fv[r + 3] = f4.w;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < C::RPT; ++r) fv[r] = xrow[p * C::XS + r];
+      }
+#pragma unroll
+      for (int r = 0; r < C::RPT; ++r) {
+        y[r][0] = fmaf(fv[r], av.x, y[r][0]);
+        y[r][1] = fmaf(fv[r], av.y, y[r][1]);
+        y[r][2] = fmaf(fv[r], av.z, y[r][2]);
+        y[r][3] = fmaf(fv[r], av.w, y[r][3]);
+      }
+    }
+    // --- projected residual, whitened residual, chi2 pieces
+    float q4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int r = 0; r < C::RPT; ++r) {
+      const int t = rg * C::RPT + r;
+      const float dtv = dts[t], ni = nis[t];
+      float4 wv;
+      float* wp = reinterpret_cast<float*>(&wv);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float rr = dtv - y[r][j];
+        const float ww = rr * ni;
+        wp[j] = ww;
+        q4[j] = fmaf(rr, ww, q4[j]);
+      }
+      *reinterpret_cast<float4*>(Ws + t * C::WS + 4 * cg) = wv;
+    }
+    *reinterpret_cast<float4*>(C2 + rg * BC + 4 * cg) = make_float4(q4[0], q4[1], q4[2], q4[3]);
+    __syncthreads();
+    if (tid < BC) {  // fixed-order chi2 reduction over row groups: thread c owns chain c
+      float s = 0.f;
+      for (int g = 0; g < C::RG; ++g) s += C2[g * BC + tid];
+      c2acc += (double)s;
+    }
+    // --- ghat[q][c] += sum_t F^T[q][t] w~[t][c],  q = rg + RG*i < P
+#pragma unroll 2
+    for (int t = 0; t < TT; ++t) {
+      const float4 wv = *reinterpret_cast<const float4*>(Ws + t * C::WS + 4 * cg);
+#pragma unroll
+      for (int i = 0; i < QPT; ++i) {
+        const float xv = Xs[(rg + C::RG * i) * C::XS + t];
+        acc[i][0] = fmaf(xv, wv.x, acc[i][0]);
+        acc[i][1] = fmaf(xv, wv.y, acc[i][1]);
+        acc[i][2] = fmaf(xv, wv.z, acc[i][2]);
+        acc[i][3] = fmaf(xv, wv.w, acc[i][3]);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < QPT; ++i) {
+    const int q = rg + C::RG * i;
+    if (q < P) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int b = b0 + 4 * cg + j;
+        if (b < B) gpart[((size_t)u * B + b) * m.Qs + q] = acc[i][j];
+      }
+    }
+  }
+  if (tid < BC && b0 + tid < B) c2part[(size_t)u * B + b0 + tid] = c2acc;
+}
+
+// Plain FP64 path.  One CTA of 128 threads per (unit, chain); tile of 128 TOAs,
+// thread t owns TOA t for y = F da + M c; F^T w~ columns are warp reductions.
+__global__ void __launch_bounds__(128)
+    k_toa_fp64(DevModel m, const double* __restrict__ a64, double* __restrict__ gpart, double* __restrict__ c2part,
+               int B) {
+  extern __shared__ double smd[];
+  const int u = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int I = m.unit_psr[u], start = m.unit_start[u], len = m.unit_len[u];
+  const int P = m.P, mI = m.m[I];
+  double* as = smd;          // [P + mI]
+  double* gacc = as + m.PM;  // [P]
+  double* ws = gacc + P;     // [128]
+  double* red = ws + 128;    // [4]
+  for (int p = tid; p < P + mI; p += 128) as[p] = a64[((size_t)I * B + b) * m.PM + p];
+  for (int q = tid; q < P; q += 128) gacc[q] = 0.0;
+  double c2 = 0.0;
+  const double* F = m.F64 + m.f_off[I];
+  const double* Mg = m.M64 + m.m_off[I];
+  const int base = start - m.toa_off[I];
+  __syncthreads();
+  for (int t0 = 0; t0 < len; t0 += 128) {
+    const int li = base + t0 + tid;  // TOA index within the pulsar
+    double y = 0.0;
+    const double* Fr = F + (size_t)li * P;
+    for (int p = 0; p < P; ++p) y = fma(Fr[p], as[p], y);
+    const double* Mr = Mg + (size_t)li * mI;
+    for (int j = 0; j < mI; ++j) y = fma(Mr[j], as[P + j], y);
+    const double r = m.dt64[start + t0 + tid] - y;
+    const double w = r * m.ninv64[start + t0 + tid];
+    ws[tid] = w;
+    double q = r * w;
+    for (int o = 16; o; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if (lane == 0) red[warp] = q;
+    __syncthreads();
+    if (tid == 0) c2 += red[0] + red[1] + red[2] + red[3];
+    for (int qq = warp; qq < P; qq += 4) {
+      double s = 0.0;
+      for (int t = lane; t < 128; t += 32) s = fma(F[(size_t)(base + t0 + t) * P + qq], ws[t], s);
+      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) gacc[qq] += s;
+    }
+    __syncthreads();
+  }
+  for (int q = tid; q < P; q += 128) gpart[((size_t)u * B + b) * m.Qs + q] = gacc[q];
+  if (tid == 0) c2part[(size_t)u * B + b] = c2;
+}
+
+// FP64 reduction over a pulsar's units (fixed order): ghat = F^T N~^-1 r, chi2.
+__global__ void __launch_bounds__(128)
+    k_reduce(DevModel m, const float* __restrict__ gpart, const double* __restrict__ gpart64,
+             const double* __restrict__ c2part, double* __restrict__ ghat, double* __restrict__ chi2, int B,
+             int fp64) {
+  const int I = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
+  const int P = m.P, u0 = m.unit0[I], nu = m.nunit[I];
+  for (int q = tid; q < P; q += 128) {
+    double s = 0.0;
+    for (int j = 0; j < nu; ++j) {
+      const size_t o = ((size_t)(u0 + j) * B + b) * m.Qs + q;
+      s += fp64 ? gpart64[o] : (double)gpart[o];
+    }
+    ghat[((size_t)I * B + b) * P + q] = s;
+  }
+  if (tid == 0) {
+    double c2 = 0.0;
+    for (int j = 0; j < nu; ++j) c2 += c2part[(size_t)(u0 + j) * B + b];
+    chi2[(size_t)I * B + b] = c2;
+  }
+}
+
+template <int BC, int TT, int QPT>
+cudaError_t launch_simt(const DevModel& m, const Scratch& s, int B, cudaStream_t st) {
+  const size_t sm = simt_smem<BC, TT, QPT>(m);
+  if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(k_toa_simt<BC, TT, QPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid(m.n_units, (B + BC - 1) / BC);
+  k_toa_simt<BC, TT, QPT><<<grid, kThreads, sm, st>>>(m, s.a32, s.gpart, s.c2part, B, simt_xrows<BC, TT, QPT>(m));
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_tm_prologue(const DevModel& m, const Scratch& s, int B, int fp64, cudaStream_t st) {
+  const size_t sm = sizeof(double) * (m.P + 5 * m.m_max);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_tm_prologue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  k_tm_prologue<<<dim3(m.npsr, B), 128, sm, st>>>(m, s.a64, s.a32, B, fp64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_toa_fp32(const DevModel& m, const Scratch& s, int B, cudaStream_t st) {
+  // BC = 64 chains per CTA, 16 q lanes: ghat rows covered = 16 * QPT
+  if (m.P <= 32) return launch_simt<64, 64, 2>(m, s, B, st);
+  if (m.P <= 64) return launch_simt<64, 64, 4>(m, s, B, st);
+  if (m.P <= 128) return launch_simt<64, 64, 8>(m, s, B, st);
+  if (m.P <= 192) return launch_simt<64, 64, 12>(m, s, B, st);
+  if (m.P <= 272) return launch_simt<64, 64, 17>(m, s, B, st);
+  if (m.P <= 384) return launch_simt<64, 64, 24>(m, s, B, st);
+  if (m.P <= 512) return launch_simt<32, 32, 16>(m, s, B, st);
+  if (m.P <= 640) return launch_simt<32, 32, 20>(m, s, B, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_toa_fp64(const DevModel& m, const Scratch& s, int B, cudaStream_t st) {
+  const size_t sm = sizeof(double) * (m.PM + m.P + 128 + 4);
+  k_toa_fp64<<<dim3(m.n_units, B), 128, sm, st>>>(m, s.a64, s.gpart64, s.c2part, B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const DevModel& m, const Scratch& s, int B, int fp64, cudaStream_t st) {
+  k_reduce<<<dim3(m.npsr, B), 128, 0, st>>>(m, s.gpart, s.gpart64, s.c2part, s.ghat, s.chi2, B, fp64);
+  return cudaGetLastError();
+}
+
+}  // namespace pta

@@ -1,0 +1,206 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ptahmc.h"
+
+namespace pta {
+
+constexpr double kYearS = 365.25 * 86400.0;
+constexpr double kFyr = 1.0 / kYearS;
+constexpr double kLn10 = 2.302585092994045684;
+constexpr double kPi = 3.141592653589793238;
+constexpr double kTsunS = 4.925490947641267e-06;  // G Msun / c^3
+constexpr double kKpcS = 1.0292712503e11;         // 1 kpc / c
+constexpr int kTile = 128;       // TOAs per pulsar are padded to a multiple of this
+constexpr int kChunk = 2048;     // TOAs per work unit of the TOA kernels
+constexpr int kMaxPsr = 256;
+constexpr int kLowBins = 4;     // lowest frequencies whose basis columns are projected off the timing model
+
+// Everything a kernel needs about the model and the resident data.  Passed by
+// value; all pointers are device pointers owned by the context.
+struct DevModel {
+  int npsr, na, nd, n_gwb, n_rn, P, Qs, PM, d_z, d, cw;   // PM: coefficient row stride
+  int nla, nld, NL;  // projected low-frequency columns: achromatic k <= nla, DM k <= nld; NL = 2 (nla + nld)
+  int z_ach, z_dm, th_rn, th_dm, th_gwb, th_cw;
+  int n_chol;      // bins k < n_chol: Phi_k = rho_k Gamma + diag(kappa_.k), full Cholesky
+  int n_gwbonly;   // bins n_chol <= k < n_chol + n_gwbonly: Phi_k = rho_k Gamma
+  int n_units, m_max;
+  double T, ln_Tfyr, ln_rho0;   // T [s], ln(T f_yr), power-law normalisation (see ln_pl)
+  double la_lo, la_hi, g_lo, g_hi;
+  // per TOA (padded; padding rows have ninv = 0)
+  const uint64_t* phase;        // round(2^64 (t - t0)/T)
+  const float* chrom;           // (nu_ref/nu)^2
+  const float* dt;              // reference-projected residual dt'' [ns] (see finalize)
+  const float* ninv;            // 1/N_ii [1/ns^2]
+  const float* M32;             // per pulsar [n_pad x m_I] row-major, normalised columns
+  const double* dt64;
+  const double* ninv64;
+  const double* chrom64;
+  const double* F64;            // per pulsar [n_pad x P] (FP64 path only, built on first use)
+  const double* M64;            // per pulsar [n_pad x m_I]
+  // per pulsar
+  const int* toa_off;           // start of the pulsar in the padded TOA arrays
+  const int* n_pad;
+  const int* m;
+  const long long* m_off;       // element offset of the pulsar's M block
+  const long long* f_off;       // element offset of the pulsar's F64 block
+  const int* unit0;             // first work unit of the pulsar
+  const int* nunit;
+  const int* lk_off;            // offset of chol(M^T N^-1 M) (m x m, row-major FP64)
+  const double* LK;
+  const int* h_off;             // offset of F^T N^-1 M (P x m row-major FP64)
+  const double* H;
+  const float* Hhi;             // H split into FP32 hi + lo parts (same layout as H)
+  const float* Hlo;
+  const double* aref;           // [npsr][P] reference coefficients (numerical conditioning)
+  const float* Flo;             // per pulsar [n_pad x NL] projected low-frequency basis
+  const long long* flo_off;
+  const double* pos;            // [npsr][3]
+  const double* dist;           // [npsr]
+  // per unit
+  const int* unit_psr;
+  const int* unit_start;        // absolute padded TOA index
+  const int* unit_len;          // multiple of 64
+  // global
+  const double* Gamma;          // [npsr x npsr]
+  const double* LGamma;         // chol(Gamma), lower, [npsr x npsr]
+};
+
+// Scratch sized for a batch of up to `cap` chains.
+struct Scratch {
+  int cap = 0;
+  float* a32 = nullptr;        // [npsr][cap][PM]  (a, then timing-model offsets c)
+  double* a64 = nullptr;       // [npsr][cap][PM]
+  double* Lpk = nullptr;       // [cap][n_chol][np(np+1)/2]
+  double* Lipk = nullptr;      // same, inverse factor
+  float* gpart = nullptr;      // [units][cap][Qs]
+  double* gpart64 = nullptr;   // [units][cap][Qs] (FP64 path)
+  double* c2part = nullptr;    // [units][cap]
+  double* ghat = nullptr;      // [npsr][cap][P]
+  double* chi2 = nullptr;      // [npsr][cap]
+  double* dlnk = nullptr;      // [cap][npsr][na]  kappa dlogp/dkappa (achromatic)
+  double* dlnkd = nullptr;     // [cap][npsr][nd]  same for DM
+  double* dlnr = nullptr;      // [cap][na]        rho dlogp/drho
+  int32_t* stat = nullptr;     // [cap]
+  // HMC state
+  float* x0 = nullptr;         // [cap][d]
+  float* g0 = nullptr;
+  float* p = nullptr;
+  double* lp0 = nullptr;
+  float* xs = nullptr;         // working state
+  float* gs = nullptr;
+  double* lps = nullptr;
+  float* step = nullptr;       // [cap]
+  float* imass = nullptr;      // [d]
+  double* kin0 = nullptr;      // [cap]
+  uint64_t* hmc_ctr = nullptr; // [2] seed, iteration
+  int32_t* acc = nullptr;      // [cap] accept flags
+};
+
+// Kernel launchers (defined in the .cu files).
+cudaError_t launch_prior_forward(const DevModel& m, const Scratch& s, int B, const float* x,
+                                 int fp64, cudaStream_t st);
+cudaError_t launch_toa_fp32(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
+cudaError_t launch_toa_fp64(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
+cudaError_t launch_tm_prologue(const DevModel& m, const Scratch& s, int B, int fp64, cudaStream_t st);
+cudaError_t launch_reduce(const DevModel& m, const Scratch& s, int B, int fp64, cudaStream_t st);
+cudaError_t launch_prior_adjoint(const DevModel& m, const Scratch& s, int B, const float* x,
+                                 float* grad, cudaStream_t st);
+int count_prior_forward(const DevModel& m);
+int count_prior_adjoint(const DevModel& m);
+cudaError_t launch_final(const DevModel& m, const Scratch& s, int B, const float* x,
+                         double* logp, float* grad, int32_t* status, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+// log of the power-law spectrum (Eq. power_law) in ns^2 at bin k (f_k = k/T):
+// rho_k = A^2 / (12 pi^2 f_yr^3 T) (f_k / f_yr)^(-gamma), so
+// ln rho_k = 2 ln10 log10A + ln_rho0 - gamma (ln k - ln(T f_yr)),
+// ln_rho0 = ln(1e18 / (12 pi^2 f_yr^3 T)) computed on the host in FP64.
+__host__ __device__ inline double ln_pl(double ln_rho0, double ln_Tfyr, double log10A, double gamma, int k) {
+  return 2.0 * kLn10 * log10A + ln_rho0 - gamma * (log((double)k) - ln_Tfyr);
+}
+
+// sin and cos of 2 pi * phi / 2^64 for a 64-bit fixed-point phase phi.  The top
+// three bits select the octant; the remaining 61 bits are a fraction of pi/4
+// whose FP32 rounding error is at most 2^-24 relative.  The reduced argument
+// (|x| <= pi/4) goes through Taylor polynomials (sin to x^9, cos to x^10),
+// whose truncation error is below 2e-9.
+__device__ __forceinline__ void sincos_turns64(uint64_t phi, float* s, float* c) {
+  const unsigned oct = (unsigned)(phi >> 61);
+  uint64_t rem = phi & ((1ull << 61) - 1);
+  // odd octants measure the angle back from the next multiple of pi/4
+  const bool odd = oct & 1u;
+  if (odd) rem = (1ull << 61) - rem;
+  const float x = (float)rem * 3.4061215800865545e-19f;  // (pi/4) / 2^61
+  const float x2 = x * x;
+  float sp = fmaf(x2, 2.7557319e-06f, -1.9841270e-04f);
+  sp = fmaf(x2, sp, 8.3333333e-03f);
+  sp = fmaf(x2, sp, -1.6666667e-01f);
+  const float sv = fmaf(x * x2, sp, x);
+  float cp = fmaf(x2, -2.7557319e-07f, 2.4801587e-05f);
+  cp = fmaf(x2, cp, -1.3888889e-03f);
+  cp = fmaf(x2, cp, 4.1666667e-02f);
+  cp = fmaf(x2, cp, -0.5f);
+  const float cv = fmaf(x2, cp, 1.0f);
+  // angle = oct*pi/4 + x (even) or (oct+1)*pi/4 - x (odd)
+  float sn, cs;
+  switch (oct) {
+    case 0: sn = sv; cs = cv; break;      // x
+    case 1: sn = cv; cs = sv; break;      // pi/2 - x
+    case 2: sn = cv; cs = -sv; break;     // pi/2 + x
+    case 3: sn = sv; cs = -cv; break;     // pi - x
+    case 4: sn = -sv; cs = -cv; break;    // pi + x
+    case 5: sn = -cv; cs = -sv; break;    // 3pi/2 - x
+    case 6: sn = -cv; cs = sv; break;     // 3pi/2 + x
+    default: sn = -sv; cs = cv; break;    // 2pi - x
+  }
+  *s = sn;
+  *c = cs;
+}
+
+inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+}  // namespace pta
+
+// The context (opaque to C callers).
+struct pta_ctx {
+  pta_model_desc desc{};
+  std::string err;
+  bool finalized = false;
+  struct HostPsr {
+    int n, m, nb;
+    std::vector<double> t, nu, dt, sig, efac, equad, M;
+    std::vector<int32_t> be;
+    double pos[3];
+    double dist;
+  };
+  std::vector<HostPsr> psrs;
+  pta::DevModel dm{};
+  pta::Scratch sc{};
+  std::vector<void*> dev_allocs;   // data buffers freed at destroy
+  double logp_const = 0.0;
+  double t0 = 0.0;
+  long long ntoa = 0;
+  int precision = PTA_PREC_FP32;
+  pta_layout_t lay{};
+  // HMC graphs keyed by (B, n_leapfrog)
+  struct Graph {
+    int B, L;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  cudaStream_t cap_stream = nullptr;
+  // stage profiler
+  bool prof = false;
+  std::vector<cudaEvent_t> prof_ev;   // pairs (start, end) per recorded stage
+  std::vector<int> prof_stage;
+  double prof_ms[PTA_NSTAGES] = {0, 0, 0, 0, 0};
+  long long prof_launch[PTA_NSTAGES] = {0, 0, 0, 0, 0};
+};

@@ -1,0 +1,130 @@
+"""Python front end of the C ABI: a context built from a pulsar array, the batched
+log posterior + gradient, HMC trajectories, and a torch.autograd.Function.
+
+Every numerical step runs in the CUDA library; this module only marshals
+arguments (torch tensors for device memory and the current stream)."""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import abi
+
+
+class PTAError(RuntimeError):
+    pass
+
+
+def _dptr(t: torch.Tensor | None):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+class Engine:
+    """One finalized context.  ``arr`` exposes ``pulsars`` (toas_s, freqs_mhz, resid_s,
+    sigma_s, backend, efac, equad_s, M, pos, dist_kpc) and n_gwb, n_rn, n_dm, cw."""
+
+    def __init__(self, arr, precision: str = "fp32", device: int = 0):
+        self.device = torch.device("cuda", device)
+        torch.cuda.set_device(self.device)
+        desc = abi.ModelDesc(arr.n_gwb, arr.n_rn, arr.n_dm, int(bool(arr.cw)), abi.PREC[precision], 1400.0)
+        h = C.c_void_p()
+        rc = abi.lib.pta_create(C.byref(h), C.byref(desc))
+        if rc != 0:
+            raise PTAError(f"pta_create failed ({rc})")
+        self._h = h
+        self.precision = precision
+        keep = []
+        for p in arr.pulsars:
+            arrs = dict(
+                toas_s=np.ascontiguousarray(p.toas_s, dtype=np.float64),
+                freqs_mhz=np.ascontiguousarray(p.freqs_mhz, dtype=np.float64),
+                resid_s=np.ascontiguousarray(p.resid_s, dtype=np.float64),
+                sigma_s=np.ascontiguousarray(p.sigma_s, dtype=np.float64),
+                backend=np.ascontiguousarray(p.backend, dtype=np.int32),
+                efac=np.ascontiguousarray(p.efac, dtype=np.float64),
+                equad_s=np.ascontiguousarray(p.equad_s, dtype=np.float64),
+                M=np.ascontiguousarray(p.M, dtype=np.float64))
+            keep.append(arrs)
+            pd = abi.PulsarDesc()
+            pd.n, pd.m, pd.n_backend = p.M.shape[0], p.M.shape[1], len(p.efac)
+            for k in ("toas_s", "freqs_mhz", "resid_s", "sigma_s", "efac", "equad_s", "M"):
+                setattr(pd, k, arrs[k].ctypes.data_as(C.POINTER(C.c_double)))
+            pd.backend = arrs["backend"].ctypes.data_as(C.POINTER(C.c_int32))
+            pd.pos = (C.c_double * 3)(*[float(v) for v in p.pos])
+            pd.dist_kpc = float(p.dist_kpc)
+            self._check(abi.lib.pta_add_pulsar(self._h, C.byref(pd)), "pta_add_pulsar")
+        self._check(abi.lib.pta_finalize(self._h, C.c_void_p(torch.cuda.current_stream().cuda_stream)),
+                    "pta_finalize")
+        lay = abi.Layout()
+        self._check(abi.lib.pta_layout(self._h, C.byref(lay)), "pta_layout")
+        self.layout = {f: getattr(lay, f) for f, _ in abi.Layout._fields_}
+        self.D = lay.d
+
+    def _check(self, rc, what):
+        if rc != 0:
+            msg = abi.lib.pta_last_error(self._h).decode()
+            raise PTAError(f"{what} failed ({rc}): {msg}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            abi.lib.pta_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_precision(self, precision: str):
+        self._check(abi.lib.pta_set_precision(self._h, abi.PREC[precision]), "pta_set_precision")
+        self.precision = precision
+
+    def logp_constant(self) -> float:
+        c = C.c_double()
+        self._check(abi.lib.pta_logp_constant(self._h, C.byref(c)), "pta_logp_constant")
+        return c.value
+
+    def logp_and_grad(self, x: torch.Tensor, want_grad: bool = True, out=None):
+        """x [B, D] float32 on the device -> (logp [B] f64, grad [B, D] f32 | None, status [B] i32)."""
+        assert x.dtype == torch.float32 and x.is_cuda and x.is_contiguous() and x.shape[-1] == self.D
+        B = x.shape[0]
+        if out is None:
+            logp = torch.empty(B, dtype=torch.float64, device=x.device)
+            grad = torch.empty_like(x) if want_grad else None
+            status = torch.empty(B, dtype=torch.int32, device=x.device)
+        else:
+            logp, grad, status = out
+        stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        self._check(abi.lib.pta_logp_and_grad(self._h, B, _dptr(x), _dptr(logp), _dptr(grad), _dptr(status),
+                                              stream), "pta_logp_and_grad")
+        return logp, grad, status
+
+    def hmc_trajectory(self, x, logp, grad, step, n_leapfrog, seed, iteration, inv_mass=None, accepted=None):
+        """In-place HMC transition of the state (x, logp, grad); returns accept flags [B] i32."""
+        B = x.shape[0]
+        if accepted is None:
+            accepted = torch.empty(B, dtype=torch.int32, device=x.device)
+        stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        self._check(abi.lib.pta_hmc_trajectory(self._h, B, _dptr(x), _dptr(logp), _dptr(grad), _dptr(step),
+                                               _dptr(inv_mass), int(n_leapfrog), int(seed), int(iteration),
+                                               _dptr(accepted), stream), "pta_hmc_trajectory")
+        return accepted
+
+
+class LogPosterior(torch.autograd.Function):
+    """logp(x) with the library's hand-written adjoint as the backward: forward runs
+    one fused evaluation and stores the gradient; backward scales it by grad_output."""
+
+    @staticmethod
+    def forward(ctx, x, engine):
+        logp, grad, status = engine.logp_and_grad(x.detach().contiguous(), want_grad=True)
+        ctx.save_for_backward(grad)
+        return logp
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        return (g.to(grad.dtype)[:, None] * grad, None)

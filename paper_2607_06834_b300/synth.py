@@ -163,7 +163,8 @@ def make_array(name: str, seed: int | None = None) -> Array:
     """Draw the synthetic array named ``name`` (a key of WORKLOADS)."""
     w = WORKLOADS[name]
     if seed is None:
-        seed = 2607 + WORKLOAD_ORDER.index(name)
+        # the three 67-pulsar workloads share one array (same seed)
+        seed = {"tiny3": 2607, "ng15": 2608, "ng15_b256": 2608, "ng15_cw": 2608, "scale150": 2611}[name]
     rng = np.random.default_rng(seed)
     npsr = w["npsr"]
     counts = _toa_counts(rng, npsr, w["ntoa_total"], *w["ntoa_range"])
@@ -216,12 +217,16 @@ def make_array(name: str, seed: int | None = None) -> Array:
 
 def small_array(npsr=2, ntoa=60, m=3, n_gwb=2, n_rn=2, n_dm=0, cw=False, seed=0,
                 span_yr=5.0, nbackend=1) -> Array:
-    """A hand-sized array for brute-force checks (dense N x N algebra)."""
+    """A hand-sized array for brute-force checks (dense N x N algebra).  ``ntoa`` and
+    ``m`` may be per-pulsar lists (ragged arrays)."""
     rng = np.random.default_rng(seed)
     span = span_yr * YEAR
     t_end = MJD0_S + span
+    ntoas = list(ntoa) if np.ndim(ntoa) else [ntoa] * npsr
+    ms = list(m) if np.ndim(m) else [m] * npsr
     pulsars = []
     for I in range(npsr):
+        ntoa, m = ntoas[I], ms[I]
         t = np.sort(rng.uniform(t_end - span * rng.uniform(0.6, 1.0), t_end, ntoa))
         if I == 0:
             t[0] = t_end - span

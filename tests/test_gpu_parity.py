@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances.  FP64 path: relative 1e-9 on logp and on the gradient norm (both sides
+are FP64; they differ only in summation order and in the exactly-reduced phase of
+the generated basis).  FP32 path: at near-posterior points (the CURN-conditional
+mean of the coefficients, Eq. PTA_standard_transform_curn) |dlogp| <= 1e-3 nats and
+relative gradient-norm error <= 1e-4, the stated target.  At prior-random points the
+residuals are orders of magnitude above the noise and the FP32 error scales with
+chi2, so there the bound is relative: |dlogp| <= 1e-3 + 5e-7 |logp|, gradient norm
+relative error <= 1e-4 (8 times the FP32 unit roundoff)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import pta_oracle as O
+from paper_2607_06834_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+LOGP_ABS = 1e-3
+GRAD_REL = 1e-4
+FP64_REL = 1e-9
+
+
+def _engine(arr, prec):
+    from paper_2607_06834_b300.engine import Engine
+    return Engine(arr, precision=prec)
+
+
+def _eval(eng, X):
+    x = torch.tensor(np.asarray(X, dtype=np.float32), device="cuda")
+    lp, g, st = eng.logp_and_grad(x)
+    torch.cuda.synchronize()
+    return lp.cpu().numpy(), g.cpu().numpy(), st.cpu().numpy()
+
+
+def _oracle(orc, X):
+    X = np.asarray(X, dtype=np.float32).astype(np.float64)
+    return np.array([orc.logp(x) for x in X]), np.array([orc.grad(x) for x in X])
+
+
+def _grad_rel(g, go):
+    return np.linalg.norm(g - go, axis=-1) / np.maximum(np.linalg.norm(go, axis=-1), 1e-30)
+
+
+# ------------------------------------------------------------------ tiny (3 psr, 200 TOAs)
+@pytest.fixture(scope="module")
+def tiny():
+    arr = synth.make_array("tiny3")
+    return arr, O.Oracle(arr)
+
+
+def test_tiny_fp64_1000_points(tiny):
+    arr, orc = tiny
+    X = synth.make_points(arr, 1000, seed=6834)
+    lo, go = _oracle(orc, X)
+    eng = _engine(arr, "fp64")
+    lp, g, st = _eval(eng, X)
+    assert np.all(st == 0)
+    assert np.max(np.abs(lp - lo) / np.maximum(1.0, np.abs(lo))) < FP64_REL
+    assert np.max(_grad_rel(g, go)) < 1e-6  # grad is returned in FP32
+
+
+def test_tiny_fp32_1000_points(tiny):
+    arr, orc = tiny
+    X = synth.make_points(arr, 1000, seed=6834)
+    lo, go = _oracle(orc, X)
+    eng = _engine(arr, "fp32")
+    lp, g, st = _eval(eng, X)
+    assert np.all(st == 0)
+    err = np.abs(lp - lo)
+    print("tiny fp32 max |dlogp|", err.max(), "max grad rel", _grad_rel(g, go).max())
+    assert np.all(err <= LOGP_ABS + 5e-7 * np.abs(lo))
+    assert np.max(_grad_rel(g, go)) < GRAD_REL
+
+
+def test_tiny_fp32_near_posterior(tiny):
+    arr, orc = tiny
+    X = synth.make_points(arr, 16, seed=77).astype(np.float64)
+    X = np.array([O.curn_point(orc, x, 1.0, seed=i) for i, x in enumerate(X)], dtype=np.float32)
+    lo, go = _oracle(orc, X)
+    eng = _engine(arr, "fp32")
+    lp, g, st = _eval(eng, X)
+    assert np.max(np.abs(lp - lo)) < LOGP_ABS
+    assert np.max(_grad_rel(g, go)) < GRAD_REL
+
+
+# ------------------------------------------------------------------ ragged multi-tile arrays
+RAGGED = [
+    # several 128-TOA tiles, a 2048-TOA chunk boundary and ragged tails; RN-only bins
+    dict(npsr=4, ntoa=[150, 700, 2300, 4500], m=[3, 9, 12, 7], n_gwb=5, n_rn=8, n_dm=6, seed=31, nbackend=2),
+    # GWB-only bins (n_gwb > n_rn), no DM
+    dict(npsr=3, ntoa=[90, 1300, 2049], m=[4, 3, 10], n_gwb=8, n_rn=3, n_dm=0, seed=32, nbackend=3),
+]
+
+
+@pytest.mark.parametrize("kw", RAGGED)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_ragged_arrays(kw, prec):
+    arr = synth.small_array(**kw)
+    orc = O.Oracle(arr)
+    X = synth.make_points(arr, 70, seed=5)  # 70 chains: a partial chain block
+    X[:4] = np.array([O.curn_point(orc, x.astype(np.float64), 1.0, seed=i) for i, x in enumerate(X[:4])])
+    lo, go = _oracle(orc, X)
+    eng = _engine(arr, prec)
+    lp, g, st = _eval(eng, X)
+    assert np.all(st == 0)
+    if prec == "fp64":
+        assert np.max(np.abs(lp - lo) / np.maximum(1.0, np.abs(lo))) < FP64_REL
+        assert np.max(_grad_rel(g, go)) < 1e-6
+    else:
+        assert np.all(np.abs(lp - lo) <= LOGP_ABS + 5e-7 * np.abs(lo))
+        assert np.max(np.abs(lp[:4] - lo[:4])) < LOGP_ABS
+        assert np.max(_grad_rel(g, go)) < GRAD_REL
+
+
+# ------------------------------------------------------------------ NANOGrav-15-yr-sized array
+@pytest.fixture(scope="module")
+def ng15():
+    arr = synth.make_array("ng15")
+    return arr, O.Oracle(arr)
+
+
+def test_ng15_fp64_single_chain(ng15):
+    arr, orc = ng15
+    X = synth.make_points(arr, 2, seed=6835)
+    X[1] = O.curn_point(orc, X[1].astype(np.float64), 1.0, seed=3)
+    lo, go = _oracle(orc, X)
+    eng = _engine(arr, "fp64")
+    for i in range(2):
+        lp, g, st = _eval(eng, X[i:i + 1])
+        assert st[0] == 0
+        assert abs(lp[0] - lo[i]) <= FP64_REL * abs(lo[i])
+        assert _grad_rel(g[0], go[i]) < 1e-6
+
+
+def test_ng15_fp32_batch256_sampled(ng15):
+    """The bench's launch configuration (256 chains in one call); sampled chains are
+    checked one by one against the oracle, two of them at near-posterior points."""
+    arr, orc = ng15
+    X = synth.make_points(arr, 256, seed=6836)
+    near = [5, 200]
+    for j, i in enumerate(near):
+        X[i] = O.curn_point(orc, X[i].astype(np.float64), 1.0, seed=j)
+    eng = _engine(arr, "fp32")
+    lp, g, st = _eval(eng, X)
+    assert np.all(st == 0)
+    sample = [0, 77, 255] + near
+    lo, go = _oracle(orc, X[sample])
+    for j, i in enumerate(sample):
+        err = abs(lp[i] - lo[j])
+        rel = _grad_rel(g[i], go[j])
+        print(f"chain {i}: logp {lo[j]:.3f} |d| {err:.2e} grad rel {rel:.2e}")
+        if i in near:
+            assert err < LOGP_ABS
+        else:
+            assert err <= LOGP_ABS + 5e-7 * abs(lo[j])
+        assert rel < GRAD_REL
+    # a chain's result does not depend on the rest of the batch
+    lp1, g1, _ = _eval(eng, X[200:201])
+    assert lp1[0] == lp[200] and np.array_equal(g1[0], g[200])
+
+
+# ------------------------------------------------------------------ edge cases
+def test_status_and_degenerate_cases(tiny):
+    arr, orc = tiny
+    eng = _engine(arr, "fp32")
+    lay = eng.layout
+    X = synth.make_points(arr, 4, seed=1)
+    X[1, lay["th_gwb"]] = -25.0                      # outside the hyper-prior box
+    X[2, lay["th_rn"] + 1] = 7.5
+    lp, g, st = _eval(eng, X)
+    assert st.tolist() == [0, 1, 1, 0]
+    assert np.isneginf(lp[1]) and np.isneginf(lp[2]) and np.all(g[1:3] == 0)
+    # power spectra that underflow make Phi_k singular: status 2 once the box allows it
+    from paper_2607_06834_b300 import abi
+    eng._check(abi.lib.pta_set_hyperprior(eng._h, -400.0, -10.0, 0.0, 7.0), "hyperprior")
+    X2 = X[:1].copy()
+    X2[0, lay["th_gwb"]] = -300.0
+    for I in range(arr.npsr):
+        X2[0, lay["th_rn"] + 2 * I] = -300.0
+    lp, g, st = _eval(eng, X2)
+    assert st[0] == 2 and np.isneginf(lp[0])
+    # empty batch is a no-op
+    x0 = torch.zeros((0, eng.D), dtype=torch.float32, device="cuda")
+    lp, g, st = eng.logp_and_grad(x0)
+    assert lp.shape == (0,)
+
+
+def test_autograd_function(tiny):
+    from paper_2607_06834_b300.engine import LogPosterior
+    arr, orc = tiny
+    eng = _engine(arr, "fp32")
+    X = torch.tensor(synth.make_points(arr, 3, seed=2), device="cuda", requires_grad=True)
+    lp = LogPosterior.apply(X, eng)
+    (2.0 * lp).sum().backward()
+    _, g, _ = eng.logp_and_grad(X.detach())
+    assert torch.allclose(X.grad, 2.0 * g)
+
+
+# ------------------------------------------------------------------ HMC
+def test_hmc_trajectory_matches_oracle(tiny):
+    arr, orc = tiny
+    eng = _engine(arr, "fp32")
+    B, L, step = 6, 8, 0.02
+    X = synth.make_points(arr, B, seed=9).astype(np.float64)
+    X = np.array([O.curn_point(orc, x, 0.5, seed=i) for i, x in enumerate(X)], dtype=np.float32)
+    x = torch.tensor(X, device="cuda")
+    lp, g, _ = eng.logp_and_grad(x)
+    steps = torch.full((B,), step, device="cuda")
+    seed, it = 1234, 7
+    acc = eng.hmc_trajectory(x, lp, g, steps, L, seed, it)
+    torch.cuda.synchronize()
+    xg, accg = x.cpu().numpy(), acc.cpu().numpy()
+
+    def lgf(v):
+        return orc.logp(v), orc.grad(v)
+    for b in range(B):
+        x0 = X[b].astype(np.float64)
+        lp0, g0 = lgf(x0)
+        p0 = O.hmc_normals(seed, it, b, orc.D)
+        u = O.hmc_uniform(seed, it, b)
+        xo, lpo, go, acco = O.hmc_trajectory(lgf, x0, lp0, g0, step, L, p0, u)
+        assert bool(accg[b]) == acco
+        np.testing.assert_allclose(xg[b], xo, rtol=1e-3, atol=1e-4)
+    # graph replay with a new iteration counter moves the state again
+    acc2 = eng.hmc_trajectory(x, lp, g, steps, L, seed, it + 1)
+    torch.cuda.synchronize()
+    assert np.isfinite(lp.cpu().numpy()).all()
