@@ -134,6 +134,24 @@ int pta_hmc_trajectory(pta_ctx* ctx, int B, float* x_dev, double* logp_dev, floa
                        const float* step_dev, const float* inv_mass_dev, int n_leapfrog,
                        uint64_t seed, uint64_t iteration, int32_t* accepted_dev, void* stream);
 
+/* Same result as pta_logp_and_grad, but the call allocates nothing: its per-call
+ * workspace is a fixed 32 MiB array compiled into the library (held on every GPU
+ * that loads the library until exit) instead of context-owned device memory.  The
+ * paper has no counterpart; it exists for callers that cannot call cudaMalloc when
+ * they evaluate (work recorded into a stream capture, or a host framework that
+ * owns every device allocation).  The context still holds the data uploaded by
+ * pta_finalize.
+ *   - B chains must fit in the array: otherwise PTA_EINVAL with the needed size in
+ *     pta_last_error (about 1.2 MB per chain for 67 pulsars, 3e5 TOAs).
+ *   - The first call on a device looks up the array's device address (with that
+ *     device current) and caches it; make that first call before any capture.
+ *   - All calls share the array and it keeps the last call's contents: calls that
+ *     overlap on the GPU race.  The status flags are cleared on `stream` per call.
+ *   - PTA_PREC_FP64 needs the stored FP64 basis, which pta_logp_and_grad builds on
+ *     its first FP64 call; without it the call returns PTA_ESTATE. */
+int pta_logp_and_grad_noalloc(pta_ctx* ctx, int B, const float* x_dev, double* logp_dev,
+                              float* grad_dev, int32_t* status_dev, void* stream);
+
 /* The data-only constant dropped from logp:
  * -1/2 sum_I [log det(2 pi N_I) + log det(M_I^T N_I^-1 M_I) - m_I log 2 pi]
  * in ns units, minus (D_z/2) log 2 pi (host value, available after finalize). */

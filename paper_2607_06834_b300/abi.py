@@ -15,7 +15,8 @@ PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2, "tf32": 3, "bf16x3": 4}
 
 EXPORTED = ["pta_create", "pta_add_pulsar", "pta_finalize", "pta_layout", "pta_set_precision",
             "pta_set_hyperprior", "pta_logp_and_grad", "pta_hmc_trajectory", "pta_logp_constant",
-            "pta_profile_enable", "pta_profile_read", "pta_last_error", "pta_destroy"]
+            "pta_profile_enable", "pta_profile_read", "pta_logp_and_grad_noalloc", "pta_last_error",
+            "pta_destroy"]
 NSTAGES = 5
 STAGES = ["prior_forward", "toa", "epilogue", "adjoint", "final"]
 
@@ -54,6 +55,7 @@ def _load():
     lib.pta_set_precision.argtypes = [vp, C.c_int]
     lib.pta_set_hyperprior.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_double]
     lib.pta_logp_and_grad.argtypes = [vp, C.c_int, f32p, f64p, f32p, i32p, vp]
+    lib.pta_logp_and_grad_noalloc.argtypes = [vp, C.c_int, f32p, f64p, f32p, i32p, vp]
     lib.pta_hmc_trajectory.argtypes = [vp, C.c_int, f32p, f64p, f32p, f32p, f32p, C.c_int,
                                        C.c_uint64, C.c_uint64, i32p, vp]
     lib.pta_logp_constant.argtypes = [vp, C.POINTER(C.c_double)]
