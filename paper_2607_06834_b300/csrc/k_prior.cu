@@ -1,13 +1,15 @@
 // Prior side of the evaluation, FP64: spectra (Eq. power_law), the per-frequency
-// prior covariance Phi_k = rho_k Gamma + diag(kappa_.k) (Eq. prior_cov), its
-// Cholesky factor and inverse, the standardizing transform a = L z
-// (Eq. standardizing_transform with mu = 0), the adjoint of that transform and
-// the final per-chain sum.
+// prior covariance Phi_k = rho_k Gamma + diag(kappa_.k) (Eq. prior_cov, Gamma of
+// Eq. HD), its Cholesky factor, inverse and log-det, the standardizing transform
+// a = L z (Eq. standardizing_transform with mu = 0), the adjoint of that transform
+// and the final per-chain sum.
 //
-// Work decomposition: one CTA per (frequency bin, chain) for bins whose Phi_k is
-// dense; the triangular updates walk a flat index over the active triangle or
-// rectangle so that every FP64 warp instruction runs with full lanes (FP64
-// issue is the scarce resource on this part).
+// FP64 issue is the scarce resource on this part (about 1/58 of the FP32 rate), so
+// the dense-bin kernel keeps every FP64 warp instruction full: the triangular
+// updates walk a flat index over the active triangle / rectangle (decoded from a
+// table, no per-element square roots), the factorisation and the inverse advance in
+// one sweep with two barriers per column, and the thread that finishes the next
+// pivot takes its square root.
 #include <cmath>
 
 #include "pta_internal.cuh"
@@ -17,79 +19,114 @@ namespace {
 
 __device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 
-// Row index of packed-lower element idx (idx = i(i+1)/2 + j, 0 <= j <= i).
-__device__ __forceinline__ int tri_row(int idx) {
-  int i = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
-  while (tri(i + 1, 0) <= idx) ++i;
-  while (tri(i, 0) > idx) --i;
-  return i;
-}
-
-__device__ __forceinline__ double pl_rho(const DevModel& m, const float* xb, int off, int k) {
-  return exp(ln_pl(m.ln_rho0, m.ln_Tfyr, (double)xb[off], (double)xb[off + 1], k));
+// ---------------------------------------------------------------------------
+// Spectra: sqrt(kappa_Ik) (red noise, k < n_rn), sqrt(kappa^DM_Ik), sqrt(rho_k)
+// (k < n_gwb), FP64, one thread per value.
+// ---------------------------------------------------------------------------
+__global__ void k_spectra(DevModel m, const float* __restrict__ x, double* sk, double* skd, double* srho) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+  const int np = m.npsr, nach = np * m.na, ndm = np * m.nd;
+  if (r >= nach + ndm + m.na) return;
+  const float* xb = x + (size_t)b * m.d;
+  double v = 0.0;
+  if (r < nach) {
+    const int I = r / m.na, k = r % m.na;
+    if (k < m.n_rn)
+      v = exp(0.5 * ln_pl(m.ln_rho0, m.ln_Tfyr, xb[m.th_rn + 2 * I], xb[m.th_rn + 2 * I + 1], m.lnk[k + 1]));
+    sk[(size_t)b * nach + r] = v;
+  } else if (r < nach + ndm) {
+    const int q = r - nach, I = q / m.nd, k = q % m.nd;
+    v = exp(0.5 * ln_pl(m.ln_rho0, m.ln_Tfyr, xb[m.th_dm + 2 * I], xb[m.th_dm + 2 * I + 1], m.lnk[k + 1]));
+    skd[(size_t)b * ndm + q] = v;
+  } else {
+    const int k = r - nach - ndm;
+    if (k < m.n_gwb) v = exp(0.5 * ln_pl(m.ln_rho0, m.ln_Tfyr, xb[m.th_gwb], xb[m.th_gwb + 1], m.lnk[k + 1]));
+    srho[(size_t)b * m.na + k] = v;
+  }
 }
 
 // ---------------------------------------------------------------------------
-// Dense bins k < n_chol: Phi_k = rho_k Gamma + diag(kappa_.k).
+// Dense bins k < n_chol: Phi_k = rho_k Gamma + diag(kappa_.k).  One CTA per
+// (bin, chain).  Column sweep j: (1) scale column j of L and row j of X = L^-1 by
+// 1/L_jj; (2) rank-1 update of the trailing triangle of A and of rows > j of X;
+// the thread that updates element (j+1, j+1) takes the next pivot's square root.
 // ---------------------------------------------------------------------------
-__global__ void k_chol_forward(DevModel m, const float* __restrict__ x, float* a32, double* a64,
-                               double* Lpk, double* Lipk, int32_t* stat, int fp64) {
+__global__ void __launch_bounds__(128)
+    k_chol_forward(DevModel m, const float* __restrict__ x, const double* __restrict__ sk,
+                   const double* __restrict__ srho, double* a64, double* Lpk, double* Lipk, int32_t* stat) {
   extern __shared__ double sm[];
   const int np = m.npsr, ntri = np * (np + 1) / 2;
   double* A = sm;              // packed lower, becomes L
   double* X = sm + ntri;       // packed lower, becomes L^-1
   double* zs = X + ntri;       // [2][np]
-  __shared__ double s_rho, s_piv;
+  double* pinv = zs + 2 * np;  // [np] 1 / L_jj
   __shared__ int s_bad;
   const int k = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, nt = blockDim.x;
   const float* xb = x + (size_t)b * m.d;
-  if (tid == 0) {
-    s_rho = pl_rho(m, xb, m.th_gwb, k + 1);
-    s_bad = 0;
-  }
-  __syncthreads();
-  const double rho = s_rho;
+  const double sr = srho[(size_t)b * m.na + k];
+  const double rho = sr * sr;
+  const double* skb = sk + (size_t)b * np * m.na + k;
+  if (tid == 0) s_bad = 0;
   for (int idx = tid; idx < ntri; idx += nt) {
-    const int i = tri_row(idx), j = idx - tri(i, 0);
+    const unsigned t = m.trimap[idx];
+    const int i = t >> 8, j = t & 255;
     double v = rho * m.Gamma[i * np + j];
-    if (i == j) v += exp(ln_pl(m.ln_rho0, m.ln_Tfyr, (double)xb[m.th_rn + 2 * i], (double)xb[m.th_rn + 2 * i + 1], k + 1));
+    if (i == j) {
+      const double s = skb[(size_t)i * m.na];
+      v = fma(s, s, v);
+    }
     A[idx] = v;
     X[idx] = (i == j) ? 1.0 : 0.0;
   }
   for (int i = tid; i < 2 * np; i += nt) zs[i] = (double)xb[m.z_ach + (2 * k) * np + i];
   __syncthreads();
-  // right-looking Cholesky
-  for (int j = 0; j < np; ++j) {
-    if (tid == 0) {
-      double d = A[tri(j, j)];
-      if (!(d > 0.0)) {
-        s_bad = 1;
-        d = 1.0;
-      }
-      s_piv = sqrt(d);
-      A[tri(j, j)] = s_piv;
+  if (tid == 0) {
+    double d = A[0];
+    if (!(d > 0.0)) {
+      s_bad = 1;
+      d = 1.0;
     }
-    __syncthreads();
-    const double inv = 1.0 / s_piv;
-    for (int i = j + 1 + tid; i < np; i += nt) A[tri(i, j)] *= inv;
-    __syncthreads();
-    const int s = np - j - 1, cnt = s * (s + 1) / 2;
-    for (int idx = tid; idx < cnt; idx += nt) {
-      const int ip = tri_row(idx), lp = idx - tri(ip, 0);
-      const int i = ip + j + 1, l = lp + j + 1;
-      A[tri(i, l)] = fma(-A[tri(i, j)], A[tri(l, j)], A[tri(i, l)]);
-    }
-    __syncthreads();
+    A[0] = sqrt(d);
+    pinv[0] = 1.0 / A[0];
   }
-  // L^-1 by right-looking forward substitution on all right-hand sides at once
+  __syncthreads();
   for (int j = 0; j < np; ++j) {
-    const double inv = 1.0 / A[tri(j, j)];
-    for (int c = tid; c <= j; c += nt) X[tri(j, c)] *= inv;
+    const double inv = pinv[j];
+    const int s = np - j - 1;
+    for (int e = tid; e < np; e += nt) {
+      if (e < s)
+        A[tri(j + 1 + e, j)] *= inv;
+      else
+        X[tri(j, e - s)] *= inv;
+    }
     __syncthreads();
-    const int w = j + 1, cnt = (np - j - 1) * w;
+    const int cntA = s * (s + 1) / 2, w = j + 1, cnt = cntA + s * w;
+    const float rw = 1.0f / (float)w;
     for (int idx = tid; idx < cnt; idx += nt) {
-      const int i = j + 1 + idx / w, c = idx % w;
-      X[tri(i, c)] = fma(-A[tri(i, j)], X[tri(j, c)], X[tri(i, c)]);
+      if (idx < cntA) {
+        const unsigned t = m.trimap[idx];
+        const int i = (t >> 8) + j + 1, l = (t & 255) + j + 1;
+        const double v = fma(-A[tri(i, j)], A[tri(l, j)], A[tri(i, l)]);
+        if (idx == 0) {  // element (j+1, j+1) receives its last update: the next pivot
+          double d = v;
+          if (!(d > 0.0)) {
+            s_bad = 1;
+            d = 1.0;
+          }
+          const double piv = sqrt(d);
+          A[tri(i, l)] = piv;
+          pinv[j + 1] = 1.0 / piv;
+        } else {
+          A[tri(i, l)] = v;
+        }
+      } else {
+        const int e = idx - cntA;
+        int q = (int)(((float)e + 0.5f) * rw);
+        q -= (q * w > e);
+        q += ((q + 1) * w <= e);
+        const int i = j + 1 + q, c = e - q * w;
+        X[tri(i, c)] = fma(-A[tri(i, j)], X[tri(j, c)], X[tri(i, c)]);
+      }
     }
     __syncthreads();
   }
@@ -120,9 +157,10 @@ __global__ void k_chol_forward(DevModel m, const float* __restrict__ x, float* a
 // with u = column I of L^-1 (from dL = L tril_half(L^-1 dPhi L^-T), dPhi = e_I e_I^T); and
 // rho d logp / d rho = 1/2 sum_c gt.z - sum_I kappa_I d logp/d kappa_I (scaling identity:
 // Phi -> s Phi gives a -> sqrt(s) a).
-__global__ void k_chol_adjoint(DevModel m, const float* __restrict__ x, const double* __restrict__ ghat,
-                               const double* __restrict__ Lpk, const double* __restrict__ Lipk, float* grad,
-                               double* dlnk, double* dlnr, int B) {
+__global__ void __launch_bounds__(128)
+    k_chol_adjoint(DevModel m, const float* __restrict__ x, const double* __restrict__ ghat,
+                   const double* __restrict__ Lpk, const double* __restrict__ Lipk, const double* __restrict__ sk,
+                   float* grad, double* dlnk, double* dlnr, int B) {
   extern __shared__ double sm[];
   const int np = m.npsr, ntri = np * (np + 1) / 2;
   double* Ls = sm;
@@ -163,8 +201,8 @@ __global__ void k_chol_adjoint(DevModel m, const float* __restrict__ x, const do
       p0 = fma(u, zs[a], p0);
       p1 = fma(u, zs[np + a], p1);
     }
-    const double kap = exp(ln_pl(m.ln_rho0, m.ln_Tfyr, (double)xb[m.th_rn + 2 * I], (double)xb[m.th_rn + 2 * I + 1], k + 1));
-    const double v = kap * acc;
+    const double s = sk[((size_t)b * np + I) * m.na + k];
+    const double v = s * s * acc;
     red[I] = v;
     dlnk[((size_t)b * np + I) * m.na + k] = v;
   }
@@ -180,10 +218,11 @@ __global__ void k_chol_adjoint(DevModel m, const float* __restrict__ x, const do
 // ---------------------------------------------------------------------------
 // GWB-only bins (no intrinsic red noise): Phi_k = rho_k Gamma, L_k = sqrt(rho_k) chol(Gamma).
 // ---------------------------------------------------------------------------
-__global__ void k_gwbonly_forward(DevModel m, const float* __restrict__ x, float* a32, double* a64, int fp64) {
+__global__ void k_gwbonly_forward(DevModel m, const float* __restrict__ x, const double* __restrict__ srho,
+                                  double* a64) {
   const int k = m.n_chol + blockIdx.x, b = blockIdx.y, np = m.npsr;
   const float* xb = x + (size_t)b * m.d;
-  const double sr = sqrt(pl_rho(m, xb, m.th_gwb, k + 1));
+  const double sr = srho[(size_t)b * m.na + k];
   for (int I = threadIdx.x; I < np; I += blockDim.x) {
     double s0 = 0.0, s1 = 0.0;
     for (int J = 0; J <= I; ++J) {
@@ -198,10 +237,10 @@ __global__ void k_gwbonly_forward(DevModel m, const float* __restrict__ x, float
 }
 
 __global__ void k_gwbonly_adjoint(DevModel m, const float* __restrict__ x, const double* __restrict__ ghat,
-                                  float* grad, double* dlnr, int B) {
+                                  const double* __restrict__ srho, float* grad, double* dlnr, int B) {
   const int k = m.n_chol + blockIdx.x, b = blockIdx.y, np = m.npsr;
   const float* xb = x + (size_t)b * m.d;
-  const double sr = sqrt(pl_rho(m, xb, m.th_gwb, k + 1));
+  const double sr = srho[(size_t)b * m.na + k];
   double part = 0.0;
   for (int i = threadIdx.x; i < 2 * np; i += blockDim.x) {
     const int c = i / np, J = i % np;
@@ -238,42 +277,41 @@ __device__ __forceinline__ void diag_index(const DevModel& m, int r, int& I, int
   k = dm ? q - nrn_only : m.n_chol + m.n_gwbonly + q;
 }
 
-__global__ void k_diag_forward(DevModel m, const float* __restrict__ x, float* a32, double* a64, int fp64,
-                               int B, int per_chain) {
+__global__ void k_diag_forward(DevModel m, const float* __restrict__ x, const double* __restrict__ sk,
+                               const double* __restrict__ skd, double* a64, int B, int per_chain) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
   if (r >= per_chain) return;
   int I, k;
   bool dm;
   diag_index(m, r, I, k, dm);
   const float* xb = x + (size_t)b * m.d;
-  const int th = dm ? m.th_dm : m.th_rn;
-  const double sk = exp(0.5 * ln_pl(m.ln_rho0, m.ln_Tfyr, (double)xb[th + 2 * I], (double)xb[th + 2 * I + 1], k + 1));
+  const double s = dm ? skd[((size_t)b * m.npsr + I) * m.nd + k] : sk[((size_t)b * m.npsr + I) * m.na + k];
   const int zo = dm ? m.z_dm + (I * m.nd + k) * 2 : 0;
   const double z0 = dm ? xb[zo] : xb[m.z_ach + (2 * k) * m.npsr + I];
   const double z1 = dm ? xb[zo + 1] : xb[m.z_ach + (2 * k + 1) * m.npsr + I];
   const size_t o = ((size_t)I * B + b) * m.PM + (dm ? 2 * m.na : 0) + 2 * k;
-  a64[o] = sk * z0;
-  a64[o + 1] = sk * z1;
+  a64[o] = s * z0;
+  a64[o + 1] = s * z1;
 }
 
 __global__ void k_diag_adjoint(DevModel m, const float* __restrict__ x, const double* __restrict__ ghat,
-                               float* grad, double* dlnk, double* dlnkd, int B, int per_chain) {
+                               const double* __restrict__ sk, const double* __restrict__ skd, float* grad,
+                               double* dlnk, double* dlnkd, int B, int per_chain) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
   if (r >= per_chain) return;
   int I, k;
   bool dm;
   diag_index(m, r, I, k, dm);
   const float* xb = x + (size_t)b * m.d;
-  const int th = dm ? m.th_dm : m.th_rn;
-  const double sk = exp(0.5 * ln_pl(m.ln_rho0, m.ln_Tfyr, (double)xb[th + 2 * I], (double)xb[th + 2 * I + 1], k + 1));
+  const double s = dm ? skd[((size_t)b * m.npsr + I) * m.nd + k] : sk[((size_t)b * m.npsr + I) * m.na + k];
   const int z0i = dm ? m.z_dm + (I * m.nd + k) * 2 : m.z_ach + (2 * k) * m.npsr + I;
   const int z1i = dm ? z0i + 1 : z0i + m.npsr;
   const size_t o = ((size_t)I * B + b) * m.P + (dm ? 2 * m.na : 0) + 2 * k;
   const double g0 = ghat[o], g1 = ghat[o + 1];
   const double z0 = xb[z0i], z1 = xb[z1i];
-  grad[(size_t)b * m.d + z0i] = (float)(sk * g0 - z0);
-  grad[(size_t)b * m.d + z1i] = (float)(sk * g1 - z1);
-  const double v = 0.5 * sk * (g0 * z0 + g1 * z1);
+  grad[(size_t)b * m.d + z0i] = (float)(s * g0 - z0);
+  grad[(size_t)b * m.d + z1i] = (float)(s * g1 - z1);
+  const double v = 0.5 * s * (g0 * z0 + g1 * z1);
   if (dm)
     dlnkd[((size_t)b * m.npsr + I) * m.nd + k] = v;
   else
@@ -342,7 +380,7 @@ __global__ void k_final(DevModel m, const float* __restrict__ x, const double* _
     for (int k = 0; k < m.n_rn; ++k) {
       const double v = dlnk[((size_t)b * np + I) * m.na + k];
       s1 += v;
-      s2 -= (log((double)(k + 1)) - m.ln_Tfyr) * v;
+      s2 -= (m.lnk[k + 1] - m.ln_Tfyr) * v;
     }
     gb[m.th_rn + 2 * I] = (float)(2.0 * kLn10 * s1);
     gb[m.th_rn + 2 * I + 1] = (float)s2;
@@ -351,7 +389,7 @@ __global__ void k_final(DevModel m, const float* __restrict__ x, const double* _
       for (int k = 0; k < m.nd; ++k) {
         const double v = dlnkd[((size_t)b * np + I) * m.nd + k];
         d1 += v;
-        d2 -= (log((double)(k + 1)) - m.ln_Tfyr) * v;
+        d2 -= (m.lnk[k + 1] - m.ln_Tfyr) * v;
       }
       gb[m.th_dm + 2 * I] = (float)(2.0 * kLn10 * d1);
       gb[m.th_dm + 2 * I + 1] = (float)d2;
@@ -362,7 +400,7 @@ __global__ void k_final(DevModel m, const float* __restrict__ x, const double* _
     for (int k = 0; k < m.n_gwb; ++k) {
       const double v = dlnr[(size_t)b * m.na + k];
       s1 += v;
-      s2 -= (log((double)(k + 1)) - m.ln_Tfyr) * v;
+      s2 -= (m.lnk[k + 1] - m.ln_Tfyr) * v;
     }
     gb[m.th_gwb] = (float)(2.0 * kLn10 * s1);
     gb[m.th_gwb + 1] = (float)s2;
@@ -373,24 +411,32 @@ __global__ void k_final(DevModel m, const float* __restrict__ x, const double* _
 
 static size_t chol_smem(const DevModel& m) {
   const size_t np = m.npsr, ntri = np * (np + 1) / 2;
-  return (2 * ntri + 2 * np) * sizeof(double);
+  return (2 * ntri + 3 * np) * sizeof(double);
 }
 static size_t adj_smem(const DevModel& m) {
   const size_t np = m.npsr, ntri = np * (np + 1) / 2;
   return (2 * ntri + 7 * np) * sizeof(double);
 }
 
+int count_prior_forward(const DevModel& m) {
+  return 1 + (m.n_chol > 0) + (m.n_gwbonly > 0) + (m.npsr * ((m.na - m.n_chol - m.n_gwbonly) + m.nd) > 0);
+}
+int count_prior_adjoint(const DevModel& m) { return count_prior_forward(m) - 1; }
+
 cudaError_t launch_prior_forward(const DevModel& m, const Scratch& s, int B, const float* x, int fp64,
                                  cudaStream_t st) {
+  (void)fp64;
+  const int nspec = m.npsr * (m.na + m.nd) + m.na;
+  k_spectra<<<dim3((nspec + 127) / 128, B), 128, 0, st>>>(m, x, s.sk, s.skd, s.srho);
   if (m.n_chol > 0) {
     const size_t sm = chol_smem(m);
     cudaError_t e = cudaFuncSetAttribute(k_chol_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_chol_forward<<<dim3(m.n_chol, B), 128, sm, st>>>(m, x, s.a32, s.a64, s.Lpk, s.Lipk, s.stat, fp64);
+    k_chol_forward<<<dim3(m.n_chol, B), 128, sm, st>>>(m, x, s.sk, s.srho, s.a64, s.Lpk, s.Lipk, s.stat);
   }
-  if (m.n_gwbonly > 0) k_gwbonly_forward<<<dim3(m.n_gwbonly, B), 128, 0, st>>>(m, x, s.a32, s.a64, fp64);
+  if (m.n_gwbonly > 0) k_gwbonly_forward<<<dim3(m.n_gwbonly, B), 128, 0, st>>>(m, x, s.srho, s.a64);
   const int per = m.npsr * ((m.na - m.n_chol - m.n_gwbonly) + m.nd);
-  if (per > 0) k_diag_forward<<<dim3((per + 127) / 128, B), 128, 0, st>>>(m, x, s.a32, s.a64, fp64, B, per);
+  if (per > 0) k_diag_forward<<<dim3((per + 127) / 128, B), 128, 0, st>>>(m, x, s.sk, s.skd, s.a64, B, per);
   return cudaGetLastError();
 }
 
@@ -400,19 +446,17 @@ cudaError_t launch_prior_adjoint(const DevModel& m, const Scratch& s, int B, con
     const size_t sm = adj_smem(m);
     cudaError_t e = cudaFuncSetAttribute(k_chol_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_chol_adjoint<<<dim3(m.n_chol, B), 128, sm, st>>>(m, x, s.ghat, s.Lpk, s.Lipk, grad, s.dlnk, s.dlnr, B);
+    k_chol_adjoint<<<dim3(m.n_chol, B), 128, sm, st>>>(m, x, s.ghat, s.Lpk, s.Lipk, s.sk, grad, s.dlnk, s.dlnr,
+                                                       B);
   }
-  if (m.n_gwbonly > 0) k_gwbonly_adjoint<<<dim3(m.n_gwbonly, B), 128, 0, st>>>(m, x, s.ghat, grad, s.dlnr, B);
+  if (m.n_gwbonly > 0)
+    k_gwbonly_adjoint<<<dim3(m.n_gwbonly, B), 128, 0, st>>>(m, x, s.ghat, s.srho, grad, s.dlnr, B);
   const int per = m.npsr * ((m.na - m.n_chol - m.n_gwbonly) + m.nd);
   if (per > 0)
-    k_diag_adjoint<<<dim3((per + 127) / 128, B), 128, 0, st>>>(m, x, s.ghat, grad, s.dlnk, s.dlnkd, B, per);
+    k_diag_adjoint<<<dim3((per + 127) / 128, B), 128, 0, st>>>(m, x, s.ghat, s.sk, s.skd, grad, s.dlnk, s.dlnkd,
+                                                               B, per);
   return cudaGetLastError();
 }
-
-int count_prior_forward(const DevModel& m) {
-  return (m.n_chol > 0) + (m.n_gwbonly > 0) + (m.npsr * ((m.na - m.n_chol - m.n_gwbonly) + m.nd) > 0);
-}
-int count_prior_adjoint(const DevModel& m) { return count_prior_forward(m); }
 
 cudaError_t launch_final(const DevModel& m, const Scratch& s, int B, const float* x, double* logp, float* grad,
                          int32_t* status, cudaStream_t st) {

@@ -51,9 +51,18 @@ __global__ void __launch_bounds__(128)
   double* da = smp;             // [P]
   double* part = da + P;        // [4][mI]
   double* cv = part + 4 * mI;   // [mI]
+  float* dah = reinterpret_cast<float*>(cv + mI);  // [P] hi part of da (0 on low columns)
+  float* dal = dah + P;                            // [P] lo part
   double* row = a64 + ((size_t)I * B + b) * m.PM;
   const double* ar = m.aref + (size_t)I * P;
-  for (int p = tid; p < P; p += 128) da[p] = row[p] - ar[p];
+  for (int p = tid; p < P; p += 128) {
+    const double v = row[p] - ar[p];
+    da[p] = v;
+    const bool lo = is_low_col(m, p);
+    const float h = lo ? 0.f : (float)v;
+    dah[p] = h;
+    dal[p] = lo ? 0.f : (float)(v - (double)h);
+  }
   __syncthreads();
   for (int j0 = 0; j0 < mI; j0 += 32) {
     const int j = j0 + lane;
@@ -68,8 +77,7 @@ __global__ void __launch_bounds__(128)
         const float* Hl = m.Hlo + m.h_off[I];
         float s = 0.f, comp = 0.f;
         for (int p = warp; p < P; p += 4) {
-          if (is_low_col(m, p)) continue;
-          const float xh = (float)da[p], xl = (float)(da[p] - (double)xh);
+          const float xh = dah[p], xl = dal[p];
           const float hh = Hh[(size_t)p * mI + j], hl = Hl[(size_t)p * mI + j];
           const float pr = hh * xh;
           const float pe = fmaf(hh, xh, -pr);          // exact product error
@@ -385,7 +393,7 @@ cudaError_t launch_simt(const DevModel& m, const Scratch& s, int B, cudaStream_t
 }  // namespace
 
 cudaError_t launch_tm_prologue(const DevModel& m, const Scratch& s, int B, int fp64, cudaStream_t st) {
-  const size_t sm = sizeof(double) * (m.P + 5 * m.m_max);
+  const size_t sm = sizeof(double) * (m.P + 5 * m.m_max) + sizeof(float) * 2 * m.P;
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_tm_prologue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;

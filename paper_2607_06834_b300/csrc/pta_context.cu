@@ -388,7 +388,7 @@ int pta_finalize(pta_ctx* c, void* stream) {
         A[(size_t)q * P + r] = A[(size_t)r * P + q] = v;
       }
       const int k = q < 2 * m.na ? q / 2 + 1 : (q - 2 * m.na) / 2 + 1;
-      A[(size_t)q * P + q] += std::exp(-ln_pl(m.ln_rho0, m.ln_Tfyr, -13.0, 4.0, k));
+      A[(size_t)q * P + q] += std::exp(-ln_pl(m.ln_rho0, m.ln_Tfyr, -13.0, 4.0, std::log((double)k)));
     }
     std::vector<double> ar(P, 0.0);
     if (host_cholesky(A, P)) {
@@ -477,6 +477,15 @@ int pta_finalize(pta_ctx* c, void* stream) {
   UP(unit_len, unit_len);
   UP(Gam, Gamma);
   UP(LG, LGamma);
+  {
+    std::vector<double> lnk(kmax + 1, 0.0);
+    for (int k = 1; k <= kmax; ++k) lnk[k] = std::log((double)k);
+    std::vector<unsigned short> tm((size_t)npsr * (npsr + 1) / 2);
+    for (int i = 0, q = 0; i < npsr; ++i)
+      for (int j = 0; j <= i; ++j) tm[q++] = (unsigned short)((i << 8) | j);
+    UP(lnk, lnk);
+    UP(tm, trimap);
+  }
   UP(nuw64, chrom64);
 #undef UP
   c->finalized = true;
@@ -491,7 +500,7 @@ namespace {
 
 void free_scratch(pta::Scratch& s) {
   void* ptrs[] = {s.a32, s.a64, s.Lpk, s.Lipk, s.gpart, s.gpart64, s.c2part, s.ghat, s.chi2,
-                  s.dlnk, s.dlnkd, s.dlnr, s.stat, s.x0, s.g0, s.p, s.lp0, s.xs, s.gs, s.lps,
+                  s.dlnk, s.dlnkd, s.dlnr, s.stat, s.sk, s.skd, s.srho, s.x0, s.g0, s.p, s.lp0, s.xs, s.gs, s.lps,
                   s.step, s.imass, s.kin0, s.hmc_ctr, s.acc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -530,6 +539,9 @@ int ensure_scratch(pta_ctx* c, int B, bool fp64) {
   AL(dlnkd, (size_t)cap * np * std::max(1, m.nd));
   AL(dlnr, (size_t)cap * m.na);
   AL(stat, cap);
+  AL(sk, (size_t)cap * np * m.na);
+  AL(skd, (size_t)cap * np * std::max(1, m.nd));
+  AL(srho, (size_t)cap * m.na);
   AL(x0, (size_t)cap * m.d);
   AL(g0, (size_t)cap * m.d);
   AL(p, (size_t)cap * m.d);

@@ -67,6 +67,8 @@ struct DevModel {
   const int* unit_start;        // absolute padded TOA index
   const int* unit_len;          // multiple of 64
   // global
+  const double* lnk;            // ln k, k = 0..max(na, nd) (entry 0 unused)
+  const unsigned short* trimap; // packed-lower index -> (row << 8) | col, for npsr <= 256
   const double* Gamma;          // [npsr x npsr]
   const double* LGamma;         // chol(Gamma), lower, [npsr x npsr]
 };
@@ -87,6 +89,9 @@ struct Scratch {
   double* dlnkd = nullptr;     // [cap][npsr][nd]  same for DM
   double* dlnr = nullptr;      // [cap][na]        rho dlogp/drho
   int32_t* stat = nullptr;     // [cap]
+  double* sk = nullptr;        // [cap][npsr][na]  sqrt(kappa) intrinsic red noise (0 above n_rn)
+  double* skd = nullptr;       // [cap][npsr][nd]  sqrt(kappa) DM
+  double* srho = nullptr;      // [cap][na]        sqrt(rho) GWB (0 above n_gwb)
   // HMC state
   float* x0 = nullptr;         // [cap][d]
   float* g0 = nullptr;
@@ -121,10 +126,10 @@ cudaError_t launch_final(const DevModel& m, const Scratch& s, int B, const float
 // ---------------------------------------------------------------------------
 // log of the power-law spectrum (Eq. power_law) in ns^2 at bin k (f_k = k/T):
 // rho_k = A^2 / (12 pi^2 f_yr^3 T) (f_k / f_yr)^(-gamma), so
-// ln rho_k = 2 ln10 log10A + ln_rho0 - gamma (ln k - ln(T f_yr)),
+// ln rho_k = 2 ln10 log10A + ln_rho0 - gamma (ln k - ln(T f_yr))  (argument lnk = ln k),
 // ln_rho0 = ln(1e18 / (12 pi^2 f_yr^3 T)) computed on the host in FP64.
-__host__ __device__ inline double ln_pl(double ln_rho0, double ln_Tfyr, double log10A, double gamma, int k) {
-  return 2.0 * kLn10 * log10A + ln_rho0 - gamma * (log((double)k) - ln_Tfyr);
+__host__ __device__ inline double ln_pl(double ln_rho0, double ln_Tfyr, double log10A, double gamma, double lnk) {
+  return 2.0 * kLn10 * log10A + ln_rho0 - gamma * (lnk - ln_Tfyr);
 }
 
 // sin and cos of 2 pi * phi / 2^64 for a 64-bit fixed-point phase phi.  The top

@@ -53,6 +53,9 @@ size_t noalloc_bytes(const pta::DevModel& m, int B) {
   s += align256((size_t)B * np * std::max(1, m.nd) * sizeof(double));
   s += align256((size_t)B * m.na * sizeof(double));
   s += align256((size_t)B * sizeof(int32_t));
+  s += align256((size_t)B * np * m.na * sizeof(double));
+  s += align256((size_t)B * np * std::max(1, m.nd) * sizeof(double));
+  s += align256((size_t)B * m.na * sizeof(double));
   return s;
 }
 
@@ -127,6 +130,9 @@ extern "C" int pta_logp_and_grad_noalloc(pta_ctx* c, int B, const float* x, doub
   s.dlnkd = (double*)take((size_t)B * np * std::max(1, m.nd) * sizeof(double));
   s.dlnr = (double*)take((size_t)B * m.na * sizeof(double));
   s.stat = (int32_t*)take((size_t)B * sizeof(int32_t));
+  s.sk = (double*)take((size_t)B * np * m.na * sizeof(double));
+  s.skd = (double*)take((size_t)B * np * std::max(1, m.nd) * sizeof(double));
+  s.srho = (double*)take((size_t)B * m.na * sizeof(double));
   // Run the same kernel sequence as pta_logp_and_grad on this workspace.
   pta::Scratch saved = c->sc;
   c->sc = s;
