@@ -231,7 +231,15 @@ def run_ours(args):
     # roofline of the dominant stage's kernel
     dom = int(np.argmax(stage_ms))
     peaks = measured_peaks()
-    if abi.STAGES[dom] == "toa":
+    if abi.STAGES[dom] == "toa" and args.precision in ("tf32x3", "tf32"):
+        flops = toa_flops_per_launch(arr, B)
+        terms = 3 if args.precision == "tf32x3" else 1
+        tf32_peak = (peaks or {}).get("bf16_tflops", 1800.0) * (1.1 / 2.25)
+        roof = {"kernel": f"k_toa_tc<{terms}> (TOA contractions, tcgen05 kind::tf32)", "bound": "tensor",
+                "unit": "TFLOP/s", "achieved": flops / (stage_ms[dom] * 1e-3) / 1e12, "peak": tf32_peak,
+                "peak_source": "measured bf16 burst x nominal TF32/BF16 ratio 1.1/2.25",
+                "pipe_terms": terms}
+    elif abi.STAGES[dom] == "toa":
         flops = toa_flops_per_launch(arr, B)
         roof = {"kernel": "k_toa_simt (TOA contractions)", "bound": "alu", "unit": "TFLOP/s",
                 "achieved": flops / (stage_ms[dom] * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,

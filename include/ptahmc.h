@@ -116,7 +116,8 @@ int pta_set_hyperprior(pta_ctx* ctx, double log10a_lo, double log10a_hi,
  *              data-only constants dropped (see pta_logp_constant)
  *   grad_dev   [B x D] float32 d logp / d x, or NULL
  *   status_dev [B] int32, or NULL: 0 ok; 1 theta outside the prior box;
- *              2 per-frequency covariance not positive definite; 3 non-finite.
+ *              2 per-frequency covariance not positive definite; 3 non-finite;
+ *              4 a bounded device wait in the tensor-core kernel gave up.
  *              Any nonzero status sets logp = -inf and grad = 0 for that chain.
  * Asynchronous on `stream`. */
 int pta_logp_and_grad(pta_ctx* ctx, int B, const float* x_dev, double* logp_dev,

@@ -241,7 +241,7 @@ int pta_finalize(pta_ctx* c, void* stream) {
   m.n_units = (int)unit_psr.size();
   m.m_max = m_max;
   m.Qs = round_up(m.P, 4);
-  m.PM = m.P + m_max + m.NL;
+  m.PM = round_up(m.P + m_max + m.NL, 32);  // whole 32-column chunks for the tensor-core kernel
   c->ntoa = 0;
   for (auto& p : c->psrs) c->ntoa += p.n;
   L.ntoa = c->ntoa;
@@ -625,7 +625,14 @@ int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* gr
   if (e == cudaSuccess) e = pta::launch_tm_prologue(m, s, B, fp64, st);
   tm.end(pta::count_prior_forward(m) + 1);
   tm.begin(1);
-  if (e == cudaSuccess) e = fp64 ? pta::launch_toa_fp64(m, s, B, st) : pta::launch_toa_fp32(m, s, B, st);
+  if (e == cudaSuccess) {
+    if (fp64)
+      e = pta::launch_toa_fp64(m, s, B, st);
+    else if (c->precision == PTA_PREC_TF32X3 || c->precision == PTA_PREC_TF32)
+      e = pta::launch_toa_tc(m, s, B, c->precision == PTA_PREC_TF32X3 ? 3 : 1, st);
+    else
+      e = pta::launch_toa_fp32(m, s, B, st);
+  }
   tm.end(1);
   tm.begin(2);
   if (e == cudaSuccess) e = pta::launch_reduce(m, s, B, fp64, st);
@@ -667,8 +674,11 @@ int pta_layout(const pta_ctx* c, pta_layout_t* out) {
 
 int pta_set_precision(pta_ctx* c, int precision) {
   if (!c) return PTA_EINVAL;
-  if (precision != PTA_PREC_FP64 && precision != PTA_PREC_FP32)
+  if (precision != PTA_PREC_FP64 && precision != PTA_PREC_FP32 && precision != PTA_PREC_TF32X3 &&
+      precision != PTA_PREC_TF32)
     return fail(c, PTA_EINVAL, "precision mode not available in this build");
+  if ((precision == PTA_PREC_TF32X3 || precision == PTA_PREC_TF32) && c->finalized && (c->dm.P + 127) / 128 > 7)
+    return fail(c, PTA_EINVAL, "tensor-core path supports at most 896 coefficients per pulsar");
   c->precision = precision;
   return PTA_OK;
 }

@@ -112,6 +112,7 @@ cudaError_t launch_prior_forward(const DevModel& m, const Scratch& s, int B, con
                                  int fp64, cudaStream_t st);
 cudaError_t launch_toa_fp32(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
 cudaError_t launch_toa_fp64(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
+cudaError_t launch_toa_tc(const DevModel& m, const Scratch& s, int B, int terms, cudaStream_t st);
 cudaError_t launch_tm_prologue(const DevModel& m, const Scratch& s, int B, int fp64, cudaStream_t st);
 cudaError_t launch_reduce(const DevModel& m, const Scratch& s, int B, int fp64, cudaStream_t st);
 cudaError_t launch_prior_adjoint(const DevModel& m, const Scratch& s, int B, const float* x,
