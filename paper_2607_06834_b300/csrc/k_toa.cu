@@ -28,6 +28,7 @@ constexpr int kThreads = 256;
 // With the reference coefficients a_ref (the projected reference residual dt''
 // satisfies M^T N^-1 dt'' = 0) and da = a - a_ref, the projected residual is
 //   r~ = dt'' - F da - M c,  c = -(M^T N^-1 M)^-1 H^T da,  H = F^T N^-1 M.
+// c is applied as an FP64 matrix-vector product with the stored (M^T N^-1 M)^-1.
 // FP64 path: c from the full H in FP64; row = [da, c].
 // FP32 path: the lowest-frequency columns (nla achromatic, nld DM bins) use the
 // stored projected basis F~_lo = F_lo - M K^-1 H_lo^T, so c only carries the other
@@ -92,24 +93,16 @@ __global__ void __launch_bounds__(128)
     }
   }
   __syncthreads();
-  if (warp == 0) {
-    for (int j = lane; j < mI; j += 32)
-      cv[j] = -(part[j] + part[mI + j] + part[2 * mI + j] + part[3 * mI + j]);
-    __syncwarp();
-    const double* Lk = m.LK + m.lk_off[I];
-    for (int i = 0; i < mI; ++i) {  // Lk y = rhs
+  // c = -(M^T N^-1 M)^-1 hv, hv = H^T da: FP64 matvec with the stored inverse
+  double* hv = part;  // in place: hv[j] = sum of the four warp partials of column j
+  for (int j = tid; j < mI; j += 128) hv[j] = ((part[j] + part[mI + j]) + part[2 * mI + j]) + part[3 * mI + j];
+  __syncthreads();
+  {
+    const double* Ki = m.Kinv + m.lk_off[I];
+    for (int i = tid; i < mI; i += 128) {
       double s = 0.0;
-      for (int l = lane; l < i; l += 32) s = fma(Lk[i * mI + l], cv[l], s);
-      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) cv[i] = (cv[i] - s) / Lk[i * mI + i];
-      __syncwarp();
-    }
-    for (int i = mI - 1; i >= 0; --i) {  // Lk^T c = y
-      double s = 0.0;
-      for (int l = i + 1 + lane; l < mI; l += 32) s = fma(Lk[l * mI + i], cv[l], s);
-      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) cv[i] = (cv[i] - s) / Lk[i * mI + i];
-      __syncwarp();
+      for (int j = 0; j < mI; ++j) s = fma(Ki[i * mI + j], hv[j], s);
+      cv[i] = -s;
     }
   }
   __syncthreads();
@@ -282,17 +275,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int g = 0; g < C::RG; ++g) s += C2[g * BC + tid];
       c2acc += (double)s;
     }
-    // --- ghat[q][c] += sum_t F^T[q][t] w~[t][c],  q = rg + RG*i < P
-#pragma unroll 2
-    for (int t = 0; t < TT; ++t) {
-      const float4 wv = *reinterpret_cast<const float4*>(Ws + t * C::WS + 4 * cg);
+    // --- ghat[q][c] += sum_t F^T[q][t] w~[t][c],  q = rg + RG*i < P; four TOAs per step
+    // so each basis row is one 16-byte load
+#pragma unroll 1
+    for (int t = 0; t < TT; t += 4) {
+      float4 wv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) wv[r] = *reinterpret_cast<const float4*>(Ws + (t + r) * C::WS + 4 * cg);
 #pragma unroll
       for (int i = 0; i < QPT; ++i) {
-        const float xv = Xs[(rg + C::RG * i) * C::XS + t];
-        acc[i][0] = fmaf(xv, wv.x, acc[i][0]);
-        acc[i][1] = fmaf(xv, wv.y, acc[i][1]);
-        acc[i][2] = fmaf(xv, wv.z, acc[i][2]);
-        acc[i][3] = fmaf(xv, wv.w, acc[i][3]);
+        const float4 xv = *reinterpret_cast<const float4*>(Xs + (rg + C::RG * i) * C::XS + t);
+        acc[i][0] = fmaf(xv.x, wv[0].x, fmaf(xv.y, wv[1].x, fmaf(xv.z, wv[2].x, fmaf(xv.w, wv[3].x, acc[i][0]))));
+        acc[i][1] = fmaf(xv.x, wv[0].y, fmaf(xv.y, wv[1].y, fmaf(xv.z, wv[2].y, fmaf(xv.w, wv[3].y, acc[i][1]))));
+        acc[i][2] = fmaf(xv.x, wv[0].z, fmaf(xv.y, wv[1].z, fmaf(xv.z, wv[2].z, fmaf(xv.w, wv[3].z, acc[i][2]))));
+        acc[i][3] = fmaf(xv.x, wv[0].w, fmaf(xv.y, wv[1].w, fmaf(xv.z, wv[2].w, fmaf(xv.w, wv[3].w, acc[i][3]))));
       }
     }
   }

@@ -260,7 +260,8 @@ int pta_finalize(pta_ctx* c, void* stream) {
   std::vector<uint64_t> phase(tot, 0);
   std::vector<float> chrom(tot, 0.f), dt(tot, 0.f), ninv(tot, 0.f), M32(moff, 0.f), Flo(floff, 0.f);
   std::vector<double> dt64(tot, 0.0), ninv64(tot, 0.0), nuw64(tot, 0.0), M64(moff, 0.0);
-  std::vector<double> LK(lkoff, 0.0), H(hoff, 0.0), aref((size_t)npsr * m.P, 0.0), pos(3 * npsr), dist(npsr);
+  std::vector<double> LK(lkoff, 0.0), KI(lkoff, 0.0), H(hoff, 0.0), aref((size_t)npsr * m.P, 0.0), pos(3 * npsr),
+      dist(npsr);
   std::vector<float> Hhi(hoff, 0.f), Hlo(hoff, 0.f);
   const double nu_ref = d.nu_ref_mhz;
   const int P = m.P, kmax = std::max(m.na, m.nd);
@@ -372,6 +373,12 @@ int pta_finalize(pta_ctx* c, void* stream) {
     // keeps the FP32 quantities near the white-noise level.
     std::vector<double> KiH((size_t)mI * P), col(mI), Kb0 = b0;
     kinv(Kb0);
+    for (int j = 0; j < mI; ++j) {  // explicit (M^T N^-1 M)^-1 by solves against unit vectors
+      std::vector<double> e(mI, 0.0);
+      e[j] = 1.0;
+      kinv(e);
+      for (int i2 = 0; i2 < mI; ++i2) KI[lk_off[I] + i2 * mI + j] = e[i2];
+    }
     for (int q = 0; q < P; ++q) {
       for (int j = 0; j < mI; ++j) col[j] = Hl[(size_t)q * mI + j];
       kinv(col);
@@ -465,6 +472,7 @@ int pta_finalize(pta_ctx* c, void* stream) {
   UP(nunit, nunit);
   UP(lk_off, lk_off);
   UP(LK, LK);
+  UP(KI, Kinv);
   UP(h_off, h_off);
   UP(H, H);
   UP(Hhi, Hhi);

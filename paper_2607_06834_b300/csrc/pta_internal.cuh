@@ -53,6 +53,7 @@ struct DevModel {
   const int* nunit;
   const int* lk_off;            // offset of chol(M^T N^-1 M) (m x m, row-major FP64)
   const double* LK;
+  const double* Kinv;           // (M^T N^-1 M)^-1, same offsets as LK
   const int* h_off;             // offset of F^T N^-1 M (P x m row-major FP64)
   const double* H;
   const float* Hhi;             // H split into FP32 hi + lo parts (same layout as H)
@@ -134,17 +135,16 @@ __host__ __device__ inline double ln_pl(double ln_rho0, double ln_Tfyr, double l
 }
 
 // sin and cos of 2 pi * phi / 2^64 for a 64-bit fixed-point phase phi.  The top
-// three bits select the octant; the remaining 61 bits are a fraction of pi/4
-// whose FP32 rounding error is at most 2^-24 relative.  The reduced argument
-// (|x| <= pi/4) goes through Taylor polynomials (sin to x^9, cos to x^10),
-// whose truncation error is below 2e-9.
+// three bits select the octant; the next 32 bits are a fraction of pi/4 (the
+// dropped bits are below 2^-32 of pi/4), so the reduced argument |x| <= pi/4 is
+// exact to float rounding.  Taylor polynomials (sin to x^9, cos to x^10, truncation
+// error below 2e-9) give sin x and cos x; the octant then swaps and negates them:
+// angle = oct*pi/4 + x for even octants, (oct+1)*pi/4 - x for odd ones.
 __device__ __forceinline__ void sincos_turns64(uint64_t phi, float* s, float* c) {
   const unsigned oct = (unsigned)(phi >> 61);
   uint64_t rem = phi & ((1ull << 61) - 1);
-  // odd octants measure the angle back from the next multiple of pi/4
-  const bool odd = oct & 1u;
-  if (odd) rem = (1ull << 61) - rem;
-  const float x = (float)rem * 3.4061215800865545e-19f;  // (pi/4) / 2^61
+  rem = (oct & 1u) ? (1ull << 61) - rem : rem;
+  const float x = (float)(unsigned)(rem >> 29) * 1.8286476e-10f;  // (pi/4) / 2^32
   const float x2 = x * x;
   float sp = fmaf(x2, 2.7557319e-06f, -1.9841270e-04f);
   sp = fmaf(x2, sp, 8.3333333e-03f);
@@ -155,20 +155,10 @@ __device__ __forceinline__ void sincos_turns64(uint64_t phi, float* s, float* c)
   cp = fmaf(x2, cp, 4.1666667e-02f);
   cp = fmaf(x2, cp, -0.5f);
   const float cv = fmaf(x2, cp, 1.0f);
-  // angle = oct*pi/4 + x (even) or (oct+1)*pi/4 - x (odd)
-  float sn, cs;
-  switch (oct) {
-    case 0: sn = sv; cs = cv; break;      // x
-    case 1: sn = cv; cs = sv; break;      // pi/2 - x
-    case 2: sn = cv; cs = -sv; break;     // pi/2 + x
-    case 3: sn = sv; cs = -cv; break;     // pi - x
-    case 4: sn = -sv; cs = -cv; break;    // pi + x
-    case 5: sn = -cv; cs = -sv; break;    // 3pi/2 - x
-    case 6: sn = -cv; cs = sv; break;     // 3pi/2 + x
-    default: sn = -sv; cs = cv; break;    // 2pi - x
-  }
-  *s = sn;
-  *c = cs;
+  const bool swap = ((oct + 1u) >> 1) & 1u;     // octants 1, 2, 5, 6
+  const float s0 = swap ? cv : sv, c0 = swap ? sv : cv;
+  *s = (oct >= 4u) ? -s0 : s0;                  // octants 4..7
+  *c = (((oct + 2u) >> 2) & 1u) ? -c0 : c0;     // octants 2..5
 }
 
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
