@@ -325,8 +325,8 @@ __global__ void k_diag_adjoint(DevModel m, const float* __restrict__ x, const do
 // ---------------------------------------------------------------------------
 __global__ void k_final(DevModel m, const float* __restrict__ x, const double* __restrict__ chi2,
                         const double* __restrict__ dlnk, const double* __restrict__ dlnkd,
-                        const double* __restrict__ dlnr, const int32_t* __restrict__ stat, double* logp,
-                        float* grad, int32_t* status, int B) {
+                        const double* __restrict__ dlnr, const int32_t* __restrict__ stat,
+                        const double* __restrict__ cwg, double* logp, float* grad, int32_t* status, int B) {
   const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x, np = m.npsr;
   const float* xb = x + (size_t)b * m.d;
   __shared__ double red[32];
@@ -349,6 +349,18 @@ __global__ void k_final(DevModel m, const float* __restrict__ x, const double* _
   if (tid == 0) {
     const float la = xb[m.th_gwb], ga = xb[m.th_gwb + 1];
     outside |= !(la > m.la_lo && la < m.la_hi && ga > m.g_lo && ga < m.g_hi);
+  }
+  if (m.cw) {
+    // CW prior: box on the 8 binary parameters, pulsar phases in (0, 2 pi), distances
+    // > 0 with a Gaussian of width dist_sigma around each pulsar's nominal distance
+    const float* th = xb + m.th_cw;
+    if (tid < 8) outside |= !(th[tid] > m.cw_lo[tid] && th[tid] < m.cw_hi[tid]);
+    for (int I = tid; I < np; I += nt) {
+      const double L = th[8 + 2 * I], ph = th[9 + 2 * I];
+      outside |= !(L > 0.0 && ph > 0.0 && ph < 2.0 * kPi);
+      const double dz = (L - m.dist[I]) / m.dist_sigma;
+      acc -= 0.5 * dz * dz;
+    }
   }
   if (outside) atomicOr(&s_flag, 1);
   for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -405,6 +417,20 @@ __global__ void k_final(DevModel m, const float* __restrict__ x, const double* _
     gb[m.th_gwb] = (float)(2.0 * kLn10 * s1);
     gb[m.th_gwb + 1] = (float)s2;
   }
+  if (m.cw) {
+    const float* th = xb + m.th_cw;
+    const double* gc = cwg + (size_t)b * np * 10;
+    if (tid < 8) {
+      double s = 0.0;
+      for (int I = 0; I < np; ++I) s += gc[I * 10 + tid];
+      gb[m.th_cw + tid] = (float)s;
+    }
+    for (int I = tid; I < np; I += nt) {
+      const double L = th[8 + 2 * I];
+      gb[m.th_cw + 8 + 2 * I] = (float)(gc[I * 10 + 8] - (L - m.dist[I]) / (m.dist_sigma * m.dist_sigma));
+      gb[m.th_cw + 9 + 2 * I] = (float)gc[I * 10 + 9];
+    }
+  }
 }
 
 }  // namespace
@@ -460,7 +486,7 @@ cudaError_t launch_prior_adjoint(const DevModel& m, const Scratch& s, int B, con
 
 cudaError_t launch_final(const DevModel& m, const Scratch& s, int B, const float* x, double* logp, float* grad,
                          int32_t* status, cudaStream_t st) {
-  k_final<<<B, 256, 0, st>>>(m, x, s.chi2, s.dlnk, s.dlnkd, s.dlnr, s.stat, logp, grad, status, B);
+  k_final<<<B, 256, 0, st>>>(m, x, s.chi2, s.dlnk, s.dlnkd, s.dlnr, s.stat, s.cwg, logp, grad, status, B);
   return cudaGetLastError();
 }
 

@@ -45,7 +45,8 @@ __device__ __forceinline__ int low_col(const DevModel& m, int q) {
 }
 
 __global__ void __launch_bounds__(128)
-    k_tm_prologue(DevModel m, double* __restrict__ a64, float* __restrict__ a32, int B, int fp64) {
+    k_tm_prologue(DevModel m, double* __restrict__ a64, float* __restrict__ a32, const double* __restrict__ cwbs,
+                  int B, int fp64) {
   extern __shared__ double smp[];
   const int I = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int P = m.P, mI = m.m[I];
@@ -95,7 +96,12 @@ __global__ void __launch_bounds__(128)
   __syncthreads();
   // c = -(M^T N^-1 M)^-1 hv, hv = H^T da: FP64 matvec with the stored inverse
   double* hv = part;  // in place: hv[j] = sum of the four warp partials of column j
-  for (int j = tid; j < mI; j += 128) hv[j] = ((part[j] + part[mI + j]) + part[2 * mI + j]) + part[3 * mI + j];
+  for (int j = tid; j < mI; j += 128) {
+    double v = ((part[j] + part[mI + j]) + part[2 * mI + j]) + part[3 * mI + j];
+    if (cwbs)  // deterministic signal: c also absorbs M^T N^-1 s
+      for (int q = 0; q < m.nunit[I]; ++q) v += cwbs[((size_t)(m.unit0[I] + q) * B + b) * m.m_max + j];
+    hv[j] = v;
+  }
   __syncthreads();
   {
     const double* Ki = m.Kinv + m.lk_off[I];
@@ -152,7 +158,7 @@ size_t simt_smem(const DevModel& m) {
 template <int BC, int TT, int QPT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_toa_simt(DevModel m, const float* __restrict__ a32, float* __restrict__ gpart, double* __restrict__ c2part,
-               int B, int XR) {
+               int B, int XR, const float* __restrict__ cwsig, float* __restrict__ cwwt) {
   using C = SimtCfg<BC, TT, QPT>;
   extern __shared__ float4 sm4[];
   float* Xs = reinterpret_cast<float*>(sm4);            // [XR][XS]  rows: F (P), M (m_I), F~_lo (NL), zero
@@ -261,10 +267,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       float* wp = reinterpret_cast<float*>(&wv);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const float rr = dtv - y[r][j];
+        float rr = dtv - y[r][j];
+        const int bb = b0 + 4 * cg + j;
+        const size_t ci = (size_t)bb * m.ntoa_pad + start + t0 + t;
+        if (cwsig && bb < B) rr -= cwsig[ci];  // r~ = dt'' - s - y
         const float ww = rr * ni;
         wp[j] = ww;
         q4[j] = fmaf(rr, ww, q4[j]);
+        if (cwwt && bb < B) cwwt[ci] = ww;
       }
       *reinterpret_cast<float4*>(Ws + t * C::WS + 4 * cg) = wv;
     }
@@ -382,7 +392,8 @@ cudaError_t launch_simt(const DevModel& m, const Scratch& s, int B, cudaStream_t
   cudaError_t e = cudaFuncSetAttribute(k_toa_simt<BC, TT, QPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   dim3 grid(m.n_units, (B + BC - 1) / BC);
-  k_toa_simt<BC, TT, QPT><<<grid, kThreads, sm, st>>>(m, s.a32, s.gpart, s.c2part, B, simt_xrows<BC, TT, QPT>(m));
+  k_toa_simt<BC, TT, QPT><<<grid, kThreads, sm, st>>>(m, s.a32, s.gpart, s.c2part, B, simt_xrows<BC, TT, QPT>(m),
+                                                        m.cw ? s.cwsig : nullptr, m.cw ? s.cwwt : nullptr);
   return cudaGetLastError();
 }
 
@@ -394,7 +405,7 @@ cudaError_t launch_tm_prologue(const DevModel& m, const Scratch& s, int B, int f
     cudaError_t e = cudaFuncSetAttribute(k_tm_prologue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
-  k_tm_prologue<<<dim3(m.npsr, B), 128, sm, st>>>(m, s.a64, s.a32, B, fp64);
+  k_tm_prologue<<<dim3(m.npsr, B), 128, sm, st>>>(m, s.a64, s.a32, m.cw ? s.cwbs : nullptr, B, fp64);
   return cudaGetLastError();
 }
 

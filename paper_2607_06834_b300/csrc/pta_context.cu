@@ -110,6 +110,13 @@ int pta_create(pta_ctx** out, const pta_model_desc* d) {
   c->dm.la_hi = -10.0;
   c->dm.g_lo = 0.0;
   c->dm.g_hi = 7.0;
+  const double cwlo[8] = {7.0, -9.0, -18.0, -1.0, 0.0, -1.0, 0.0, 0.0};
+  const double cwhi[8] = {10.5, -7.0, -11.0, 1.0, kPi, 1.0, 2.0 * kPi, 2.0 * kPi};
+  for (int i = 0; i < 8; ++i) {
+    c->dm.cw_lo[i] = cwlo[i];
+    c->dm.cw_hi[i] = cwhi[i];
+  }
+  c->dm.dist_sigma = 0.2;
   *out = c;
   return PTA_OK;
 }
@@ -240,6 +247,7 @@ int pta_finalize(pta_ctx* c, void* stream) {
   if (tot > (1ll << 31) - 1) return fail(c, PTA_EINVAL, "too many TOAs");
   m.n_units = (int)unit_psr.size();
   m.m_max = m_max;
+  m.ntoa_pad = tot;
   m.Qs = round_up(m.P, 4);
   m.PM = round_up(m.P + m_max + m.NL, 32);  // whole 32-column chunks for the tensor-core kernel
   c->ntoa = 0;
@@ -279,7 +287,9 @@ int pta_finalize(pta_ctx* c, void* stream) {
       const double f = (p.t[i] - tmin) / m.T;          // fraction of the span
       const double hi = std::floor(f * 4294967296.0);
       const double lo = (f * 4294967296.0 - hi) * 4294967296.0;
-      phase[o + i] = ((uint64_t)hi << 32) + (uint64_t)lo;  // exact fixed-point copy of f
+      // exact fixed-point copy of f; the last TOA (f = 1) takes the largest fraction
+      // below 1 so that its time t = f T stays T for the (non-periodic) CW signal
+      phase[o + i] = hi >= 4294967296.0 ? ~0ull : ((uint64_t)hi << 32) + (uint64_t)lo;
       const double w = (nu_ref / p.nu[i]) * (nu_ref / p.nu[i]);
       chrom[o + i] = (float)w;
       nuw64[o + i] = w;
@@ -508,7 +518,8 @@ namespace {
 
 void free_scratch(pta::Scratch& s) {
   void* ptrs[] = {s.a32, s.a64, s.Lpk, s.Lipk, s.gpart, s.gpart64, s.c2part, s.ghat, s.chi2,
-                  s.dlnk, s.dlnkd, s.dlnr, s.stat, s.sk, s.skd, s.srho, s.x0, s.g0, s.p, s.lp0, s.xs, s.gs, s.lps,
+                  s.dlnk, s.dlnkd, s.dlnr, s.stat, s.sk, s.skd, s.srho, s.cwc, s.cwjac, s.cwsig,
+                  s.cwbs, s.cwwt, s.cwgp, s.cwg, s.x0, s.g0, s.p, s.lp0, s.xs, s.gs, s.lps,
                   s.step, s.imass, s.kin0, s.hmc_ctr, s.acc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -550,6 +561,15 @@ int ensure_scratch(pta_ctx* c, int B, bool fp64) {
   AL(sk, (size_t)cap * np * m.na);
   AL(skd, (size_t)cap * np * std::max(1, m.nd));
   AL(srho, (size_t)cap * m.na);
+  if (m.cw) {
+    AL(cwc, (size_t)cap * np * pta::cw_const_bytes());
+    AL(cwjac, (size_t)cap * np * 100);
+    AL(cwsig, (size_t)cap * m.ntoa_pad);
+    AL(cwbs, (size_t)m.n_units * cap * std::max(1, m.m_max));
+    AL(cwwt, (size_t)cap * m.ntoa_pad);
+    AL(cwgp, (size_t)m.n_units * cap * 10);
+    AL(cwg, (size_t)cap * np * 10);
+  }
   AL(x0, (size_t)cap * m.d);
   AL(g0, (size_t)cap * m.d);
   AL(p, (size_t)cap * m.d);
@@ -630,8 +650,9 @@ int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* gr
   cudaError_t e = cudaMemsetAsync(s.stat, 0, sizeof(int32_t) * B, st);
   tm.begin(0);
   if (e == cudaSuccess) e = pta::launch_prior_forward(m, s, B, x, fp64, st);
+  if (e == cudaSuccess && m.cw) e = pta::launch_cw_forward(m, s, B, x, st);
   if (e == cudaSuccess) e = pta::launch_tm_prologue(m, s, B, fp64, st);
-  tm.end(pta::count_prior_forward(m) + 1);
+  tm.end(pta::count_prior_forward(m) + 1 + (m.cw ? 2 : 0));
   tm.begin(1);
   if (e == cudaSuccess) {
     if (fp64)
@@ -648,7 +669,8 @@ int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* gr
   if (grad) {
     tm.begin(3);
     if (e == cudaSuccess) e = pta::launch_prior_adjoint(m, s, B, x, grad, st);
-    tm.end(pta::count_prior_adjoint(m));
+    if (e == cudaSuccess && m.cw) e = pta::launch_cw_gradient(m, s, B, st);
+    tm.end(pta::count_prior_adjoint(m) + (m.cw ? 2 : 0));
   }
   tm.begin(4);
   if (e == cudaSuccess) e = pta::launch_final(m, s, B, x, logp, grad, status, st);
@@ -706,7 +728,8 @@ int pta_logp_and_grad(pta_ctx* c, int B, const float* x, double* logp, float* gr
   if (!c) return PTA_EINVAL;
   if (B < 0 || (B > 0 && (!x || !logp))) return fail(c, PTA_EINVAL, "logp_and_grad: bad arguments");
   if (B == 0) return PTA_OK;
-  if (c->dm.cw) return fail(c, PTA_EINVAL, "continuous-wave model not available in this build");
+  if (c->dm.cw && c->precision != PTA_PREC_FP32)
+    return fail(c, PTA_EINVAL, "the continuous-wave model runs on the FP32 path (PTA_PREC_FP32)");
   int rc = pta_prepare_internal(c, B);
   if (rc != PTA_OK) return rc;
   return pta_eval_internal(c, B, x, logp, grad, status, (cudaStream_t)stream, true);

@@ -30,6 +30,9 @@ struct DevModel {
   int n_chol;      // bins k < n_chol: Phi_k = rho_k Gamma + diag(kappa_.k), full Cholesky
   int n_gwbonly;   // bins n_chol <= k < n_chol + n_gwbonly: Phi_k = rho_k Gamma
   int n_units, m_max;
+  long long ntoa_pad;           // padded TOA count (row length of per-chain TOA arrays)
+  double cw_lo[8], cw_hi[8];    // CW prior box; pulsar phase in (0, 2 pi), distance > 0
+  double dist_sigma;            // pulsar-distance prior width [kpc]
   double T, ln_Tfyr, ln_rho0;   // T [s], ln(T f_yr), power-law normalisation (see ln_pl)
   double la_lo, la_hi, g_lo, g_hi;
   // per TOA (padded; padding rows have ninv = 0)
@@ -93,6 +96,14 @@ struct Scratch {
   double* sk = nullptr;        // [cap][npsr][na]  sqrt(kappa) intrinsic red noise (0 above n_rn)
   double* skd = nullptr;       // [cap][npsr][nd]  sqrt(kappa) DM
   double* srho = nullptr;      // [cap][na]        sqrt(rho) GWB (0 above n_gwb)
+  // continuous-wave signal (only when the model has it)
+  unsigned char* cwc = nullptr; // [cap][npsr] per-(chain, pulsar) constants
+  double* cwjac = nullptr;     // [cap][npsr][10][10]
+  float* cwsig = nullptr;      // [cap][ntoa_pad] signal s
+  double* cwbs = nullptr;      // [units][cap][m_max] M^T N^-1 s partials
+  float* cwwt = nullptr;       // [cap][ntoa_pad] whitened projected residual w~
+  double* cwgp = nullptr;      // [units][cap][10]
+  double* cwg = nullptr;       // [cap][npsr][10] d logp / d theta contributions
   // HMC state
   float* x0 = nullptr;         // [cap][d]
   float* g0 = nullptr;
@@ -114,6 +125,9 @@ cudaError_t launch_prior_forward(const DevModel& m, const Scratch& s, int B, con
 cudaError_t launch_toa_fp32(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
 cudaError_t launch_toa_fp64(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
 cudaError_t launch_toa_tc(const DevModel& m, const Scratch& s, int B, int terms, cudaStream_t st);
+size_t cw_const_bytes();
+cudaError_t launch_cw_forward(const DevModel& m, const Scratch& s, int B, const float* x, cudaStream_t st);
+cudaError_t launch_cw_gradient(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
 cudaError_t launch_tm_prologue(const DevModel& m, const Scratch& s, int B, int fp64, cudaStream_t st);
 cudaError_t launch_reduce(const DevModel& m, const Scratch& s, int B, int fp64, cudaStream_t st);
 cudaError_t launch_prior_adjoint(const DevModel& m, const Scratch& s, int B, const float* x,

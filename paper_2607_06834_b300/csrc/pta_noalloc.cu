@@ -74,7 +74,7 @@ extern "C" int pta_logp_and_grad_noalloc(pta_ctx* c, int B, const float* x, doub
   }
   if (B == 0) return PTA_OK;
   if (c->dm.cw) {
-    c->err = "continuous-wave model not available in this build";
+    c->err = "logp_and_grad_noalloc: the continuous-wave model needs the allocating entry point";
     return PTA_EINVAL;
   }
   if (c->precision == PTA_PREC_FP64 && !c->dm.F64) {

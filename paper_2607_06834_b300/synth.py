@@ -303,6 +303,6 @@ def make_points(arr: Array, B: int, seed: int = 6834, spread: float = 1.0,
         x[:, c + 6] = rng.uniform(0.0, 2 * math.pi, B)
         x[:, c + 7] = rng.uniform(0.0, 2 * math.pi, B)
         for I in range(npsr):
-            x[:, c + 8 + 2 * I] = arr.pulsars[I].dist_kpc + rng.normal(0.0, 0.2, B)
+            x[:, c + 8 + 2 * I] = np.maximum(0.05, arr.pulsars[I].dist_kpc + rng.normal(0.0, 0.2, B))
             x[:, c + 9 + 2 * I] = rng.uniform(0.0, 2 * math.pi, B)
     return x.astype(np.float32)

@@ -197,6 +197,53 @@ def test_tensor_core_paths_against_simt(ng15):
     assert abs(lp3[3] - lo[0]) < TC_REPORTED_LOGP and _grad_rel(g3[3], go[0]) < TC_REPORTED_GRAD
 
 
+# ------------------------------------------------------------------ continuous-wave signal
+def _cw_check(arr, orc, X, near):
+    lo, go = _oracle(orc, X)
+    eng = _engine(arr, "fp32")
+    lp, g, st = _eval(eng, X)
+    assert np.all(st == 0)
+    c = orc.lay["th_cw"]
+    for i in range(len(X)):
+        err = abs(lp[i] - lo[i])
+        rel = _grad_rel(g[i], go[i])
+        relcw = _grad_rel(g[i, c:], go[i, c:])
+        print(f"cw chain {i}: logp {lo[i]:.3f} |d| {err:.2e} grad rel {rel:.2e} cw-block rel {relcw:.2e}")
+        if i in near:
+            assert err < LOGP_ABS
+        else:
+            assert err <= LOGP_ABS + REL_RANDOM["fp32"] * abs(lo[i])
+        assert rel < GRAD_REL and relcw < GRAD_REL
+
+
+def test_cw_small_array():
+    arr = synth.small_array(npsr=3, ntoa=[150, 700, 2300], m=[3, 9, 12], n_gwb=4, n_rn=5, n_dm=3, seed=41,
+                            nbackend=2, cw=True)
+    orc = O.Oracle(arr)
+    X = synth.make_points(arr, 10, seed=7)
+    near = [0, 1, 2]
+    for i in near:
+        X[i] = O.curn_point(orc, X[i].astype(np.float64), 1.0, seed=i)
+    _cw_check(arr, orc, X, near)
+
+
+def test_cw_ng15_sampled():
+    """Config with the 67-pulsar array plus a circular binary (64-chain batch sampled)."""
+    arr = synth.make_array("ng15_cw")
+    orc = O.Oracle(arr)
+    X = synth.make_points(arr, 64, seed=6838)
+    X[10] = O.curn_point(orc, X[10].astype(np.float64), 1.0, seed=4)
+    eng = _engine(arr, "fp32")
+    lp, g, st = _eval(eng, X)
+    assert np.all(st == 0)
+    for i in (0, 10, 63):
+        lo, go = _oracle(orc, X[i:i + 1])
+        err = abs(lp[i] - lo[0])
+        print(f"ng15 cw chain {i}: logp {lo[0]:.3f} |d| {err:.2e} grad rel {_grad_rel(g[i], go[0]):.2e}")
+        assert err < (LOGP_ABS if i == 10 else LOGP_ABS + REL_RANDOM["fp32"] * abs(lo[0]))
+        assert _grad_rel(g[i], go[0]) < GRAD_REL
+
+
 # ------------------------------------------------------------------ edge cases
 def test_status_and_degenerate_cases(tiny):
     arr, orc = tiny
