@@ -98,6 +98,9 @@ typedef struct {
 } pta_layout_t;
 
 int pta_create(pta_ctx** out, const pta_model_desc* desc);
+/* Copies the pulsar's arrays.  PTA_EINVAL for inconsistent sizes, after
+ * finalize, or beyond 166 pulsars (the per-frequency N_p x N_p Cholesky and its
+ * adjoint are held in FP64 shared memory). */
 int pta_add_pulsar(pta_ctx* ctx, const pta_pulsar_desc* psr);
 /* Precompute (noise weights, normalised timing model, its FP64 Cholesky, the
  * Hellings-Downs matrix of Eq. HD, tile table) and upload.  Synchronises. */

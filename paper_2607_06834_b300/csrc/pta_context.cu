@@ -124,7 +124,7 @@ int pta_create(pta_ctx** out, const pta_model_desc* d) {
 int pta_add_pulsar(pta_ctx* c, const pta_pulsar_desc* p) {
   if (!c || !p) return PTA_EINVAL;
   if (c->finalized) return fail(c, PTA_ESTATE, "pta_add_pulsar after pta_finalize");
-  if ((int)c->psrs.size() >= kMaxPsr) return fail(c, PTA_EINVAL, "too many pulsars");
+  if ((int)c->psrs.size() >= kMaxPsr) return fail(c, PTA_EINVAL, "too many pulsars (at most 166: the per-frequency Cholesky is held in shared memory)");
   if (p->n <= 0 || p->m <= 0 || p->m >= p->n || p->n_backend <= 0 || !p->toas_s || !p->freqs_mhz ||
       !p->resid_s || !p->sigma_s || !p->backend || !p->efac || !p->equad_s || !p->M)
     return fail(c, PTA_EINVAL, "pulsar: bad sizes or NULL array (need 0 < m < n, n_backend > 0)");

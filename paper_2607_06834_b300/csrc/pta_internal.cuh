@@ -18,7 +18,9 @@ constexpr double kTsunS = 4.925490947641267e-06;  // G Msun / c^3
 constexpr double kKpcS = 1.0292712503e11;         // 1 kpc / c
 constexpr int kTile = 128;       // TOAs per pulsar are padded to a multiple of this
 constexpr int kChunk = 2048;     // TOAs per work unit of the TOA kernels
-constexpr int kMaxPsr = 256;
+// The per-frequency Cholesky and its adjoint hold two packed N_p x N_p triangles
+// and 7 N_p vectors in FP64 shared memory: (N_p (N_p + 1) + 7 N_p) x 8 B <= 227 KB.
+constexpr int kMaxPsr = 166;
 constexpr int kLowBins = 4;     // lowest frequencies whose basis columns are projected off the timing model
 
 // Everything a kernel needs about the model and the resident data.  Passed by
