@@ -131,6 +131,32 @@ def cpu_baseline(arr, n_eval: int):
                       f"({dt:.1f} s, numpy FP64)"}
 
 
+def hmc_ess_tiny(dev):
+    """Control run of the same driver on the 3-pulsar, 10-bin array (64 chains,
+    20 leapfrog steps), where the posterior is benign enough to mix in seconds."""
+    import torch
+    from paper_2607_06834_b300 import sampler, synth
+    from paper_2607_06834_b300.engine import Engine
+    arr = synth.make_array("tiny3")
+    eng = Engine(arr, precision="fp32")
+    lay = eng.layout
+    x0 = torch.tensor(synth.make_points(arr, 64, seed=6834 + 30), device=dev)
+    th0 = lay["d_z"]
+    res = sampler.run_hmc(eng, x0, n_warmup=400, n_samples=400, n_leapfrog=20, record=slice(0, eng.D),
+                          seed=6834 + 30, eps0=0.05, init_dz=th0)
+    e = sampler.ess_columns(res.draws)
+    rh = np.array([sampler.split_rhat(res.draws[:, :, k]) for k in range(res.draws.shape[2])])
+    g0 = lay["th_gwb"]
+    t = res.sampling_s
+    eng.close()
+    return {"workload": "3 pulsars x 200 TOAs, RN/GWB 10 bins, 64 chains, 20 leapfrog steps, FP32 path",
+            "warmup_trajectories": 400, "sampling_trajectories": 400,
+            "ess_per_s_gwb_min": float(np.nanmin(e[g0:g0 + 2])) / t, "ess_per_s_median": float(np.nanmedian(e)) / t,
+            "ess_gwb_min": float(np.nanmin(e[g0:g0 + 2])), "ess_median": float(np.nanmedian(e)),
+            "rhat_max": float(np.nanmax(rh)), "rhat_median": float(np.nanmedian(rh)), "sampling_s": t,
+            "accept_rate": res.accept_rate, "stuck_chains": res.stats["stuck_chains"]}
+
+
 def hmc_ess(args, dev):
     """HMC effective samples per second on the NG15-like array plus a circular binary:
     64 chains, trajectories of 20 leapfrog steps (one CUDA graph each), warm-up with
@@ -168,6 +194,8 @@ def hmc_ess(args, dev):
             "evals_per_s": B * L * args.hmc_samples / t, "accept_rate": res.accept_rate, "step": res.step,
             "rhat_gwb_max": float(np.nanmax(rh[g0:g0 + 2])), "rhat_theta_median": float(np.nanmedian(rh)),
             "init": "z at the conditional mode given the starting hyper-parameters (batched CG)",
+            "stuck_chains": res.stats["stuck_chains"], "chain_accept_min": res.stats["chain_accept_min"],
+            "step_range": [res.stats["step_min"], res.stats["step_max"]],
             "ess_estimator": "multi-chain, Geyer initial monotone sequence"}
 
 
@@ -344,6 +372,8 @@ def run_ours(args):
         eng.set_precision(args.precision)
     cpu = None if args.skip_cpu else cpu_baseline(arr, args.cpu_evals)
     hmc = None if args.skip_hmc else hmc_ess(args, dev)
+    if hmc is not None:
+        hmc["control_small_array"] = hmc_ess_tiny(dev)
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32",
@@ -372,7 +402,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-hmc", action="store_true")
-    ap.add_argument("--hmc-warmup", type=int, default=200)
+    ap.add_argument("--hmc-warmup", type=int, default=400)
     ap.add_argument("--hmc-samples", type=int, default=200)
     args = ap.parse_args()
     if args.impl == "reference":

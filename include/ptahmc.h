@@ -106,7 +106,11 @@ int pta_add_pulsar(pta_ctx* ctx, const pta_pulsar_desc* psr);
  * Hellings-Downs matrix of Eq. HD, tile table) and upload.  Synchronises. */
 int pta_finalize(pta_ctx* ctx, void* stream);
 int pta_layout(const pta_ctx* ctx, pta_layout_t* out);
-/* Select the contraction precision (PTA_PREC_*) for later calls. */
+/* Select the contraction precision (PTA_PREC_*) for later calls.  PTA_EINVAL for
+ * an unknown mode, for the TF32 modes beyond 896 coefficients per pulsar, and for
+ * PTA_PREC_BF16X3 when P > 416 or P + max m_I + n_low > 384, n_low = 16 projected
+ * low-frequency columns (the 4 lowest achromatic and 4 lowest DM bins).  The
+ * continuous-wave model runs only with PTA_PREC_FP32. */
 int pta_set_precision(pta_ctx* ctx, int precision);
 /* Hyper-prior box for (log10 A, gamma) of the GWB, red noise and DM (Sec.
  * "Priors": log10 A ~ U(-20,-10), gamma ~ U(0,7) by default). */
@@ -152,7 +156,9 @@ int pta_hmc_trajectory(pta_ctx* ctx, int B, float* x_dev, double* logp_dev, floa
  *   - All calls share the array and it keeps the last call's contents: calls that
  *     overlap on the GPU race.  The status flags are cleared on `stream` per call.
  *   - PTA_PREC_FP64 needs the stored FP64 basis, which pta_logp_and_grad builds on
- *     its first FP64 call; without it the call returns PTA_ESTATE. */
+ *     its first FP64 call; without it the call returns PTA_ESTATE.
+ *   - PTA_PREC_BF16X3 (its packed coefficients need their own buffer) and the
+ *     continuous-wave model return PTA_EINVAL. */
 int pta_logp_and_grad_noalloc(pta_ctx* ctx, int B, const float* x_dev, double* logp_dev,
                               float* grad_dev, int32_t* status_dev, void* stream);
 

@@ -1,0 +1,377 @@
+// TOA contractions on the tcgen05 tensor cores with BF16 operands and a 3-term
+// split (x = hi + lo, both BF16; products hi*hi + lo*hi + hi*lo, FP32 accumulation
+// in tensor memory).  Same quantities as k_toa_simt:
+//   y  = [F | M | F~_lo] coef,  r~ = dt'' - y,  w~ = N^-1 r~,  chi2 += r~ . w~
+//   ghat += F^T w~
+// Reported precision: the split keeps about 16 significant bits per operand.
+//
+// One CTA per (work unit, block of 128 chains); the chains are the MMA's M
+// dimension, so both products accumulate per chain in tensor-memory lanes:
+//   GEMM1  D1[n][t] = sum_q C[n][q] X[t][q]    M = 128 chains, N = 64 TOAs, K = q
+//   GEMM2  D2[n][q] += sum_t W[n][t] X[t][q]   M = 128 chains, N = q (<= 256 a piece), K = t
+// X (the basis tile of 64 TOAs, hi and lo) is generated once per tile in shared
+// memory and read by GEMM1 as a K-major operand (K = q) and by GEMM2 as an
+// MN-major one (N = q): with core matrices of 8 TOAs x 8 columns (16 B rows along
+// q) both views are the same bytes.  C (coefficients, hi and lo, pre-split by
+// k_pack_bf16 in the MMA's layout) streams from global memory in 64-column chunks
+// through a two-slot ring filled by cp.async.bulk.  W (whitened residuals, hi and
+// lo) is written by the epilogue.
+//
+// Warp roles: warps 0-7 generate X; warps 0-3 also run the epilogue (thread =
+// chain = tensor-memory lane); warp 8 lane 0 issues the bulk copies; warp 9 lane 0
+// issues the MMAs.  Every mbarrier wait is bounded; a wait that gives up marks
+// the CTA's chains with status bit 4, and the CTA drains its own copies and MMAs
+// before it frees tensor memory and exits.
+#include <cuda_bf16.h>
+
+#include "pta_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace pta {
+namespace {
+
+constexpr int TT = 64;                   // TOAs per tile
+constexpr int NCH = 128;                 // chains per CTA
+constexpr int KCH = 64;                  // coefficient columns per chunk
+constexpr int CHB = NCH * KCH * 2;       // 16 KB: one chunk, hi or lo
+constexpr int XG = TT * 16;              // 1 KB: one 8-column group of X
+constexpr int KX_MAX = 384;              // basis columns held in shared memory
+constexpr int P_MAX = 416;               // ghat columns held in tensor memory (64 + 416 + 32 <= 512)
+constexpr int XBYTES = (KX_MAX / 8) * XG;  // 48 KB per hi / lo
+constexpr int WBYTES = NCH * TT * 2;       // 16 KB per hi / lo
+constexpr int SMEM = 2 * XBYTES + 4 * CHB + 2 * WBYTES;  // 192 KB
+constexpr int kThreads = 320;
+constexpr uint32_t kWaitLimit = 4000000u;
+constexpr uint32_t kDrainLimit = 4000000u;
+
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int b_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)b_mn_major << 16) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(mbar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(mbar)), "r"(bytes)
+               : "memory");
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          tc::smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(tc::smem_u32(mbar))
+      : "memory");
+}
+__device__ __forceinline__ void named_bar(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+// 8 floats -> 16 bytes of BF16 heads and 16 bytes of BF16 tails
+__device__ __forceinline__ void split8(const float (&v)[8], uint4& hi, uint4& lo) {
+  __nv_bfloat16 h[8], l[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    h[i] = __float2bfloat16_rn(v[i]);
+    l[i] = __float2bfloat16_rn(v[i] - __bfloat162float(h[i]));
+  }
+  hi = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
+  lo = make_uint4(pack2(l[0], l[1]), pack2(l[2], l[3]), pack2(l[4], l[5]), pack2(l[6], l[7]));
+}
+
+__device__ __forceinline__ int kx_of(const DevModel& m, int I) { return (m.P + m.m[I] + m.NL + 15) & ~15; }
+__device__ __forceinline__ int nkc_of(int kx) { return (kx + KCH - 1) / KCH; }
+
+// a16[((I * nCB + cb) * nKC + kc) * 2 + h] is one 16 KB chunk: element (chain n,
+// column q = 64 kc + ql) at (n/8) 1024 + (ql/8) 128 + (n%8) 16 + (ql%8) 2.
+__global__ void __launch_bounds__(256)
+    k_pack_bf16(DevModel m, const float* __restrict__ a32, unsigned char* __restrict__ a16, int B, int nCB, int nKC) {
+  const int I = blockIdx.x, cb = blockIdx.y, kc = blockIdx.z;
+  for (int e = threadIdx.x; e < NCH * (KCH / 8); e += blockDim.x) {
+    const int n = e % NCH, g = e / NCH;  // consecutive threads: consecutive chains
+    const int b = cb * NCH + n;
+    float v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int q = kc * KCH + 8 * g + i;
+      v[i] = (b < B && q < m.PM) ? a32[((size_t)I * B + b) * m.PM + q] : 0.f;
+    }
+    uint4 hi, lo;
+    split8(v, hi, lo);
+    const size_t base = ((size_t)((I * nCB + cb) * nKC + kc) * 2) * CHB;
+    const int off = (n >> 3) * 1024 + g * 128 + (n & 7) * 16;
+    *reinterpret_cast<uint4*>(a16 + base + off) = hi;
+    *reinterpret_cast<uint4*>(a16 + base + CHB + off) = lo;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_toa_bf16(DevModel m, const unsigned char* __restrict__ a16, float* __restrict__ gpart,
+               double* __restrict__ c2part, int32_t* __restrict__ stat, int B, int nCB, int nKCmax) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ float dts[TT], nis[TT];
+  __shared__ __align__(8) uint64_t full[2], empty[2], x_ready, d1_full, w_ready, x_free, drain;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int s_bad;
+  unsigned char* Xh = smem;
+  unsigned char* Xl = Xh + XBYTES;
+  unsigned char* Cs = Xl + XBYTES;  // slot s: hi at Cs + 2 s CHB, lo at + CHB
+  unsigned char* Wh = Cs + 4 * CHB;
+  unsigned char* Wl = Wh + WBYTES;
+
+  const int u = blockIdx.x, cb = blockIdx.y, b0 = cb * NCH, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int I = m.unit_psr[u], start = m.unit_start[u], len = m.unit_len[u];
+  const int P = m.P, na = m.na, mI = m.m[I], NL = m.NL;
+  const int KX = kx_of(m, I), nKC = nkc_of(KX), ntiles = len / TT;
+  const int NQ2 = (P + 15) & ~15;
+  const int nvalid = min(NCH, B - b0);
+  const float* Mg = m.M32 + m.m_off[I] + (long long)(start - m.toa_off[I]) * mI;
+  const float* Lg = m.Flo + m.flo_off[I] + (long long)(start - m.toa_off[I]) * NL;
+
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
+  if (tid == 0) {
+    tc::mbar_init(&full[0], 1);
+    tc::mbar_init(&full[1], 1);
+    tc::mbar_init(&empty[0], 1);
+    tc::mbar_init(&empty[1], 1);
+    tc::mbar_init(&x_ready, 1);
+    tc::mbar_init(&d1_full, 1);
+    tc::mbar_init(&w_ready, 1);
+    tc::mbar_init(&x_free, 1);
+    tc::mbar_init(&drain, 1);
+    s_bad = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_base;  // D1: columns [0, 64); D2: columns [64, 64 + NQ2)
+
+  // bounded wait that gives up at once when another role already has
+  auto wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+    if (s_bad) return false;
+    if (tc::mbar_wait(bar, parity, kWaitLimit)) return true;
+    s_bad = 1;
+    return false;
+  };
+
+  if (warp < 8) {
+    // ------------------------------------------------ basis generation + epilogue
+    double c2acc = 0.0;
+    for (int i = 0; i < ntiles; ++i) {
+      if (i > 0) wait(&x_free, (i - 1) & 1);  // GEMM2 of the previous tile has read X and W
+      const int ta = start + i * TT;
+      if (!s_bad) {
+        if (tid < TT) {
+          dts[tid] = m.dt[ta + tid];
+          nis[tid] = m.ninv[ta + tid];
+        }
+        const int t = tid & (TT - 1);
+        const uint64_t U = m.phase[ta + t];
+        const float wch = m.chrom[ta + t];
+        const float* Mrow = Mg + (long long)(i * TT + t) * mI;
+        const float* Lrow = Lg + (long long)(i * TT + t) * NL;
+        for (int g = tid >> 6; g < KX / 8; g += 4) {
+          float v[8];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int q = 8 * g + 2 * j;
+            if (q < P) {
+              const bool dm = q >= 2 * na;
+              const int k = dm ? (q - 2 * na) / 2 + 1 : q / 2 + 1;
+              float sn, cs;
+              sincos_turns64(U * (uint64_t)k, &sn, &cs);
+              const float wt = dm ? wch : 1.0f;
+              v[2 * j] = sn * wt;
+              v[2 * j + 1] = cs * wt;
+            } else {
+#pragma unroll
+              for (int f = 0; f < 2; ++f) {
+                const int qq = q + f - P;
+                v[2 * j + f] = qq < mI ? Mrow[qq] : (qq < mI + NL ? Lrow[qq - mI] : 0.f);
+              }
+            }
+          }
+          uint4 hi, lo;
+          split8(v, hi, lo);
+          const int off = g * XG + (t >> 3) * 128 + (t & 7) * 16;
+          *reinterpret_cast<uint4*>(Xh + off) = hi;
+          *reinterpret_cast<uint4*>(Xl + off) = lo;
+        }
+      }
+      tc::fence_async_smem();
+      named_bar(1, 256);
+      if (tid == 0) mbar_arrive(&x_ready);
+      if (warp < 4) {
+        // epilogue: thread n = chain b0 + n = tensor-memory lane n
+        // warp-uniform decision: tcgen05.ld is a .sync.aligned warp instruction
+        if (__all_sync(0xffffffffu, wait(&d1_full, i & 1))) {
+          tc::fence_after();
+          const int n = tid;
+          float q = 0.f;
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            uint32_t r[32];
+            tc::ld32(tmem + ((uint32_t)(32 * warp) << 16) + 32 * half, r);
+#pragma unroll
+            for (int g8 = 0; g8 < 4; ++g8) {
+              float wv[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const int t = 32 * half + 8 * g8 + j;
+                const float rr = dts[t] - __uint_as_float(r[8 * g8 + j]);
+                const float ww = rr * nis[t];
+                q = fmaf(rr, ww, q);
+                wv[j] = ww;
+              }
+              uint4 hi, lo;
+              split8(wv, hi, lo);
+              const int tg = 4 * half + g8;
+              const int off = (n >> 3) * 1024 + tg * 128 + (n & 7) * 16;
+              *reinterpret_cast<uint4*>(Wh + off) = hi;
+              *reinterpret_cast<uint4*>(Wl + off) = lo;
+            }
+          }
+          c2acc += (double)q;
+        }
+        tc::fence_async_smem();
+        tc::fence_before();
+        named_bar(2, 128);
+        if (tid == 0) mbar_arrive(&w_ready);
+      }
+    }
+    if (warp < 4) {
+      // ghat rows of this unit: D2 after the last GEMM2
+      const int n = tid;
+      if (__all_sync(0xffffffffu, ntiles > 0 && wait(&x_free, (ntiles - 1) & 1))) {
+        tc::fence_after();
+        for (int c0 = 0; c0 < NQ2; c0 += 32) {
+          uint32_t r[32];
+          tc::ld32(tmem + ((uint32_t)(32 * warp) << 16) + 64 + c0, r);
+          if (n < nvalid) {
+            float* dst = gpart + ((size_t)u * B + b0 + n) * m.Qs;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (c0 + j < P) dst[c0 + j] = __uint_as_float(r[j]);
+          }
+        }
+        if (n < nvalid) c2part[(size_t)u * B + b0 + n] = c2acc;
+      }
+      tc::fence_before();
+    }
+  } else if (warp == 8) {
+    // ------------------------------------------------ coefficient chunks (bulk copies)
+    int last_use[2] = {-1, -1};
+    const int nuse = ntiles * nKC;
+    for (int use = 0; use < nuse; ++use) {
+      if (lane == 0 && !s_bad) {
+        const int slot = use & 1;
+        bool ok = true;
+        if (use >= 2) ok = wait(&empty[slot], ((use >> 1) - 1) & 1);
+        if (ok) {
+          const int kc = use % nKC;
+          const unsigned char* src = a16 + ((size_t)((I * nCB + cb) * nKCmax + kc) * 2) * CHB;
+          unsigned char* dst = Cs + 2 * slot * CHB;
+          mbar_expect_tx(&full[slot], 2 * CHB);
+          bulk_g2s(dst, src, CHB, &full[slot]);
+          bulk_g2s(dst + CHB, src + CHB, CHB, &full[slot]);
+          last_use[slot] = use;
+        }
+      }
+      __syncwarp();
+    }
+    if (lane == 0)  // the copies this thread issued have landed before the CTA may exit
+      for (int s = 0; s < 2; ++s)
+        if (last_use[s] >= 0 && !tc::mbar_wait(&full[s], (last_use[s] >> 1) & 1, kDrainLimit)) s_bad = 1;
+    __syncwarp();
+  } else {
+    // ------------------------------------------------ MMA issue (warp 9, lane 0)
+    constexpr uint32_t ID1 = idesc_bf16(128, 64, 0);
+    int use = 0;
+    for (int i = 0; i < ntiles; ++i) {
+      if (lane == 0) {
+        if (wait(&x_ready, i & 1)) {
+          tc::fence_after();
+          for (int kc = 0; kc < nKC; ++kc, ++use) {
+            const int slot = use & 1;
+            if (!wait(&full[slot], (use >> 1) & 1)) break;
+            tc::fence_after();
+            const uint32_t ch = tc::smem_u32(Cs + 2 * slot * CHB), cl = ch + CHB;
+            const int nks = min(KCH / 16, (KX - kc * KCH) / 16);
+            for (int ks = 0; ks < nks; ++ks) {
+              const uint64_t ah = tc::desc(ch + ks * 256, 128, 1024), al = tc::desc(cl + ks * 256, 128, 1024);
+              const uint32_t xo = (uint32_t)(kc * 8 + ks * 2) * XG;
+              const uint64_t bh = tc::desc(tc::smem_u32(Xh) + xo, XG, 128);
+              const uint64_t bl = tc::desc(tc::smem_u32(Xl) + xo, XG, 128);
+              tc::mma_f16(tmem, ah, bh, ID1, (kc | ks) ? 1u : 0u);
+              tc::mma_f16(tmem, al, bh, ID1, 1u);
+              tc::mma_f16(tmem, ah, bl, ID1, 1u);
+            }
+            tc::commit(&empty[slot]);
+          }
+          tc::commit(&d1_full);
+          if (wait(&w_ready, i & 1)) {
+            tc::fence_after();
+            const uint32_t wh = tc::smem_u32(Wh), wl = tc::smem_u32(Wl);
+            for (int ks = 0; ks < TT / 16; ++ks) {
+              const uint64_t ah = tc::desc(wh + ks * 256, 128, 1024), al = tc::desc(wl + ks * 256, 128, 1024);
+              for (int q0 = 0; q0 < NQ2; q0 += 256) {
+                const int nq = min(256, NQ2 - q0);
+                const uint32_t id2 = idesc_bf16(128, nq, 1);
+                const uint32_t xo = (uint32_t)(q0 / 8) * XG + ks * 256;
+                const uint64_t bh = tc::desc(tc::smem_u32(Xh) + xo, 128, XG);
+                const uint64_t bl = tc::desc(tc::smem_u32(Xl) + xo, 128, XG);
+                const uint32_t d2 = tmem + 64 + q0;
+                tc::mma_f16(d2, ah, bh, id2, (i | ks) ? 1u : 0u);
+                tc::mma_f16(d2, al, bh, id2, 1u);
+                tc::mma_f16(d2, ah, bl, id2, 1u);
+              }
+            }
+            tc::commit(&x_free);
+          }
+        } else {
+          use += nKC;
+        }
+      }
+      __syncwarp();
+    }
+    if (lane == 0) {  // every MMA this thread issued has completed before the CTA may exit
+      tc::commit(&drain);
+      if (!tc::mbar_wait(&drain, 0, kDrainLimit)) s_bad = 1;
+    }
+    __syncwarp();
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (s_bad && tid < nvalid) atomicOr(&stat[b0 + tid], 4);
+  if (warp == 0) {
+    tc::fence_after();
+    tc::tmem_dealloc(tmem, 512);
+  }
+}
+
+}  // namespace
+
+bool bf16_supported(const DevModel& m) {
+  return m.P <= P_MAX && ((m.P + m.m_max + m.NL + 15) & ~15) <= KX_MAX && !m.cw;
+}
+
+size_t bf16_pack_bytes(const DevModel& m, int cap) {
+  const int nCB = (cap + NCH - 1) / NCH, nKC = ((m.P + m.m_max + m.NL + 15) / 16 * 16 + KCH - 1) / KCH;
+  return (size_t)m.npsr * nCB * nKC * 2 * CHB;
+}
+
+cudaError_t launch_toa_bf16(const DevModel& m, const Scratch& s, int B, cudaStream_t st) {
+  if (!bf16_supported(m) || !s.a16) return cudaErrorInvalidValue;
+  const int nCB = (B + NCH - 1) / NCH;
+  const int nKCmax = ((m.P + m.m_max + m.NL + 15) / 16 * 16 + KCH - 1) / KCH;
+  k_pack_bf16<<<dim3(m.npsr, nCB, nKCmax), 256, 0, st>>>(m, s.a32, s.a16, B, nCB, nKCmax);
+  cudaError_t e = cudaFuncSetAttribute(k_toa_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+  if (e != cudaSuccess) return e;
+  k_toa_bf16<<<dim3(m.n_units, nCB), kThreads, SMEM, st>>>(m, s.a16, s.gpart, s.c2part, s.stat, B, nCB, nKCmax);
+  return cudaGetLastError();
+}
+
+}  // namespace pta

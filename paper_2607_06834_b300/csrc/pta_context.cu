@@ -520,7 +520,7 @@ void free_scratch(pta::Scratch& s) {
   void* ptrs[] = {s.a32, s.a64, s.Lpk, s.Lipk, s.gpart, s.gpart64, s.c2part, s.ghat, s.chi2,
                   s.dlnk, s.dlnkd, s.dlnr, s.stat, s.sk, s.skd, s.srho, s.cwc, s.cwjac, s.cwsig,
                   s.cwbs, s.cwwt, s.cwgp, s.cwg, s.x0, s.g0, s.p, s.lp0, s.xs, s.gs, s.lps,
-                  s.step, s.imass, s.kin0, s.hmc_ctr, s.acc};
+                  s.step, s.imass, s.kin0, s.hmc_ctr, s.acc, s.a16};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   s = pta::Scratch{};
@@ -546,6 +546,7 @@ int ensure_scratch(pta_ctx* c, int B, bool fp64) {
 #define AL(ptr, n) \
   if (e == cudaSuccess) e = dalloc(&s.ptr, (size_t)(n));
   AL(a32, np * cap * m.PM);
+  if (pta::bf16_supported(m)) AL(a16, pta::bf16_pack_bytes(m, cap));
   AL(a64, np * cap * m.PM);
   AL(Lpk, (size_t)cap * std::max(1, m.n_chol) * tri);
   AL(Lipk, (size_t)cap * std::max(1, m.n_chol) * tri);
@@ -659,6 +660,8 @@ int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* gr
       e = pta::launch_toa_fp64(m, s, B, st);
     else if (c->precision == PTA_PREC_TF32X3 || c->precision == PTA_PREC_TF32)
       e = pta::launch_toa_tc(m, s, B, c->precision == PTA_PREC_TF32X3 ? 3 : 1, st);
+    else if (c->precision == PTA_PREC_BF16X3)
+      e = pta::launch_toa_bf16(m, s, B, st);
     else
       e = pta::launch_toa_fp32(m, s, B, st);
   }
@@ -705,8 +708,11 @@ int pta_layout(const pta_ctx* c, pta_layout_t* out) {
 int pta_set_precision(pta_ctx* c, int precision) {
   if (!c) return PTA_EINVAL;
   if (precision != PTA_PREC_FP64 && precision != PTA_PREC_FP32 && precision != PTA_PREC_TF32X3 &&
-      precision != PTA_PREC_TF32)
+      precision != PTA_PREC_TF32 && precision != PTA_PREC_BF16X3)
     return fail(c, PTA_EINVAL, "precision mode not available in this build");
+  if (precision == PTA_PREC_BF16X3 && c->finalized && !pta::bf16_supported(c->dm))
+    return fail(c, PTA_EINVAL,
+                "BF16 tensor-core path needs P <= 416, P + m_max + 2 (low bins) <= 384 and no CW signal");
   if ((precision == PTA_PREC_TF32X3 || precision == PTA_PREC_TF32) && c->finalized && (c->dm.P + 127) / 128 > 7)
     return fail(c, PTA_EINVAL, "tensor-core path supports at most 896 coefficients per pulsar");
   c->precision = precision;

@@ -83,6 +83,7 @@ struct DevModel {
 struct Scratch {
   int cap = 0;
   float* a32 = nullptr;        // [npsr][cap][PM]  (a, then timing-model offsets c)
+  unsigned char* a16 = nullptr; // BF16 hi/lo coefficient chunks in the tensor-core layout
   double* a64 = nullptr;       // [npsr][cap][PM]
   double* Lpk = nullptr;       // [cap][n_chol][np(np+1)/2]
   double* Lipk = nullptr;      // same, inverse factor
@@ -127,6 +128,9 @@ cudaError_t launch_prior_forward(const DevModel& m, const Scratch& s, int B, con
 cudaError_t launch_toa_fp32(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
 cudaError_t launch_toa_fp64(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
 cudaError_t launch_toa_tc(const DevModel& m, const Scratch& s, int B, int terms, cudaStream_t st);
+bool bf16_supported(const DevModel& m);
+size_t bf16_pack_bytes(const DevModel& m, int cap);
+cudaError_t launch_toa_bf16(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
 size_t cw_const_bytes();
 cudaError_t launch_cw_forward(const DevModel& m, const Scratch& s, int B, const float* x, cudaStream_t st);
 cudaError_t launch_cw_gradient(const DevModel& m, const Scratch& s, int B, cudaStream_t st);

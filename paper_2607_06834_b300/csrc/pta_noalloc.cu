@@ -77,6 +77,10 @@ extern "C" int pta_logp_and_grad_noalloc(pta_ctx* c, int B, const float* x, doub
     c->err = "logp_and_grad_noalloc: the continuous-wave model needs the allocating entry point";
     return PTA_EINVAL;
   }
+  if (c->precision == PTA_PREC_BF16X3) {
+    c->err = "logp_and_grad_noalloc: the BF16 tensor-core path needs the allocating entry point";
+    return PTA_EINVAL;
+  }
   if (c->precision == PTA_PREC_FP64 && !c->dm.F64) {
     c->err = "logp_and_grad_noalloc: the FP64 path needs the stored FP64 basis, which the allocating "
              "entry point builds on its first FP64 call";

@@ -9,9 +9,13 @@ namespace tc {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Shared-memory operand descriptor, no swizzle.  A K-major operand with R rows and
-// K columns of 32-bit elements is stored as core matrices of 8 rows x 16 bytes
-// (row r at +16 r); core matrix (r/8, k/4) sits at (r/8)*sbo + (k/4)*lbo.
+// Shared-memory operand descriptor, no swizzle.  Operands are stored as core
+// matrices of 8 rows x 16 bytes.  In both K-major and MN-major layouts, lbo is the
+// byte stride between core matrices adjacent along K and sbo the stride between
+// core matrices adjacent along M (or N).  K-major: the 16-byte rows run along K
+// (core matrix (r/8, k/4) of a 32-bit operand at (r/8) sbo + (k/4) lbo);
+// MN-major: they run along M (or N) and the 8 rows of a core matrix are 8 values
+// of K.
 __device__ __forceinline__ uint64_t desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFF);
@@ -40,6 +44,12 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void commit(uint64_t* mbar) {

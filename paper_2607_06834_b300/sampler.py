@@ -7,12 +7,12 @@ the CUDA library (one CUDA graph per batch size and trajectory length).  This
 module only chooses the step size and the diagonal inverse mass during warm-up
 and computes effective sample sizes from the stored draws:
 
-* step size: dual averaging of Hoffman & Gelman (2014, Sec. 3.2) on the mean
-  acceptance rate of all chains (one step size shared by the batch, jittered by
-  +-10 % per trajectory);
-* inverse mass: windowed estimates of the per-coordinate posterior variance,
-  pooled over chains, in windows that double in length (the scheme Stan and
-  NumPyro use), regularised towards 1e-3 as n/(n + 5);
+* step size: dual averaging of Hoffman & Gelman (2014, Sec. 3.2), one per chain
+  on that chain's accept indicators, jittered by +-10 % per trajectory;
+* inverse mass: windowed estimates of the per-coordinate posterior variance
+  (the median over chains of the within-chain variances, so that chains which
+  have not met, or one that is stuck, do not set it), in windows that double in
+  length (the scheme Stan and NumPyro use), regularised towards 1e-3 as n/(n + 5);
 * effective sample size: the multi-chain estimator with Geyer's initial
   monotone sequence (Geyer 1992; Vehtari et al. 2021, Sec. 3.2).
 """
@@ -101,31 +101,41 @@ def conditional_mode(engine, x: torch.Tensor, dz: int, iters: int = 100) -> torc
     g(z) = b - H z with H symmetric positive definite, and conjugate gradients
     solve H z = b chain by chain.  Each iteration takes a fresh gradient at z (the
     exact residual) and one at z + s p, s = 1 / rms(p), for H p = (g(z) - g(z + s p)) / s
-    (exact for a quadratic up to rounding); beta is Fletcher-Reeves."""
+    (exact for a quadratic up to rounding); beta is Fletcher-Reeves.  A chain whose
+    step does not raise log p (rounding in the FP32 gradients) keeps its last point
+    and stops."""
     x = x.clone().contiguous()
-
-    def gz(xx):
-        _, g, st = engine.logp_and_grad(xx)
-        return g[:, :dz].double(), st
-
-    r, st0 = gz(x)
-    ok = (st0 == 0)
+    lp, g, st = engine.logp_and_grad(x)
+    r = g[:, :dz].double()
+    active = (st == 0)
     p = r.clone()
     rr = (r * r).sum(1)
+    lp = lp.double()
     for it in range(iters):
+        if not bool(active.any()):
+            break
         sc = 1.0 / (p * p).mean(1).sqrt().clamp_min(1e-30)
         xp = x.clone()
         xp[:, :dz] += (sc[:, None] * p).float()
-        gp, _ = gz(xp)
-        Hp = (r - gp) / sc[:, None]
+        _, gp, _ = engine.logp_and_grad(xp)
+        Hp = (r - gp[:, :dz].double()) / sc[:, None]
         pHp = (p * Hp).sum(1)
-        alpha = torch.where((pHp > 0) & ok, rr / pHp.clamp_min(1e-300), torch.zeros_like(rr))
-        x[:, :dz] += (alpha[:, None] * p).float()
-        r, _ = gz(x)
-        rr_new = (r * r).sum(1)
+        ok = active & (pHp > 0)
+        alpha = torch.where(ok, rr / pHp.clamp_min(1e-300), torch.zeros_like(rr))
+        xn = x.clone()
+        xn[:, :dz] += (alpha[:, None] * p).float()
+        lpn, gn, stn = engine.logp_and_grad(xn)
+        better = ok & (stn == 0) & (lpn.double() > lp)
+        x = torch.where(better[:, None], xn, x)
+        lp = torch.where(better, lpn.double(), lp)
+        rn = gn[:, :dz].double()
+        rr_new = (rn * rn).sum(1)
         beta = rr_new / rr.clamp_min(1e-300)
-        p = r + beta[:, None] * p
-        rr = rr_new
+        pn = rn + beta[:, None] * p
+        r = torch.where(better[:, None], rn, r)
+        p = torch.where(better[:, None], pn, p)
+        rr = torch.where(better, rr_new, rr)
+        active = better
     return x
 
 
@@ -133,33 +143,35 @@ def conditional_mode(engine, x: torch.Tensor, dz: int, iters: int = 100) -> torc
 # warm-up adaptation
 # ---------------------------------------------------------------------------
 class DualAveraging:
-    """Step-size adaptation of Hoffman & Gelman (2014), Sec. 3.2, on log(eps)."""
+    """Step-size adaptation of Hoffman & Gelman (2014), Sec. 3.2, on log(eps); one
+    independent adaptation per chain (arrays of length B)."""
 
-    def __init__(self, eps0: float, target: float = 0.8, gamma: float = 0.05, t0: float = 10.0,
+    def __init__(self, eps0, target: float = 0.8, gamma: float = 0.05, t0: float = 10.0,
                  kappa: float = 0.75):
         self.target, self.gamma, self.t0, self.kappa = target, gamma, t0, kappa
         self.restart(eps0)
 
-    def restart(self, eps0: float):
-        self.mu = math.log(10.0 * eps0)
-        self.hbar = 0.0
-        self.log_eps = math.log(eps0)
-        self.log_eps_bar = 0.0
+    def restart(self, eps0):
+        eps0 = np.asarray(eps0, dtype=np.float64)
+        self.mu = np.log(10.0 * eps0)
+        self.hbar = np.zeros_like(eps0)
+        self.log_eps = np.log(eps0)
+        self.log_eps_bar = np.zeros_like(eps0)
         self.m = 0
 
-    def update(self, accept_rate: float) -> float:
+    def update(self, accept):
         self.m += 1
         m = self.m
         w = 1.0 / (m + self.t0)
-        self.hbar = (1.0 - w) * self.hbar + w * (self.target - accept_rate)
+        self.hbar = (1.0 - w) * self.hbar + w * (self.target - np.asarray(accept, dtype=np.float64))
         self.log_eps = self.mu - math.sqrt(m) / self.gamma * self.hbar
         eta = m ** (-self.kappa)
         self.log_eps_bar = eta * self.log_eps + (1.0 - eta) * self.log_eps_bar
-        return math.exp(self.log_eps)
+        return np.exp(self.log_eps)
 
     @property
-    def final(self) -> float:
-        return math.exp(self.log_eps_bar)
+    def final(self):
+        return np.exp(self.log_eps_bar)
 
 
 def warmup_schedule(n: int, init: int = 15, term: int = 10, base: int = 25) -> list[tuple[int, int]]:
@@ -219,31 +231,32 @@ def run_hmc(engine, x0: torch.Tensor, n_warmup: int, n_samples: int, n_leapfrog:
         raise ValueError("initial points outside the prior support")
     init_lp = float(logp.mean())
     inv_mass = torch.ones(D, dtype=torch.float32, device=dev)
-    da = DualAveraging(eps0, target=target_accept)
-    eps = eps0
+    da = DualAveraging(np.full(B, eps0), target=target_accept)
+    eps = np.full(B, eps0)
     rng = np.random.default_rng(seed)
     step = torch.empty(B, dtype=torch.float32, device=dev)
     windows = warmup_schedule(n_warmup)
     wi = 0
-    s1 = torch.zeros(D, dtype=torch.float64, device=dev)
-    s2 = torch.zeros(D, dtype=torch.float64, device=dev)
+    s1 = torch.zeros((B, D), dtype=torch.float64, device=dev)
+    s2 = torch.zeros((B, D), dtype=torch.float64, device=dev)
     cnt = 0
     it = 0
     for i in range(n_warmup):
-        step.fill_(eps * (1.0 + jitter * (2.0 * rng.random() - 1.0)))
+        step.copy_(torch.tensor(eps * (1.0 + jitter * (2.0 * rng.random(B) - 1.0)), dtype=torch.float32))
         acc = engine.hmc_trajectory(x, logp, grad, step, n_leapfrog, seed, it, inv_mass=inv_mass)
         it += 1
-        rate = float(acc.float().mean())
-        eps = da.update(rate)
+        eps = da.update(acc.cpu().numpy())
         if wi < len(windows) and windows[wi][0] <= i < windows[wi][1]:
             xd = x.double()
-            s1 += xd.sum(0)
-            s2 += (xd * xd).sum(0)
-            cnt += B
+            s1 += xd
+            s2 += xd * xd
+            cnt += 1
             if i == windows[wi][1] - 1:
+                # within-chain variance, averaged over chains (chains that have not
+                # met yet must not inflate it with their spread)
                 mean = s1 / cnt
-                var = (s2 / cnt - mean * mean).clamp_min(0.0) * cnt / max(cnt - 1, 1)
-                n = cnt / B  # iterations in the window (draws of one chain)
+                var = ((s2 / cnt - mean * mean).clamp_min(0.0) * cnt / max(cnt - 1, 1)).median(0).values
+                n = cnt * B  # draws behind the estimate
                 var = (n / (n + 5.0)) * var + 1e-3 * (5.0 / (n + 5.0))
                 inv_mass = var.float().contiguous()
                 s1.zero_()
@@ -259,14 +272,18 @@ def run_hmc(engine, x0: torch.Tensor, n_warmup: int, n_samples: int, n_leapfrog:
     draws = torch.empty((n_samples, B, K), dtype=torch.float32, device=dev)
     accs = torch.zeros(B, dtype=torch.float64, device=dev)
     for j in range(n_samples):
-        step.fill_(eps * (1.0 + jitter * (2.0 * rng.random() - 1.0)))
+        step.copy_(torch.tensor(eps * (1.0 + jitter * (2.0 * rng.random(B) - 1.0)), dtype=torch.float32))
         acc = engine.hmc_trajectory(x, logp, grad, step, n_leapfrog, seed, it, inv_mass=inv_mass)
         it += 1
         accs += acc.double()
         draws[j].copy_(x[:, rec])
     t_end = timer()
     d = draws.permute(1, 0, 2).cpu().numpy()
-    return HMCResult(draws=d, accept_rate=float(accs.mean()) / max(n_samples, 1), step=eps,
+    chain_rate = (accs / max(n_samples, 1)).cpu().numpy()
+    return HMCResult(draws=d, accept_rate=float(chain_rate.mean()), step=float(np.median(eps)),
                      inv_mass=inv_mass.cpu().numpy(), warmup_s=t_warm - t_start, sampling_s=t_end - t_warm,
                      trajectories=n_warmup + n_samples, leapfrog=n_leapfrog,
-                     stats={"final_logp_mean": float(logp.mean()), "init_logp_mean": init_lp})
+                     stats={"final_logp_mean": float(logp.mean()), "init_logp_mean": init_lp,
+                            "chain_accept_min": float(chain_rate.min()),
+                            "stuck_chains": int((chain_rate < 0.05).sum()),
+                            "step_min": float(eps.min()), "step_max": float(eps.max())})

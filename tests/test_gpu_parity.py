@@ -25,7 +25,11 @@ pytestmark = pytest.mark.gpu
 LOGP_ABS = 1e-3
 GRAD_REL = 1e-4
 FP64_REL = 1e-9
-REL_RANDOM = {"fp32": 8 * 2.0 ** -24, "tf32x3": 8 * 2.0 ** -21}
+REL_RANDOM = {"fp32": 8 * 2.0 ** -24, "tf32x3": 8 * 2.0 ** -21, "bf16x3": 8 * 2.0 ** -15}
+# BF16 3-term split (reported precision): each operand keeps ~16 significant bits
+# (8-bit head + 8-bit tail), so products carry ~2^-15 relative error
+BF16_REPORTED_LOGP = 0.05
+BF16_REPORTED_GRAD = 1e-2
 
 
 def _engine(arr, prec):
@@ -168,6 +172,31 @@ def test_ng15_batch256_sampled(ng15, prec):
     assert lp1[0] == lp[200] and np.array_equal(g1[0], g[200])
 
 
+@pytest.mark.parametrize("kw", RAGGED)
+@pytest.mark.parametrize("B", [70, 130])
+def test_ragged_arrays_bf16x3(kw, B):
+    """BF16 tensor-core path (reported precision) on ragged arrays: a partial block of
+    128 chains, and two blocks with a partial second one."""
+    arr = synth.small_array(**kw)
+    orc = O.Oracle(arr)
+    X = synth.make_points(arr, B, seed=5)
+    X[:4] = np.array([O.curn_point(orc, x.astype(np.float64), 1.0, seed=i) for i, x in enumerate(X[:4])])
+    sample = list(range(4)) + [B // 2, B - 1]
+    lo, go = _oracle(orc, X[sample])
+    eng = _engine(arr, "bf16x3")
+    lp, g, st = _eval(eng, X)
+    assert np.all(st == 0) and np.all(np.isfinite(lp))
+    err = np.abs(lp[sample] - lo)
+    rel = _grad_rel(g[sample], go)
+    print(f"bf16x3 ragged B={B}: max |dlogp| near {err[:4].max():.2e} random {err[4:].max():.2e}; "
+          f"max grad rel {rel.max():.2e}")
+    assert np.all(err <= BF16_REPORTED_LOGP + REL_RANDOM["bf16x3"] * np.abs(lo))
+    assert np.max(rel) < BF16_REPORTED_GRAD
+    # batch independence
+    lp1, g1, _ = _eval(eng, X[B - 1:B])
+    assert lp1[0] == lp[B - 1] and np.array_equal(g1[0], g[B - 1])
+
+
 TC_REPORTED_LOGP = 0.05   # tensor-core variants: error reported, bound set from the
 TC_REPORTED_GRAD = 1e-3   # FP32-accumulation truncation analysis (not the FP32 target)
 
@@ -195,6 +224,13 @@ def test_tensor_core_paths_against_simt(ng15):
           f"tf32 {abs(lp1[3]-lo[0]):.2e}; grad rel fp32 {_grad_rel(g32[3], go[0]):.2e} "
           f"tf32x3 {_grad_rel(g3[3], go[0]):.2e} tf32 {_grad_rel(g1[3], go[0]):.2e}")
     assert abs(lp3[3] - lo[0]) < TC_REPORTED_LOGP and _grad_rel(g3[3], go[0]) < TC_REPORTED_GRAD
+    eng.set_precision("bf16x3")
+    lpb, gb, stb = _eval(eng, X)
+    assert np.all(stb == 0) and np.all(np.isfinite(lpb))
+    print(f"bf16x3: near-posterior |dlogp| {abs(lpb[3]-lo[0]):.2e} grad rel {_grad_rel(gb[3], go[0]):.2e}; "
+          f"max |dlogp| vs fp32 over 70 chains {np.max(np.abs(lpb - lp32)):.2e}")
+    assert np.all(np.abs(lpb - lp32) <= BF16_REPORTED_LOGP + REL_RANDOM["bf16x3"] * np.abs(lp32))
+    assert abs(lpb[3] - lo[0]) < BF16_REPORTED_LOGP and _grad_rel(gb[3], go[0]) < BF16_REPORTED_GRAD
 
 
 # ------------------------------------------------------------------ continuous-wave signal
