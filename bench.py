@@ -31,6 +31,11 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "ng15_b256"
 WORKLOAD_DESC = "NANOGrav-15-yr-like: 67 pulsars, 3.0e5 TOAs, RN 30 / DM 100 / HD-GWB 14 bins, 256 chains"
 METRIC = "logp+grad evals/s (all chains) at 67-psr size vs FP64 plain path; % roofline"
+DTYPE = {"fp32": "f32", "fp64": "f64", "tf32x3": "tf32x3", "tf32": "tf32", "bf16x3": "bf16x3"}
+DTYPE_DETAIL = {"fp32": "FP32 TOA contractions (SIMT)", "fp64": "FP64 TOA contractions (stored basis)",
+                "tf32x3": "3-term split TF32 tensor-core TOA contractions, FP32 accumulation",
+                "tf32": "single TF32 tensor-core TOA contractions, FP32 accumulation",
+                "bf16x3": "3-term split BF16 tensor-core TOA contractions, FP32 accumulation"}
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12     # SMs x 2 FP64 FMA/clk x 2 flop x max SM clock
 
@@ -259,6 +264,12 @@ def run_ours(args):
     X = synth.make_points(arr, B, seed=6834 + 2 + 1000 * rank)
     eng = Engine(arr, precision=args.precision)
     D = eng.D
+    tuned = None
+    if args.precision == "fp32":  # the autotuner picks the SIMT tile shape (setup, not timed)
+        from paper_2607_06834_b300.engine import toa_config_info
+        chosen, table = eng.autotune(B)
+        tuned = {"entry": chosen, **toa_config_info(chosen),
+                 "candidates_ms": {str(k): round(v, 4) for k, v in sorted(table.items())}}
     dev = torch.device("cuda", local)
     x = torch.tensor(X, device=dev)
     logp = torch.empty(B, dtype=torch.float64, device=dev)
@@ -314,9 +325,17 @@ def run_ours(args):
                 "unit": "TFLOP/s", "achieved": flops / (stage_ms[dom] * 1e-3) / 1e12, "peak": tf32_peak,
                 "peak_source": "measured bf16 burst x nominal TF32/BF16 ratio 1.1/2.25",
                 "pipe_terms": terms}
+    elif abi.STAGES[dom] == "toa" and args.precision == "bf16x3":
+        flops = toa_flops_per_launch(arr, B)
+        roof = {"kernel": "k_toa_bf16 (TOA contractions, tcgen05 kind::f16, 3-term BF16 split)",
+                "bound": "tensor", "unit": "TFLOP/s", "achieved": flops / (stage_ms[dom] * 1e-3) / 1e12,
+                "peak": (peaks or {}).get("bf16_tflops", 1800.0),
+                "peak_source": "measured bf16 burst (cuBLAS)", "pipe_terms": 3}
     elif abi.STAGES[dom] == "toa":
         flops = toa_flops_per_launch(arr, B)
-        roof = {"kernel": "k_toa_simt (TOA contractions)", "bound": "alu", "unit": "TFLOP/s",
+        shape = f"<{tuned['chains_per_cta']},{tuned['toas_per_tile']},{tuned['rows_per_thread']},{tuned['order']}>" \
+            if tuned else ""
+        roof = {"kernel": f"k_toa_simt{shape} (TOA contractions)", "bound": "alu", "unit": "TFLOP/s",
                 "achieved": flops / (stage_ms[dom] * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
                 "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 flop x 2.032 GHz"}
     else:
@@ -376,11 +395,12 @@ def run_ours(args):
         hmc["control_small_array"] = hmc_ess_tiny(dev)
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32",
-            "dtype_detail": "FP32 TOA contractions; FP64 Cholesky, log-det, timing-model solve and sums",
+            "vs_baseline": None, "dtype": DTYPE[args.precision],
+            "dtype_detail": DTYPE_DETAIL[args.precision] + "; FP64 Cholesky, log-det, timing-model solve and sums",
             "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC, "chains_per_gpu": B, "ntoa": arr.ntoa, "npsr": arr.npsr,
-                       "precision": args.precision, "l2": "flushed between timed steps (512 MB write)"},
+                       "precision": args.precision, "l2": "flushed between timed steps (512 MB write)",
+                       "toa_kernel_autotuned": tuned},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": world * B / (e2e_ms * 1e-3), "unit": "evals/s",
                     "h2d_bytes_per_step": int(B * D * 4), "d2h_bytes_per_step": int(B * 8 + B * D * 4)},

@@ -112,6 +112,21 @@ int pta_layout(const pta_ctx* ctx, pta_layout_t* out);
  * low-frequency columns (the 4 lowest achromatic and 4 lowest DM bins).  The
  * continuous-wave model runs only with PTA_PREC_FP32. */
 int pta_set_precision(pta_ctx* ctx, int precision);
+/* Autotuner of the FP32 TOA kernel's tile shape (no counterpart in the paper).
+ * Times every table entry that can run this model (chains per CTA, TOAs per tile,
+ * ghat rows per thread, instruction order) on B chains, three launches each after
+ * one warm-up, on `stream` with CUDA events, and keeps the fastest for later calls.
+ * Needs PTA_PREC_FP32 (PTA_EINVAL otherwise).  Overwrites the context's scratch
+ * coefficients (it is not an evaluation) and synchronises `stream`.  `ms`, if not
+ * NULL, receives the mean time per launch of entry i (-1 for entries that cannot
+ * run) for i < n_ms; `chosen` the selected entry.  Recaptures HMC graphs lazily. */
+int pta_autotune(pta_ctx* ctx, int B, void* stream, int* chosen, double* ms, int n_ms);
+/* Force TOA kernel table entry `cfg` (-1: the untuned default).  PTA_EINVAL if the
+ * entry cannot run this model. */
+int pta_set_toa_config(pta_ctx* ctx, int cfg);
+/* Shape of table entry cfg: chains per CTA, TOAs per tile, ghat rows per thread,
+ * instruction order.  PTA_EINVAL past the end of the table (use it to count). */
+int pta_toa_config_info(int cfg, int* bc, int* tt, int* qpt, int* order);
 /* Hyper-prior box for (log10 A, gamma) of the GWB, red noise and DM (Sec.
  * "Priors": log10 A ~ U(-20,-10), gamma ~ U(0,7) by default). */
 int pta_set_hyperprior(pta_ctx* ctx, double log10a_lo, double log10a_hi,

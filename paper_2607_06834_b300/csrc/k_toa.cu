@@ -155,7 +155,12 @@ size_t simt_smem(const DevModel& m) {
                           (size_t)TT * C::WS + (size_t)C::RG * BC + 2 * TT);
 }
 
-template <int BC, int TT, int QPT>
+// ORD selects the instruction order of the two register-blocked products:
+//   0: F a unrolled by 2 along the coefficient index; F^T w as nested FMAs over the
+//      four TOAs of a step (one dependent chain of 4 per accumulator);
+//   1: F a unrolled by 4; F^T w with the four TOAs outermost, so every FMA of a
+//      TOA is independent of the others (longer register lifetimes, no chains).
+template <int BC, int TT, int QPT, int ORD>
 __global__ void __launch_bounds__(kThreads, 1)
     k_toa_simt(DevModel m, const float* __restrict__ a32, float* __restrict__ gpart, double* __restrict__ c2part,
                int B, int XR, const float* __restrict__ cwsig, float* __restrict__ cwwt) {
@@ -232,7 +237,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int j = 0; j < 4; ++j) y[r][j] = 0.f;
     const float* xrow = Xs + rg * C::RPT;
     const float* arow = As + 4 * cg;
-#pragma unroll 2
+#pragma unroll(ORD == 0 ? 2 : 4)
     for (int p = 0; p < KA; ++p) {
       const float4 av = *reinterpret_cast<const float4*>(arow + p * C::AS);
       float fv[C::RPT];
@@ -292,13 +297,30 @@ __global__ void __launch_bounds__(kThreads, 1)
       float4 wv[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) wv[r] = *reinterpret_cast<const float4*>(Ws + (t + r) * C::WS + 4 * cg);
+      if constexpr (ORD == 0) {
 #pragma unroll
-      for (int i = 0; i < QPT; ++i) {
-        const float4 xv = *reinterpret_cast<const float4*>(Xs + (rg + C::RG * i) * C::XS + t);
-        acc[i][0] = fmaf(xv.x, wv[0].x, fmaf(xv.y, wv[1].x, fmaf(xv.z, wv[2].x, fmaf(xv.w, wv[3].x, acc[i][0]))));
-        acc[i][1] = fmaf(xv.x, wv[0].y, fmaf(xv.y, wv[1].y, fmaf(xv.z, wv[2].y, fmaf(xv.w, wv[3].y, acc[i][1]))));
-        acc[i][2] = fmaf(xv.x, wv[0].z, fmaf(xv.y, wv[1].z, fmaf(xv.z, wv[2].z, fmaf(xv.w, wv[3].z, acc[i][2]))));
-        acc[i][3] = fmaf(xv.x, wv[0].w, fmaf(xv.y, wv[1].w, fmaf(xv.z, wv[2].w, fmaf(xv.w, wv[3].w, acc[i][3]))));
+        for (int i = 0; i < QPT; ++i) {
+          const float4 xv = *reinterpret_cast<const float4*>(Xs + (rg + C::RG * i) * C::XS + t);
+          acc[i][0] = fmaf(xv.x, wv[0].x, fmaf(xv.y, wv[1].x, fmaf(xv.z, wv[2].x, fmaf(xv.w, wv[3].x, acc[i][0]))));
+          acc[i][1] = fmaf(xv.x, wv[0].y, fmaf(xv.y, wv[1].y, fmaf(xv.z, wv[2].y, fmaf(xv.w, wv[3].y, acc[i][1]))));
+          acc[i][2] = fmaf(xv.x, wv[0].z, fmaf(xv.y, wv[1].z, fmaf(xv.z, wv[2].z, fmaf(xv.w, wv[3].z, acc[i][2]))));
+          acc[i][3] = fmaf(xv.x, wv[0].w, fmaf(xv.y, wv[1].w, fmaf(xv.z, wv[2].w, fmaf(xv.w, wv[3].w, acc[i][3]))));
+        }
+      } else {
+        float4 xv[QPT];
+#pragma unroll
+        for (int i = 0; i < QPT; ++i) xv[i] = *reinterpret_cast<const float4*>(Xs + (rg + C::RG * i) * C::XS + t);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+#pragma unroll
+          for (int i = 0; i < QPT; ++i) {
+            const float xr = r == 0 ? xv[i].x : (r == 1 ? xv[i].y : (r == 2 ? xv[i].z : xv[i].w));
+            acc[i][0] = fmaf(xr, wv[r].x, acc[i][0]);
+            acc[i][1] = fmaf(xr, wv[r].y, acc[i][1]);
+            acc[i][2] = fmaf(xr, wv[r].z, acc[i][2]);
+            acc[i][3] = fmaf(xr, wv[r].w, acc[i][3]);
+          }
+        }
       }
     }
   }
@@ -385,18 +407,85 @@ __global__ void __launch_bounds__(128)
   }
 }
 
-template <int BC, int TT, int QPT>
+template <int BC, int TT, int QPT, int ORD>
 cudaError_t launch_simt(const DevModel& m, const Scratch& s, int B, cudaStream_t st) {
   const size_t sm = simt_smem<BC, TT, QPT>(m);
   if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(k_toa_simt<BC, TT, QPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_toa_simt<BC, TT, QPT, ORD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   dim3 grid(m.n_units, (B + BC - 1) / BC);
-  k_toa_simt<BC, TT, QPT><<<grid, kThreads, sm, st>>>(m, s.a32, s.gpart, s.c2part, B, simt_xrows<BC, TT, QPT>(m),
-                                                        m.cw ? s.cwsig : nullptr, m.cw ? s.cwwt : nullptr);
+  k_toa_simt<BC, TT, QPT, ORD><<<grid, kThreads, sm, st>>>(m, s.a32, s.gpart, s.c2part, B,
+                                                             simt_xrows<BC, TT, QPT>(m), m.cw ? s.cwsig : nullptr,
+                                                             m.cw ? s.cwwt : nullptr);
   return cudaGetLastError();
 }
 
+// The tile shapes the autotuner chooses from: chains per CTA (BC), TOAs per tile
+// (TT), ghat rows per thread (QPT; 256 / (BC / 4) q lanes x QPT rows must cover P)
+// and the instruction order (ORD).
+struct SimtEntry {
+  int bc, tt, qpt, ord;
+  cudaError_t (*launch)(const DevModel&, const Scratch&, int, cudaStream_t);
+  size_t (*smem)(const DevModel&);
+};
+#define SIMT_E(BC, TT, Q, O) {BC, TT, Q, O, &launch_simt<BC, TT, Q, O>, &simt_smem<BC, TT, Q>}
+#define SIMT_Q16(BC, TT, O) \
+  SIMT_E(BC, TT, 2, O), SIMT_E(BC, TT, 4, O), SIMT_E(BC, TT, 8, O), SIMT_E(BC, TT, 12, O), SIMT_E(BC, TT, 17, O), \
+      SIMT_E(BC, TT, 24, O)
+#define SIMT_Q32(BC, TT, O)                                                                                      \
+  SIMT_E(BC, TT, 1, O), SIMT_E(BC, TT, 2, O), SIMT_E(BC, TT, 4, O), SIMT_E(BC, TT, 6, O), SIMT_E(BC, TT, 9, O), \
+      SIMT_E(BC, TT, 12, O), SIMT_E(BC, TT, 16, O), SIMT_E(BC, TT, 20, O)
+const SimtEntry kSimt[] = {SIMT_Q16(64, 64, 0), SIMT_Q16(64, 64, 1), SIMT_Q16(64, 32, 0), SIMT_Q16(64, 32, 1),
+                           SIMT_Q32(32, 64, 0), SIMT_Q32(32, 64, 1), SIMT_Q32(32, 32, 0), SIMT_Q32(32, 32, 1)};
+constexpr int kNSimt = sizeof(kSimt) / sizeof(kSimt[0]);
+
+int simt_rows(const SimtEntry& e) { return (kThreads / (e.bc / 4)) * e.qpt; }
+
+// usable for this model: ghat rows covered, fits in shared memory, and the
+// smallest QPT of its (BC, TT, ORD) family that covers P
+bool simt_usable(const DevModel& m, int i) {
+  const SimtEntry& e = kSimt[i];
+  if (simt_rows(e) < m.P || e.smem(m) > 227 * 1024) return false;
+  for (int j = 0; j < kNSimt; ++j) {
+    const SimtEntry& f = kSimt[j];
+    if (f.bc == e.bc && f.tt == e.tt && f.ord == e.ord && f.qpt < e.qpt && simt_rows(f) >= m.P) return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+int simt_count() { return kNSimt; }
+int simt_info(int i, int* bc, int* tt, int* qpt, int* ord) {
+  if (i < 0 || i >= kNSimt) return -1;
+  *bc = kSimt[i].bc;
+  *tt = kSimt[i].tt;
+  *qpt = kSimt[i].qpt;
+  *ord = kSimt[i].ord;
+  return 0;
+}
+bool simt_valid(const DevModel& m, int i) { return i >= 0 && i < kNSimt && simt_usable(m, i); }
+
+// default before tuning: 64 chains x 64 TOAs, nested order, smallest QPT covering P;
+// 32 x 32 when that does not fit
+int simt_default(const DevModel& m) {
+  for (int pass = 0; pass < 2; ++pass)
+    for (int i = 0; i < kNSimt; ++i) {
+      const SimtEntry& e = kSimt[i];
+      const bool shape = pass == 0 ? (e.bc == 64 && e.tt == 64) : (e.bc == 32 && e.tt == 32);
+      if (shape && e.ord == 0 && simt_usable(m, i)) return i;
+    }
+  return -1;
+}
+
+cudaError_t launch_toa_fp32_cfg(const DevModel& m, const Scratch& s, int B, int cfg, cudaStream_t st) {
+  if (cfg < 0) cfg = simt_default(m);
+  if (!simt_valid(m, cfg)) return cudaErrorInvalidValue;
+  return kSimt[cfg].launch(m, s, B, st);
+}
+
+namespace {
 }  // namespace
 
 cudaError_t launch_tm_prologue(const DevModel& m, const Scratch& s, int B, int fp64, cudaStream_t st) {
@@ -410,16 +499,7 @@ cudaError_t launch_tm_prologue(const DevModel& m, const Scratch& s, int B, int f
 }
 
 cudaError_t launch_toa_fp32(const DevModel& m, const Scratch& s, int B, cudaStream_t st) {
-  // BC = 64 chains per CTA, 16 q lanes: ghat rows covered = 16 * QPT
-  if (m.P <= 32) return launch_simt<64, 64, 2>(m, s, B, st);
-  if (m.P <= 64) return launch_simt<64, 64, 4>(m, s, B, st);
-  if (m.P <= 128) return launch_simt<64, 64, 8>(m, s, B, st);
-  if (m.P <= 192) return launch_simt<64, 64, 12>(m, s, B, st);
-  if (m.P <= 272) return launch_simt<64, 64, 17>(m, s, B, st);
-  if (m.P <= 384) return launch_simt<64, 64, 24>(m, s, B, st);
-  if (m.P <= 512) return launch_simt<32, 32, 16>(m, s, B, st);
-  if (m.P <= 640) return launch_simt<32, 32, 20>(m, s, B, st);
-  return cudaErrorInvalidValue;
+  return launch_toa_fp32_cfg(m, s, B, -1, st);
 }
 
 cudaError_t launch_toa_fp64(const DevModel& m, const Scratch& s, int B, cudaStream_t st) {

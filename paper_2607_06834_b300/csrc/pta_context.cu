@@ -663,7 +663,7 @@ int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* gr
     else if (c->precision == PTA_PREC_BF16X3)
       e = pta::launch_toa_bf16(m, s, B, st);
     else
-      e = pta::launch_toa_fp32(m, s, B, st);
+      e = pta::launch_toa_fp32_cfg(m, s, B, c->toa_cfg, st);
   }
   tm.end(1);
   tm.begin(2);
@@ -716,6 +716,87 @@ int pta_set_precision(pta_ctx* c, int precision) {
   if ((precision == PTA_PREC_TF32X3 || precision == PTA_PREC_TF32) && c->finalized && (c->dm.P + 127) / 128 > 7)
     return fail(c, PTA_EINVAL, "tensor-core path supports at most 896 coefficients per pulsar");
   c->precision = precision;
+  return PTA_OK;
+}
+
+int pta_toa_config_info(int cfg, int* bc, int* tt, int* qpt, int* order) {
+  int b, t, q, o;
+  if (pta::simt_info(cfg, &b, &t, &q, &o) != 0) return PTA_EINVAL;
+  if (bc) *bc = b;
+  if (tt) *tt = t;
+  if (qpt) *qpt = q;
+  if (order) *order = o;
+  return PTA_OK;
+}
+
+static void drop_graphs(pta_ctx* c) {
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+}
+
+int pta_set_toa_config(pta_ctx* c, int cfg) {
+  if (!c) return PTA_EINVAL;
+  if (!c->finalized) return fail(c, PTA_ESTATE, "context not finalized");
+  if (cfg != -1 && !pta::simt_valid(c->dm, cfg))
+    return fail(c, PTA_EINVAL, "TOA kernel configuration " + std::to_string(cfg) + " cannot run this model");
+  if (cfg != c->toa_cfg) drop_graphs(c);
+  c->toa_cfg = cfg;
+  return PTA_OK;
+}
+
+int pta_autotune(pta_ctx* c, int B, void* stream, int* chosen, double* ms, int n_ms) {
+  if (!c) return PTA_EINVAL;
+  if (B <= 0) return fail(c, PTA_EINVAL, "autotune: B must be positive");
+  if (c->precision != PTA_PREC_FP32) return fail(c, PTA_EINVAL, "autotune tunes the FP32 TOA kernel (PTA_PREC_FP32)");
+  int rc = pta_prepare_internal(c, B);
+  if (rc != PTA_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const pta::DevModel& m = c->dm;
+  const pta::Scratch& s = c->sc;
+  // the kernel's running time does not depend on the values: time it on zeroed
+  // coefficients (and signal), which also keeps every intermediate finite
+  cudaError_t e = cudaMemsetAsync(s.a32, 0, sizeof(float) * (size_t)m.npsr * B * m.PM, st);
+  if (e == cudaSuccess && m.cw) e = cudaMemsetAsync(s.cwsig, 0, sizeof(float) * (size_t)B * m.ntoa_pad, st);
+  if (e != cudaSuccess) return fail(c, PTA_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = -1;
+  float best_ms = 0.f;
+  const int n = pta::simt_count();
+  for (int i = 0; i < n; ++i) {
+    float t = -1.f;
+    if (pta::simt_valid(m, i)) {
+      e = pta::launch_toa_fp32_cfg(m, s, B, i, st);  // warm-up (and shared-memory attribute)
+      if (e == cudaSuccess) {
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r)
+          if (e == cudaSuccess) e = pta::launch_toa_fp32_cfg(m, s, B, i, st);
+        cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) {
+          cudaEventElapsedTime(&t, e0, e1);
+          t /= 3.f;
+        }
+      }
+      if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return fail(c, PTA_ECUDA, std::string("autotune launch: ") + cudaGetErrorString(e));
+      }
+      if (best < 0 || t < best_ms) {
+        best = i;
+        best_ms = t;
+      }
+    }
+    if (ms && i < n_ms) ms[i] = t;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best < 0) return fail(c, PTA_EINVAL, "autotune: no TOA kernel configuration fits this model");
+  if (best != c->toa_cfg) drop_graphs(c);
+  c->toa_cfg = best;
+  if (chosen) *chosen = best;
   return PTA_OK;
 }
 

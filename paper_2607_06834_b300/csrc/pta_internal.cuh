@@ -126,6 +126,13 @@ struct Scratch {
 cudaError_t launch_prior_forward(const DevModel& m, const Scratch& s, int B, const float* x,
                                  int fp64, cudaStream_t st);
 cudaError_t launch_toa_fp32(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
+// SIMT tile-shape table (autotuner): entry count, shape of entry i, whether entry i
+// can run this model, the default entry, and a launch with a chosen entry (-1: default)
+int simt_count();
+int simt_info(int i, int* bc, int* tt, int* qpt, int* ord);
+bool simt_valid(const DevModel& m, int i);
+int simt_default(const DevModel& m);
+cudaError_t launch_toa_fp32_cfg(const DevModel& m, const Scratch& s, int B, int cfg, cudaStream_t st);
 cudaError_t launch_toa_fp64(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
 cudaError_t launch_toa_tc(const DevModel& m, const Scratch& s, int B, int terms, cudaStream_t st);
 bool bf16_supported(const DevModel& m);
@@ -205,6 +212,7 @@ struct pta_ctx {
   double t0 = 0.0;
   long long ntoa = 0;
   int precision = PTA_PREC_FP32;
+  int toa_cfg = -1;                // SIMT tile-shape entry (-1: default), set by the autotuner
   pta_layout_t lay{};
   // HMC graphs keyed by (B, n_leapfrog)
   struct Graph {

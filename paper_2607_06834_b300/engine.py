@@ -82,6 +82,19 @@ class Engine:
         self._check(abi.lib.pta_set_precision(self._h, abi.PREC[precision]), "pta_set_precision")
         self.precision = precision
 
+    def autotune(self, B: int):
+        """Time every FP32 TOA-kernel tile shape that fits this model on B chains and
+        keep the fastest.  Returns (chosen entry, {entry: ms per launch})."""
+        n = toa_config_count()
+        ms = (C.c_double * n)()
+        chosen = C.c_int(-1)
+        stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        self._check(abi.lib.pta_autotune(self._h, int(B), stream, C.byref(chosen), ms, n), "pta_autotune")
+        return chosen.value, {i: ms[i] for i in range(n) if ms[i] >= 0}
+
+    def set_toa_config(self, cfg: int):
+        self._check(abi.lib.pta_set_toa_config(self._h, int(cfg)), "pta_set_toa_config")
+
     def logp_constant(self) -> float:
         c = C.c_double()
         self._check(abi.lib.pta_logp_constant(self._h, C.byref(c)), "pta_logp_constant")
@@ -112,6 +125,21 @@ class Engine:
                                                _dptr(inv_mass), int(n_leapfrog), int(seed), int(iteration),
                                                _dptr(accepted), stream), "pta_hmc_trajectory")
         return accepted
+
+
+def toa_config_count() -> int:
+    n = 0
+    while abi.lib.pta_toa_config_info(n, None, None, None, None) == 0:
+        n += 1
+    return n
+
+
+def toa_config_info(cfg: int) -> dict:
+    v = [C.c_int() for _ in range(4)]
+    if abi.lib.pta_toa_config_info(int(cfg), *[C.byref(x) for x in v]) != 0:
+        raise IndexError(cfg)
+    return dict(chains_per_cta=v[0].value, toas_per_tile=v[1].value, rows_per_thread=v[2].value,
+                order=v[3].value)
 
 
 class LogPosterior(torch.autograd.Function):

@@ -90,3 +90,16 @@ def test_null_arguments():
     assert abi.lib.pta_add_pulsar(None, None) == abi.PTA_EINVAL
     assert abi.lib.pta_logp_and_grad(None, 1, None, None, None, None, None) == abi.PTA_EINVAL
     assert abi.lib.pta_last_error(None) == b"null context"
+
+
+def test_toa_config_table_is_queryable_without_a_gpu():
+    from paper_2607_06834_b300 import engine
+    n = engine.toa_config_count()
+    assert n >= 8
+    shapes = [engine.toa_config_info(i) for i in range(n)]
+    for s in shapes:
+        assert s["chains_per_cta"] in (32, 64) and s["toas_per_tile"] in (32, 64)
+        assert s["rows_per_thread"] >= 1 and s["order"] in (0, 1)
+    assert len({tuple(s.values()) for s in shapes}) == n   # no duplicate entries
+    with pytest.raises(IndexError):
+        engine.toa_config_info(n)

@@ -197,6 +197,53 @@ def test_ragged_arrays_bf16x3(kw, B):
     assert lp1[0] == lp[B - 1] and np.array_equal(g1[0], g[B - 1])
 
 
+def _usable_configs(eng):
+    from paper_2607_06834_b300.engine import PTAError, toa_config_count
+    ok = []
+    for cfg in range(toa_config_count()):
+        try:
+            eng.set_toa_config(cfg)
+            ok.append(cfg)
+        except PTAError:
+            pass
+    eng.set_toa_config(-1)
+    return ok
+
+
+@pytest.mark.parametrize("which", ["ragged", "ng15"])
+def test_every_toa_config_matches_oracle(which, ng15):
+    """Every FP32 tile shape the autotuner may pick (chains per CTA, TOAs per tile,
+    ghat rows per thread, instruction order) meets the FP32 bar, and the tuner's
+    choice is one of them."""
+    if which == "ragged":
+        arr = synth.small_array(**RAGGED[0])
+        orc = O.Oracle(arr)
+        X = synth.make_points(arr, 70, seed=9)
+        sample = [0, 1, 69]
+    else:
+        arr, orc = ng15
+        X = synth.make_points(arr, 64, seed=6839)
+        sample = [0, 63]
+    X[0] = O.curn_point(orc, X[0].astype(np.float64), 1.0, seed=2)
+    lo, go = _oracle(orc, X[sample])
+    eng = _engine(arr, "fp32")
+    cfgs = _usable_configs(eng)
+    assert len(cfgs) >= 4
+    for cfg in cfgs:
+        eng.set_toa_config(cfg)
+        lp, g, st = _eval(eng, X)
+        assert np.all(st == 0)
+        err = np.abs(lp[sample] - lo)
+        rel = _grad_rel(g[sample], go)
+        assert err[0] < LOGP_ABS, (cfg, err)
+        assert np.all(err <= LOGP_ABS + REL_RANDOM["fp32"] * np.abs(lo)), (cfg, err)
+        assert np.max(rel) < GRAD_REL, (cfg, rel)
+    chosen, ms = eng.autotune(len(X))
+    assert chosen in cfgs and set(ms) == set(cfgs)
+    print(f"{which}: {len(cfgs)} configurations; autotuner chose {chosen}: "
+          + ", ".join(f"{k}:{v:.3f}" for k, v in sorted(ms.items())))
+
+
 TC_REPORTED_LOGP = 0.05   # tensor-core variants: error reported, bound set from the
 TC_REPORTED_GRAD = 1e-3   # FP32-accumulation truncation analysis (not the FP32 target)
 
