@@ -17,9 +17,17 @@
 // through a two-slot ring filled by cp.async.bulk.  W (whitened residuals, hi and
 // lo) is written by the epilogue.
 //
-// Warp roles: warps 0-7 generate X; warps 0-3 also run the epilogue (thread =
-// chain = tensor-memory lane); warp 8 lane 0 issues the bulk copies; warp 9 lane 0
-// issues the MMAs.  Every mbarrier wait is bounded; a wait that gives up marks
+// Column order of X and C in this kernel: Fourier columns [0, P), zeros up to P8 =
+// P rounded up to 8, then the timing-model and projected low-frequency columns, then
+// zeros up to KX (a multiple of 16).  The timing-model / low-frequency part of X
+// does not change between evaluations: k_build_xmlo stores it once per 64-TOA tile
+// as BF16 hi/lo in the shared-memory layout, and a producer warp copies it in with
+// the tile's phases, chromatic weights, residuals and noise weights.
+//
+// Warp roles: warps 0-7 generate the Fourier part of X; warps 0-3 also run the
+// epilogue (thread = chain = tensor-memory lane); warp 8 lane 0 streams the C
+// chunks; warp 9 lane 0 issues the MMAs; warp 10 lane 0 copies each tile's fixed
+// part.  Every mbarrier wait is bounded; a wait that gives up marks
 // the CTA's chains with status bit 4, and the CTA drains its own copies and MMAs
 // before it frees tensor memory and exits.
 #include <cuda_bf16.h>
@@ -40,7 +48,7 @@ constexpr int P_MAX = 416;               // ghat columns held in tensor memory (
 constexpr int XBYTES = (KX_MAX / 8) * XG;  // 48 KB per hi / lo
 constexpr int WBYTES = NCH * TT * 2;       // 16 KB per hi / lo
 constexpr int SMEM = 2 * XBYTES + 4 * CHB + 2 * WBYTES;  // 192 KB
-constexpr int kThreads = 320;
+constexpr int kThreads = 352;
 constexpr uint32_t kWaitLimit = 4000000u;
 constexpr uint32_t kDrainLimit = 4000000u;
 
@@ -81,11 +89,16 @@ __device__ __forceinline__ void split8(const float (&v)[8], uint4& hi, uint4& lo
   lo = make_uint4(pack2(l[0], l[1]), pack2(l[2], l[3]), pack2(l[4], l[5]), pack2(l[6], l[7]));
 }
 
-__device__ __forceinline__ int kx_of(const DevModel& m, int I) { return (m.P + m.m[I] + m.NL + 15) & ~15; }
+__host__ __device__ __forceinline__ int p8_of(int P) { return (P + 7) & ~7; }
+__device__ __forceinline__ int kx_of(const DevModel& m, int I) { return (p8_of(m.P) + m.m[I] + m.NL + 15) & ~15; }
+__host__ __device__ __forceinline__ int gm_max(int P, int m_max, int NL) {
+  return (((p8_of(P) + m_max + NL + 15) & ~15) - p8_of(P)) / 8;
+}
 __device__ __forceinline__ int nkc_of(int kx) { return (kx + KCH - 1) / KCH; }
 
 // a16[((I * nCB + cb) * nKC + kc) * 2 + h] is one 16 KB chunk: element (chain n,
-// column q = 64 kc + ql) at (n/8) 1024 + (ql/8) 128 + (n%8) 16 + (ql%8) 2.
+// column q = 64 kc + ql of this kernel's order) at (n/8) 1024 + (ql/8) 128 + (n%8) 16
+// + (ql%8) 2.
 __global__ void __launch_bounds__(256)
     k_pack_bf16(DevModel m, const float* __restrict__ a32, unsigned char* __restrict__ a16, int B, int nCB, int nKC) {
   const int I = blockIdx.x, cb = blockIdx.y, kc = blockIdx.z;
@@ -93,10 +106,12 @@ __global__ void __launch_bounds__(256)
     const int n = e % NCH, g = e / NCH;  // consecutive threads: consecutive chains
     const int b = cb * NCH + n;
     float v[8];
+    const int P8 = p8_of(m.P);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int q = kc * KCH + 8 * g + i;
-      v[i] = (b < B && q < m.PM) ? a32[((size_t)I * B + b) * m.PM + q] : 0.f;
+      const int q = kc * KCH + 8 * g + i;                       // column of this kernel's order
+      const int src = q < m.P ? q : (q < P8 ? -1 : q - P8 + m.P);  // column of the a32 row
+      v[i] = (b < B && src >= 0 && src < m.PM) ? a32[((size_t)I * B + b) * m.PM + src] : 0.f;
     }
     uint4 hi, lo;
     split8(v, hi, lo);
@@ -107,12 +122,41 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Fixed part of X per 64-TOA tile: GM groups of 8 columns (timing model, projected
+// low-frequency basis, zeros), hi then lo, each group 1 KB in the X layout.
+__global__ void __launch_bounds__(256)
+    k_build_xmlo(DevModel m, unsigned char* __restrict__ out, int GM) {
+  const int tile = blockIdx.x, ta = tile * TT;
+  int I = 0;
+  while (I + 1 < m.npsr && m.toa_off[I + 1] <= ta) ++I;
+  const int mI = m.m[I], NL = m.NL, row0 = ta - m.toa_off[I];
+  const float* Mg = m.M32 + m.m_off[I] + (long long)row0 * mI;
+  const float* Lg = m.Flo + m.flo_off[I] + (long long)row0 * NL;
+  unsigned char* hi_base = out + (size_t)tile * GM * 2 * XG;
+  for (int e = threadIdx.x; e < TT * GM; e += blockDim.x) {
+    const int t = e % TT, g = e / TT;
+    float v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int j = 8 * g + i;
+      v[i] = j < mI ? Mg[(long long)t * mI + j] : (j < mI + NL ? Lg[(long long)t * NL + (j - mI)] : 0.f);
+    }
+    uint4 hi, lo;
+    split8(v, hi, lo);
+    const int off = g * XG + (t >> 3) * 128 + (t & 7) * 16;
+    *reinterpret_cast<uint4*>(hi_base + off) = hi;
+    *reinterpret_cast<uint4*>(hi_base + GM * XG + off) = lo;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
-    k_toa_bf16(DevModel m, const unsigned char* __restrict__ a16, float* __restrict__ gpart,
-               double* __restrict__ c2part, int32_t* __restrict__ stat, int B, int nCB, int nKCmax) {
+    k_toa_bf16(DevModel m, const unsigned char* __restrict__ a16, const unsigned char* __restrict__ xmlo,
+               float* __restrict__ gpart, double* __restrict__ c2part, int32_t* __restrict__ stat, int B, int nCB,
+               int nKCmax, int GMmax) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ float dts[TT], nis[TT];
-  __shared__ __align__(8) uint64_t full[2], empty[2], x_ready, d1_full, w_ready, x_free, drain;
+  __shared__ __align__(16) uint64_t s_phase[TT];
+  __shared__ __align__(16) float s_chrom[TT], dts[TT], nis[TT];
+  __shared__ __align__(8) uint64_t full[2], empty[2], aux_full, x_ready, d1_full, w_ready, x_free, drain;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_bad;
   unsigned char* Xh = smem;
@@ -123,12 +167,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int u = blockIdx.x, cb = blockIdx.y, b0 = cb * NCH, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int I = m.unit_psr[u], start = m.unit_start[u], len = m.unit_len[u];
-  const int P = m.P, na = m.na, mI = m.m[I], NL = m.NL;
-  const int KX = kx_of(m, I), nKC = nkc_of(KX), ntiles = len / TT;
+  const int P = m.P, na = m.na, P8 = p8_of(P);
+  const int KX = kx_of(m, I), nKC = nkc_of(KX), ntiles = len / TT, GM = (KX - P8) / 8;
   const int NQ2 = (P + 15) & ~15;
   const int nvalid = min(NCH, B - b0);
-  const float* Mg = m.M32 + m.m_off[I] + (long long)(start - m.toa_off[I]) * mI;
-  const float* Lg = m.Flo + m.flo_off[I] + (long long)(start - m.toa_off[I]) * NL;
 
   if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
   if (tid == 0) {
@@ -136,6 +178,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::mbar_init(&full[1], 1);
     tc::mbar_init(&empty[0], 1);
     tc::mbar_init(&empty[1], 1);
+    tc::mbar_init(&aux_full, 1);
     tc::mbar_init(&x_ready, 1);
     tc::mbar_init(&d1_full, 1);
     tc::mbar_init(&w_ready, 1);
@@ -161,19 +204,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------ basis generation + epilogue
     double c2acc = 0.0;
     for (int i = 0; i < ntiles; ++i) {
-      if (i > 0) wait(&x_free, (i - 1) & 1);  // GEMM2 of the previous tile has read X and W
-      const int ta = start + i * TT;
+      // the tile's fixed part has landed (the copy was issued after GEMM2 of the
+      // previous tile had read X and W)
+      wait(&aux_full, i & 1);
       if (!s_bad) {
-        if (tid < TT) {
-          dts[tid] = m.dt[ta + tid];
-          nis[tid] = m.ninv[ta + tid];
-        }
         const int t = tid & (TT - 1);
-        const uint64_t U = m.phase[ta + t];
-        const float wch = m.chrom[ta + t];
-        const float* Mrow = Mg + (long long)(i * TT + t) * mI;
-        const float* Lrow = Lg + (long long)(i * TT + t) * NL;
-        for (int g = tid >> 6; g < KX / 8; g += 4) {
+        const uint64_t U = s_phase[t];
+        const float wch = s_chrom[t];
+        for (int g = tid >> 6; g < P8 / 8; g += 4) {
           float v[8];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
@@ -187,11 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               v[2 * j] = sn * wt;
               v[2 * j + 1] = cs * wt;
             } else {
-#pragma unroll
-              for (int f = 0; f < 2; ++f) {
-                const int qq = q + f - P;
-                v[2 * j + f] = qq < mI ? Mrow[qq] : (qq < mI + NL ? Lrow[qq - mI] : 0.f);
-              }
+              v[2 * j] = v[2 * j + 1] = 0.f;
             }
           }
           uint4 hi, lo;
@@ -286,6 +320,28 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int s = 0; s < 2; ++s)
         if (last_use[s] >= 0 && !tc::mbar_wait(&full[s], (last_use[s] >> 1) & 1, kDrainLimit)) s_bad = 1;
     __syncwarp();
+  } else if (warp == 10) {
+    // ------------------------------------------------ fixed part of each tile (bulk copies)
+    int last = -1;
+    for (int i = 0; i < ntiles; ++i) {
+      if (lane == 0 && !s_bad) {
+        if (i == 0 || wait(&x_free, (i - 1) & 1)) {
+          const int ta = start + i * TT;
+          const unsigned char* src = xmlo + (size_t)(ta / TT) * GMmax * 2 * XG;
+          mbar_expect_tx(&aux_full, 2 * GM * XG + TT * 8 + 3 * TT * 4);
+          bulk_g2s(Xh + P8 / 8 * XG, src, GM * XG, &aux_full);
+          bulk_g2s(Xl + P8 / 8 * XG, src + GMmax * XG, GM * XG, &aux_full);
+          bulk_g2s(s_phase, m.phase + ta, TT * 8, &aux_full);
+          bulk_g2s(s_chrom, m.chrom + ta, TT * 4, &aux_full);
+          bulk_g2s(dts, m.dt + ta, TT * 4, &aux_full);
+          bulk_g2s(nis, m.ninv + ta, TT * 4, &aux_full);
+          last = i;
+        }
+      }
+      __syncwarp();
+    }
+    if (lane == 0 && last >= 0 && !tc::mbar_wait(&aux_full, last & 1, kDrainLimit)) s_bad = 1;
+    __syncwarp();
   } else {
     // ------------------------------------------------ MMA issue (warp 9, lane 0)
     constexpr uint32_t ID1 = idesc_bf16(128, 64, 0);
@@ -355,22 +411,33 @@ __global__ void __launch_bounds__(kThreads, 1)
 }  // namespace
 
 bool bf16_supported(const DevModel& m) {
-  return m.P <= P_MAX && ((m.P + m.m_max + m.NL + 15) & ~15) <= KX_MAX && !m.cw;
+  return m.P <= P_MAX && ((p8_of(m.P) + m.m_max + m.NL + 15) & ~15) <= KX_MAX && !m.cw;
 }
 
+static int nkc_max(const DevModel& m) { return (((p8_of(m.P) + m.m_max + m.NL + 15) & ~15) + KCH - 1) / KCH; }
+
 size_t bf16_pack_bytes(const DevModel& m, int cap) {
-  const int nCB = (cap + NCH - 1) / NCH, nKC = ((m.P + m.m_max + m.NL + 15) / 16 * 16 + KCH - 1) / KCH;
-  return (size_t)m.npsr * nCB * nKC * 2 * CHB;
+  const int nCB = (cap + NCH - 1) / NCH;
+  return (size_t)m.npsr * nCB * nkc_max(m) * 2 * CHB;
+}
+
+size_t bf16_xmlo_bytes(const DevModel& m) {
+  return (size_t)(m.ntoa_pad / TT) * gm_max(m.P, m.m_max, m.NL) * 2 * XG;
+}
+
+cudaError_t build_bf16_xmlo(const DevModel& m, unsigned char* out, cudaStream_t st) {
+  k_build_xmlo<<<(unsigned)(m.ntoa_pad / TT), 256, 0, st>>>(m, out, gm_max(m.P, m.m_max, m.NL));
+  return cudaGetLastError();
 }
 
 cudaError_t launch_toa_bf16(const DevModel& m, const Scratch& s, int B, cudaStream_t st) {
-  if (!bf16_supported(m) || !s.a16) return cudaErrorInvalidValue;
-  const int nCB = (B + NCH - 1) / NCH;
-  const int nKCmax = ((m.P + m.m_max + m.NL + 15) / 16 * 16 + KCH - 1) / KCH;
+  if (!bf16_supported(m) || !s.a16 || !m.xmlo) return cudaErrorInvalidValue;
+  const int nCB = (B + NCH - 1) / NCH, nKCmax = nkc_max(m);
   k_pack_bf16<<<dim3(m.npsr, nCB, nKCmax), 256, 0, st>>>(m, s.a32, s.a16, B, nCB, nKCmax);
   cudaError_t e = cudaFuncSetAttribute(k_toa_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
   if (e != cudaSuccess) return e;
-  k_toa_bf16<<<dim3(m.n_units, nCB), kThreads, SMEM, st>>>(m, s.a16, s.gpart, s.c2part, s.stat, B, nCB, nKCmax);
+  k_toa_bf16<<<dim3(m.n_units, nCB), kThreads, SMEM, st>>>(m, s.a16, m.xmlo, s.gpart, s.c2part, s.stat, B, nCB,
+                                                             nKCmax, gm_max(m.P, m.m_max, m.NL));
   return cudaGetLastError();
 }
 

@@ -687,12 +687,29 @@ int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* gr
   return pta_eval_internal(c, B, x, logp, grad, status, st, false);
 }
 
+// Fixed timing-model / low-frequency part of the BF16 tensor-core basis, built on
+// the first BF16 evaluation.
+static int ensure_bf16(pta_ctx* c) {
+  pta::DevModel& m = c->dm;
+  if (m.xmlo) return PTA_OK;
+  unsigned char* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, std::max<size_t>(16, pta::bf16_xmlo_bytes(m)));
+  if (e != cudaSuccess) return fail(c, PTA_ENOMEM, "BF16 basis allocation failed");
+  c->dev_allocs.push_back(p);
+  e = pta::build_bf16_xmlo(m, p, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(c, PTA_ECUDA, std::string("BF16 basis build: ") + cudaGetErrorString(e));
+  m.xmlo = p;
+  return PTA_OK;
+}
+
 int pta_prepare_internal(pta_ctx* c, int B) {
   if (!c->finalized) return fail(c, PTA_ESTATE, "context not finalized");
   const bool fp64 = c->precision == PTA_PREC_FP64;
   int rc = ensure_scratch(c, B, fp64);
   if (rc != PTA_OK) return rc;
   if (fp64) rc = ensure_f64(c);
+  if (rc == PTA_OK && c->precision == PTA_PREC_BF16X3) rc = ensure_bf16(c);
   return rc;
 }
 

@@ -47,6 +47,7 @@ struct DevModel {
   const double* ninv64;
   const double* chrom64;
   const double* F64;            // per pulsar [n_pad x P] (FP64 path only, built on first use)
+  const unsigned char* xmlo;    // BF16 tensor-core path: fixed basis columns per 64-TOA tile (built on first use)
   const double* M64;            // per pulsar [n_pad x m_I]
   // per pulsar
   const int* toa_off;           // start of the pulsar in the padded TOA arrays
@@ -137,6 +138,8 @@ cudaError_t launch_toa_fp64(const DevModel& m, const Scratch& s, int B, cudaStre
 cudaError_t launch_toa_tc(const DevModel& m, const Scratch& s, int B, int terms, cudaStream_t st);
 bool bf16_supported(const DevModel& m);
 size_t bf16_pack_bytes(const DevModel& m, int cap);
+size_t bf16_xmlo_bytes(const DevModel& m);
+cudaError_t build_bf16_xmlo(const DevModel& m, unsigned char* out, cudaStream_t st);
 cudaError_t launch_toa_bf16(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
 size_t cw_const_bytes();
 cudaError_t launch_cw_forward(const DevModel& m, const Scratch& s, int B, const float* x, cudaStream_t st);
