@@ -192,6 +192,70 @@ def warmup_schedule(n: int, init: int = 15, term: int = 10, base: int = 25) -> l
 
 
 @dataclass
+class ChainState:
+    """Everything a sampling run needs to continue: the chains' state (x, logp, grad
+    on the device), the adapted step sizes and inverse mass, and the random-stream
+    position.  The library's momenta and accept draws are Philox streams keyed by
+    (seed, iteration), and the step jitter comes from a numpy generator whose state
+    is kept here, so a resumed run repeats an uninterrupted one bit for bit."""
+    x: torch.Tensor
+    logp: torch.Tensor
+    grad: torch.Tensor
+    step: np.ndarray
+    inv_mass: torch.Tensor
+    seed: int
+    iteration: int
+    n_leapfrog: int
+    jitter: float
+    rng_state: dict
+
+
+def save_state(path: str, st: ChainState) -> None:
+    """Checkpoint a ChainState to an .npz file."""
+    import json
+    meta = dict(seed=st.seed, iteration=st.iteration, n_leapfrog=st.n_leapfrog, jitter=st.jitter,
+                rng_state=st.rng_state)
+    np.savez(path, x=st.x.cpu().numpy(), logp=st.logp.cpu().numpy(), grad=st.grad.cpu().numpy(),
+             step=np.asarray(st.step), inv_mass=st.inv_mass.cpu().numpy(), meta=np.array(json.dumps(meta)))
+
+
+def load_state(path: str, device=None) -> ChainState:
+    """Read a checkpoint written by save_state onto ``device``."""
+    import json
+    z = np.load(path, allow_pickle=False)
+    meta = json.loads(str(z["meta"]))
+    dev = torch.device(device) if device is not None else torch.device("cpu")
+    return ChainState(x=torch.tensor(z["x"], device=dev), logp=torch.tensor(z["logp"], device=dev),
+                      grad=torch.tensor(z["grad"], device=dev), step=np.array(z["step"]),
+                      inv_mass=torch.tensor(z["inv_mass"], device=dev), seed=int(meta["seed"]),
+                      iteration=int(meta["iteration"]), n_leapfrog=int(meta["n_leapfrog"]),
+                      jitter=float(meta["jitter"]), rng_state=meta["rng_state"])
+
+
+def sample(engine, st: ChainState, n: int, record: slice | None = None):
+    """Advance the chains by n trajectories with fixed step sizes and mass (updates
+    ``st`` in place).  Returns (draws [n, B, K] on the device, accept counts [B])."""
+    B, D = st.x.shape
+    dev = st.x.device
+    rng = np.random.default_rng()
+    rng.bit_generator.state = st.rng_state
+    rec = record if record is not None else slice(0, D)
+    K = len(range(D)[rec])
+    draws = torch.empty((n, B, K), dtype=torch.float32, device=dev)
+    accs = torch.zeros(B, dtype=torch.float64, device=dev)
+    step = torch.empty(B, dtype=torch.float32, device=dev)
+    for j in range(n):
+        step.copy_(torch.tensor(st.step * (1.0 + st.jitter * (2.0 * rng.random(B) - 1.0)), dtype=torch.float32))
+        acc = engine.hmc_trajectory(st.x, st.logp, st.grad, step, st.n_leapfrog, st.seed, st.iteration,
+                                    inv_mass=st.inv_mass)
+        st.iteration += 1
+        accs += acc.double()
+        draws[j].copy_(st.x[:, rec])
+    st.rng_state = rng.bit_generator.state
+    return draws, accs
+
+
+@dataclass
 class HMCResult:
     draws: np.ndarray                 # [chains, n_samples, K] of the recorded coordinates
     accept_rate: float                # mean over chains and sampling iterations
@@ -202,6 +266,7 @@ class HMCResult:
     trajectories: int
     leapfrog: int
     stats: dict = field(default_factory=dict)
+    state: ChainState | None = None   # where sampling stopped (checkpoint with save_state)
 
 
 def run_hmc(engine, x0: torch.Tensor, n_warmup: int, n_samples: int, n_leapfrog: int,
@@ -267,16 +332,10 @@ def run_hmc(engine, x0: torch.Tensor, n_warmup: int, n_samples: int, n_leapfrog:
     if n_warmup > 0:
         eps = da.final
     t_warm = timer()
-    rec = record if record is not None else slice(0, D)
-    K = len(range(D)[rec])
-    draws = torch.empty((n_samples, B, K), dtype=torch.float32, device=dev)
-    accs = torch.zeros(B, dtype=torch.float64, device=dev)
-    for j in range(n_samples):
-        step.copy_(torch.tensor(eps * (1.0 + jitter * (2.0 * rng.random(B) - 1.0)), dtype=torch.float32))
-        acc = engine.hmc_trajectory(x, logp, grad, step, n_leapfrog, seed, it, inv_mass=inv_mass)
-        it += 1
-        accs += acc.double()
-        draws[j].copy_(x[:, rec])
+    st = ChainState(x=x, logp=logp, grad=grad, step=np.asarray(eps, dtype=np.float64), inv_mass=inv_mass,
+                    seed=seed, iteration=it, n_leapfrog=n_leapfrog, jitter=jitter,
+                    rng_state=rng.bit_generator.state)
+    draws, accs = sample(engine, st, n_samples, record)
     t_end = timer()
     d = draws.permute(1, 0, 2).cpu().numpy()
     chain_rate = (accs / max(n_samples, 1)).cpu().numpy()
@@ -286,4 +345,5 @@ def run_hmc(engine, x0: torch.Tensor, n_warmup: int, n_samples: int, n_leapfrog:
                      stats={"final_logp_mean": float(logp.mean()), "init_logp_mean": init_lp,
                             "chain_accept_min": float(chain_rate.min()),
                             "stuck_chains": int((chain_rate < 0.05).sum()),
-                            "step_min": float(eps.min()), "step_max": float(eps.max())})
+                            "step_min": float(eps.min()), "step_max": float(eps.max())},
+                     state=st)

@@ -393,3 +393,23 @@ def test_hmc_trajectory_matches_oracle(tiny):
     acc2 = eng.hmc_trajectory(x, lp, g, steps, L, seed, it + 1)
     torch.cuda.synchronize()
     assert np.isfinite(lp.cpu().numpy()).all()
+
+
+def test_hmc_checkpoint_resume_bit_exact(tiny, tmp_path):
+    """Sampling resumed from a checkpoint repeats the uninterrupted run bit for bit
+    (Philox streams keyed by seed and iteration; step jitter state saved)."""
+    from paper_2607_06834_b300 import sampler
+    arr, _ = tiny
+    eng = _engine(arr, "fp32")
+    x0 = torch.tensor(synth.make_points(arr, 16, seed=41), device="cuda")
+    res = sampler.run_hmc(eng, x0, n_warmup=20, n_samples=2, n_leapfrog=5, seed=77, eps0=0.02)
+    path = str(tmp_path / "chains.npz")
+    sampler.save_state(path, res.state)
+    straight, acc_a = sampler.sample(eng, res.state, 6)
+    st = sampler.load_state(path, device="cuda")
+    first, acc_b = sampler.sample(eng, st, 3)
+    sampler.save_state(path, st)
+    st = sampler.load_state(path, device="cuda")
+    second, acc_c = sampler.sample(eng, st, 3)
+    assert torch.equal(torch.cat([first, second]), straight)
+    assert torch.equal(acc_b + acc_c, acc_a)
