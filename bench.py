@@ -31,11 +31,13 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "ng15_b256"
 WORKLOAD_DESC = "NANOGrav-15-yr-like: 67 pulsars, 3.0e5 TOAs, RN 30 / DM 100 / HD-GWB 14 bins, 256 chains"
 METRIC = "logp+grad evals/s (all chains) at 67-psr size vs FP64 plain path; % roofline"
-DTYPE = {"fp32": "f32", "fp64": "f64", "tf32x3": "tf32x3", "tf32": "tf32", "bf16x3": "bf16x3"}
+DTYPE = {"fp32": "f32", "fp64": "f64", "tf32x3": "tf32x3", "tf32": "tf32", "bf16x3": "bf16x3",
+         "gram": "f32 (compensated)"}
 DTYPE_DETAIL = {"fp32": "FP32 TOA contractions (SIMT)", "fp64": "FP64 TOA contractions (stored basis)",
                 "tf32x3": "3-term split TF32 tensor-core TOA contractions, FP32 accumulation",
                 "tf32": "single TF32 tensor-core TOA contractions, FP32 accumulation",
-                "bf16x3": "3-term split BF16 tensor-core TOA contractions, FP32 accumulation"}
+                "bf16x3": "3-term split BF16 tensor-core TOA contractions, FP32 accumulation",
+                "gram": "Gram form: per-pulsar F^T N~^-1 F products in compensated FP32 (hi/lo, Dot2)"}
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12     # SMs x 2 FP64 FMA/clk x 2 flop x max SM clock
 
@@ -354,6 +356,14 @@ def run_ours(args):
                 "unit": "TFLOP/s", "achieved": flops / (stage_ms[dom] * 1e-3) / 1e12, "peak": tf32_peak,
                 "peak_source": "measured bf16 burst x nominal TF32/BF16 ratio 1.1/2.25",
                 "pipe_terms": terms}
+    elif abi.STAGES[dom] == "toa" and args.precision == "gram":
+        P = 2 * max(arr.n_gwb, arr.n_rn) + 2 * arr.n_dm
+        flops = 2.0 * P * P * arr.npsr * B
+        roof = {"kernel": "k_gram (Gram form, compensated FP32 P x P products)", "bound": "alu",
+                "unit": "TFLOP/s", "achieved": flops / (stage_ms[dom] * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
+                "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 flop x 2.032 GHz",
+                "note": "algorithmic 2 P^2 flop per (pulsar, chain); the error-free products and sums issue "
+                        "about 11 FP32 operations per multiply-add"}
     elif abi.STAGES[dom] == "toa" and args.precision == "bf16x3":
         flops = toa_flops_per_launch(arr, B)
         roof = {"kernel": "k_toa_bf16 (TOA contractions, tcgen05 kind::f16, 3-term BF16 split)",

@@ -47,6 +47,12 @@ extern "C" {
 #define PTA_PREC_TF32X3 2 /* tcgen05 tensor cores, 3-term split TF32 */
 #define PTA_PREC_TF32 3   /* tcgen05, single TF32 product (reported only) */
 #define PTA_PREC_BF16X3 4 /* tcgen05, 3-term split BF16 (reported only) */
+/* Gram form of the same posterior (Eq. posterior_implemented): per pulsar
+ * F^T N~^-1 F, F^T N^-1 dt'' and dt''^T N^-1 dt'' stored at finalize (FP64, the
+ * matrix kept as FP32 hi/lo), each evaluation a P x P product per (pulsar, chain)
+ * in compensated FP32 (error-free products and sums) with FP64 dot products.  No
+ * continuous-wave signal (PTA_EINVAL). */
+#define PTA_PREC_GRAM 5
 
 typedef struct pta_ctx pta_ctx;
 

@@ -100,7 +100,8 @@ int pta_create(pta_ctx** out, const pta_model_desc* d) {
   if (d->n_gwb < 0 || d->n_rn < 0 || d->n_dm < 0 || (d->n_gwb == 0 && d->n_rn == 0) ||
       d->n_gwb > 512 || d->n_rn > 512 || d->n_dm > 512)
     return PTA_EINVAL;
-  if (d->precision < PTA_PREC_FP64 || d->precision > PTA_PREC_BF16X3) return PTA_EINVAL;
+  if (d->precision < PTA_PREC_FP64 || d->precision > PTA_PREC_GRAM) return PTA_EINVAL;
+  if (d->precision == PTA_PREC_GRAM && d->cw) return PTA_EINVAL;
   pta_ctx* c = new (std::nothrow) pta_ctx();
   if (!c) return PTA_ENOMEM;
   c->desc = *d;
@@ -271,6 +272,9 @@ int pta_finalize(pta_ctx* c, void* stream) {
   std::vector<double> LK(lkoff, 0.0), KI(lkoff, 0.0), H(hoff, 0.0), aref((size_t)npsr * m.P, 0.0), pos(3 * npsr),
       dist(npsr);
   std::vector<float> Hhi(hoff, 0.f), Hlo(hoff, 0.f);
+  const int P4 = (m.P + 3) & ~3;
+  std::vector<float> Gth((size_t)npsr * m.P * P4, 0.f), Gtl((size_t)npsr * m.P * P4, 0.f);
+  std::vector<double> gg2((size_t)npsr * m.P, 0.0), cc2(npsr, 0.0);
   const double nu_ref = d.nu_ref_mhz;
   const int P = m.P, kmax = std::max(m.na, m.nd);
   double logc = 0.0;
@@ -403,6 +407,11 @@ int pta_finalize(pta_ctx* c, void* stream) {
         double v = G[(size_t)q * P + r];
         for (int j = 0; j < mI; ++j) v -= Hl[(size_t)q * mI + j] * KiH[(size_t)j * P + r];
         A[(size_t)q * P + r] = A[(size_t)r * P + q] = v;
+        // G~ = F^T N~^-1 F for the Gram form, as FP32 hi/lo (symmetric, both halves)
+        const float vh = (float)v, vl = (float)(v - (double)vh);
+        const size_t go = (size_t)I * P * P4;  // rows padded to P4 columns (zeros)
+        Gth[go + (size_t)q * P4 + r] = Gth[go + (size_t)r * P4 + q] = vh;
+        Gtl[go + (size_t)q * P4 + r] = Gtl[go + (size_t)r * P4 + q] = vl;
       }
       const int k = q < 2 * m.na ? q / 2 + 1 : (q - 2 * m.na) / 2 + 1;
       A[(size_t)q * P + q] += std::exp(-ln_pl(m.ln_rho0, m.ln_Tfyr, -13.0, 4.0, std::log((double)k)));
@@ -437,6 +446,11 @@ int pta_finalize(pta_ctx* c, void* stream) {
       const double r = p.dt[i] * 1e9 - y;
       dt[o + i] = (float)r;
       dt64[o + i] = r;
+      // Gram form: g'' = F^T N^-1 dt'' and c'' = dt''^T N^-1 dt'' (M^T N^-1 dt'' = 0, so
+      // N~^-1 dt'' = N^-1 dt'')
+      const double rn = r / Nv[i];
+      for (int q = 0; q < P; ++q) gg2[(size_t)I * P + q] += Fall[(size_t)i * P + q] * rn;
+      cc2[I] += r * rn;
     }
     // projected low-frequency basis F~_lo = F_lo - M K^-1 H_lo^T (N^-1-orthogonal to M)
     for (int i = 0; i < n; ++i)
@@ -463,6 +477,10 @@ int pta_finalize(pta_ctx* c, void* stream) {
   int rc;
 #define UP(vec, field)                                  \
   if ((rc = upload(c, vec, &m.field)) != PTA_OK) return rc;
+  UP(Gth, Gth);
+  UP(Gtl, Gtl);
+  UP(gg2, g2);
+  UP(cc2, c2);
   UP(phase, phase);
   UP(chrom, chrom);
   UP(dt, dt);
@@ -649,13 +667,16 @@ int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* gr
   const bool fp64 = c->precision == PTA_PREC_FP64;
   StageTimer tm{c, st, profile && c->prof};
   cudaError_t e = cudaMemsetAsync(s.stat, 0, sizeof(int32_t) * B, st);
+  const bool gram = c->precision == PTA_PREC_GRAM;
   tm.begin(0);
   if (e == cudaSuccess) e = pta::launch_prior_forward(m, s, B, x, fp64, st);
   if (e == cudaSuccess && m.cw) e = pta::launch_cw_forward(m, s, B, x, st);
-  if (e == cudaSuccess) e = pta::launch_tm_prologue(m, s, B, fp64, st);
-  tm.end(pta::count_prior_forward(m) + 1 + (m.cw ? 2 : 0));
+  if (e == cudaSuccess && !gram) e = pta::launch_tm_prologue(m, s, B, fp64, st);
+  tm.end(pta::count_prior_forward(m) + (gram ? 0 : 1) + (m.cw ? 2 : 0));
   tm.begin(1);
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && gram) {
+    e = pta::launch_gram(m, s, B, st);  // writes ghat and chi2 directly
+  } else if (e == cudaSuccess) {
     if (fp64)
       e = pta::launch_toa_fp64(m, s, B, st);
     else if (c->precision == PTA_PREC_TF32X3 || c->precision == PTA_PREC_TF32)
@@ -667,8 +688,8 @@ int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* gr
   }
   tm.end(1);
   tm.begin(2);
-  if (e == cudaSuccess) e = pta::launch_reduce(m, s, B, fp64, st);
-  tm.end(1);
+  if (e == cudaSuccess && !gram) e = pta::launch_reduce(m, s, B, fp64, st);
+  tm.end(gram ? 0 : 1);
   if (grad) {
     tm.begin(3);
     if (e == cudaSuccess) e = pta::launch_prior_adjoint(m, s, B, x, grad, st);
@@ -725,8 +746,10 @@ int pta_layout(const pta_ctx* c, pta_layout_t* out) {
 int pta_set_precision(pta_ctx* c, int precision) {
   if (!c) return PTA_EINVAL;
   if (precision != PTA_PREC_FP64 && precision != PTA_PREC_FP32 && precision != PTA_PREC_TF32X3 &&
-      precision != PTA_PREC_TF32 && precision != PTA_PREC_BF16X3)
+      precision != PTA_PREC_TF32 && precision != PTA_PREC_BF16X3 && precision != PTA_PREC_GRAM)
     return fail(c, PTA_EINVAL, "precision mode not available in this build");
+  if (precision == PTA_PREC_GRAM && c->dm.cw)
+    return fail(c, PTA_EINVAL, "the Gram form has no deterministic signal: use a TOA-form mode with CW");
   if (precision == PTA_PREC_BF16X3 && c->finalized && !pta::bf16_supported(c->dm))
     return fail(c, PTA_EINVAL,
                 "BF16 tensor-core path needs P <= 416, P + m_max + 2 (low bins) <= 384 and no CW signal");

@@ -48,6 +48,12 @@ struct DevModel {
   const double* chrom64;
   const double* F64;            // per pulsar [n_pad x P] (FP64 path only, built on first use)
   const unsigned char* xmlo;    // BF16 tensor-core path: fixed basis columns per 64-TOA tile (built on first use)
+  // Gram form (Eq. posterior_implemented) with the reference fit: per pulsar
+  // G~ = F^T N~^-1 F [P x P] as FP32 hi/lo, g'' = F^T N^-1 dt'' [P], c'' = dt''^T N^-1 dt''
+  const float* Gth;
+  const float* Gtl;
+  const double* g2;
+  const double* c2;
   const double* M64;            // per pulsar [n_pad x m_I]
   // per pulsar
   const int* toa_off;           // start of the pulsar in the padded TOA arrays
@@ -141,6 +147,7 @@ size_t bf16_pack_bytes(const DevModel& m, int cap);
 size_t bf16_xmlo_bytes(const DevModel& m);
 cudaError_t build_bf16_xmlo(const DevModel& m, unsigned char* out, cudaStream_t st);
 cudaError_t launch_toa_bf16(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
+cudaError_t launch_gram(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
 size_t cw_const_bytes();
 cudaError_t launch_cw_forward(const DevModel& m, const Scratch& s, int B, const float* x, cudaStream_t st);
 cudaError_t launch_cw_gradient(const DevModel& m, const Scratch& s, int B, cudaStream_t st);

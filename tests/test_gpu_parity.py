@@ -105,7 +105,7 @@ RAGGED = [
 
 
 @pytest.mark.parametrize("kw", RAGGED)
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "gram"])
 def test_ragged_arrays(kw, prec):
     arr = synth.small_array(**kw)
     orc = O.Oracle(arr)
@@ -115,7 +115,7 @@ def test_ragged_arrays(kw, prec):
     eng = _engine(arr, prec)
     lp, g, st = _eval(eng, X)
     assert np.all(st == 0)
-    if prec == "fp64":
+    if prec in ("fp64", "gram"):  # the Gram form's compensated FP32 matches FP64
         assert np.max(np.abs(lp - lo) / np.maximum(1.0, np.abs(lo))) < FP64_REL
         assert np.max(_grad_rel(g, go)) < 1e-6
     else:
@@ -144,7 +144,7 @@ def test_ng15_fp64_single_chain(ng15):
         assert _grad_rel(g[0], go[i]) < 1e-6
 
 
-@pytest.mark.parametrize("prec", ["fp32"])
+@pytest.mark.parametrize("prec", ["fp32", "gram"])
 def test_ng15_batch256_sampled(ng15, prec):
     """The bench's launch configuration (256 chains in one call); sampled chains are
     checked one by one against the oracle, two of them at near-posterior points."""
@@ -161,8 +161,10 @@ def test_ng15_batch256_sampled(ng15, prec):
     for j, i in enumerate(sample):
         err = abs(lp[i] - lo[j])
         rel = _grad_rel(g[i], go[j])
-        print(f"chain {i}: logp {lo[j]:.3f} |d| {err:.2e} grad rel {rel:.2e}")
-        if i in near:
+        print(f"{prec} chain {i}: logp {lo[j]:.3f} |d| {err:.2e} grad rel {rel:.2e}")
+        if prec == "gram":
+            assert err / max(1.0, abs(lo[j])) < FP64_REL and rel < 1e-6
+        elif i in near:
             assert err < LOGP_ABS
         else:
             assert err <= LOGP_ABS + REL_RANDOM[prec] * abs(lo[j])
@@ -413,3 +415,27 @@ def test_hmc_checkpoint_resume_bit_exact(tiny, tmp_path):
     second, acc_c = sampler.sample(eng, st, 3)
     assert torch.equal(torch.cat([first, second]), straight)
     assert torch.equal(acc_b + acc_c, acc_a)
+
+
+def test_gram_form_rejects_cw_and_runs_hmc(tiny):
+    """The Gram form has no deterministic signal; with the noise model it drives HMC
+    trajectories that match the TOA-form FP32 ones up to the FP32 path's rounding."""
+    from paper_2607_06834_b300.engine import PTAError
+    arr = synth.small_array(npsr=2, ntoa=[150, 300], m=[3, 4], n_gwb=2, n_rn=2, seed=3, cw=True)
+    eng = _engine(arr, "fp32")
+    with pytest.raises(PTAError):
+        eng.set_precision("gram")
+    arr, orc = tiny
+    X = synth.make_points(arr, 8, seed=12)
+    outs = []
+    for prec in ("gram", "fp64"):
+        eng = _engine(arr, prec)
+        x = torch.tensor(X, device="cuda")
+        lp, g, st = eng.logp_and_grad(x)
+        step = torch.full((8,), 0.01, device="cuda")
+        acc = eng.hmc_trajectory(x, lp, g, step, 5, 3, 0)
+        torch.cuda.synchronize()
+        outs.append((x.cpu().numpy(), lp.cpu().numpy(), acc.cpu().numpy()))
+    assert np.array_equal(outs[0][2], outs[1][2])
+    np.testing.assert_allclose(outs[0][1], outs[1][1], rtol=1e-9)
+    np.testing.assert_allclose(outs[0][0], outs[1][0], rtol=0, atol=1e-5)

@@ -44,6 +44,16 @@ def test_scale150_b1024_sampled():
     rel = np.linalg.norm(g[near] - go) / np.linalg.norm(go)
     print(f"scale150 chain {near}: grad rel {rel:.2e}")
     assert rel < GRAD_REL
+    # the Gram form on the whole batch (compensated FP32, FP64-level agreement)
+    eng.set_precision("gram")
+    lpg, gg, stg = eng.logp_and_grad(x)
+    torch.cuda.synchronize()
+    lpg, gg = lpg.cpu().numpy(), gg.cpu().numpy()
+    assert np.all(stg.cpu().numpy() == 0)
+    for i in (0, near, B - 1):
+        lo = orc.logp(Xd[i])
+        assert abs(lpg[i] - lo) / max(1.0, abs(lo)) < FP64_REL
+    assert np.linalg.norm(gg[near] - go) / np.linalg.norm(go) < 1e-6
     # the plain FP64 path on the same chain
     eng.set_precision("fp64")
     lp64, g64, st64 = eng.logp_and_grad(x[near:near + 1].contiguous())
