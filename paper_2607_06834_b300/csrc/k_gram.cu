@@ -68,36 +68,20 @@ __global__ void __launch_bounds__(kGThreads)
   double t2 = 0.0;  // da . v for this thread's rows
   double* gout = ghat + ((size_t)I * B + b0 + c) * P;
   const double* g2 = m.g2 + (size_t)I * P;
-  // two rows per pass (r and r + NR): the da loads are shared and the two Dot2 chains
-  // are independent
-  for (int r0 = rg; r0 < P; r0 += 2 * NR) {
-    const int r1 = r0 + NR;
-    const bool two = r1 < P;
-    const float4* gh0 = reinterpret_cast<const float4*>(Gh + (size_t)r0 * P4);
-    const float4* gl0 = reinterpret_cast<const float4*>(Gl + (size_t)r0 * P4);
-    const float4* gh1 = reinterpret_cast<const float4*>(Gh + (size_t)(two ? r1 : r0) * P4);
-    const float4* gl1 = reinterpret_cast<const float4*>(Gl + (size_t)(two ? r1 : r0) * P4);
-    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+  for (int r = rg; r < P; r += NR) {
+    const float4* gh4 = reinterpret_cast<const float4*>(Gh + (size_t)r * P4);
+    const float4* gl4 = reinterpret_cast<const float4*>(Gl + (size_t)r * P4);
+    float s = 0.f, cmp = 0.f;
     for (int q = 0; q < P4 / 4; ++q) {
-      const float4 x = xh4[q], xl = xl4[q];
-      const float4 a0 = __ldg(gh0 + q), l0 = __ldg(gl0 + q), a1 = __ldg(gh1 + q), l1 = __ldg(gl1 + q);
-      const float xv[4] = {x.x, x.y, x.z, x.w}, xlv[4] = {xl.x, xl.y, xl.z, xl.w};
-      const float av0[4] = {a0.x, a0.y, a0.z, a0.w}, bv0[4] = {l0.x, l0.y, l0.z, l0.w};
-      const float av1[4] = {a1.x, a1.y, a1.z, a1.w}, bv1[4] = {l1.x, l1.y, l1.z, l1.w};
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        dot2_step(av0[j], bv0[j], xv[j], xlv[j], s0, c0);
-        dot2_step(av1[j], bv1[j], xv[j], xlv[j], s1, c1);
-      }
+      const float4 a = __ldg(gh4 + q), al = __ldg(gl4 + q), x = xh4[q], xl = xl4[q];
+      dot2_step(a.x, al.x, x.x, xl.x, s, cmp);
+      dot2_step(a.y, al.y, x.y, xl.y, s, cmp);
+      dot2_step(a.z, al.z, x.z, xl.z, s, cmp);
+      dot2_step(a.w, al.w, x.w, xl.w, s, cmp);
     }
-    const double v0 = (double)s0 + (double)c0;
-    if (b0 + c < B) gout[r0] = g2[r0] - v0;
-    t2 = fma((double)dh[c * SP + r0] + (double)dl[c * SP + r0], v0, t2);
-    if (two) {
-      const double v1 = (double)s1 + (double)c1;
-      if (b0 + c < B) gout[r1] = g2[r1] - v1;
-      t2 = fma((double)dh[c * SP + r1] + (double)dl[c * SP + r1], v1, t2);
-    }
+    const double v = (double)s + (double)cmp;
+    if (b0 + c < B) gout[r] = g2[r] - v;
+    t2 = fma((double)dh[c * SP + r] + (double)dl[c * SP + r], v, t2);
   }
   // da . g'' over this thread's share of the coefficients
   double t1 = 0.0;

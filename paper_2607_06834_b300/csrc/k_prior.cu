@@ -8,8 +8,9 @@
 // the dense-bin kernel keeps every FP64 warp instruction full: the triangular
 // updates walk a flat index over the active triangle / rectangle (decoded from a
 // table, no per-element square roots), the factorisation and the inverse advance in
-// one sweep with two barriers per column, and the thread that finishes the next
-// pivot takes its square root.
+// one sweep with two barriers per column, and the per-column pivot work is one
+// Newton-refined reciprocal (LDL^T form; the square roots come at the end, all
+// pivots at once).
 #include <cmath>
 
 #include "pta_internal.cuh"
@@ -45,21 +46,49 @@ __global__ void k_spectra(DevModel m, const float* __restrict__ x, double* sk, d
   }
 }
 
+// 1/d in FP64 from an FP32 seed and two Newton steps (r <- r + r (1 - d r)); the
+// relative error squares at each step, 2^-24 -> 2^-48 -> FP64 rounding.  Outside the
+// FP32 normal range the plain FP64 division is used.
+__device__ __forceinline__ double recip64(double d) {
+  const float f = (float)d;
+  if (!(fabsf(f) >= 1.2e-38f && fabsf(f) <= 3.0e38f)) return 1.0 / d;
+  double r = (double)__frcp_rn(f);
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+// 1/sqrt(d) likewise (y <- y (3/2 - d y^2 / 2)), d > 0
+__device__ __forceinline__ double rsqrt64(double d) {
+  const float f = (float)d;
+  if (!(f >= 1.2e-38f && f <= 3.0e38f)) return 1.0 / sqrt(d);
+  double y = (double)rsqrtf(f);
+  const double h = 0.5 * d;
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  return y * fma(-h * y, y, 1.5);
+}
+
 // ---------------------------------------------------------------------------
 // Dense bins k < n_chol: Phi_k = rho_k Gamma + diag(kappa_.k).  One CTA per
-// (bin, chain).  Column sweep j: (1) scale column j of L and row j of X = L^-1 by
-// 1/L_jj; (2) rank-1 update of the trailing triangle of A and of rows > j of X;
-// the thread that updates element (j+1, j+1) takes the next pivot's square root.
+// (bin, chain).  The sweep is the LDL^T form of the Cholesky factorisation
+// (Phi = L D L^T, L unit lower): column j is scaled by 1/d_j (the pivot's
+// reciprocal from recip64, taken by the thread that finishes the pivot), the
+// trailing triangle takes the rank-1 update with the unscaled column, and the rows
+// of X = L^-1 below j take the same elimination step.  No square root or division
+// sits on the column-to-column path; sqrt(d) for all pivots at once at the end
+// gives the Cholesky factor L D^(1/2), its inverse D^(-1/2) X and the transform.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128)
     k_chol_forward(DevModel m, const float* __restrict__ x, const double* __restrict__ sk,
                    const double* __restrict__ srho, double* a64, double* Lpk, double* Lipk, int32_t* stat) {
   extern __shared__ double sm[];
   const int np = m.npsr, ntri = np * (np + 1) / 2;
-  double* A = sm;              // packed lower, becomes L
-  double* X = sm + ntri;       // packed lower, becomes L^-1
+  double* A = sm;              // packed lower: becomes L (unit, below the diagonal) and D (diagonal)
+  double* X = sm + ntri;       // packed lower: becomes L^-1 (unit lower)
   double* zs = X + ntri;       // [2][np]
-  double* pinv = zs + 2 * np;  // [np] 1 / L_jj
+  double* rd = zs + 2 * np;    // [np] 1 / d_j, then 1 / sqrt(d_j)
+  double* u = rd + np;         // [np] unscaled column j, then sqrt(d_j)
   __shared__ int s_bad;
   const int k = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, nt = blockDim.x;
   const float* xb = x + (size_t)b * m.d;
@@ -85,19 +114,19 @@ __global__ void __launch_bounds__(128)
     if (!(d > 0.0)) {
       s_bad = 1;
       d = 1.0;
+      A[0] = d;
     }
-    A[0] = sqrt(d);
-    pinv[0] = 1.0 / A[0];
+    rd[0] = recip64(d);
   }
   __syncthreads();
   for (int j = 0; j < np; ++j) {
-    const double inv = pinv[j];
+    const double r = rd[j];
     const int s = np - j - 1;
-    for (int e = tid; e < np; e += nt) {
-      if (e < s)
-        A[tri(j + 1 + e, j)] *= inv;
-      else
-        X[tri(j, e - s)] *= inv;
+    for (int e = tid; e < s; e += nt) {
+      const int i = j + 1 + e;
+      const double v = A[tri(i, j)];
+      u[i] = v;
+      A[tri(i, j)] = v * r;  // l_ij
     }
     __syncthreads();
     const int cntA = s * (s + 1) / 2, w = j + 1, cnt = cntA + s * w;
@@ -106,16 +135,15 @@ __global__ void __launch_bounds__(128)
       if (idx < cntA) {
         const unsigned t = m.trimap[idx];
         const int i = (t >> 8) + j + 1, l = (t & 255) + j + 1;
-        const double v = fma(-A[tri(i, j)], A[tri(l, j)], A[tri(i, l)]);
-        if (idx == 0) {  // element (j+1, j+1) receives its last update: the next pivot
+        const double v = fma(-A[tri(i, j)], u[l], A[tri(i, l)]);
+        if (idx == 0) {  // element (j+1, j+1) receives its last update: the next pivot d_{j+1}
           double d = v;
           if (!(d > 0.0)) {
             s_bad = 1;
             d = 1.0;
           }
-          const double piv = sqrt(d);
-          A[tri(i, l)] = piv;
-          pinv[j + 1] = 1.0 / piv;
+          A[tri(i, l)] = d;
+          rd[j + 1] = recip64(d);
         } else {
           A[tri(i, l)] = v;
         }
@@ -131,11 +159,18 @@ __global__ void __launch_bounds__(128)
     __syncthreads();
   }
   if (s_bad && tid == 0) atomicOr(&stat[b], 2);
-  // a_{I,k,c} = sum_J L[I][J] z_{J,k,c}
+  // sqrt(d_j) and 1/sqrt(d_j) for all pivots at once
+  for (int j = tid; j < np; j += nt) {
+    const double y = rsqrt64(A[tri(j, j)]);
+    u[j] = A[tri(j, j)] * y;
+    rd[j] = y;
+  }
+  __syncthreads();
+  // a_{I,k,c} = sum_J (L D^(1/2))[I][J] z_{J,k,c} = sum_{J<=I} L[I][J] sqrt(d_J) z_{J,k,c}
   for (int I = tid; I < np; I += nt) {
-    double s0 = 0.0, s1 = 0.0;
-    for (int J = 0; J <= I; ++J) {
-      const double l = A[tri(I, J)];
+    double s0 = u[I] * zs[I], s1 = u[I] * zs[np + I];
+    for (int J = 0; J < I; ++J) {
+      const double l = A[tri(I, J)] * u[J];
       s0 = fma(l, zs[J], s0);
       s1 = fma(l, zs[np + J], s1);
     }
@@ -143,11 +178,14 @@ __global__ void __launch_bounds__(128)
     a64[o] = s0;
     a64[o + 1] = s1;
   }
+  // Cholesky factor L D^(1/2) and its inverse D^(-1/2) L^-1 for the adjoint
   double* Lg = Lpk + ((size_t)b * m.n_chol + k) * ntri;
   double* Xg = Lipk + ((size_t)b * m.n_chol + k) * ntri;
   for (int idx = tid; idx < ntri; idx += nt) {
-    Lg[idx] = A[idx];
-    Xg[idx] = X[idx];
+    const unsigned t = m.trimap[idx];
+    const int i = t >> 8, j = t & 255;
+    Lg[idx] = (i == j) ? u[j] : A[idx] * u[j];
+    Xg[idx] = (i == j) ? rd[i] : X[idx] * rd[i];
   }
 }
 
@@ -437,7 +475,7 @@ __global__ void k_final(DevModel m, const float* __restrict__ x, const double* _
 
 static size_t chol_smem(const DevModel& m) {
   const size_t np = m.npsr, ntri = np * (np + 1) / 2;
-  return (2 * ntri + 3 * np) * sizeof(double);
+  return (2 * ntri + 4 * np) * sizeof(double);
 }
 static size_t adj_smem(const DevModel& m) {
   const size_t np = m.npsr, ntri = np * (np + 1) / 2;
