@@ -127,6 +127,13 @@ int pta_set_precision(pta_ctx* ctx, int precision);
  * NULL, receives the mean time per launch of entry i (-1 for entries that cannot
  * run) for i < n_ms; `chosen` the selected entry.  Recaptures HMC graphs lazily. */
 int pta_autotune(pta_ctx* ctx, int B, void* stream, int* chosen, double* ms, int n_ms);
+/* Test hook for the bounded device waits (no counterpart in the paper).  code 1:
+ * in PTA_PREC_BF16X3 evaluations the tensor-core kernel withholds the completion
+ * signal of its first tile's F a product, so its epilogue's bounded mbarrier wait
+ * runs out (a bounded poll, seconds at most); every CTA then drains its own copies and MMAs, frees
+ * tensor memory and marks its chains with status bit 4 (PTA_OK is returned: the
+ * context stays usable).  code 0 restores normal operation.  PTA_EINVAL otherwise. */
+int pta_debug_inject(pta_ctx* ctx, int code);
 /* Force TOA kernel table entry `cfg` (-1: the untuned default).  PTA_EINVAL if the
  * entry cannot run this model. */
 int pta_set_toa_config(pta_ctx* ctx, int cfg);

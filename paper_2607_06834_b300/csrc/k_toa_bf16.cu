@@ -367,7 +367,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc::commit(&empty[slot]);
           }
-          tc::commit(&d1_full);
+          // test hook: tile 0's F a completion is never signalled, so the epilogue's
+          // bounded wait runs out and the CTA reports status bit 4
+          if (!(m.inject == 1 && i == 0)) tc::commit(&d1_full);
           if (wait(&w_ready, i & 1)) {
             tc::fence_after();
             const uint32_t wh = tc::smem_u32(Wh), wl = tc::smem_u32(Wl);

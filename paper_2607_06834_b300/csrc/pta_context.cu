@@ -774,6 +774,14 @@ static void drop_graphs(pta_ctx* c) {
   c->graphs.clear();
 }
 
+int pta_debug_inject(pta_ctx* c, int code) {
+  if (!c) return PTA_EINVAL;
+  if (code < 0 || code > 1) return fail(c, PTA_EINVAL, "debug_inject: unknown code");
+  if (code != c->dm.inject) drop_graphs(c);
+  c->dm.inject = code;
+  return PTA_OK;
+}
+
 int pta_set_toa_config(pta_ctx* c, int cfg) {
   if (!c) return PTA_EINVAL;
   if (!c->finalized) return fail(c, PTA_ESTATE, "context not finalized");

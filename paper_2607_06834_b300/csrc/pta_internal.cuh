@@ -50,6 +50,7 @@ struct DevModel {
   const unsigned char* xmlo;    // BF16 tensor-core path: fixed basis columns per 64-TOA tile (built on first use)
   // Gram form (Eq. posterior_implemented) with the reference fit: per pulsar
   // G~ = F^T N~^-1 F [P x P] as FP32 hi/lo, g'' = F^T N^-1 dt'' [P], c'' = dt''^T N^-1 dt''
+  int inject;                   // test hook (pta_debug_inject): 1 = the BF16 kernel withholds one MMA completion
   const float* Gth;
   const float* Gtl;
   const double* g2;
