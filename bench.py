@@ -175,7 +175,7 @@ def hmc_ess_tiny(dev):
     x0 = torch.tensor(synth.make_points(arr, 64, seed=6834 + 30), device=dev)
     th0 = lay["d_z"]
     res = sampler.run_hmc(eng, x0, n_warmup=400, n_samples=400, n_leapfrog=20, record=slice(0, eng.D),
-                          seed=6834 + 30, eps0=0.05, init_dz=th0)
+                          seed=6834 + 30, eps0=0.05, init_dz=th0, consensus=100)
     e = sampler.ess_columns(res.draws)
     rh = np.array([sampler.split_rhat(res.draws[:, :, k]) for k in range(res.draws.shape[2])])
     g0 = lay["th_gwb"]
@@ -204,10 +204,17 @@ def hmc_ess(args, dev):
     lay = eng.layout
     x0 = torch.tensor(synth.make_points(arr, B, seed=6834 + 3), device=dev)
     th0 = lay["d_z"]
+    # record the hyper-parameters and CW parameters plus every 50th whitened coefficient
+    zpick = np.arange(0, th0, 50)
+    rec = np.concatenate([zpick, np.arange(th0, eng.D)])
     res = sampler.run_hmc(eng, x0, n_warmup=args.hmc_warmup, n_samples=args.hmc_samples, n_leapfrog=L,
-                          record=slice(th0, eng.D), seed=6834 + 3, eps0=0.01, init_dz=th0)
-    e = sampler.ess_columns(res.draws)
-    rh = np.array([sampler.split_rhat(res.draws[:, :, k]) for k in range(res.draws.shape[2])])
+                          record=torch.tensor(rec, device=dev), seed=6834 + 3, eps0=0.01, init_dz=th0,
+                          consensus=args.hmc_warmup // 4)
+    e_all = sampler.ess_columns(res.draws)
+    rh_all = np.array([sampler.split_rhat(res.draws[:, :, k]) for k in range(res.draws.shape[2])])
+    nz = len(zpick)
+    e, rh = e_all[nz:], rh_all[nz:]
+    e_z = float(np.nanmedian(e_all[:nz]))
     g0 = lay["th_gwb"] - th0
     cw0 = lay["th_cw"] - th0
     e_gwb = float(np.nanmin(e[g0:g0 + 2]))
@@ -221,6 +228,9 @@ def hmc_ess(args, dev):
             "ess_per_s_gwb_min": e_gwb / t, "ess_per_s_theta_median": e_med / t,
             "ess_per_s_cw_median": e_cw / t,
             "ess_gwb_min": e_gwb, "ess_theta_median": e_med, "ess_cw_median": e_cw,
+            "ess_z_median": e_z, "ess_per_s_z_median": e_z / t,
+            "start": "conditional mode in z, then all chains restart from the best chain after a quarter "
+                     "of the warm-up (consensus start)",
             "sampling_s": t, "warmup_s": res.warmup_s,
             "ms_per_trajectory": 1e3 * t / max(args.hmc_samples, 1),
             "evals_per_s": B * L * args.hmc_samples / t, "accept_rate": res.accept_rate, "step": res.step,

@@ -142,33 +142,54 @@ struct SimtCfg {
   static_assert(RPT >= 1 && RG * RPT == TT, "tile shape");
 };
 
-template <int BC, int TT, int QPT>
+// Basis-tile rows.  PF = 0: [F (P) | M (m_I) | F~_lo (NL) | zero], PM coefficient rows.
+// PF = 1: [F (P) | zero up to QPAD | M | F~_lo]: F^T w never reads the M / F~_lo rows,
+// so those rows can be refilled for the next tile while it runs.
+template <int BC, int TT, int QPT, int PF>
 int simt_xrows(const DevModel& m) {
   using C = SimtCfg<BC, TT, QPT>;
+  if (PF) return C::QPAD + m.m_max + m.NL;
   return C::QPAD > m.PM ? C::QPAD : m.PM;
 }
+template <int BC, int TT, int QPT, int PF>
+int simt_arows(const DevModel& m) {
+  return PF ? simt_xrows<BC, TT, QPT, PF>(m) : m.PM;
+}
 
-template <int BC, int TT, int QPT>
+template <int BC, int TT, int QPT, int PF>
 size_t simt_smem(const DevModel& m) {
   using C = SimtCfg<BC, TT, QPT>;
-  return sizeof(float) * ((size_t)simt_xrows<BC, TT, QPT>(m) * C::XS + (size_t)m.PM * C::AS +
-                          (size_t)TT * C::WS + (size_t)C::RG * BC + 2 * TT);
+  return sizeof(float) * ((size_t)simt_xrows<BC, TT, QPT, PF>(m) * C::XS +
+                          (size_t)simt_arows<BC, TT, QPT, PF>(m) * C::AS + (size_t)TT * C::WS +
+                          (size_t)C::RG * BC + 2 * TT);
 }
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // ORD selects the instruction order of the two register-blocked products:
 //   0: F a unrolled by 2 along the coefficient index; F^T w as nested FMAs over the
 //      four TOAs of a step (one dependent chain of 4 per accumulator);
 //   1: F a unrolled by 4; F^T w with the four TOAs outermost, so every FMA of a
 //      TOA is independent of the others (longer register lifetimes, no chains).
-template <int BC, int TT, int QPT, int ORD>
+// PF = 1 prefetches the next tile while F^T w of the current one runs: its timing-
+// model and F~_lo rows by cp.async into the (then unread) rows of the basis tile,
+// its phases, weights, residuals and noise weights into registers.
+template <int BC, int TT, int QPT, int ORD, int PF>
 __global__ void __launch_bounds__(kThreads, 1)
     k_toa_simt(DevModel m, const float* __restrict__ a32, float* __restrict__ gpart, double* __restrict__ c2part,
                int B, int XR, const float* __restrict__ cwsig, float* __restrict__ cwwt) {
   using C = SimtCfg<BC, TT, QPT>;
   extern __shared__ float4 sm4[];
-  float* Xs = reinterpret_cast<float*>(sm4);            // [XR][XS]  rows: F (P), M (m_I), F~_lo (NL), zero
-  float* As = Xs + XR * C::XS;                          // [PM][AS]  coefficient rows in the same order
-  float* Ws = As + m.PM * C::AS;                        // [TT][WS]
+  float* Xs = reinterpret_cast<float*>(sm4);            // [XR][XS]  basis rows (layout above)
+  float* As = Xs + XR * C::XS;                          // [AR][AS]  coefficient rows in the same order
+  const int AR = PF ? XR : m.PM;
+  float* Ws = As + AR * C::AS;                          // [TT][WS]
   float* C2 = Ws + TT * C::WS;                          // [RG][BC]
   float* dts = C2 + C::RG * BC;                         // [TT]
   float* nis = dts + TT;                                // [TT]
@@ -178,9 +199,35 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int kmax = na > nd ? na : nd;
   const float* Mg = m.M32 + m.m_off[I] + (long long)(start - m.toa_off[I]) * mI;
   const float* Lg = m.Flo + m.flo_off[I] + (long long)(start - m.toa_off[I]) * NL;
+  const int rowM = PF ? C::QPAD : P;  // first timing-model row of the tile
   for (int e = tid; e < KA * BC; e += kThreads) {
     const int c = e / KA, p = e % KA;
-    As[p * C::AS + c] = (b0 + c < B) ? a32[((size_t)I * B + b0 + c) * m.PM + p] : 0.f;
+    As[(p < P ? p : rowM + p - P) * C::AS + c] = (b0 + c < B) ? a32[((size_t)I * B + b0 + c) * m.PM + p] : 0.f;
+  }
+  // PF: prefetched per-TOA data of the next tile, and the first tile's fixed rows
+  uint64_t pf_U = 0;
+  float pf_w = 0.f, pf_dt = 0.f, pf_ni = 0.f;
+  auto prefetch = [&](int t1) {
+    const int t = tid % TT;
+    pf_U = m.phase[start + t1 + t];
+    pf_w = m.chrom[start + t1 + t];
+    if (tid < TT) {
+      pf_dt = m.dt[start + t1 + tid];
+      pf_ni = m.ninv[start + t1 + tid];
+    }
+    for (int e = tid; e < TT * mI; e += kThreads) {
+      const int tt = e / mI, j = e % mI;
+      cp_async4(Xs + (rowM + j) * C::XS + tt, Mg + (long long)(t1 + tt) * mI + j);
+    }
+    for (int e = tid; e < TT * NL; e += kThreads) {
+      const int tt = e / NL, j = e % NL;
+      cp_async4(Xs + (rowM + mI + j) * C::XS + tt, Lg + (long long)(t1 + tt) * NL + j);
+    }
+    cp_async_commit();
+  };
+  if constexpr (PF) {
+    for (int e = tid; e < (C::QPAD - P) * TT; e += kThreads) Xs[(P + e / TT) * C::XS + e % TT] = 0.f;
+    prefetch(0);
   }
   const int cg = tid % C::CG, rg = tid / C::CG;
   float acc[QPT][4];
@@ -191,12 +238,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   double c2acc = 0.0;
 
   for (int t0 = 0; t0 < len; t0 += TT) {
+    if constexpr (PF) cp_async_wait_all();
     __syncthreads();  // previous tile fully consumed
     {
       const int t = tid % TT;
       const int lane_k = tid / TT, kstride = kThreads / TT;
-      const uint64_t U = m.phase[start + t0 + t];
-      const float wch = m.chrom[start + t0 + t];
+      const uint64_t U = PF ? pf_U : m.phase[start + t0 + t];
+      const float wch = PF ? pf_w : m.chrom[start + t0 + t];
       uint64_t ph = U * (uint64_t)(lane_k + 1);
       const uint64_t dph = U * (uint64_t)kstride;
       for (int k = lane_k + 1; k <= kmax; k += kstride, ph += dph) {
@@ -211,21 +259,28 @@ __global__ void __launch_bounds__(kThreads, 1)
           Xs[(2 * na + 2 * (k - 1) + 1) * C::XS + t] = c * wch;
         }
       }
-      for (int e = tid; e < TT * mI; e += kThreads) {
-        const int tt = e / mI, j = e % mI;
-        Xs[(P + j) * C::XS + tt] = Mg[(long long)(t0 + tt) * mI + j];
-      }
-      for (int e = tid; e < TT * NL; e += kThreads) {
-        const int tt = e / NL, j = e % NL;
-        Xs[(P + mI + j) * C::XS + tt] = Lg[(long long)(t0 + tt) * NL + j];
-      }
-      for (int e = tid; e < (XR - KA) * TT; e += kThreads) {
-        const int q = KA + e / TT, tt = e % TT;
-        Xs[q * C::XS + tt] = 0.f;
-      }
-      if (tid < TT) {
-        dts[tid] = m.dt[start + t0 + tid];
-        nis[tid] = m.ninv[start + t0 + tid];
+      if constexpr (PF) {
+        if (tid < TT) {
+          dts[tid] = pf_dt;
+          nis[tid] = pf_ni;
+        }
+      } else {
+        for (int e = tid; e < TT * mI; e += kThreads) {
+          const int tt = e / mI, j = e % mI;
+          Xs[(P + j) * C::XS + tt] = Mg[(long long)(t0 + tt) * mI + j];
+        }
+        for (int e = tid; e < TT * NL; e += kThreads) {
+          const int tt = e / NL, j = e % NL;
+          Xs[(P + mI + j) * C::XS + tt] = Lg[(long long)(t0 + tt) * NL + j];
+        }
+        for (int e = tid; e < (XR - KA) * TT; e += kThreads) {
+          const int q = KA + e / TT, tt = e % TT;
+          Xs[q * C::XS + tt] = 0.f;
+        }
+        if (tid < TT) {
+          dts[tid] = m.dt[start + t0 + tid];
+          nis[tid] = m.ninv[start + t0 + tid];
+        }
       }
     }
     __syncthreads();
@@ -237,8 +292,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int j = 0; j < 4; ++j) y[r][j] = 0.f;
     const float* xrow = Xs + rg * C::RPT;
     const float* arow = As + 4 * cg;
-#pragma unroll(ORD == 0 ? 2 : 4)
-    for (int p = 0; p < KA; ++p) {
+    auto g1 = [&](int p) {
       const float4 av = *reinterpret_cast<const float4*>(arow + p * C::AS);
       float fv[C::RPT];
       if constexpr (C::RPT % 4 == 0) {
@@ -261,6 +315,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         y[r][2] = fmaf(fv[r], av.z, y[r][2]);
         y[r][3] = fmaf(fv[r], av.w, y[r][3]);
       }
+    };
+    if constexpr (PF) {
+#pragma unroll(ORD == 0 ? 2 : 4)
+      for (int p = 0; p < P; ++p) g1(p);
+#pragma unroll(ORD == 0 ? 2 : 4)
+      for (int p = rowM; p < rowM + mI + NL; ++p) g1(p);
+    } else {
+#pragma unroll(ORD == 0 ? 2 : 4)
+      for (int p = 0; p < KA; ++p) g1(p);
     }
     // --- projected residual, whitened residual, chi2 pieces
     float q4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -290,6 +353,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int g = 0; g < C::RG; ++g) s += C2[g * BC + tid];
       c2acc += (double)s;
     }
+    // F a of this tile is done with the timing-model rows: fetch the next tile's
+    if constexpr (PF)
+      if (t0 + TT < len) prefetch(t0 + TT);
     // --- ghat[q][c] += sum_t F^T[q][t] w~[t][c],  q = rg + RG*i < P; four TOAs per step
     // so each basis row is one 16-byte load
 #pragma unroll 1
@@ -407,37 +473,39 @@ __global__ void __launch_bounds__(128)
   }
 }
 
-template <int BC, int TT, int QPT, int ORD>
+template <int BC, int TT, int QPT, int ORD, int PF>
 cudaError_t launch_simt(const DevModel& m, const Scratch& s, int B, cudaStream_t st) {
-  const size_t sm = simt_smem<BC, TT, QPT>(m);
+  const size_t sm = simt_smem<BC, TT, QPT, PF>(m);
   if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e =
-      cudaFuncSetAttribute(k_toa_simt<BC, TT, QPT, ORD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaFuncSetAttribute(k_toa_simt<BC, TT, QPT, ORD, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   dim3 grid(m.n_units, (B + BC - 1) / BC);
-  k_toa_simt<BC, TT, QPT, ORD><<<grid, kThreads, sm, st>>>(m, s.a32, s.gpart, s.c2part, B,
-                                                             simt_xrows<BC, TT, QPT>(m), m.cw ? s.cwsig : nullptr,
-                                                             m.cw ? s.cwwt : nullptr);
+  k_toa_simt<BC, TT, QPT, ORD, PF><<<grid, kThreads, sm, st>>>(m, s.a32, s.gpart, s.c2part, B,
+                                                                 simt_xrows<BC, TT, QPT, PF>(m),
+                                                                 m.cw ? s.cwsig : nullptr, m.cw ? s.cwwt : nullptr);
   return cudaGetLastError();
 }
 
 // The tile shapes the autotuner chooses from: chains per CTA (BC), TOAs per tile
-// (TT), ghat rows per thread (QPT; 256 / (BC / 4) q lanes x QPT rows must cover P)
-// and the instruction order (ORD).
+// (TT), ghat rows per thread (QPT; 256 / (BC / 4) q lanes x QPT rows must cover P),
+// the instruction order (ORD) and next-tile prefetch (PF); ord = ORD + 2 PF.
 struct SimtEntry {
   int bc, tt, qpt, ord;
   cudaError_t (*launch)(const DevModel&, const Scratch&, int, cudaStream_t);
   size_t (*smem)(const DevModel&);
 };
-#define SIMT_E(BC, TT, Q, O) {BC, TT, Q, O, &launch_simt<BC, TT, Q, O>, &simt_smem<BC, TT, Q>}
-#define SIMT_Q16(BC, TT, O) \
-  SIMT_E(BC, TT, 2, O), SIMT_E(BC, TT, 4, O), SIMT_E(BC, TT, 8, O), SIMT_E(BC, TT, 12, O), SIMT_E(BC, TT, 17, O), \
-      SIMT_E(BC, TT, 24, O)
-#define SIMT_Q32(BC, TT, O)                                                                                      \
-  SIMT_E(BC, TT, 1, O), SIMT_E(BC, TT, 2, O), SIMT_E(BC, TT, 4, O), SIMT_E(BC, TT, 6, O), SIMT_E(BC, TT, 9, O), \
-      SIMT_E(BC, TT, 12, O), SIMT_E(BC, TT, 16, O), SIMT_E(BC, TT, 20, O)
-const SimtEntry kSimt[] = {SIMT_Q16(64, 64, 0), SIMT_Q16(64, 64, 1), SIMT_Q16(64, 32, 0), SIMT_Q16(64, 32, 1),
-                           SIMT_Q32(32, 64, 0), SIMT_Q32(32, 64, 1), SIMT_Q32(32, 32, 0), SIMT_Q32(32, 32, 1)};
+#define SIMT_E(BC, TT, Q, O, F) {BC, TT, Q, O + 2 * F, &launch_simt<BC, TT, Q, O, F>, &simt_smem<BC, TT, Q, F>}
+#define SIMT_Q16(BC, TT, O, F)                                                                         \
+  SIMT_E(BC, TT, 2, O, F), SIMT_E(BC, TT, 4, O, F), SIMT_E(BC, TT, 8, O, F), SIMT_E(BC, TT, 12, O, F), \
+      SIMT_E(BC, TT, 17, O, F), SIMT_E(BC, TT, 24, O, F)
+#define SIMT_Q32(BC, TT, O, F)                                                                        \
+  SIMT_E(BC, TT, 1, O, F), SIMT_E(BC, TT, 2, O, F), SIMT_E(BC, TT, 4, O, F), SIMT_E(BC, TT, 6, O, F), \
+      SIMT_E(BC, TT, 9, O, F), SIMT_E(BC, TT, 12, O, F), SIMT_E(BC, TT, 16, O, F), SIMT_E(BC, TT, 20, O, F)
+const SimtEntry kSimt[] = {SIMT_Q16(64, 64, 0, 0), SIMT_Q16(64, 64, 1, 0), SIMT_Q16(64, 32, 0, 0),
+                           SIMT_Q16(64, 32, 1, 0), SIMT_Q32(32, 64, 0, 0), SIMT_Q32(32, 64, 1, 0),
+                           SIMT_Q32(32, 32, 0, 0), SIMT_Q32(32, 32, 1, 0), SIMT_Q16(64, 64, 0, 1),
+                           SIMT_Q16(64, 64, 1, 1), SIMT_Q16(64, 32, 0, 1), SIMT_Q16(64, 32, 1, 1)};
 constexpr int kNSimt = sizeof(kSimt) / sizeof(kSimt[0]);
 
 int simt_rows(const SimtEntry& e) { return (kThreads / (e.bc / 4)) * e.qpt; }
@@ -474,7 +542,7 @@ int simt_default(const DevModel& m) {
     for (int i = 0; i < kNSimt; ++i) {
       const SimtEntry& e = kSimt[i];
       const bool shape = pass == 0 ? (e.bc == 64 && e.tt == 64) : (e.bc == 32 && e.tt == 32);
-      if (shape && e.ord == 0 && simt_usable(m, i)) return i;
+      if (shape && e.ord == 0 && simt_usable(m, i)) return i;  // nested order, no prefetch
     }
   return -1;
 }

@@ -240,7 +240,7 @@ def sample(engine, st: ChainState, n: int, record: slice | None = None):
     rng = np.random.default_rng()
     rng.bit_generator.state = st.rng_state
     rec = record if record is not None else slice(0, D)
-    K = len(range(D)[rec])
+    K = len(range(D)[rec]) if isinstance(rec, slice) else int(len(rec))
     draws = torch.empty((n, B, K), dtype=torch.float32, device=dev)
     accs = torch.zeros(B, dtype=torch.float64, device=dev)
     step = torch.empty(B, dtype=torch.float32, device=dev)
@@ -270,13 +270,20 @@ class HMCResult:
 
 
 def run_hmc(engine, x0: torch.Tensor, n_warmup: int, n_samples: int, n_leapfrog: int,
-            record: slice | None = None, seed: int = 1, eps0: float = 0.05, target_accept: float = 0.8,
-            jitter: float = 0.1, timer=None, init_dz: int = 0, init_iters: int = 100) -> HMCResult:
+            record=None, seed: int = 1, eps0: float = 0.05, target_accept: float = 0.8,
+            jitter: float = 0.1, timer=None, init_dz: int = 0, init_iters: int = 100,
+            consensus: int = 0) -> HMCResult:
     """Warm up and sample ``x0.shape[0]`` chains.  ``engine`` provides ``D``,
     ``logp_and_grad(x)`` and ``hmc_trajectory(x, logp, grad, step, L, seed, it, inv_mass)``
-    working on tensors of x0's device.  ``record`` selects the coordinates stored
-    for the ESS (default: all).  ``timer()`` returns seconds after synchronising
-    the device (default: torch.cuda.synchronize + perf_counter)."""
+    working on tensors of x0's device.  ``record`` (a slice or an index tensor) selects
+    the coordinates stored for the ESS (default: all).  ``timer()`` returns seconds
+    after synchronising the device (default: torch.cuda.synchronize + perf_counter).
+    With ``init_dz`` > 0 the first init_dz coordinates start at their conditional mode
+    (``conditional_mode``, counted in the warm-up time).  With ``consensus`` > 0 the
+    chains first run that many warm-up trajectories from their own starts, then all
+    restart from the state of the chain with the highest log posterior (the rest of
+    the warm-up and the Philox momenta then separate them): chains that start in
+    regions far apart would otherwise need far longer to meet than the run allows."""
     import time
 
     if timer is None:
@@ -311,6 +318,14 @@ def run_hmc(engine, x0: torch.Tensor, n_warmup: int, n_samples: int, n_leapfrog:
         acc = engine.hmc_trajectory(x, logp, grad, step, n_leapfrog, seed, it, inv_mass=inv_mass)
         it += 1
         eps = da.update(acc.cpu().numpy())
+        if consensus > 0 and i == consensus - 1:
+            lpf = torch.where(torch.isfinite(logp), logp, torch.full_like(logp, -math.inf))
+            best = int(torch.argmax(lpf))
+            x.copy_(x[best:best + 1].expand_as(x))
+            grad.copy_(grad[best:best + 1].expand_as(grad))
+            logp.fill_(float(logp[best]))
+            eps = np.full(B, float(eps[best]))
+            da.restart(eps)
         if wi < len(windows) and windows[wi][0] <= i < windows[wi][1]:
             xd = x.double()
             s1 += xd

@@ -156,3 +156,16 @@ def test_checkpoint_resume_is_bit_exact(tmp_path):
     second, _ = sampler.sample(eng, st3, 5)
     assert torch.equal(torch.cat([first, second]), straight)
     assert st3.iteration == st.iteration
+
+
+def test_consensus_start_mixes_dispersed_chains():
+    sig = np.array([0.05, 1.0, 0.3])
+    mu = np.array([2.0, -1.0, 0.5])
+    eng = GaussEngine(mu, sig, seed=4)
+    B = 16
+    x0 = torch.tensor(np.random.default_rng(5).normal(size=(B, 3)) * 20.0, dtype=torch.float32)
+    res = sampler.run_hmc(eng, x0, n_warmup=200, n_samples=200, n_leapfrog=8, seed=6, eps0=0.01,
+                          consensus=40, timer=lambda: 0.0, record=torch.tensor([0, 1, 2]))
+    rh = [sampler.split_rhat(res.draws[:, :, k]) for k in range(3)]
+    assert max(rh) < 1.05, rh
+    assert np.all(np.abs(res.draws.reshape(-1, 3).mean(0) - mu) < 5 * sig / math.sqrt(B * 20))
