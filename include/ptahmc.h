@@ -139,7 +139,8 @@ int pta_debug_inject(pta_ctx* ctx, int code);
 int pta_set_toa_config(pta_ctx* ctx, int cfg);
 /* Shape of table entry cfg: chains per CTA, TOAs per tile, ghat rows per thread,
  * and `order` = instruction order (bit 0: TOA-outermost F^T w) + 2 x next-tile
- * prefetch (bit 1).  PTA_EINVAL past the end of the table (use it to count). */
+ * prefetch (bit 1) + 4 x persistent launch (bit 2: resident CTAs take work units,
+ * longest first, from an atomic counter).  PTA_EINVAL past the end of the table. */
 int pta_toa_config_info(int cfg, int* bc, int* tt, int* qpt, int* order);
 /* Hyper-prior box for (log10 A, gamma) of the GWB, red noise and DM (Sec.
  * "Priors": log10 A ~ U(-20,-10), gamma ~ U(0,7) by default). */

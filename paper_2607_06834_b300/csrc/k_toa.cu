@@ -16,6 +16,8 @@
 // k * U_i mod 2^64 (exact argument reduction); with the timing-model rows they
 // form one transposed tile X^T[q][t] used by both contractions.
 // FP64 variant (plain path): stored FP64 basis, one CTA per (unit, chain).
+#include <algorithm>
+
 #include "pta_internal.cuh"
 
 namespace pta {
@@ -183,7 +185,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <int BC, int TT, int QPT, int ORD, int PF>
 __global__ void __launch_bounds__(kThreads, 1)
     k_toa_simt(DevModel m, const float* __restrict__ a32, float* __restrict__ gpart, double* __restrict__ c2part,
-               int B, int XR, const float* __restrict__ cwsig, float* __restrict__ cwwt) {
+               int B, int XR, const float* __restrict__ cwsig, float* __restrict__ cwwt, int* __restrict__ queue,
+               int nCB) {
   using C = SimtCfg<BC, TT, QPT>;
   extern __shared__ float4 sm4[];
   float* Xs = reinterpret_cast<float*>(sm4);            // [XR][XS]  basis rows (layout above)
@@ -193,7 +196,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   float* C2 = Ws + TT * C::WS;                          // [RG][BC]
   float* dts = C2 + C::RG * BC;                         // [TT]
   float* nis = dts + TT;                                // [TT]
-  const int u = blockIdx.x, b0 = blockIdx.y * BC, tid = threadIdx.x;
+  // Work items are (unit, block of BC chains).  queue == nullptr: one item per CTA
+  // (blockIdx.x = unit, blockIdx.y = chain block).  Otherwise the launch is
+  // persistent: every resident CTA takes items from an atomic counter, units in the
+  // order m.unit_order (longest first), until none are left.
+  __shared__ int s_item;
+  const int tid = threadIdx.x;
+  int item = 0;
+  if (queue) {
+    if (tid == 0) s_item = atomicAdd(queue, 1);
+    __syncthreads();
+    item = s_item;
+  }
+  for (;;) {
+  if (queue && item >= m.n_units * nCB) break;
+  const int u = queue ? m.unit_order[item / nCB] : blockIdx.x;
+  const int b0 = (queue ? item % nCB : blockIdx.y) * BC;
   const int I = m.unit_psr[u], start = m.unit_start[u], len = m.unit_len[u];
   const int P = m.P, mI = m.m[I], NL = m.NL, KA = P + mI + NL, na = m.na, nd = m.nd;
   const int kmax = na > nd ? na : nd;
@@ -402,6 +420,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   }
   if (tid < BC && b0 + tid < B) c2part[(size_t)u * B + b0 + tid] = c2acc;
+  if (!queue) break;
+  __syncthreads();  // the item's shared-memory state is no longer read
+  if (tid == 0) s_item = atomicAdd(queue, 1);
+  __syncthreads();
+  item = s_item;
+  }
 }
 
 // Plain FP64 path.  One CTA of 128 threads per (unit, chain); tile of 128 TOAs,
@@ -474,16 +498,27 @@ __global__ void __launch_bounds__(128)
 }
 
 template <int BC, int TT, int QPT, int ORD, int PF>
-cudaError_t launch_simt(const DevModel& m, const Scratch& s, int B, cudaStream_t st) {
+cudaError_t launch_simt(const DevModel& m, const Scratch& s, int B, int ps, cudaStream_t st) {
   const size_t sm = simt_smem<BC, TT, QPT, PF>(m);
   if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e =
-      cudaFuncSetAttribute(k_toa_simt<BC, TT, QPT, ORD, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  auto kern = k_toa_simt<BC, TT, QPT, ORD, PF>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  dim3 grid(m.n_units, (B + BC - 1) / BC);
-  k_toa_simt<BC, TT, QPT, ORD, PF><<<grid, kThreads, sm, st>>>(m, s.a32, s.gpart, s.c2part, B,
-                                                                 simt_xrows<BC, TT, QPT, PF>(m),
-                                                                 m.cw ? s.cwsig : nullptr, m.cw ? s.cwwt : nullptr);
+  const int nCB = (B + BC - 1) / BC;
+  dim3 grid(m.n_units, nCB);
+  int* queue = nullptr;
+  if (ps) {  // persistent: as many CTAs as are resident at once
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, sm);
+    if (e != cudaSuccess) return e;
+    const int resident = std::max(1, per_sm) * m.nsm;
+    grid = dim3(std::min(resident, m.n_units * nCB), 1);
+    queue = s.queue;
+    e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<grid, kThreads, sm, st>>>(m, s.a32, s.gpart, s.c2part, B, simt_xrows<BC, TT, QPT, PF>(m),
+                                   m.cw ? s.cwsig : nullptr, m.cw ? s.cwwt : nullptr, queue, nCB);
   return cudaGetLastError();
 }
 
@@ -491,11 +526,15 @@ cudaError_t launch_simt(const DevModel& m, const Scratch& s, int B, cudaStream_t
 // (TT), ghat rows per thread (QPT; 256 / (BC / 4) q lanes x QPT rows must cover P),
 // the instruction order (ORD) and next-tile prefetch (PF); ord = ORD + 2 PF.
 struct SimtEntry {
-  int bc, tt, qpt, ord;
-  cudaError_t (*launch)(const DevModel&, const Scratch&, int, cudaStream_t);
+  int bc, tt, qpt, ord;  // ord = ORD + 2 PF + 4 persistent
+  cudaError_t (*launch)(const DevModel&, const Scratch&, int, int, cudaStream_t);
   size_t (*smem)(const DevModel&);
 };
 #define SIMT_E(BC, TT, Q, O, F) {BC, TT, Q, O + 2 * F, &launch_simt<BC, TT, Q, O, F>, &simt_smem<BC, TT, Q, F>}
+#define SIMT_EP(BC, TT, Q, O, F) {BC, TT, Q, O + 2 * F + 4, &launch_simt<BC, TT, Q, O, F>, &simt_smem<BC, TT, Q, F>}
+#define SIMT_Q16P(BC, TT, O, F)                                                                            \
+  SIMT_EP(BC, TT, 2, O, F), SIMT_EP(BC, TT, 4, O, F), SIMT_EP(BC, TT, 8, O, F), SIMT_EP(BC, TT, 12, O, F), \
+      SIMT_EP(BC, TT, 17, O, F), SIMT_EP(BC, TT, 24, O, F)
 #define SIMT_Q16(BC, TT, O, F)                                                                         \
   SIMT_E(BC, TT, 2, O, F), SIMT_E(BC, TT, 4, O, F), SIMT_E(BC, TT, 8, O, F), SIMT_E(BC, TT, 12, O, F), \
       SIMT_E(BC, TT, 17, O, F), SIMT_E(BC, TT, 24, O, F)
@@ -505,7 +544,9 @@ struct SimtEntry {
 const SimtEntry kSimt[] = {SIMT_Q16(64, 64, 0, 0), SIMT_Q16(64, 64, 1, 0), SIMT_Q16(64, 32, 0, 0),
                            SIMT_Q16(64, 32, 1, 0), SIMT_Q32(32, 64, 0, 0), SIMT_Q32(32, 64, 1, 0),
                            SIMT_Q32(32, 32, 0, 0), SIMT_Q32(32, 32, 1, 0), SIMT_Q16(64, 64, 0, 1),
-                           SIMT_Q16(64, 64, 1, 1), SIMT_Q16(64, 32, 0, 1), SIMT_Q16(64, 32, 1, 1)};
+                           SIMT_Q16(64, 64, 1, 1), SIMT_Q16(64, 32, 0, 1), SIMT_Q16(64, 32, 1, 1),
+                           SIMT_Q16P(64, 64, 0, 1), SIMT_Q16P(64, 64, 1, 1), SIMT_Q16P(64, 32, 0, 1),
+                           SIMT_Q16P(64, 32, 1, 1)};
 constexpr int kNSimt = sizeof(kSimt) / sizeof(kSimt[0]);
 
 int simt_rows(const SimtEntry& e) { return (kThreads / (e.bc / 4)) * e.qpt; }
@@ -550,7 +591,7 @@ int simt_default(const DevModel& m) {
 cudaError_t launch_toa_fp32_cfg(const DevModel& m, const Scratch& s, int B, int cfg, cudaStream_t st) {
   if (cfg < 0) cfg = simt_default(m);
   if (!simt_valid(m, cfg)) return cudaErrorInvalidValue;
-  return kSimt[cfg].launch(m, s, B, st);
+  return kSimt[cfg].launch(m, s, B, (kSimt[cfg].ord & 4) ? 1 : 0, st);
 }
 
 namespace {

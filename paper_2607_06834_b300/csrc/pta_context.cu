@@ -1,4 +1,5 @@
 // Context management, host-side precompute and the C ABI entry points.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -511,6 +512,15 @@ int pta_finalize(pta_ctx* c, void* stream) {
   UP(unit_psr, unit_psr);
   UP(unit_start, unit_start);
   UP(unit_len, unit_len);
+  {
+    std::vector<int> order(unit_len.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return unit_len[a] > unit_len[b]; });
+    UP(order, unit_order);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&m.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || m.nsm < 1) m.nsm = 1;
+  }
   UP(Gam, Gamma);
   UP(LG, LGamma);
   {
@@ -538,7 +548,7 @@ void free_scratch(pta::Scratch& s) {
   void* ptrs[] = {s.a32, s.a64, s.Lpk, s.Lipk, s.gpart, s.gpart64, s.c2part, s.ghat, s.chi2,
                   s.dlnk, s.dlnkd, s.dlnr, s.stat, s.sk, s.skd, s.srho, s.cwc, s.cwjac, s.cwsig,
                   s.cwbs, s.cwwt, s.cwgp, s.cwg, s.x0, s.g0, s.p, s.lp0, s.xs, s.gs, s.lps,
-                  s.step, s.imass, s.kin0, s.hmc_ctr, s.acc, s.a16};
+                  s.step, s.imass, s.kin0, s.hmc_ctr, s.acc, s.a16, s.queue};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   s = pta::Scratch{};
@@ -601,6 +611,7 @@ int ensure_scratch(pta_ctx* c, int B, bool fp64) {
   AL(kin0, cap);
   AL(hmc_ctr, 2);
   AL(acc, cap);
+  AL(queue, 1);
 #undef AL
   if (e != cudaSuccess) {
     free_scratch(s);

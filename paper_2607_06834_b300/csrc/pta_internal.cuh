@@ -80,6 +80,8 @@ struct DevModel {
   const int* unit_psr;
   const int* unit_start;        // absolute padded TOA index
   const int* unit_len;          // multiple of 64
+  const int* unit_order;        // units by decreasing length (persistent TOA launches)
+  int nsm;                      // streaming multiprocessors of the device
   // global
   const double* lnk;            // ln k, k = 0..max(na, nd) (entry 0 unused)
   const unsigned short* trimap; // packed-lower index -> (row << 8) | col, for npsr <= 256
@@ -128,6 +130,7 @@ struct Scratch {
   double* kin0 = nullptr;      // [cap]
   uint64_t* hmc_ctr = nullptr; // [2] seed, iteration
   int32_t* acc = nullptr;      // [cap] accept flags
+  int* queue = nullptr;        // [1] work counter of persistent launches
 };
 
 // Kernel launchers (defined in the .cu files).

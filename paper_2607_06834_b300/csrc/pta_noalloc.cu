@@ -56,6 +56,7 @@ size_t noalloc_bytes(const pta::DevModel& m, int B) {
   s += align256((size_t)B * np * m.na * sizeof(double));
   s += align256((size_t)B * np * std::max(1, m.nd) * sizeof(double));
   s += align256((size_t)B * m.na * sizeof(double));
+  s += align256(16);  // work counter of persistent launches
   return s;
 }
 
@@ -137,6 +138,7 @@ extern "C" int pta_logp_and_grad_noalloc(pta_ctx* c, int B, const float* x, doub
   s.sk = (double*)take((size_t)B * np * m.na * sizeof(double));
   s.skd = (double*)take((size_t)B * np * std::max(1, m.nd) * sizeof(double));
   s.srho = (double*)take((size_t)B * m.na * sizeof(double));
+  s.queue = (int*)take(16);
   // Run the same kernel sequence as pta_logp_and_grad on this workspace.
   pta::Scratch saved = c->sc;
   c->sc = s;
