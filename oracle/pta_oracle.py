@@ -386,17 +386,19 @@ class Oracle:
                 lp += -0.5 * d * d
         return lp
 
-    def logp(self, x) -> float:
+    def logp(self, x, beta: float = 1.0) -> float:
         """Canonical log posterior (the quantity the GPU path computes):
         -1/2 sum_I chi2_I - 1/2 |z|^2 + log p(theta), data-only constants dropped.
         Under the prior-whitened transform the Gaussian prior on a and the Jacobian
-        det L combine to -1/2 |z|^2 - (D_z/2) log 2 pi (constant dropped here)."""
+        det L combine to -1/2 |z|^2 - (D_z/2) log 2 pi (constant dropped here).
+        beta < 1: the tempered posterior of Eq. (tempered_post), the likelihood raised
+        to the power beta (its chi2 term scaled by beta), prior unchanged."""
         lpt = self.log_prior_theta(x)
         if not math.isfinite(lpt):
             return -math.inf
         x = np.asarray(x, dtype=np.float64)
         z = x[: self.Dz]
-        return -0.5 * float(self.chi2_terms(x).sum()) - 0.5 * float(z @ z) + lpt
+        return -0.5 * beta * float(self.chi2_terms(x).sum()) - 0.5 * float(z @ z) + lpt
 
     def data_constant(self) -> float:
         """-1/2 sum_I [log det(2 pi N_I) + log det(M_I^T N_I^-1 M_I) - m_I log 2 pi]
@@ -439,11 +441,13 @@ class Oracle:
         return -0.5 * chi2 + self.data_constant() + lp_a + logdetL + self.log_prior_theta(x)
 
     # -- gradient (analytic chain, pinned by central differences) -----------------
-    def grad(self, x, theta_only_idx=None) -> np.ndarray:
+    def grad(self, x, theta_only_idx=None, beta: float = 1.0) -> np.ndarray:
         """d logp / dx.  z-block: g_z = L_k^T F^T N~^-1 r - z.  Hyper-parameters: the
         chain rule through a = L(phi(eta)) z with the forward-mode Cholesky tangent for
         each spectral parameter.  CW parameters: (N~^-1 r)^T dh/dtheta with dh/dtheta
-        from complex-step differentiation of ``cw_signal`` (exact to rounding)."""
+        from complex-step differentiation of ``cw_signal`` (exact to rounding).
+        beta: gradient of the tempered posterior of Eq. (tempered_post), every
+        likelihood derivative (d logp / d a and the CW term) scaled by beta."""
         x = np.asarray(x, dtype=np.float64)
         g = np.zeros(self.D)
         if not math.isfinite(self.log_prior_theta(x)):
@@ -456,7 +460,7 @@ class Oracle:
         for I in range(npsr):
             wt = ntilde_inv_woodbury(self.Nvar[I], self.psrs[I].M, rs[I])
             wts.append(wt)
-            ghat[I] = self.get_F(I).T @ wt                       # d logp / d a_I
+            ghat[I] = beta * (self.get_F(I).T @ wt)              # d logp / d a_I
         o = self.lay
         gz = np.zeros((na, 2, npsr))
         for k in range(na):
@@ -519,7 +523,7 @@ class Oracle:
                     else:
                         pph_c += 1j * h
                     ds = np.imag(cw_signal(self.t_rel[I], self.psrs[I].pos, th8c, dist_c, pph_c)) / h
-                    acc += wts[I] @ ds        # r = dt - F a - h  =>  d(-chi2/2) = +w~ . dh
+                    acc += beta * (wts[I] @ ds)  # r = dt - F a - h  =>  d(-chi2/2) = +w~ . dh
                 g[o["th_cw"] + j] = acc
             for I in range(npsr):
                 g[o["th_cw"] + 8 + 2 * I] += -(th_cw[8 + 2 * I] - self.psrs[I].dist_kpc) / DIST_SIGMA_KPC ** 2

@@ -336,3 +336,39 @@ def test_hmc_reversibility_and_gaussian_target():
     xs = np.array(xs[500:])
     np.testing.assert_allclose(xs.var(0), 1 / np.diag(prec), rtol=0.15)
     assert np.abs(xs.mean(0)).max() < 0.1
+
+
+
+def test_tempered_posterior_limits_and_linearity():
+    """Eq. (tempered_post): beta = 0 leaves the prior alone (closed form: logp = -|z|^2/2
+    + log p(theta), gradient -z on the whitened coefficients, 0 on the box-prior
+    hyper-parameters); logp and its gradient are affine in beta."""
+    arr = synth.small_array(npsr=2, ntoa=[40, 55], m=[3, 4], n_gwb=2, n_rn=3, n_dm=2, seed=21)
+    orc = O.Oracle(arr)
+    x = synth.make_points(arr, 1, seed=4)[0].astype(np.float64)
+    dz = orc.Dz
+    lp0 = orc.logp(x, beta=0.0)
+    assert lp0 == pytest.approx(-0.5 * float(x[:dz] @ x[:dz]) + orc.log_prior_theta(x), rel=1e-14, abs=1e-12)
+    g0 = orc.grad(x, beta=0.0)
+    np.testing.assert_allclose(g0[:dz], -x[:dz], rtol=0, atol=1e-12)
+    assert np.all(g0[dz:] == 0.0)
+    lp1, g1 = orc.logp(x), orc.grad(x)
+    for beta in (0.25, 0.6):
+        assert orc.logp(x, beta=beta) == pytest.approx((1 - beta) * lp0 + beta * lp1, rel=1e-12)
+        np.testing.assert_allclose(orc.grad(x, beta=beta), (1 - beta) * g0 + beta * g1, rtol=1e-10, atol=1e-10)
+
+
+def test_tempered_gradient_central_differences():
+    arr = synth.small_array(npsr=2, ntoa=[40, 55], m=[3, 4], n_gwb=2, n_rn=3, n_dm=2, seed=22)
+    orc = O.Oracle(arr)
+    x = synth.make_points(arr, 1, seed=5)[0].astype(np.float64)
+    beta = 0.37
+    g = orc.grad(x, beta=beta)
+    rng = np.random.default_rng(1)
+    for j in rng.choice(orc.D, size=12, replace=False):
+        h = 1e-6 * max(1.0, abs(x[j]))
+        xp, xm = x.copy(), x.copy()
+        xp[j] += h
+        xm[j] -= h
+        fd = (orc.logp(xp, beta=beta) - orc.logp(xm, beta=beta)) / (2 * h)
+        assert fd == pytest.approx(g[j], rel=1e-5, abs=1e-6 * max(1.0, abs(g).max()))
