@@ -127,6 +127,17 @@ int pta_set_precision(pta_ctx* ctx, int precision);
  * NULL, receives the mean time per launch of entry i (-1 for entries that cannot
  * run) for i < n_ms; `chosen` the selected entry.  Recaptures HMC graphs lazily. */
 int pta_autotune(pta_ctx* ctx, int B, void* stream, int* chosen, double* ms, int n_ms);
+/* Tempered likelihood (App. "The standardizing transform for tempered likelihoods",
+ * Eq. tempered_post): later evaluations (pta_logp_and_grad, the no-allocation call
+ * and HMC trajectories) return log p_beta = -beta/2 sum_I chi2_I - |z|^2/2 + log p(eta)
+ * and its gradient for chain b with beta = beta[b], under the untempered
+ * prior-whitened transform (valid, as the paper notes).  The data constant of
+ * pta_logp_constant is the beta = 1 one; the tempered likelihood's constant is beta
+ * times its likelihood part.  beta: n doubles in device or host memory, copied on
+ * `stream` (the caller's array may be reused once the stream passes the call); the
+ * context keeps its own copy.  Evaluations of more than n chains then return
+ * PTA_EINVAL.  n = 0 or beta = NULL turns tempering off.  Expected 0 <= beta. */
+int pta_set_beta(pta_ctx* ctx, int n, const double* beta, void* stream);
 /* Test hook for the bounded device waits (no counterpart in the paper).  code 1:
  * in PTA_PREC_BF16X3 evaluations the tensor-core kernel withholds the completion
  * signal of its first tile's F a product, so its epilogue's bounded mbarrier wait

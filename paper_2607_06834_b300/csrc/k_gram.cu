@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(kGThreads)
   const float4* xl4 = reinterpret_cast<const float4*>(dl + c * SP);
   double t2 = 0.0;  // da . v for this thread's rows
   double* gout = ghat + ((size_t)I * B + b0 + c) * P;
+  const double bt = (m.beta && b0 + c < B) ? m.beta[b0 + c] : 1.0;  // tempered likelihood
   const double* g2 = m.g2 + (size_t)I * P;
   for (int r = rg; r < P; r += NR) {
     const float4* gh4 = reinterpret_cast<const float4*>(Gh + (size_t)r * P4);
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(kGThreads)
       dot2_step(a.w, al.w, x.w, xl.w, s, cmp);
     }
     const double v = (double)s + (double)cmp;
-    if (b0 + c < B) gout[r] = g2[r] - v;
+    if (b0 + c < B) gout[r] = bt * (g2[r] - v);
     t2 = fma((double)dh[c * SP + r] + (double)dl[c * SP + r], v, t2);
   }
   // da . g'' over this thread's share of the coefficients

@@ -374,7 +374,8 @@ __global__ void k_final(DevModel m, const float* __restrict__ x, const double* _
   double acc = 0.0;
   for (int j = tid; j < m.d_z; j += nt) acc = fma((double)xb[j], (double)xb[j], acc);
   acc *= -0.5;
-  for (int I = tid; I < np; I += nt) acc -= 0.5 * chi2[(size_t)I * B + b];
+  const double bt = m.beta ? m.beta[b] : 1.0;  // tempered likelihood: beta chi2
+  for (int I = tid; I < np; I += nt) acc -= 0.5 * bt * chi2[(size_t)I * B + b];
   int outside = 0;
   for (int I = tid; I < np; I += nt) {
     const float la = xb[m.th_rn + 2 * I], ga = xb[m.th_rn + 2 * I + 1];
@@ -461,12 +462,12 @@ __global__ void k_final(DevModel m, const float* __restrict__ x, const double* _
     if (tid < 8) {
       double s = 0.0;
       for (int I = 0; I < np; ++I) s += gc[I * 10 + tid];
-      gb[m.th_cw + tid] = (float)s;
+      gb[m.th_cw + tid] = (float)(bt * s);
     }
     for (int I = tid; I < np; I += nt) {
       const double L = th[8 + 2 * I];
-      gb[m.th_cw + 8 + 2 * I] = (float)(gc[I * 10 + 8] - (L - m.dist[I]) / (m.dist_sigma * m.dist_sigma));
-      gb[m.th_cw + 9 + 2 * I] = (float)gc[I * 10 + 9];
+      gb[m.th_cw + 8 + 2 * I] = (float)(bt * gc[I * 10 + 8] - (L - m.dist[I]) / (m.dist_sigma * m.dist_sigma));
+      gb[m.th_cw + 9 + 2 * I] = (float)(bt * gc[I * 10 + 9]);
     }
   }
 }

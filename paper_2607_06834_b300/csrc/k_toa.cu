@@ -482,13 +482,14 @@ __global__ void __launch_bounds__(128)
              int fp64) {
   const int I = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
   const int P = m.P, u0 = m.unit0[I], nu = m.nunit[I];
+  const double bt = m.beta ? m.beta[b] : 1.0;  // tempered likelihood: d logp / d a scales with beta
   for (int q = tid; q < P; q += 128) {
     double s = 0.0;
     for (int j = 0; j < nu; ++j) {
       const size_t o = ((size_t)(u0 + j) * B + b) * m.Qs + q;
       s += fp64 ? gpart64[o] : (double)gpart[o];
     }
-    ghat[((size_t)I * B + b) * P + q] = s;
+    ghat[((size_t)I * B + b) * P + q] = bt * s;
   }
   if (tid == 0) {
     double c2 = 0.0;

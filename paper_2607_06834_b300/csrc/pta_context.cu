@@ -737,6 +737,9 @@ static int ensure_bf16(pta_ctx* c) {
 
 int pta_prepare_internal(pta_ctx* c, int B) {
   if (!c->finalized) return fail(c, PTA_ESTATE, "context not finalized");
+  if (c->dm.beta && B > c->beta_n)
+    return fail(c, PTA_EINVAL, "tempered evaluation of " + std::to_string(B) + " chains, but pta_set_beta gave " +
+                                   std::to_string(c->beta_n));
   const bool fp64 = c->precision == PTA_PREC_FP64;
   int rc = ensure_scratch(c, B, fp64);
   if (rc != PTA_OK) return rc;
@@ -783,6 +786,36 @@ int pta_toa_config_info(int cfg, int* bc, int* tt, int* qpt, int* order) {
 static void drop_graphs(pta_ctx* c) {
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
   c->graphs.clear();
+}
+
+int pta_set_beta(pta_ctx* c, int n, const double* beta, void* stream) {
+  if (!c) return PTA_EINVAL;
+  if (!c->finalized) return fail(c, PTA_ESTATE, "context not finalized");
+  if (n < 0) return fail(c, PTA_EINVAL, "set_beta: negative count");
+  if (n == 0 || !beta) {
+    if (c->dm.beta) drop_graphs(c);
+    c->dm.beta = nullptr;
+    c->beta_n = 0;
+    return PTA_OK;
+  }
+  if (n > c->beta_n || !c->beta_dev) {
+    if (c->beta_dev) {
+      cudaStreamSynchronize((cudaStream_t)stream);
+      cudaFree(c->beta_dev);
+      c->beta_dev = nullptr;
+    }
+    if (cudaMalloc(&c->beta_dev, sizeof(double) * n) != cudaSuccess) {
+      c->beta_n = 0;
+      c->dm.beta = nullptr;
+      return fail(c, PTA_ENOMEM, "set_beta: allocation failed");
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(c->beta_dev, beta, sizeof(double) * n, cudaMemcpyDefault, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(c, PTA_ECUDA, std::string("set_beta copy: ") + cudaGetErrorString(e));
+  if (c->dm.beta != c->beta_dev) drop_graphs(c);
+  c->dm.beta = c->beta_dev;
+  c->beta_n = n;
+  return PTA_OK;
 }
 
 int pta_debug_inject(pta_ctx* c, int code) {
@@ -924,6 +957,7 @@ const char* pta_last_error(const pta_ctx* c) { return c ? c->err.c_str() : "null
 void pta_destroy(pta_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
+  if (c->beta_dev) cudaFree(c->beta_dev);
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   free_scratch(c->sc);

@@ -50,6 +50,7 @@ struct DevModel {
   const unsigned char* xmlo;    // BF16 tensor-core path: fixed basis columns per 64-TOA tile (built on first use)
   // Gram form (Eq. posterior_implemented) with the reference fit: per pulsar
   // G~ = F^T N~^-1 F [P x P] as FP32 hi/lo, g'' = F^T N^-1 dt'' [P], c'' = dt''^T N^-1 dt''
+  const double* beta;           // per-chain inverse temperature (App. "tempered likelihoods"); nullptr: 1
   int inject;                   // test hook (pta_debug_inject): 1 = the BF16 kernel withholds one MMA completion
   const float* Gth;
   const float* Gtl;
@@ -226,6 +227,8 @@ struct pta_ctx {
   double t0 = 0.0;
   long long ntoa = 0;
   int precision = PTA_PREC_FP32;
+  double* beta_dev = nullptr;      // pta_set_beta's copy of the inverse temperatures
+  int beta_n = 0;                  // chains it covers
   int toa_cfg = -1;                // SIMT tile-shape entry (-1: default), set by the autotuner
   pta_layout_t lay{};
   // HMC graphs keyed by (B, n_leapfrog)

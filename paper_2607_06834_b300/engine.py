@@ -92,6 +92,19 @@ class Engine:
         self._check(abi.lib.pta_autotune(self._h, int(B), stream, C.byref(chosen), ms, n), "pta_autotune")
         return chosen.value, {i: ms[i] for i in range(n) if ms[i] >= 0}
 
+    def set_beta(self, beta):
+        """Per-chain inverse temperatures for the tempered likelihood (tensor of B
+        values, any device), or None to switch tempering off.  The library copies them
+        on the current stream."""
+        stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        if beta is None:
+            self._check(abi.lib.pta_set_beta(self._h, 0, None, stream), "pta_set_beta")
+            return
+        b = beta.to(dtype=torch.float64).contiguous()
+        self._beta_keep = b  # alive until the stream has copied it
+        self._check(abi.lib.pta_set_beta(self._h, int(b.numel()), C.c_void_p(b.data_ptr()), stream),
+                    "pta_set_beta")
+
     def set_toa_config(self, cfg: int):
         self._check(abi.lib.pta_set_toa_config(self._h, int(cfg)), "pta_set_toa_config")
 

@@ -439,3 +439,35 @@ def test_gram_form_rejects_cw_and_runs_hmc(tiny):
     assert np.array_equal(outs[0][2], outs[1][2])
     np.testing.assert_allclose(outs[0][1], outs[1][1], rtol=1e-9)
     np.testing.assert_allclose(outs[0][0], outs[1][0], rtol=0, atol=1e-5)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "gram", "fp64"])
+def test_tempered_likelihood_matches_oracle(prec):
+    """Per-chain beta (Eq. tempered_post) on a ragged array with CW off: logp and gradient
+    of the tempered posterior against the oracle, beta = 0 (prior only) included."""
+    arr = synth.small_array(**RAGGED[0])
+    orc = O.Oracle(arr)
+    B = 9
+    X = synth.make_points(arr, B, seed=14)
+    X[:3] = np.array([O.curn_point(orc, x.astype(np.float64), 1.0, seed=i) for i, x in enumerate(X[:3])])
+    beta = np.array([1.0, 0.5, 0.1, 0.0, 0.3, 0.9, 0.05, 0.7, 0.2])
+    eng = _engine(arr, prec)
+    eng.set_beta(torch.tensor(beta, device="cuda"))
+    lp, g, st = _eval(eng, X)
+    assert np.all(st == 0)
+    Xd = X.astype(np.float64)
+    lo = np.array([orc.logp(x, beta=b) for x, b in zip(Xd, beta)])
+    go = np.array([orc.grad(x, beta=b) for x, b in zip(Xd, beta)])
+    if prec == "fp32":
+        assert np.all(np.abs(lp - lo) <= LOGP_ABS + REL_RANDOM["fp32"] * np.abs(lo))
+        assert np.max(_grad_rel(g, go)) < GRAD_REL
+    else:
+        assert np.max(np.abs(lp - lo) / np.maximum(1.0, np.abs(lo))) < FP64_REL
+        assert np.max(_grad_rel(g, go)) < 1e-6
+    # more chains than beta values: refused; beta off: the untempered result
+    from paper_2607_06834_b300.engine import PTAError
+    with pytest.raises(PTAError):
+        _eval(eng, np.concatenate([X, X[:1]]))
+    eng.set_beta(None)
+    lp1, _, _ = _eval(eng, X)
+    assert abs(lp1[0] - lp[0]) <= 1e-9 * max(1.0, abs(lp[0]))
