@@ -57,6 +57,7 @@ LN10 = math.log(10.0)
 # identical for intrinsic red noise; the same box is used for DM)
 PRIOR_LOG10A = (-20.0, -10.0)
 PRIOR_GAMMA = (0.0, 7.0)
+PRIOR_LOG10RHO = (-20.0, -5.0)   # free spectral model: log10 of the per-bin variance (s^2), Sec. "Priors"
 # CW prior boxes (order: log10 Mc, log10 f, log10 h, cos iota, psi, cos theta, phi, Phi0)
 PRIOR_CW = [(7.0, 10.5), (-9.0, -7.0), (-18.0, -11.0), (-1.0, 1.0), (0.0, math.pi),
             (-1.0, 1.0), (0.0, 2.0 * math.pi), (0.0, 2.0 * math.pi)]
@@ -246,6 +247,9 @@ class Oracle:
         self.npsr = len(self.psrs)
         self.n_gwb, self.n_rn, self.n_dm = arr.n_gwb, arr.n_rn, arr.n_dm
         self.cw = bool(arr.cw)
+        # free spectral models (Sec. "Priors"): each rho_k / kappa_Ik its own parameter
+        self.gwb_free = bool(getattr(arr, "gwb_free", False))
+        self.rn_free = bool(getattr(arr, "rn_free", False))
         self.na = max(self.n_gwb, self.n_rn)
         self.P = 2 * self.na + 2 * self.n_dm
         tmin = min(p.toas_s.min() for p in self.psrs)
@@ -260,10 +264,12 @@ class Oracle:
         o = {}
         o["z_dm"] = self.na * 2 * self.npsr
         o["dz"] = o["z_dm"] + self.npsr * self.n_dm * 2
+        self.nthr = self.n_rn if self.rn_free else 2
+        self.nthg = self.n_gwb if self.gwb_free else 2
         o["th_rn"] = o["dz"]
-        o["th_dm"] = o["th_rn"] + 2 * self.npsr
+        o["th_dm"] = o["th_rn"] + self.nthr * self.npsr
         o["th_gwb"] = o["th_dm"] + (2 * self.npsr if self.n_dm else 0)
-        o["th_cw"] = o["th_gwb"] + 2
+        o["th_cw"] = o["th_gwb"] + self.nthg
         o["d"] = o["th_cw"] + ((8 + 2 * self.npsr) if self.cw else 0)
         self.lay = o
         self.D = o["d"]
@@ -288,9 +294,9 @@ class Oracle:
         o, npsr, na, nd = self.lay, self.npsr, self.na, self.n_dm
         z_ach = x[: o["z_dm"]].reshape(na, 2, npsr)            # [k][c][I]
         z_dm = x[o["z_dm"]: o["dz"]].reshape(npsr, nd, 2)        # [I][k][c]
-        th_rn = x[o["th_rn"]: o["th_rn"] + 2 * npsr].reshape(npsr, 2)
+        th_rn = x[o["th_rn"]: o["th_rn"] + self.nthr * npsr].reshape(npsr, self.nthr)
         th_dm = x[o["th_dm"]: o["th_dm"] + 2 * npsr].reshape(npsr, 2) if nd else np.zeros((npsr, 2))
-        th_gwb = x[o["th_gwb"]: o["th_gwb"] + 2]
+        th_gwb = x[o["th_gwb"]: o["th_gwb"] + self.nthg]
         th_cw = x[o["th_cw"]: o["d"]] if self.cw else None
         return z_ach, z_dm, th_rn, th_dm, th_gwb, th_cw
 
@@ -298,8 +304,14 @@ class Oracle:
         _, _, th_rn, th_dm, th_gwb, th_cw = self.unpack(x)
         def box(v, lo_hi):
             return bool(np.all((v > lo_hi[0]) & (v < lo_hi[1])))
-        ok = box(th_rn[:, 0], PRIOR_LOG10A) and box(th_rn[:, 1], PRIOR_GAMMA)
-        ok = ok and box(th_gwb[0:1], PRIOR_LOG10A) and box(th_gwb[1:2], PRIOR_GAMMA)
+        if self.rn_free:
+            ok = box(th_rn, PRIOR_LOG10RHO)
+        else:
+            ok = box(th_rn[:, 0], PRIOR_LOG10A) and box(th_rn[:, 1], PRIOR_GAMMA)
+        if self.gwb_free:
+            ok = ok and box(th_gwb, PRIOR_LOG10RHO)
+        else:
+            ok = ok and box(th_gwb[0:1], PRIOR_LOG10A) and box(th_gwb[1:2], PRIOR_GAMMA)
         if self.n_dm:
             ok = ok and box(th_dm[:, 0], PRIOR_LOG10A) and box(th_dm[:, 1], PRIOR_GAMMA)
         if self.cw:
@@ -313,10 +325,16 @@ class Oracle:
     def spectra(self, th_rn, th_dm, th_gwb):
         ks = np.arange(1, self.na + 1)
         rho = np.zeros(self.na)
-        rho[: self.n_gwb] = power_law(th_gwb[0], th_gwb[1], ks[: self.n_gwb], self.T)
+        if self.gwb_free:   # free spectral model: rho_k = 10^theta_k s^2, in ns^2
+            rho[: self.n_gwb] = 10.0 ** np.asarray(th_gwb, dtype=float) * 1e18
+        else:
+            rho[: self.n_gwb] = power_law(th_gwb[0], th_gwb[1], ks[: self.n_gwb], self.T)
         kappa = np.zeros((self.npsr, self.na))
         for I in range(self.npsr):
-            kappa[I, : self.n_rn] = power_law(th_rn[I, 0], th_rn[I, 1], ks[: self.n_rn], self.T)
+            if self.rn_free:
+                kappa[I, : self.n_rn] = 10.0 ** np.asarray(th_rn[I], dtype=float) * 1e18
+            else:
+                kappa[I, : self.n_rn] = power_law(th_rn[I, 0], th_rn[I, 1], ks[: self.n_rn], self.T)
         kdm = np.zeros((self.npsr, self.n_dm))
         if self.n_dm:
             kd = np.arange(1, self.n_dm + 1)
@@ -492,12 +510,20 @@ class Oracle:
                     d_kap[I, k] = dir_deriv(E)
         ks = np.arange(1, na + 1)
         lnf = np.log(ks / self.T / F_YR)
-        # rho = A^2 ... f^-gamma: d rho/d log10A = 2 ln10 rho, d rho/d gamma = -ln(f/f_yr) rho
-        g[o["th_gwb"]] = np.sum(d_rho * 2 * LN10 * rho)
-        g[o["th_gwb"] + 1] = np.sum(d_rho * (-lnf) * rho)
+        # rho = A^2 ... f^-gamma: d rho/d log10A = 2 ln10 rho, d rho/d gamma = -ln(f/f_yr) rho;
+        # free spectrum rho_k = 10^theta_k: d rho_k / d theta_k = ln10 rho_k
+        if self.gwb_free:
+            g[o["th_gwb"]: o["th_gwb"] + self.n_gwb] = (d_rho * LN10 * rho)[: self.n_gwb]
+        else:
+            g[o["th_gwb"]] = np.sum(d_rho * 2 * LN10 * rho)
+            g[o["th_gwb"] + 1] = np.sum(d_rho * (-lnf) * rho)
         for I in range(npsr):
-            g[o["th_rn"] + 2 * I] = np.sum(d_kap[I] * 2 * LN10 * kappa[I])
-            g[o["th_rn"] + 2 * I + 1] = np.sum(d_kap[I] * (-lnf) * kappa[I])
+            if self.rn_free:
+                g[o["th_rn"] + self.n_rn * I: o["th_rn"] + self.n_rn * (I + 1)] = \
+                    (d_kap[I] * LN10 * kappa[I])[: self.n_rn]
+            else:
+                g[o["th_rn"] + 2 * I] = np.sum(d_kap[I] * 2 * LN10 * kappa[I])
+                g[o["th_rn"] + 2 * I + 1] = np.sum(d_kap[I] * (-lnf) * kappa[I])
         if nd:
             kd = np.arange(1, nd + 1)
             lnfd = np.log(kd / self.T / F_YR)

@@ -83,6 +83,8 @@ class Array:
     cw: bool
     name: str = ""
     meta: dict = field(default_factory=dict)
+    gwb_free: bool = False    # free spectral model for the GWB: one log10 rho per bin
+    rn_free: bool = False     # free spectral model for every pulsar's red noise
 
     @property
     def npsr(self) -> int:
@@ -216,7 +218,7 @@ def make_array(name: str, seed: int | None = None) -> Array:
 
 
 def small_array(npsr=2, ntoa=60, m=3, n_gwb=2, n_rn=2, n_dm=0, cw=False, seed=0,
-                span_yr=5.0, nbackend=1) -> Array:
+                span_yr=5.0, nbackend=1, gwb_free=False, rn_free=False) -> Array:
     """A hand-sized array for brute-force checks (dense N x N algebra).  ``ntoa`` and
     ``m`` may be per-pulsar lists (ragged arrays)."""
     rng = np.random.default_rng(seed)
@@ -246,7 +248,7 @@ def small_array(npsr=2, ntoa=60, m=3, n_gwb=2, n_rn=2, n_dm=0, cw=False, seed=0,
             backend=backend, efac=efac, equad_s=equad_ns * 1e-9, M=np.ascontiguousarray(M),
             pos=_sky(rng), dist_kpc=float(rng.uniform(0.5, 5.0))))
     return Array(pulsars=pulsars, n_gwb=n_gwb, n_rn=n_rn, n_dm=n_dm, cw=cw, name="small",
-                 meta=dict(seed=seed))
+                 meta=dict(seed=seed), gwb_free=gwb_free, rn_free=rn_free)
 
 
 # ---------------------------------------------------------------------------
@@ -254,7 +256,8 @@ def small_array(npsr=2, ntoa=60, m=3, n_gwb=2, n_rn=2, n_dm=0, cw=False, seed=0,
 # the C ABI (pta_layout) and the oracle, each of which states it independently:
 #   z_ach[k][c][I]  k < N_a = max(n_gwb, n_rn), c in {0: sin, 1: cos}
 #   z_dm [I][k][c]  k < n_dm
-#   theta_rn [I][2] (log10 A, gamma), theta_dm [I][2], theta_gwb [2],
+#   theta_rn [I][2] (log10 A, gamma) or, free spectrum, [I][n_rn] (log10 kappa_Ik, s^2),
+#   theta_dm [I][2], theta_gwb [2] or, free spectrum, [n_gwb] (log10 rho_k, s^2),
 #   theta_cw [8] (log10 Mc, log10 f, log10 h, cos iota, psi, cos theta, phi, Phi0)
 #   followed by per-pulsar (L_I [kpc], Phi_I [rad]) when cw is on.
 # ---------------------------------------------------------------------------
@@ -266,10 +269,12 @@ def layout(arr: Array) -> dict:
     o["z_ach"] = 0
     o["z_dm"] = na * 2 * npsr
     o["dz"] = o["z_dm"] + npsr * nd * 2
+    o["n_th_rn"] = arr.n_rn if arr.rn_free else 2
+    o["n_th_gwb"] = arr.n_gwb if arr.gwb_free else 2
     o["th_rn"] = o["dz"]
-    o["th_dm"] = o["th_rn"] + 2 * npsr
+    o["th_dm"] = o["th_rn"] + o["n_th_rn"] * npsr
     o["th_gwb"] = o["th_dm"] + (2 * npsr if nd > 0 else 0)
-    o["th_cw"] = o["th_gwb"] + 2
+    o["th_cw"] = o["th_gwb"] + o["n_th_gwb"]
     o["d"] = o["th_cw"] + ((8 + 2 * npsr) if arr.cw else 0)
     o["na"] = na
     return o
@@ -278,20 +283,29 @@ def layout(arr: Array) -> dict:
 def make_points(arr: Array, B: int, seed: int = 6834, spread: float = 1.0,
                 z_scale: float = 1.0) -> np.ndarray:
     """Evaluation points x[B, D] (float32): z ~ N(0, z_scale^2), hyper-parameters
-    drawn around the injection values, CW parameters from their prior ranges."""
+    drawn around the injection values, CW parameters from their prior ranges.  Free
+    spectral parameters (log10 of the per-bin variance in s^2) are drawn from
+    U(-19, -13), the band the injected processes span."""
     rng = np.random.default_rng(seed)
     L = layout(arr)
     x = np.zeros((B, L["d"]), dtype=np.float64)
     x[:, : L["dz"]] = z_scale * rng.normal(size=(B, L["dz"]))
     npsr = arr.npsr
+    nr = L["n_th_rn"]
     for I in range(npsr):
-        x[:, L["th_rn"] + 2 * I] = rng.uniform(-16.0, -13.5, B)
-        x[:, L["th_rn"] + 2 * I + 1] = rng.uniform(2.0, 5.0, B)
+        if arr.rn_free:
+            x[:, L["th_rn"] + nr * I: L["th_rn"] + nr * (I + 1)] = rng.uniform(-19.0, -13.0, (B, nr))
+        else:
+            x[:, L["th_rn"] + 2 * I] = rng.uniform(-16.0, -13.5, B)
+            x[:, L["th_rn"] + 2 * I + 1] = rng.uniform(2.0, 5.0, B)
         if arr.n_dm:
             x[:, L["th_dm"] + 2 * I] = rng.uniform(-14.5, -13.0, B)
             x[:, L["th_dm"] + 2 * I + 1] = rng.uniform(1.0, 4.0, B)
-    x[:, L["th_gwb"]] = -14.7 + spread * rng.uniform(-0.5, 0.5, B)
-    x[:, L["th_gwb"] + 1] = 13.0 / 3.0 + spread * rng.uniform(-1.0, 1.0, B)
+    if arr.gwb_free:
+        x[:, L["th_gwb"]: L["th_gwb"] + L["n_th_gwb"]] = rng.uniform(-19.0, -13.0, (B, L["n_th_gwb"]))
+    else:
+        x[:, L["th_gwb"]] = -14.7 + spread * rng.uniform(-0.5, 0.5, B)
+        x[:, L["th_gwb"] + 1] = 13.0 / 3.0 + spread * rng.uniform(-1.0, 1.0, B)
     if arr.cw:
         c = L["th_cw"]
         x[:, c + 0] = rng.uniform(8.5, 10.0, B)

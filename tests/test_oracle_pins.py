@@ -162,6 +162,9 @@ def _closed_form_logZ(orc, x):
     dict(npsr=2, ntoa=40, m=3, n_gwb=2, n_rn=3, n_dm=2, seed=1),
     dict(npsr=3, ntoa=30, m=3, n_gwb=3, n_rn=2, n_dm=0, seed=2),
     dict(npsr=2, ntoa=45, m=9, n_gwb=2, n_rn=2, n_dm=1, seed=4, nbackend=2),
+    # free spectral models (Sec. "Priors"): one variance parameter per bin
+    dict(npsr=2, ntoa=40, m=3, n_gwb=3, n_rn=2, n_dm=1, seed=5, gwb_free=True),
+    dict(npsr=3, ntoa=35, m=3, n_gwb=2, n_rn=3, n_dm=0, seed=6, gwb_free=True, rn_free=True),
 ])
 def test_marginal_likelihood_matches_dense_gaussian(kw):
     arr = synth.small_array(**kw)
@@ -215,6 +218,8 @@ def _fd_grad(orc, x, idx, rel=1e-6):
     dict(npsr=3, ntoa=40, m=3, n_gwb=3, n_rn=4, n_dm=2, seed=11),
     dict(npsr=3, ntoa=40, m=5, n_gwb=4, n_rn=2, n_dm=0, seed=12, nbackend=2),
     dict(npsr=2, ntoa=40, m=3, n_gwb=2, n_rn=2, n_dm=1, seed=13, cw=True),
+    dict(npsr=3, ntoa=40, m=3, n_gwb=3, n_rn=4, n_dm=2, seed=14, gwb_free=True, rn_free=True),
+    dict(npsr=2, ntoa=40, m=4, n_gwb=4, n_rn=2, n_dm=0, seed=15, gwb_free=True),
 ])
 def test_gradient_central_differences(kw):
     arr = synth.small_array(**kw)
@@ -372,3 +377,33 @@ def test_tempered_gradient_central_differences():
         xm[j] -= h
         fd = (orc.logp(xp, beta=beta) - orc.logp(xm, beta=beta)) / (2 * h)
         assert fd == pytest.approx(g[j], rel=1e-5, abs=1e-6 * max(1.0, abs(g).max()))
+
+
+
+def test_free_spectrum_reduces_to_power_law():
+    """A free spectrum whose per-bin variances are set to the power law's values gives
+    the power-law posterior exactly (Sec. "Priors": both are choices of rho_k / kappa_Ik),
+    and the free-spectrum gradient summed with the power law's chain rule
+    (d rho_k / d log10 A = 2 ln10 rho_k) reproduces the power-law gradient."""
+    kw = dict(npsr=2, ntoa=40, m=3, n_gwb=3, n_rn=3, n_dm=1, seed=8)
+    arr_pl = synth.small_array(**kw)
+    arr_fr = synth.small_array(**kw, gwb_free=True, rn_free=True)
+    pl, fr = O.Oracle(arr_pl), O.Oracle(arr_fr)
+    x = synth.make_points(arr_pl, 1, seed=3)[0].astype(np.float64)
+    z_ach, z_dm, th_rn, th_dm, th_gwb, _ = pl.unpack(x)
+    rho, kappa, _ = pl.spectra(th_rn, th_dm, th_gwb)
+    lp, lf = pl.lay, fr.lay
+    xf = np.zeros(fr.D)
+    xf[: pl.Dz] = x[: pl.Dz]
+    xf[lf["th_dm"]: lf["th_dm"] + 2 * arr_pl.npsr] = x[lp["th_dm"]: lp["th_dm"] + 2 * arr_pl.npsr]
+    xf[lf["th_gwb"]: lf["th_gwb"] + 3] = np.log10(rho[:3] / 1e18)
+    for I in range(2):
+        xf[lf["th_rn"] + 3 * I: lf["th_rn"] + 3 * I + 3] = np.log10(kappa[I, :3] / 1e18)
+    assert fr.logp(xf) == pytest.approx(pl.logp(x), rel=1e-12)
+    gp, gf = pl.grad(x), fr.grad(xf)
+    np.testing.assert_allclose(gf[: pl.Dz], gp[: pl.Dz], rtol=1e-10, atol=1e-12)
+    # d/d log10 A_GWB = sum_k (d/d log10 rho_k)(d log10 rho_k / d log10 A) = 2 sum_k g_k
+    assert 2.0 * gf[lf["th_gwb"]: lf["th_gwb"] + 3].sum() == pytest.approx(gp[lp["th_gwb"]], rel=1e-10)
+    for I in range(2):
+        assert 2.0 * gf[lf["th_rn"] + 3 * I: lf["th_rn"] + 3 * I + 3].sum() == \
+            pytest.approx(gp[lp["th_rn"] + 2 * I], rel=1e-10)
