@@ -67,7 +67,11 @@ typedef struct {
   int cw;             /* 1: add the circular-binary deterministic signal */
   int precision;      /* PTA_PREC_* */
   double nu_ref_mhz;  /* DM reference frequency; 0 selects 1400 MHz */
+  int spectrum;       /* spectral models (Sec. Priors): 0 power laws; bit 0 (PTA_FREE_GWB) a free
+                         spectrum for the GWB, bit 1 (PTA_FREE_RN) for every pulsar's red noise */
 } pta_model_desc;
+#define PTA_FREE_GWB 1
+#define PTA_FREE_RN 2
 
 /* One pulsar.  All arrays have n entries except efac/equad (n_backend) and M
  * (n x m, row-major).  White noise N_ii = efac[b_i]^2 sigma_i^2 + equad[b_i]^2
@@ -89,9 +93,11 @@ typedef struct {
 /* Offsets into the parameter vector x[D] of one chain:
  *   z_ach[k][c][I]  k < max(n_gwb, n_rn), c = 0 sin / 1 cos, I < npsr
  *   z_dm [I][k][c]  k < n_dm
- *   th_rn[I][2]     (log10 A, gamma) intrinsic red noise, Eq. (power_law)
+ *   th_rn[I][2]     (log10 A, gamma) intrinsic red noise, Eq. (power_law); with
+ *                   PTA_FREE_RN th_rn[I][n_rn]: log10 kappa_Ik (variance per bin, s^2)
  *   th_dm[I][2]     (log10 A, gamma) DM            (absent if n_dm == 0)
- *   th_gwb[2]       (log10 A, gamma) GWB
+ *   th_gwb[2]       (log10 A, gamma) GWB; with PTA_FREE_GWB th_gwb[n_gwb]: log10 rho_k (s^2)
+ *                   (free-spectrum prior: log10 ~ U(-20, -5) per bin)
  *   th_cw[8]        log10 Mc[Msun], log10 f_gw[Hz], log10 h, cos iota, psi,
  *                   cos theta, phi, Phi0; then per pulsar (L_I[kpc], Phi_I)
  *                   (absent unless cw) */
@@ -101,6 +107,7 @@ typedef struct {
   int z_ach, z_dm, th_rn, th_dm, th_gwb, th_cw;
   long long ntoa;             /* total TOAs */
   double tspan_s, t0_s;       /* basis span T and origin t0 */
+  int n_th_rn, n_th_gwb;      /* red-noise parameters per pulsar, GWB parameters (2 or bins) */
 } pta_layout_t;
 
 int pta_create(pta_ctx** out, const pta_model_desc* desc);

@@ -24,7 +24,7 @@ STAGES = ["prior_forward", "toa", "epilogue", "adjoint", "final"]
 
 class ModelDesc(C.Structure):
     _fields_ = [("n_gwb", C.c_int), ("n_rn", C.c_int), ("n_dm", C.c_int), ("cw", C.c_int),
-                ("precision", C.c_int), ("nu_ref_mhz", C.c_double)]
+                ("precision", C.c_int), ("nu_ref_mhz", C.c_double), ("spectrum", C.c_int)]
 
 
 class PulsarDesc(C.Structure):
@@ -40,7 +40,8 @@ class Layout(C.Structure):
     _fields_ = [("npsr", C.c_int), ("n_ach", C.c_int), ("n_dm", C.c_int), ("P", C.c_int),
                 ("d_z", C.c_int), ("d", C.c_int), ("z_ach", C.c_int), ("z_dm", C.c_int),
                 ("th_rn", C.c_int), ("th_dm", C.c_int), ("th_gwb", C.c_int), ("th_cw", C.c_int),
-                ("ntoa", C.c_longlong), ("tspan_s", C.c_double), ("t0_s", C.c_double)]
+                ("ntoa", C.c_longlong), ("tspan_s", C.c_double), ("t0_s", C.c_double),
+                ("n_th_rn", C.c_int), ("n_th_gwb", C.c_int)]
 
 
 def _load():

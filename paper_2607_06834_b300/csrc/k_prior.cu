@@ -32,8 +32,10 @@ __global__ void k_spectra(DevModel m, const float* __restrict__ x, double* sk, d
   double v = 0.0;
   if (r < nach) {
     const int I = r / m.na, k = r % m.na;
-    if (k < m.n_rn)
-      v = exp(0.5 * ln_pl(m.ln_rho0, m.ln_Tfyr, xb[m.th_rn + 2 * I], xb[m.th_rn + 2 * I + 1], m.lnk[k + 1]));
+    if (k < m.n_rn)  // free spectrum: kappa = 10^theta s^2 = 10^(theta + 18) ns^2
+      v = m.rn_free ? exp(0.5 * kLn10 * ((double)xb[m.th_rn + m.n_rn * I + k] + 18.0))
+                    : exp(0.5 * ln_pl(m.ln_rho0, m.ln_Tfyr, xb[m.th_rn + 2 * I], xb[m.th_rn + 2 * I + 1],
+                                      m.lnk[k + 1]));
     sk[(size_t)b * nach + r] = v;
   } else if (r < nach + ndm) {
     const int q = r - nach, I = q / m.nd, k = q % m.nd;
@@ -41,7 +43,9 @@ __global__ void k_spectra(DevModel m, const float* __restrict__ x, double* sk, d
     skd[(size_t)b * ndm + q] = v;
   } else {
     const int k = r - nach - ndm;
-    if (k < m.n_gwb) v = exp(0.5 * ln_pl(m.ln_rho0, m.ln_Tfyr, xb[m.th_gwb], xb[m.th_gwb + 1], m.lnk[k + 1]));
+    if (k < m.n_gwb)
+      v = m.gwb_free ? exp(0.5 * kLn10 * ((double)xb[m.th_gwb + k] + 18.0))
+                     : exp(0.5 * ln_pl(m.ln_rho0, m.ln_Tfyr, xb[m.th_gwb], xb[m.th_gwb + 1], m.lnk[k + 1]));
     srho[(size_t)b * m.na + k] = v;
   }
 }
@@ -378,16 +382,27 @@ __global__ void k_final(DevModel m, const float* __restrict__ x, const double* _
   for (int I = tid; I < np; I += nt) acc -= 0.5 * bt * chi2[(size_t)I * B + b];
   int outside = 0;
   for (int I = tid; I < np; I += nt) {
-    const float la = xb[m.th_rn + 2 * I], ga = xb[m.th_rn + 2 * I + 1];
-    outside |= !(la > m.la_lo && la < m.la_hi && ga > m.g_lo && ga < m.g_hi);
+    if (m.rn_free) {
+      for (int k = 0; k < m.n_rn; ++k) {
+        const float v = xb[m.th_rn + m.n_rn * I + k];
+        outside |= !(v > kFreeLo && v < kFreeHi);
+      }
+    } else {
+      const float la = xb[m.th_rn + 2 * I], ga = xb[m.th_rn + 2 * I + 1];
+      outside |= !(la > m.la_lo && la < m.la_hi && ga > m.g_lo && ga < m.g_hi);
+    }
     if (m.nd) {
       const float ld = xb[m.th_dm + 2 * I], gd = xb[m.th_dm + 2 * I + 1];
       outside |= !(ld > m.la_lo && ld < m.la_hi && gd > m.g_lo && gd < m.g_hi);
     }
   }
   if (tid == 0) {
-    const float la = xb[m.th_gwb], ga = xb[m.th_gwb + 1];
-    outside |= !(la > m.la_lo && la < m.la_hi && ga > m.g_lo && ga < m.g_hi);
+    if (m.gwb_free) {
+      for (int k = 0; k < m.n_gwb; ++k) outside |= !(xb[m.th_gwb + k] > kFreeLo && xb[m.th_gwb + k] < kFreeHi);
+    } else {
+      const float la = xb[m.th_gwb], ga = xb[m.th_gwb + 1];
+      outside |= !(la > m.la_lo && la < m.la_hi && ga > m.g_lo && ga < m.g_hi);
+    }
   }
   if (m.cw) {
     // CW prior: box on the 8 binary parameters, pulsar phases in (0, 2 pi), distances
@@ -429,12 +444,15 @@ __global__ void k_final(DevModel m, const float* __restrict__ x, const double* _
   for (int I = tid; I < np; I += nt) {
     double s1 = 0.0, s2 = 0.0;
     for (int k = 0; k < m.n_rn; ++k) {
-      const double v = dlnk[((size_t)b * np + I) * m.na + k];
+      const double v = dlnk[((size_t)b * np + I) * m.na + k];  // kappa d logp / d kappa
+      if (m.rn_free) gb[m.th_rn + m.n_rn * I + k] = (float)(kLn10 * v);  // d kappa / d theta = ln10 kappa
       s1 += v;
       s2 -= (m.lnk[k + 1] - m.ln_Tfyr) * v;
     }
-    gb[m.th_rn + 2 * I] = (float)(2.0 * kLn10 * s1);
-    gb[m.th_rn + 2 * I + 1] = (float)s2;
+    if (!m.rn_free) {  // power-law chain rule
+      gb[m.th_rn + 2 * I] = (float)(2.0 * kLn10 * s1);
+      gb[m.th_rn + 2 * I + 1] = (float)s2;
+    }
     if (m.nd) {
       double d1 = 0.0, d2 = 0.0;
       for (int k = 0; k < m.nd; ++k) {
@@ -449,12 +467,15 @@ __global__ void k_final(DevModel m, const float* __restrict__ x, const double* _
   if (tid == 0) {
     double s1 = 0.0, s2 = 0.0;
     for (int k = 0; k < m.n_gwb; ++k) {
-      const double v = dlnr[(size_t)b * m.na + k];
+      const double v = dlnr[(size_t)b * m.na + k];  // rho d logp / d rho
+      if (m.gwb_free) gb[m.th_gwb + k] = (float)(kLn10 * v);
       s1 += v;
       s2 -= (m.lnk[k + 1] - m.ln_Tfyr) * v;
     }
-    gb[m.th_gwb] = (float)(2.0 * kLn10 * s1);
-    gb[m.th_gwb + 1] = (float)s2;
+    if (!m.gwb_free) {
+      gb[m.th_gwb] = (float)(2.0 * kLn10 * s1);
+      gb[m.th_gwb + 1] = (float)s2;
+    }
   }
   if (m.cw) {
     const float* th = xb + m.th_cw;

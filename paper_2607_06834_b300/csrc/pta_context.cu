@@ -103,6 +103,7 @@ int pta_create(pta_ctx** out, const pta_model_desc* d) {
     return PTA_EINVAL;
   if (d->precision < PTA_PREC_FP64 || d->precision > PTA_PREC_GRAM) return PTA_EINVAL;
   if (d->precision == PTA_PREC_GRAM && d->cw) return PTA_EINVAL;
+  if (d->spectrum < 0 || d->spectrum > (PTA_FREE_GWB | PTA_FREE_RN)) return PTA_EINVAL;
   pta_ctx* c = new (std::nothrow) pta_ctx();
   if (!c) return PTA_ENOMEM;
   c->desc = *d;
@@ -199,10 +200,15 @@ int pta_finalize(pta_ctx* c, void* stream) {
   L.z_ach = 0;
   L.z_dm = m.na * 2 * npsr;
   L.d_z = L.z_dm + npsr * m.nd * 2;
+  m.rn_free = (d.spectrum & PTA_FREE_RN) ? 1 : 0;
+  m.gwb_free = (d.spectrum & PTA_FREE_GWB) ? 1 : 0;
+  L.n_th_rn = m.rn_free ? m.n_rn : 2;
+  L.n_th_gwb = m.gwb_free ? m.n_gwb : 2;
+  m.nthr = L.n_th_rn;
   L.th_rn = L.d_z;
-  L.th_dm = L.th_rn + 2 * npsr;
+  L.th_dm = L.th_rn + L.n_th_rn * npsr;
   L.th_gwb = L.th_dm + (m.nd > 0 ? 2 * npsr : 0);
-  L.th_cw = L.th_gwb + 2;
+  L.th_cw = L.th_gwb + L.n_th_gwb;
   L.d = L.th_cw + (m.cw ? 8 + 2 * npsr : 0);
   L.tspan_s = m.T;
   L.t0_s = tmin;

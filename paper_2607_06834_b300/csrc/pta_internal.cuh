@@ -21,7 +21,8 @@ constexpr int kChunk = 2048;     // TOAs per work unit of the TOA kernels
 // The per-frequency Cholesky and its adjoint hold two packed N_p x N_p triangles
 // and 7 N_p vectors in FP64 shared memory: (N_p (N_p + 1) + 7 N_p) x 8 B <= 227 KB.
 constexpr int kMaxPsr = 166;
-constexpr int kLowBins = 4;     // lowest frequencies whose basis columns are projected off the timing model
+constexpr int kLowBins = 4;
+constexpr double kFreeLo = -20.0, kFreeHi = -5.0;  // free-spectrum prior box, log10 (s^2) (Sec. Priors)     // lowest frequencies whose basis columns are projected off the timing model
 
 // Everything a kernel needs about the model and the resident data.  Passed by
 // value; all pointers are device pointers owned by the context.
@@ -50,6 +51,8 @@ struct DevModel {
   const unsigned char* xmlo;    // BF16 tensor-core path: fixed basis columns per 64-TOA tile (built on first use)
   // Gram form (Eq. posterior_implemented) with the reference fit: per pulsar
   // G~ = F^T N~^-1 F [P x P] as FP32 hi/lo, g'' = F^T N^-1 dt'' [P], c'' = dt''^T N^-1 dt''
+  int gwb_free, rn_free;        // free spectral models (one log10 variance per bin)
+  int nthr;                     // red-noise parameters per pulsar (2, or n_rn when free)
   const double* beta;           // per-chain inverse temperature (App. "tempered likelihoods"); nullptr: 1
   int inject;                   // test hook (pta_debug_inject): 1 = the BF16 kernel withholds one MMA completion
   const float* Gth;

@@ -28,7 +28,9 @@ class Engine:
     def __init__(self, arr, precision: str = "fp32", device: int = 0):
         self.device = torch.device("cuda", device)
         torch.cuda.set_device(self.device)
-        desc = abi.ModelDesc(arr.n_gwb, arr.n_rn, arr.n_dm, int(bool(arr.cw)), abi.PREC[precision], 1400.0)
+        spectrum = (1 if getattr(arr, "gwb_free", False) else 0) | (2 if getattr(arr, "rn_free", False) else 0)
+        desc = abi.ModelDesc(arr.n_gwb, arr.n_rn, arr.n_dm, int(bool(arr.cw)), abi.PREC[precision], 1400.0,
+                             spectrum)
         h = C.c_void_p()
         rc = abi.lib.pta_create(C.byref(h), C.byref(desc))
         if rc != 0:

@@ -471,3 +471,35 @@ def test_tempered_likelihood_matches_oracle(prec):
     eng.set_beta(None)
     lp1, _, _ = _eval(eng, X)
     assert abs(lp1[0] - lp[0]) <= 1e-9 * max(1.0, abs(lp[0]))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "gram"])
+@pytest.mark.parametrize("free", [(True, False), (True, True)])
+def test_free_spectrum_matches_oracle(prec, free):
+    """Free spectral models (Sec. Priors): one log10 variance per bin for the GWB and,
+    in the second case, for every pulsar's red noise; ragged array, near-posterior and
+    random points, FP32 bar / FP64 tolerances as in test_ragged_arrays."""
+    kw = dict(RAGGED[0], gwb_free=free[0], rn_free=free[1])
+    arr = synth.small_array(**kw)
+    orc = O.Oracle(arr)
+    X = synth.make_points(arr, 40, seed=16)
+    X[:3] = np.array([O.curn_point(orc, x.astype(np.float64), 1.0, seed=i) for i, x in enumerate(X[:3])])
+    lo, go = _oracle(orc, X)
+    eng = _engine(arr, prec)
+    lay = synth.layout(arr)
+    for k in ("th_rn", "th_dm", "th_gwb", "th_cw", "d", "n_th_rn", "n_th_gwb"):
+        assert eng.layout[k] == lay[k], k
+    lp, g, st = _eval(eng, X)
+    assert np.all(st == 0)
+    if prec in ("fp64", "gram"):
+        assert np.max(np.abs(lp - lo) / np.maximum(1.0, np.abs(lo))) < FP64_REL
+        assert np.max(_grad_rel(g, go)) < 1e-6
+    else:
+        assert np.all(np.abs(lp - lo) <= LOGP_ABS + REL_RANDOM[prec] * np.abs(lo))
+        assert np.max(np.abs(lp[:3] - lo[:3])) < LOGP_ABS
+        assert np.max(_grad_rel(g, go)) < GRAD_REL
+    # outside the free-spectrum box: -inf, status 1
+    Y = X[:2].copy()
+    Y[1, lay["th_gwb"]] = -4.0
+    lpy, gy, sty = _eval(eng, Y)
+    assert sty.tolist() == [0, 1] and np.isneginf(lpy[1])
