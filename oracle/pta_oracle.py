@@ -18,6 +18,9 @@ analysis of pulsar timing data"):
   * standardizing transform a = L z     Eqs. (standardizing_transform),
                                         (standardized_density) with mu = 0 and
                                         Sigma = phi (prior-whitened reading)
+  * CURN-posterior transform            Eqs. (PTA_standard_transform_curn),
+    a = ahat_CURN + L_CURN z            (standardized_stochastic_posterior); the
+                                        tempered T_beta of App. "tempered likelihoods"
   * posterior with deterministic signal Eq. (raw_det_posterior)
   * CW phase / frequency evolution      Eqs. (phase_evolve), (CW_evolve),
                                         (phase_evolve_Taylor)
@@ -241,7 +244,13 @@ class Oracle:
     backend, efac, equad_s, M, pos, dist_kpc), ``n_gwb``, ``n_rn``, ``n_dm``, ``cw``.
     """
 
-    def __init__(self, arr, store_basis: bool = True):
+    def __init__(self, arr, store_basis: bool = True, transform: str = "prior"):
+        if transform not in ("prior", "curn"):
+            raise ValueError("transform must be 'prior' or 'curn'")
+        if transform == "curn" and arr.cw:
+            raise NotImplementedError("CURN transform with a deterministic signal (Eq. decenter_det_PTA)")
+        self.transform_kind = transform
+        self._curn_fixed = None
         self.arr = arr
         self.psrs = arr.pulsars
         self.npsr = len(self.psrs)
@@ -366,6 +375,194 @@ class Oracle:
                         a[I, off + 2 * k + c] = math.sqrt(kdm[I, k]) * z_dm[I, k, c]
         return a, Ls
 
+    # -- CURN-posterior standardizing transform ------------------------------------
+    # Eq. (PTA_standard_transform_curn): per pulsar, a_I = ahat_I + L_I z_I with
+    # Sigma_I = (beta F_I^T N~_I^-1 F_I + phi_CURN,I^-1)^-1 = L_I L_I^T (Cholesky, lower)
+    # and ahat_I = beta Sigma_I F_I^T N~_I^-1 dt_I.  phi_CURN is the prior covariance of
+    # Eq. (prior_cov) with the inter-pulsar correlations dropped (alpha_IJ = delta_IJ,
+    # Gamma_II = 1), diagonal per pulsar.  beta = 1 is the transform of the paper's main
+    # result; beta < 1 the tempered transform T_beta of App. "tempered likelihoods".
+    # The density sampled is Eq. (standardized_stochastic_posterior): the posterior of
+    # Eq. (stochastic_posterior) at a(z) times det L_CURN, which (completing the square
+    # back) is the likelihood times the HD prior N(a; 0, phi) times det L_CURN.
+    def curn_fixed(self, I):
+        """(F^T N~^-1 F, F^T N~^-1 dt) of pulsar I: parameter-independent."""
+        if self._curn_fixed is None:
+            self._curn_fixed = [None] * self.npsr
+        if self._curn_fixed[I] is None:
+            F = self.get_F(I)
+            NF = ntilde_inv_woodbury(self.Nvar[I], self.psrs[I].M, F)
+            self._curn_fixed[I] = (F.T @ NF, NF.T @ self.dt_ns[I])
+        return self._curn_fixed[I]
+
+    def curn_prior_var(self, I, rho, kappa, kdm):
+        """Diagonal of phi_CURN for pulsar I: rho_k + kappa_Ik on both achromatic columns
+        of bin k, kappa^DM_Ik on the DM columns."""
+        phi = np.zeros(self.P)
+        for k in range(self.na):
+            phi[2 * k: 2 * k + 2] = rho[k] + kappa[I, k]
+        for k in range(self.n_dm):
+            phi[2 * self.na + 2 * k: 2 * self.na + 2 * k + 2] = kdm[I, k]
+        return phi
+
+    def curn_moments(self, I, phiC, beta):
+        """ahat_I, L_I (lower Cholesky factor of Sigma_I) and Sigma_I."""
+        FNF, FNd = self.curn_fixed(I)
+        Sigma = np.linalg.inv(beta * FNF + np.diag(1.0 / phiC))
+        Sigma = 0.5 * (Sigma + Sigma.T)
+        return beta * Sigma @ FNd, np.linalg.cholesky(Sigma), Sigma
+
+    def z_per_pulsar(self, z_ach, z_dm):
+        """z regrouped per pulsar in the coefficient order of a_I: z_I[2k + c] is
+        z_ach[k][c][I], z_I[2 N_a + 2k + c] is z_dm[I][k][c] (the parameter layout of the
+        prior-whitened transform, reused)."""
+        Z = np.zeros((self.npsr, self.P))
+        for k in range(self.na):
+            for c in range(2):
+                Z[:, 2 * k + c] = z_ach[k, c]
+        for I in range(self.npsr):
+            for k in range(self.n_dm):
+                for c in range(2):
+                    Z[I, 2 * self.na + 2 * k + c] = z_dm[I, k, c]
+        return Z
+
+    def curn_transform(self, z_ach, z_dm, rho, kappa, kdm, beta: float = 1.0):
+        """a_I = ahat_I + L_I z_I for every pulsar; returns (a, [L_I])."""
+        Z = self.z_per_pulsar(z_ach, z_dm)
+        a = np.zeros((self.npsr, self.P))
+        Ls = []
+        for I in range(self.npsr):
+            ahat, L, _ = self.curn_moments(I, self.curn_prior_var(I, rho, kappa, kdm), beta)
+            a[I] = ahat + L @ Z[I]
+            Ls.append(L)
+        return a, Ls
+
+    def log_det_phi(self, rho, kappa, kdm) -> float:
+        """log det phi over all coefficient columns (two per bin)."""
+        ld = 0.0
+        for k in range(self.na):
+            ld += 2.0 * np.linalg.slogdet(self.phi_bin(rho[k], kappa[:, k]))[1]
+        for I in range(self.npsr):
+            for k in range(self.n_dm):
+                ld += 2.0 * math.log(kdm[I, k])
+        return ld
+
+    def _logp_curn(self, x, beta, lpt):
+        z_ach, z_dm, th_rn, th_dm, th_gwb, _ = self.unpack(x)
+        rho, kappa, kdm = self.spectra(th_rn, th_dm, th_gwb)
+        a, Ls = self.curn_transform(z_ach, z_dm, rho, kappa, kdm, beta)
+        chi2 = 0.0
+        for I in range(self.npsr):
+            r = self.dt_ns[I] - self.get_F(I) @ a[I]
+            chi2 += r @ ntilde_inv_woodbury(self.Nvar[I], self.psrs[I].M, r)
+        logdetL = sum(float(np.sum(np.log(np.diag(L)))) for L in Ls)
+        return (-0.5 * beta * chi2 - 0.5 * self._a_phi_a(a, rho, kappa, kdm)
+                - 0.5 * self.log_det_phi(rho, kappa, kdm) + logdetL + lpt)
+
+    def spectra_tangent(self, j, rho, kappa, kdm):
+        """d(rho, kappa, kappa^DM) / d x_j for a hyper-parameter index j (closed forms of
+        the power law and the free spectrum); None if x_j is not a spectral parameter."""
+        o, npsr = self.lay, self.npsr
+        drho, dkap, dkdm = np.zeros(self.na), np.zeros((npsr, self.na)), np.zeros((npsr, self.n_dm))
+        ks = np.arange(1, self.na + 1)
+        lnf = np.log(ks / self.T / F_YR)
+        if o["th_rn"] <= j < o["th_rn"] + self.nthr * npsr:
+            I, q = divmod(j - o["th_rn"], self.nthr)
+            if self.rn_free:
+                dkap[I, q] = LN10 * kappa[I, q]
+            else:
+                dkap[I] = (2 * LN10 if q == 0 else -lnf) * kappa[I]
+        elif self.n_dm and o["th_dm"] <= j < o["th_dm"] + 2 * npsr:
+            I, q = divmod(j - o["th_dm"], 2)
+            lnfd = np.log(np.arange(1, self.n_dm + 1) / self.T / F_YR)
+            dkdm[I] = (2 * LN10 if q == 0 else -lnfd) * kdm[I]
+        elif o["th_gwb"] <= j < o["th_gwb"] + self.nthg:
+            q = j - o["th_gwb"]
+            if self.gwb_free:
+                drho[q] = LN10 * rho[q]
+            else:
+                drho = (2 * LN10 if q == 0 else -lnf) * rho
+        else:
+            return None
+        return drho, dkap, dkdm
+
+    def _grad_curn(self, x, beta):
+        """Gradient under the CURN transform.  z-block: d logp / d z_I = L_I^T gbar_I
+        with gbar = beta F^T N~^-1 r - phi^-1 a (likelihood and HD prior in a).
+        Hyper-parameters: the forward-mode derivative along each spectral parameter:
+        at fixed a, 1/2 v^T dphi v - 1/2 tr(phi^-1 dphi) (v = phi^-1 a); through
+        a(eta) = ahat + L z, gbar . da with dSigma = -Sigma dSigma^-1 Sigma,
+        dL = chol_tangent(L, dSigma), dahat = beta dSigma F^T N~^-1 dt; and
+        d log det L = tr(L^-1 dL)."""
+        g = np.zeros(self.D)
+        if not math.isfinite(self.log_prior_theta(x)):
+            return g
+        z_ach, z_dm, th_rn, th_dm, th_gwb, _ = self.unpack(x)
+        rho, kappa, kdm = self.spectra(th_rn, th_dm, th_gwb)
+        npsr, na, nd, P = self.npsr, self.na, self.n_dm, self.P
+        Z = self.z_per_pulsar(z_ach, z_dm)
+        mom = []
+        a = np.zeros((npsr, P))
+        for I in range(npsr):
+            phiC = self.curn_prior_var(I, rho, kappa, kdm)
+            ahat, L, Sigma = self.curn_moments(I, phiC, beta)
+            a[I] = ahat + L @ Z[I]
+            mom.append((phiC, L, Sigma))
+        gbar = np.zeros((npsr, P))
+        for I in range(npsr):
+            r = self.dt_ns[I] - self.get_F(I) @ a[I]
+            gbar[I] = beta * (self.get_F(I).T @ ntilde_inv_woodbury(self.Nvar[I], self.psrs[I].M, r))
+        Phis = [self.phi_bin(rho[k], kappa[:, k]) for k in range(na)]
+        v = np.zeros((npsr, P))
+        for k in range(na):
+            for c in range(2):
+                v[:, 2 * k + c] = np.linalg.solve(Phis[k], a[:, 2 * k + c])
+        for I in range(npsr):
+            for k in range(nd):
+                v[I, 2 * na + 2 * k: 2 * na + 2 * k + 2] = a[I, 2 * na + 2 * k: 2 * na + 2 * k + 2] / kdm[I, k]
+        gbar -= v
+        # z block, scattered back to the parameter layout
+        GZ = np.array([mom[I][1].T @ gbar[I] for I in range(npsr)])
+        o = self.lay
+        gz = np.zeros((na, 2, npsr))
+        for k in range(na):
+            for c in range(2):
+                gz[k, c] = GZ[:, 2 * k + c]
+        g[: o["z_dm"]] = gz.reshape(-1)
+        if nd:
+            g[o["z_dm"]: o["dz"]] = GZ[:, 2 * na:].reshape(npsr, nd, 2).reshape(-1)
+        for j in range(o["dz"], self.D):
+            tan = self.spectra_tangent(j, rho, kappa, kdm)
+            if tan is None:
+                continue
+            drho, dkap, dkdm = tan
+            d = 0.0
+            for k in range(na):  # HD prior at fixed a
+                dPhi = drho[k] * self.Gamma + np.diag(dkap[:, k])
+                if not np.any(dPhi):
+                    continue
+                for c in range(2):
+                    d += 0.5 * v[:, 2 * k + c] @ dPhi @ v[:, 2 * k + c]
+                d -= np.trace(np.linalg.solve(Phis[k], dPhi))
+            for I in range(npsr):
+                for k in range(nd):
+                    if dkdm[I, k]:
+                        vv = v[I, 2 * na + 2 * k: 2 * na + 2 * k + 2]
+                        d += 0.5 * dkdm[I, k] * (vv @ vv) - dkdm[I, k] / kdm[I, k]
+            for I in range(npsr):  # the transform a(eta) and log det L
+                dphiC = self.curn_prior_var(I, drho, dkap, dkdm)
+                if not np.any(dphiC):
+                    continue
+                phiC, L, Sigma = mom[I]
+                dSinv = -dphiC / phiC ** 2                 # d(phi_CURN^-1), diagonal
+                dSigma = -(Sigma * dSinv[None, :]) @ Sigma
+                dL = chol_tangent(L, dSigma)
+                FNd = self.curn_fixed(I)[1]
+                da = beta * dSigma @ FNd + dL @ Z[I]
+                d += gbar[I] @ da + np.trace(sla.solve_triangular(L, dL, lower=True))
+            g[j] = d
+        return g
+
     # -- deterministic signal ---------------------------------------------------
     def cw_th(self, th_cw, I):
         return th_cw[:8], th_cw[8 + 2 * I], th_cw[9 + 2 * I]
@@ -377,16 +574,21 @@ class Oracle:
         return cw_signal(self.t_rel[I], self.psrs[I].pos, th8, dist, pph)
 
     # -- log posterior ----------------------------------------------------------
-    def residuals(self, x):
+    def residuals(self, x, beta: float = 1.0):
+        """Residuals r_I = dt_I - F_I a_I - h_I(theta) with a from the chosen
+        standardizing transform (the CURN transform depends on beta when tempered)."""
         z_ach, z_dm, th_rn, th_dm, th_gwb, th_cw = self.unpack(x)
         rho, kappa, kdm = self.spectra(th_rn, th_dm, th_gwb)
-        a, Ls = self.transform(z_ach, z_dm, rho, kappa, kdm)
+        if self.transform_kind == "curn":
+            a, Ls = self.curn_transform(z_ach, z_dm, rho, kappa, kdm, beta)
+        else:
+            a, Ls = self.transform(z_ach, z_dm, rho, kappa, kdm)
         rs = [self.dt_ns[I] - self.get_F(I) @ a[I] - self.signal(th_cw, I) for I in range(self.npsr)]
         return rs, a, Ls, (rho, kappa, kdm)
 
-    def chi2_terms(self, x):
+    def chi2_terms(self, x, beta: float = 1.0):
         """Per-pulsar r_I^T N~_I^-1 r_I with r_I = dt_I - F_I a_I - h_I(theta)."""
-        rs, *_ = self.residuals(x)
+        rs, *_ = self.residuals(x, beta)
         out = np.zeros(self.npsr)
         for I in range(self.npsr):
             wt = ntilde_inv_woodbury(self.Nvar[I], self.psrs[I].M, rs[I])
@@ -415,6 +617,8 @@ class Oracle:
         if not math.isfinite(lpt):
             return -math.inf
         x = np.asarray(x, dtype=np.float64)
+        if self.transform_kind == "curn":
+            return self._logp_curn(x, beta, lpt)
         z = x[: self.Dz]
         return -0.5 * beta * float(self.chi2_terms(x).sum()) - 0.5 * float(z @ z) + lpt
 
@@ -433,8 +637,11 @@ class Oracle:
     def logp_full(self, x) -> float:
         """Normalised log density in (z, theta) at fixed theta: logp + data_constant
         - (D_z/2) log 2 pi, with the prior on a and the Jacobian written out literally:
-        log N(a; 0, phi) + log det L (Eqs. a_prior, standardized_density)."""
+        log N(a; 0, phi) + log det L (Eqs. a_prior, standardized_density).  Under the CURN
+        transform ``logp`` already carries the prior on a and det L_CURN literally."""
         x = np.asarray(x, dtype=np.float64)
+        if self.transform_kind == "curn":
+            return self.logp(x) + self.data_constant() - 0.5 * self.Dz * math.log(2 * math.pi)
         z_ach, z_dm, th_rn, th_dm, th_gwb, th_cw = self.unpack(x)
         rho, kappa, kdm = self.spectra(th_rn, th_dm, th_gwb)
         a, Ls = self.transform(z_ach, z_dm, rho, kappa, kdm)
@@ -467,6 +674,8 @@ class Oracle:
         beta: gradient of the tempered posterior of Eq. (tempered_post), every
         likelihood derivative (d logp / d a and the CW term) scaled by beta."""
         x = np.asarray(x, dtype=np.float64)
+        if self.transform_kind == "curn":
+            return self._grad_curn(x, beta)
         g = np.zeros(self.D)
         if not math.isfinite(self.log_prior_theta(x)):
             return g

@@ -503,3 +503,41 @@ def test_free_spectrum_matches_oracle(prec, free):
     Y[1, lay["th_gwb"]] = -4.0
     lpy, gy, sty = _eval(eng, Y)
     assert sty.tolist() == [0, 1] and np.isneginf(lpy[1])
+
+
+# ------------------------------------------------------------------ feature combinations
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "tf32x3", "bf16x3"])
+def test_cw_tempered_free_spectra_combined(prec):
+    """Model features at once: free spectral models for the GWB and the red noise and
+    per-chain temperatures on a ragged array with DM, plus a circular binary on the FP32
+    path (the one that carries it).  FP32/FP64 bars as above; the tensor-core splits at
+    their reported precision."""
+    arr = synth.small_array(npsr=3, ntoa=[150, 700, 2300], m=[3, 9, 12], n_gwb=4, n_rn=5, n_dm=3, seed=43,
+                            nbackend=2, cw=(prec == "fp32"), gwb_free=True, rn_free=True)
+    orc = O.Oracle(arr)
+    B = 9
+    X = synth.make_points(arr, B, seed=18)
+    X[:3] = np.array([O.curn_point(orc, x.astype(np.float64), 1.0, seed=i) for i, x in enumerate(X[:3])])
+    beta = np.array([1.0, 0.4, 0.0, 0.8, 0.25, 1.0, 0.6, 0.05, 0.9])
+    eng = _engine(arr, prec)
+    eng.set_beta(torch.tensor(beta, device="cuda"))
+    lp, g, st = _eval(eng, X)
+    assert np.all(st == 0)
+    Xd = X.astype(np.float64)
+    lo = np.array([orc.logp(x, beta=b) for x, b in zip(Xd, beta)])
+    go = np.array([orc.grad(x, beta=b) for x, b in zip(Xd, beta)])
+    err, rel = np.abs(lp - lo), _grad_rel(g, go)
+    print(f"{prec}: max |dlogp| {err.max():.2e} (near-posterior {err[:3].max():.2e}) max grad rel {rel.max():.2e}")
+    if prec == "fp64":
+        assert np.max(err / np.maximum(1.0, np.abs(lo))) < FP64_REL
+        assert rel.max() < 1e-6
+    elif prec == "fp32":
+        assert np.all(err <= LOGP_ABS + REL_RANDOM["fp32"] * np.abs(lo))
+        assert err[:3].max() < LOGP_ABS and rel.max() < GRAD_REL
+    elif prec == "tf32x3":
+        assert np.all(err <= TC_REPORTED_LOGP + REL_RANDOM["tf32x3"] * np.abs(lo))
+        assert rel.max() < TC_REPORTED_GRAD
+    else:
+        assert np.all(err <= BF16_REPORTED_LOGP + REL_RANDOM["bf16x3"] * np.abs(lo))
+        assert rel.max() < BF16_REPORTED_GRAD
+    eng.set_beta(None)

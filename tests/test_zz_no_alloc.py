@@ -46,6 +46,31 @@ def test_noalloc_matches_allocating_entry(kw):
         assert np.all(np.linalg.norm(g - g_ref, axis=1) <= GRAD_REL * np.linalg.norm(g_ref, axis=1))
 
 
+@pytest.mark.parametrize("precision", ["fp32", "gram"])
+def test_noalloc_tempered_free_spectra(precision):
+    """Feature combination on the allocation-free entry point: free spectral models for
+    the GWB and the red noise, a per-chain inverse temperature, and the Gram form."""
+    from paper_2607_06834_b300.engine import Engine
+    arr = synth.small_array(npsr=3, ntoa=[400, 900, 1500], m=[3, 6, 8], n_gwb=4, n_rn=5, n_dm=3, seed=47,
+                            nbackend=2, gwb_free=True, rn_free=True)
+    eng = Engine(arr, precision=precision)
+    B = 7
+    X = torch.tensor(synth.make_points(arr, B, seed=404), device="cuda")
+    eng.set_beta(torch.linspace(0.1, 1.0, B, dtype=torch.float64))
+    lp_ref, g_ref, st_ref = _call(abi.lib.pta_logp_and_grad, eng, X)
+    lp, g, st = _call(abi.lib.pta_logp_and_grad_noalloc, eng, X)
+    assert np.all(st_ref == 0) and np.array_equal(st, st_ref)
+    assert np.all(np.abs(lp - lp_ref) <= LOGP_ABS)
+    assert np.all(np.linalg.norm(g - g_ref, axis=1) <= GRAD_REL * np.linalg.norm(g_ref, axis=1))
+    # more chains than the temperatures given: refused, nothing computed
+    X2 = torch.tensor(synth.make_points(arr, B + 1, seed=405), device="cuda")
+    lp2 = torch.empty(B + 1, dtype=torch.float64, device="cuda")
+    rc = abi.lib.pta_logp_and_grad_noalloc(eng._h, B + 1, C.c_void_p(X2.data_ptr()), C.c_void_p(lp2.data_ptr()),
+                                           None, None, None)
+    assert rc == abi.PTA_EINVAL
+    eng.set_beta(None)
+
+
 def test_noalloc_rejects_oversized_batch():
     from paper_2607_06834_b300.engine import Engine
     eng = Engine(synth.make_array("ng15"), precision="fp32")
