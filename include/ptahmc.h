@@ -145,6 +145,31 @@ int pta_autotune(pta_ctx* ctx, int B, void* stream, int* chosen, double* ms, int
  * context keeps its own copy.  Evaluations of more than n chains then return
  * PTA_EINVAL.  n = 0 or beta = NULL turns tempering off.  Expected 0 <= beta. */
 int pta_set_beta(pta_ctx* ctx, int n, const double* beta, void* stream);
+/* Standardizing transform of the Fourier coefficients for later evaluations and HMC
+ * trajectories (PTA_TRANSFORM_*).
+ *   PTA_TRANSFORM_PRIOR (default): a_{.,k,c} = L_k z_{.,k,c} with Phi_k = L_k L_k^T per
+ *     frequency bin (Eq. standardizing_transform with mu = 0, Sigma = phi);
+ *     logp = -beta/2 sum_I chi2_I - |z|^2/2 + log p(eta).
+ *   PTA_TRANSFORM_CURN: per pulsar a_I = ahat_I + L_I z_I (Eq. PTA_standard_transform_curn)
+ *     with Sigma_I = (beta F_I^T N~_I^-1 F_I + phi_CURN,I^-1)^-1 = L_I L_I^T (lower
+ *     Cholesky factor) and ahat_I = beta Sigma_I F_I^T N~_I^-1 dt_I; phi_CURN is the prior
+ *     covariance without inter-pulsar correlations (rho_k + kappa_Ik, kappa^DM_Ik on the
+ *     diagonal).  With tempering this is the tempered transform T_beta of App. "The
+ *     standardizing transform for tempered likelihoods".  logp = -beta/2 sum_I chi2_I
+ *     - 1/2 a^T phi^-1 a - 1/2 log det phi + sum_I log det L_I + log p(eta) with the
+ *     Hellings-Downs-correlated phi (Eq. standardized_stochastic_posterior, the
+ *     (2 pi)^(-D_z/2) and the data constant dropped as in the default transform).  z
+ *     keeps the layout of pta_layout: the entry of coefficient (I, p) sits where the
+ *     prior-whitened transform keeps it.  Each evaluation factorises one P x P FP64
+ *     matrix per (pulsar, chain), about P^3/3 FP64 multiply-adds, and keeps
+ *     B N_p P (P + 1) / 2 doubles of inverse factors between the value and the gradient
+ *     (PTA_ENOMEM from the evaluation if they do not fit).
+ * PTA_EINVAL for an unknown value and, for PTA_TRANSFORM_CURN, for models with the
+ * continuous-wave signal (the deterministic generalisation, Eq. decenter_det_PTA, is not
+ * built).  pta_logp_and_grad_noalloc rejects the CURN transform.  Recaptures HMC graphs. */
+#define PTA_TRANSFORM_PRIOR 0
+#define PTA_TRANSFORM_CURN 1
+int pta_set_transform(pta_ctx* ctx, int transform);
 /* Test hook for the bounded device waits (no counterpart in the paper).  code 1:
  * in PTA_PREC_BF16X3 evaluations the tensor-core kernel withholds the completion
  * signal of its first tile's F a product, so its epilogue's bounded mbarrier wait

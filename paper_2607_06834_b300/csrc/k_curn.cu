@@ -1,0 +1,438 @@
+// CURN-posterior standardizing transform (Eq. PTA_standard_transform_curn; with a
+// per-chain beta, the tempered transform T_beta of App. "The standardizing transform
+// for tempered likelihoods"), FP64.  Per (pulsar I, chain b):
+//   A = beta G~ + diag(1 / phi_C),  G~ = F^T N~^-1 F,
+//   phi_C,p = rho_k + kappa_Ik on the two achromatic columns of bin k, kappa^DM_Ik on
+//   the DM columns (the prior covariance without inter-pulsar correlations);
+//   A = U U^T with U upper triangular and W = U^-1, so that L_CURN = W^T is the lower
+//   Cholesky factor of Sigma_CURN = A^-1;
+//   a = ahat + W^T z, ahat = beta W^T W g (g = F^T N~^-1 dt), log det L_CURN = sum log W_pp.
+// The density (Eq. standardized_stochastic_posterior) is the likelihood times the
+// Hellings-Downs prior N(a; 0, phi) times det L_CURN; the prior term is evaluated per
+// frequency bin with the factors of Phi_k from the prior stage.
+//
+// Reversed order.  With p' = P-1-p the upper factor U becomes a lower one:
+// A' = J A J = L' D L'^T (LDL^T, L' unit lower) and Y' = D^-1/2 L'^-1 = J W J.  The
+// factorisation and the inverse share one packed lower triangle: in the LDL^T sweep
+// column j of L' is consumed by step j, and the inverse's column j (-l_ij) takes its
+// place, so at every step the triangle holds the trailing part of A' and the finished
+// rows of L'^-1.  P^3/3 FP64 multiply-adds per (pulsar, chain), the same count as a
+// Cholesky factorisation plus a triangular inverse.  The triangle lives in shared
+// memory when it fits, else in the per-(pulsar, chain) slot of the global inverse
+// buffer (L2-resident for the CTAs in flight).
+//
+// Gradient.  With gbar = d logp / d a = beta F^T N~^-1 r - phi^-1 a (likelihood and HD
+// prior), d logp / d z = W gbar, and for the diagonal d_p = 1 / phi_C,p of A
+//   d logp / d d_p = -(A^-1 gbar)_p ahat_p
+//                    - sum_{i<j<=p} W_ip z_i s_j W_jp - 1/2 sum_i W_ip^2 (z_i s_i + 1),
+// s = W gbar (from dahat = -A^-1 dA ahat, dW^T = -W^T Psi(W dA W^T)^T with Psi the
+// upper triangle and half the diagonal, and d log det L_CURN = -1/2 tr(A^-1 dA)): the
+// columns of W give every p in O(P^2).
+#include <cmath>
+
+#include "pta_internal.cuh"
+
+namespace pta {
+namespace {
+
+constexpr int kCT = 128;  // threads per (pulsar, chain) CTA
+
+__device__ __forceinline__ int trl(int i, int j) { return i * (i + 1) / 2 + j; }
+
+// packed lower index e -> (row, column), e < 2^23
+__device__ __forceinline__ void tri_decode(int e, int& i, int& j) {
+  int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  if (r * (r + 1) / 2 > e) --r;
+  else if ((r + 1) * (r + 2) / 2 <= e) ++r;
+  i = r;
+  j = e - r * (r + 1) / 2;
+}
+
+// position in x of the z entry of coefficient p of pulsar I (prior-whitened layout)
+__device__ __forceinline__ int zidx(const DevModel& m, int I, int p) {
+  if (p < 2 * m.na) return m.z_ach + p * m.npsr + I;
+  const int q = p - 2 * m.na;
+  return m.z_dm + (I * m.nd + (q >> 1)) * 2 + (q & 1);
+}
+
+// phi_CURN of coefficient p of pulsar I for chain b
+__device__ __forceinline__ double phic(const DevModel& m, const double* sk, const double* skd,
+                                       const double* srho, int b, int I, int p) {
+  if (p < 2 * m.na) {
+    const int k = p >> 1;
+    const double r = srho[(size_t)b * m.na + k], q = sk[((size_t)b * m.npsr + I) * m.na + k];
+    return fma(r, r, q * q);
+  }
+  const double q = skd[((size_t)b * m.npsr + I) * m.nd + ((p - 2 * m.na) >> 1)];
+  return q * q;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];  // fixed order
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Forward: factor, inverse, a = ahat + W^T z, ahat, log det L_CURN.  Grid (npsr, B).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kCT)
+    k_curn_forward(DevModel m, const float* __restrict__ x, const double* __restrict__ sk,
+                   const double* __restrict__ skd, const double* __restrict__ srho, double* a64, double* Wg,
+                   double* ahat, double* ld, int32_t* stat, int B, int in_smem) {
+  extern __shared__ double sm[];
+  __shared__ int s_bad;
+  __shared__ double red[kCT / 32];
+  const int I = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, P = m.P;
+  const int ntri = P * (P + 1) / 2;
+  const size_t o = (size_t)I * B + b;
+  double* Wslot = Wg + o * ntri;
+  double* T = in_smem ? sm : Wslot;
+  double* d = in_smem ? sm + ntri : sm;  // pivots d_j, then d_j^-1/2
+  double* rd = d + P;                     // diagonal prior precision, then 1/d_j
+  double* u = rd + P;                     // unscaled column j
+  double* lc = u + P;                     // l_ij of column j
+  double* gp = lc + P;                    // g, reversed
+  double* zp = gp + P;                    // z, reversed
+  double* up = zp + P;                    // Y' g'
+  double* tp = up + P;                    // beta Y' g' + z'
+  const double bt = m.beta ? m.beta[b] : 1.0;
+  const float* xb = x + (size_t)b * m.d;
+  const double* G = m.Grev + (size_t)I * ntri;
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (int i = tid; i < P; i += kCT) {
+    const int p = P - 1 - i;
+    const double ph = phic(m, sk, skd, srho, b, I, p);
+    double dv = 1.0;
+    if (ph > 0.0 && ph < INFINITY)
+      dv = 1.0 / ph;
+    else
+      s_bad = 1;
+    rd[i] = dv;
+    gp[i] = m.gt[(size_t)I * P + p];
+    zp[i] = (double)xb[zidx(m, I, p)];
+  }
+  __syncthreads();
+  for (int e = tid; e < ntri; e += kCT) {
+    int i, j;
+    tri_decode(e, i, j);
+    const double v = bt * G[e];
+    T[e] = (i == j) ? v + rd[i] : v;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double dd = T[0];
+    if (!(dd > 0.0)) {
+      s_bad = 1;
+      dd = 1.0;
+    }
+    d[0] = dd;
+    rd[0] = recip64(dd);
+  }
+  __syncthreads();
+  for (int j = 0; j < P; ++j) {
+    const double r = rd[j];
+    const int s = P - 1 - j;
+    for (int e = tid; e < s; e += kCT) {
+      const int i = j + 1 + e;
+      const double v = T[trl(i, j)];
+      const double l = v * r;
+      u[i] = v;
+      lc[i] = l;
+      T[trl(i, j)] = -l;  // column j of L'^-1
+    }
+    __syncthreads();
+    // trailing triangle (rank-1 update) and the rows of L'^-1 below j (columns < j)
+    const int cntA = s * (s + 1) / 2, w = j, cnt = cntA + s * w;
+    const float rw = w > 0 ? 1.0f / (float)w : 0.0f;
+    for (int idx = tid; idx < cnt; idx += kCT) {
+      if (idx < cntA) {
+        int ii, ll;
+        tri_decode(idx, ii, ll);
+        const int i = j + 1 + ii, l = j + 1 + ll;
+        const double v = fma(-lc[i], u[l], T[trl(i, l)]);
+        if (idx == 0) {  // (j+1, j+1) receives its last update: the next pivot
+          double dd = v;
+          if (!(dd > 0.0)) {
+            s_bad = 1;
+            dd = 1.0;
+          }
+          T[trl(i, l)] = dd;
+          d[j + 1] = dd;
+          rd[j + 1] = recip64(dd);
+        } else {
+          T[trl(i, l)] = v;
+        }
+      } else {
+        const int e = idx - cntA;
+        int q = (int)(((float)e + 0.5f) * rw);
+        q -= (q * w > e);
+        q += ((q + 1) * w <= e);
+        const int i = j + 1 + q, c = e - q * w;
+        T[trl(i, c)] = fma(-lc[i], T[trl(j, c)], T[trl(i, c)]);
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < P; i += kCT) d[i] = rsqrt64(d[i]);
+  __syncthreads();
+  // Y' = D^-1/2 L'^-1 (unit diagonal implied in the sweep)
+  for (int e = tid; e < ntri; e += kCT) {
+    int i, j;
+    tri_decode(e, i, j);
+    T[e] = (i == j) ? d[i] : T[e] * d[i];
+  }
+  __syncthreads();
+  for (int i = tid; i < P; i += kCT) {
+    const double* row = T + trl(i, 0);
+    double sacc = 0.0;
+    for (int c = 0; c <= i; ++c) sacc = fma(row[c], gp[c], sacc);
+    up[i] = sacc;
+    tp[i] = fma(bt, sacc, zp[i]);
+  }
+  __syncthreads();
+  for (int c = tid; c < P; c += kCT) {
+    double sa = 0.0, sh = 0.0;
+    for (int i = c; i < P; ++i) {
+      const double y = T[trl(i, c)];
+      sa = fma(y, tp[i], sa);
+      sh = fma(y, up[i], sh);
+    }
+    const int p = P - 1 - c;
+    a64[o * m.PM + p] = sa;
+    ahat[o * P + p] = bt * sh;
+  }
+  double acc = 0.0;
+  for (int i = tid; i < P; i += kCT) acc += log(d[i]);
+  acc = block_sum(acc, red);
+  if (tid == 0) {
+    ld[o] = acc;
+    if (s_bad) atomicOr(&stat[b], 2);
+  }
+  if (in_smem)
+    for (int e = tid; e < ntri; e += kCT) Wslot[e] = T[e];
+}
+
+// ---------------------------------------------------------------------------
+// HD prior at the transformed coefficients, per (achromatic bin or DM block, chain):
+// v = Phi_k^-1 a (stored for the gradient), the term -1/2 a^T Phi_k^-1 a - log det Phi_k
+// over both columns, and its derivatives at fixed a:
+//   kappa_I d/dkappa_I = kappa_I (1/2 sum_c v_cI^2 - (Phi_k^-1)_II),
+//   rho d/drho = 1/2 sum_c a_c . v_c - N_p - sum_I kappa_I d/dkappa_I (scaling identity).
+// Dense bins use L_k^-1 from the prior stage, GWB-only bins chol(Gamma)^-1 / sqrt(rho),
+// diagonal bins 1 / kappa.  Grid (na + 1, B).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kCT)
+    k_curn_whiten(DevModel m, const double* __restrict__ a64, const double* __restrict__ Lipk,
+                  const double* __restrict__ sk, const double* __restrict__ skd, const double* __restrict__ srho,
+                  double* vbuf, double* qout, double* dlnk, double* dlnkd, double* dlnr, int B) {
+  extern __shared__ double sm[];
+  __shared__ double red[kCT / 32];
+  const int kb = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, np = m.npsr, P = m.P;
+  double q = 0.0;  // this thread's part of the prior term
+  if (kb == m.na) {  // DM block: Phi = kappa^DM per (pulsar, bin)
+    for (int r = tid; r < np * m.nd; r += kCT) {
+      const int I = r / m.nd, k = r % m.nd;
+      const double s = skd[((size_t)b * np + I) * m.nd + k], kap = s * s, ik = 1.0 / kap;
+      const size_t o = (size_t)I * B + b;
+      const int p = 2 * m.na + 2 * k;
+      const double a0 = a64[o * m.PM + p], a1 = a64[o * m.PM + p + 1];
+      vbuf[o * P + p] = a0 * ik;
+      vbuf[o * P + p + 1] = a1 * ik;
+      const double qq = fma(a0, a0, a1 * a1) * ik;
+      q += -0.5 * qq - log(kap);
+      dlnkd[((size_t)b * np + I) * m.nd + k] = 0.5 * qq - 1.0;
+    }
+    q = block_sum(q, red);
+    if (tid == 0) qout[(size_t)b * (m.na + 1) + kb] = q;
+    return;
+  }
+  const int k = kb;
+  if (k >= m.n_chol + m.n_gwbonly) {  // red noise only: Phi = diag(kappa)
+    for (int I = tid; I < np; I += kCT) {
+      const double s = sk[((size_t)b * np + I) * m.na + k], kap = s * s, ik = 1.0 / kap;
+      const size_t o = (size_t)I * B + b;
+      const double a0 = a64[o * m.PM + 2 * k], a1 = a64[o * m.PM + 2 * k + 1];
+      vbuf[o * P + 2 * k] = a0 * ik;
+      vbuf[o * P + 2 * k + 1] = a1 * ik;
+      const double qq = fma(a0, a0, a1 * a1) * ik;
+      q += -0.5 * qq - log(kap);
+      dlnk[((size_t)b * np + I) * m.na + k] = 0.5 * qq - 1.0;
+    }
+    q = block_sum(q, red);
+    if (tid == 0) {
+      qout[(size_t)b * (m.na + 1) + kb] = q;
+      dlnr[(size_t)b * m.na + k] = 0.0;
+    }
+    return;
+  }
+  // correlated bins: X = L_k^-1 packed (dense) or chol(Gamma)^-1 / sqrt(rho) (GWB only)
+  const bool dense = k < m.n_chol;
+  const int ntri = np * (np + 1) / 2;
+  double* X = sm;
+  double* a = X + ntri;   // [2][np]
+  double* zq = a + 2 * np; // [2][np] X a
+  const double sr = srho[(size_t)b * m.na + k];
+  if (dense) {
+    const double* Xg = Lipk + ((size_t)b * m.n_chol + k) * ntri;
+    for (int e = tid; e < ntri; e += kCT) X[e] = Xg[e];
+  } else {
+    const double isr = 1.0 / sr;
+    for (int e = tid; e < ntri; e += kCT) {
+      int i, j;
+      tri_decode(e, i, j);
+      X[e] = m.LGammaInv[i * np + j] * isr;
+    }
+  }
+  for (int e = tid; e < 2 * np; e += kCT) {
+    const int c = e / np, I = e % np;
+    a[e] = a64[((size_t)I * B + b) * m.PM + 2 * k + c];
+  }
+  __syncthreads();
+  for (int e = tid; e < 2 * np; e += kCT) {
+    const int c = e / np, I = e % np;
+    const double* row = X + trl(I, 0);
+    const double* ac = a + c * np;
+    double s = 0.0;
+    for (int J = 0; J <= I; ++J) s = fma(row[J], ac[J], s);
+    zq[e] = s;
+    q -= 0.5 * s * s;
+  }
+  __syncthreads();
+  double part = 0.0;  // 1/2 sum_c a_c . v_c - kappa d/dkappa, this thread's pulsars
+  for (int J = tid; J < np; J += kCT) {
+    double v0 = 0.0, v1 = 0.0, dg = 0.0;
+    for (int I = J; I < np; ++I) {
+      const double xij = X[trl(I, J)];
+      v0 = fma(xij, zq[I], v0);
+      v1 = fma(xij, zq[np + I], v1);
+      dg = fma(xij, xij, dg);
+    }
+    const size_t o = (size_t)J * B + b;
+    vbuf[o * P + 2 * k] = v0;
+    vbuf[o * P + 2 * k + 1] = v1;
+    q += 2.0 * log(X[trl(J, J)]);  // -log det Phi_k = 2 sum log (L_k^-1)_JJ
+    const double s = sk[((size_t)b * np + J) * m.na + k], kap = s * s;
+    const double dk = kap * (0.5 * fma(v0, v0, v1 * v1) - dg);
+    dlnk[((size_t)b * np + J) * m.na + k] = dk;
+    part += 0.5 * fma(a[J], v0, a[np + J] * v1) - dk;
+  }
+  q = block_sum(q, red);
+  part = block_sum(part, red);
+  if (tid == 0) {
+    qout[(size_t)b * (m.na + 1) + kb] = q;
+    dlnr[(size_t)b * m.na + k] = part - (double)np;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gradient through the transform.  Grid (npsr, B).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kCT)
+    k_curn_adjoint(DevModel m, const float* __restrict__ x, const double* __restrict__ ghat,
+                   const double* __restrict__ Wg, const double* __restrict__ vbuf, const double* __restrict__ ahat,
+                   const double* __restrict__ sk, const double* __restrict__ skd, const double* __restrict__ srho,
+                   float* grad, double* dlnk, double* dlnkd, double* dlnrc, int B, int in_smem) {
+  extern __shared__ double sm[];
+  const int I = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, P = m.P, np = m.npsr;
+  const int ntri = P * (P + 1) / 2;
+  const size_t o = (size_t)I * B + b;
+  const double* Yg = Wg + o * ntri;
+  double* Ys = sm;
+  double* gb = in_smem ? sm + ntri : sm;  // gbar, reversed
+  double* zp = gb + P;                     // z, reversed
+  double* sp = zp + P;                     // s' = Y' gbar'
+  double* ah = sp + P;                     // ahat, reversed
+  double* pd = ah + P;                     // phi_C d logp / d phi_C, coefficient order
+  const double* Y = in_smem ? Ys : Yg;
+  if (in_smem)
+    for (int e = tid; e < ntri; e += kCT) Ys[e] = Yg[e];
+  const float* xb = x + (size_t)b * m.d;
+  for (int i = tid; i < P; i += kCT) {
+    const int p = P - 1 - i;
+    gb[i] = ghat[o * P + p] - vbuf[o * P + p];
+    zp[i] = (double)xb[zidx(m, I, p)];
+    ah[i] = ahat[o * P + p];
+  }
+  __syncthreads();
+  float* gout = grad + (size_t)b * m.d;
+  for (int i = tid; i < P; i += kCT) {
+    const double* row = Y + trl(i, 0);
+    double s = 0.0;
+    for (int c = 0; c <= i; ++c) s = fma(row[c], gb[c], s);
+    sp[i] = s;
+    gout[zidx(m, I, P - 1 - i)] = (float)s;  // d logp / d z = W gbar
+  }
+  __syncthreads();
+  for (int c = tid; c < P; c += kCT) {
+    double h = 0.0, R = 0.0, Tc = 0.0, Dg = 0.0;
+    for (int i = P - 1; i >= c; --i) {
+      const double y = Y[trl(i, c)];
+      const double ys = y * sp[i];
+      h += ys;                               // (A^-1 gbar)'_c
+      Tc = fma(ys, R, Tc);                   // sum over rows below of y z' times y s'
+      R = fma(y, zp[i], R);
+      Dg = fma(y * y, fma(zp[i], sp[i], 1.0), Dg);
+    }
+    const double ab = -h * ah[c] - Tc - 0.5 * Dg;  // d logp / d d_p
+    const int p = P - 1 - c;
+    pd[p] = -ab / phic(m, sk, skd, srho, b, I, p);  // phi d/dphi = -d_p d/dd_p
+  }
+  __syncthreads();
+  for (int k = tid; k < m.na; k += kCT) {
+    const double S = pd[2 * k] + pd[2 * k + 1];
+    const double r = srho[(size_t)b * m.na + k], q = sk[((size_t)b * np + I) * m.na + k];
+    const double rho = r * r, kap = q * q, iphi = 1.0 / (rho + kap);
+    dlnrc[((size_t)b * np + I) * m.na + k] = S * rho * iphi;
+    dlnk[((size_t)b * np + I) * m.na + k] += S * kap * iphi;
+  }
+  for (int k = tid; k < m.nd; k += kCT)
+    dlnkd[((size_t)b * np + I) * m.nd + k] += pd[2 * m.na + 2 * k] + pd[2 * m.na + 2 * k + 1];
+}
+
+size_t fwd_smem(const DevModel& m, bool tri) {
+  const size_t P = m.P;
+  return ((tri ? P * (P + 1) / 2 : 0) + 8 * P) * sizeof(double);
+}
+size_t adj_smem(const DevModel& m, bool tri) {
+  const size_t P = m.P;
+  return ((tri ? P * (P + 1) / 2 : 0) + 5 * P) * sizeof(double);
+}
+constexpr size_t kCurnSmemMax = 200 * 1024;
+
+}  // namespace
+
+size_t curn_w_doubles(const DevModel& m) { return (size_t)m.P * (m.P + 1) / 2; }
+
+cudaError_t launch_curn_forward(const DevModel& m, const Scratch& s, int B, const float* x, cudaStream_t st) {
+  const bool tri = fwd_smem(m, true) <= kCurnSmemMax;
+  const size_t sm = fwd_smem(m, tri);
+  cudaError_t e = cudaFuncSetAttribute(k_curn_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_curn_forward<<<dim3(m.npsr, B), kCT, sm, st>>>(m, x, s.sk, s.skd, s.srho, s.a64, s.curnW, s.curnAhat, s.curnLd,
+                                                    s.stat, B, tri ? 1 : 0);
+  const size_t ws = ((size_t)m.npsr * (m.npsr + 1) / 2 + 4 * m.npsr) * sizeof(double);
+  e = cudaFuncSetAttribute(k_curn_whiten, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws);
+  if (e != cudaSuccess) return e;
+  k_curn_whiten<<<dim3(m.na + 1, B), kCT, ws, st>>>(m, s.a64, s.Lipk, s.sk, s.skd, s.srho, s.curnV, s.curnQ, s.dlnk,
+                                                    s.dlnkd, s.dlnr, B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_curn_adjoint(const DevModel& m, const Scratch& s, int B, const float* x, float* grad,
+                                cudaStream_t st) {
+  const bool tri = adj_smem(m, true) <= kCurnSmemMax;
+  const size_t sm = adj_smem(m, tri);
+  cudaError_t e = cudaFuncSetAttribute(k_curn_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_curn_adjoint<<<dim3(m.npsr, B), kCT, sm, st>>>(m, x, s.ghat, s.curnW, s.curnV, s.curnAhat, s.sk, s.skd, s.srho,
+                                                    grad, s.dlnk, s.dlnkd, s.dlnrc, B, tri ? 1 : 0);
+  return cudaGetLastError();
+}
+
+}  // namespace pta

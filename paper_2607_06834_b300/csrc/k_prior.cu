@@ -50,29 +50,6 @@ __global__ void k_spectra(DevModel m, const float* __restrict__ x, double* sk, d
   }
 }
 
-// 1/d in FP64 from an FP32 seed and two Newton steps (r <- r + r (1 - d r)); the
-// relative error squares at each step, 2^-24 -> 2^-48 -> FP64 rounding.  Outside the
-// FP32 normal range the plain FP64 division is used.
-__device__ __forceinline__ double recip64(double d) {
-  const float f = (float)d;
-  if (!(fabsf(f) >= 1.2e-38f && fabsf(f) <= 3.0e38f)) return 1.0 / d;
-  double r = (double)__frcp_rn(f);
-  double e = fma(-d, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-d, r, 1.0);
-  return fma(r, e, r);
-}
-// 1/sqrt(d) likewise (y <- y (3/2 - d y^2 / 2)), d > 0
-__device__ __forceinline__ double rsqrt64(double d) {
-  const float f = (float)d;
-  if (!(f >= 1.2e-38f && f <= 3.0e38f)) return 1.0 / sqrt(d);
-  double y = (double)rsqrtf(f);
-  const double h = 0.5 * d;
-  y = y * fma(-h * y, y, 1.5);
-  y = y * fma(-h * y, y, 1.5);
-  return y * fma(-h * y, y, 1.5);
-}
-
 // ---------------------------------------------------------------------------
 // Dense bins k < n_chol: Phi_k = rho_k Gamma + diag(kappa_.k).  One CTA per
 // (bin, chain).  The sweep is the LDL^T form of the Cholesky factorisation
@@ -368,7 +345,9 @@ __global__ void k_diag_adjoint(DevModel m, const float* __restrict__ x, const do
 __global__ void k_final(DevModel m, const float* __restrict__ x, const double* __restrict__ chi2,
                         const double* __restrict__ dlnk, const double* __restrict__ dlnkd,
                         const double* __restrict__ dlnr, const int32_t* __restrict__ stat,
-                        const double* __restrict__ cwg, double* logp, float* grad, int32_t* status, int B) {
+                        const double* __restrict__ cwg, const double* __restrict__ curnQ,
+                        const double* __restrict__ curnLd, const double* __restrict__ dlnrc, double* logp,
+                        float* grad, int32_t* status, int B) {
   const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x, np = m.npsr;
   const float* xb = x + (size_t)b * m.d;
   __shared__ double red[32];
@@ -376,8 +355,13 @@ __global__ void k_final(DevModel m, const float* __restrict__ x, const double* _
   if (tid == 0) s_flag = stat[b];
   __syncthreads();
   double acc = 0.0;
-  for (int j = tid; j < m.d_z; j += nt) acc = fma((double)xb[j], (double)xb[j], acc);
-  acc *= -0.5;
+  if (m.curn) {  // CURN transform: HD prior terms per bin and log det L_CURN per pulsar
+    for (int j = tid; j <= m.na; j += nt) acc += curnQ[(size_t)b * (m.na + 1) + j];
+    for (int I = tid; I < np; I += nt) acc += curnLd[(size_t)I * B + b];
+  } else {
+    for (int j = tid; j < m.d_z; j += nt) acc = fma((double)xb[j], (double)xb[j], acc);
+    acc *= -0.5;
+  }
   const double bt = m.beta ? m.beta[b] : 1.0;  // tempered likelihood: beta chi2
   for (int I = tid; I < np; I += nt) acc -= 0.5 * bt * chi2[(size_t)I * B + b];
   int outside = 0;
@@ -467,7 +451,9 @@ __global__ void k_final(DevModel m, const float* __restrict__ x, const double* _
   if (tid == 0) {
     double s1 = 0.0, s2 = 0.0;
     for (int k = 0; k < m.n_gwb; ++k) {
-      const double v = dlnr[(size_t)b * m.na + k];  // rho d logp / d rho
+      double v = dlnr[(size_t)b * m.na + k];  // rho d logp / d rho
+      if (m.curn)  // the transform's part, per pulsar, summed in a fixed order
+        for (int I = 0; I < np; ++I) v += dlnrc[((size_t)b * np + I) * m.na + k];
       if (m.gwb_free) gb[m.th_gwb + k] = (float)(kLn10 * v);
       s1 += v;
       s2 -= (m.lnk[k + 1] - m.ln_Tfyr) * v;
@@ -505,9 +491,10 @@ static size_t adj_smem(const DevModel& m) {
 }
 
 int count_prior_forward(const DevModel& m) {
+  if (m.curn) return 1 + (m.n_chol > 0) + 2;  // spectra, Phi_k factors, CURN transform, HD prior
   return 1 + (m.n_chol > 0) + (m.n_gwbonly > 0) + (m.npsr * ((m.na - m.n_chol - m.n_gwbonly) + m.nd) > 0);
 }
-int count_prior_adjoint(const DevModel& m) { return count_prior_forward(m) - 1; }
+int count_prior_adjoint(const DevModel& m) { return m.curn ? 1 : count_prior_forward(m) - 1; }
 
 cudaError_t launch_prior_forward(const DevModel& m, const Scratch& s, int B, const float* x, int fp64,
                                  cudaStream_t st) {
@@ -520,6 +507,7 @@ cudaError_t launch_prior_forward(const DevModel& m, const Scratch& s, int B, con
     if (e != cudaSuccess) return e;
     k_chol_forward<<<dim3(m.n_chol, B), 128, sm, st>>>(m, x, s.sk, s.srho, s.a64, s.Lpk, s.Lipk, s.stat);
   }
+  if (m.curn) return cudaGetLastError();  // a comes from the CURN transform (launch_curn_forward)
   if (m.n_gwbonly > 0) k_gwbonly_forward<<<dim3(m.n_gwbonly, B), 128, 0, st>>>(m, x, s.srho, s.a64);
   const int per = m.npsr * ((m.na - m.n_chol - m.n_gwbonly) + m.nd);
   if (per > 0) k_diag_forward<<<dim3((per + 127) / 128, B), 128, 0, st>>>(m, x, s.sk, s.skd, s.a64, B, per);
@@ -546,7 +534,8 @@ cudaError_t launch_prior_adjoint(const DevModel& m, const Scratch& s, int B, con
 
 cudaError_t launch_final(const DevModel& m, const Scratch& s, int B, const float* x, double* logp, float* grad,
                          int32_t* status, cudaStream_t st) {
-  k_final<<<B, 256, 0, st>>>(m, x, s.chi2, s.dlnk, s.dlnkd, s.dlnr, s.stat, s.cwg, logp, grad, status, B);
+  k_final<<<B, 256, 0, st>>>(m, x, s.chi2, s.dlnk, s.dlnkd, s.dlnr, s.stat, s.cwg, s.curnQ, s.curnLd, s.dlnrc, logp,
+                             grad, status, B);
   return cudaGetLastError();
 }
 

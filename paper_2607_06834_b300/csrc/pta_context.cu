@@ -282,6 +282,8 @@ int pta_finalize(pta_ctx* c, void* stream) {
   const int P4 = (m.P + 3) & ~3;
   std::vector<float> Gth((size_t)npsr * m.P * P4, 0.f), Gtl((size_t)npsr * m.P * P4, 0.f);
   std::vector<double> gg2((size_t)npsr * m.P, 0.0), cc2(npsr, 0.0);
+  const size_t ntriP = (size_t)m.P * (m.P + 1) / 2;
+  std::vector<double> Grev((size_t)npsr * ntriP, 0.0), gtv((size_t)npsr * m.P, 0.0);  // CURN transform
   const double nu_ref = d.nu_ref_mhz;
   const int P = m.P, kmax = std::max(m.na, m.nd);
   double logc = 0.0;
@@ -419,7 +421,12 @@ int pta_finalize(pta_ctx* c, void* stream) {
         const size_t go = (size_t)I * P * P4;  // rows padded to P4 columns (zeros)
         Gth[go + (size_t)q * P4 + r] = Gth[go + (size_t)r * P4 + q] = vh;
         Gtl[go + (size_t)q * P4 + r] = Gtl[go + (size_t)r * P4 + q] = vl;
+        // FP64 copy for the CURN transform, packed lower in reversed order:
+        // (q, r), r <= q, is element (P-1-r, P-1-q) of the reversed triangle
+        const size_t rr = (size_t)(P - 1 - r), qq = (size_t)(P - 1 - q);
+        Grev[(size_t)I * ntriP + rr * (rr + 1) / 2 + qq] = v;
       }
+      gtv[(size_t)I * P + q] = rhs[q];  // F^T N~^-1 dt
       const int k = q < 2 * m.na ? q / 2 + 1 : (q - 2 * m.na) / 2 + 1;
       A[(size_t)q * P + q] += std::exp(-ln_pl(m.ln_rho0, m.ln_Tfyr, -13.0, 4.0, std::log((double)k)));
     }
@@ -480,6 +487,15 @@ int pta_finalize(pta_ctx* c, void* stream) {
   LG = Gam;
   if (!host_cholesky(LG, npsr))
     return fail(c, PTA_EINVAL, "Hellings-Downs matrix not positive definite (coincident pulsars?)");
+  std::vector<double> LGi((size_t)npsr * npsr, 0.0);  // chol(Gamma)^-1 by forward substitution
+  for (int j = 0; j < npsr; ++j) {
+    LGi[(size_t)j * npsr + j] = 1.0 / LG[(size_t)j * npsr + j];
+    for (int i = j + 1; i < npsr; ++i) {
+      double s2 = 0.0;
+      for (int l = j; l < i; ++l) s2 += LG[(size_t)i * npsr + l] * LGi[(size_t)l * npsr + j];
+      LGi[(size_t)i * npsr + j] = -s2 / LG[(size_t)i * npsr + i];
+    }
+  }
 
   int rc;
 #define UP(vec, field)                                  \
@@ -529,6 +545,9 @@ int pta_finalize(pta_ctx* c, void* stream) {
   }
   UP(Gam, Gamma);
   UP(LG, LGamma);
+  UP(LGi, LGammaInv);
+  UP(Grev, Grev);
+  UP(gtv, gt);
   {
     std::vector<double> lnk(kmax + 1, 0.0);
     for (int k = 1; k <= kmax; ++k) lnk[k] = std::log((double)k);
@@ -554,7 +573,8 @@ void free_scratch(pta::Scratch& s) {
   void* ptrs[] = {s.a32, s.a64, s.Lpk, s.Lipk, s.gpart, s.gpart64, s.c2part, s.ghat, s.chi2,
                   s.dlnk, s.dlnkd, s.dlnr, s.stat, s.sk, s.skd, s.srho, s.cwc, s.cwjac, s.cwsig,
                   s.cwbs, s.cwwt, s.cwgp, s.cwg, s.x0, s.g0, s.p, s.lp0, s.xs, s.gs, s.lps,
-                  s.step, s.imass, s.kin0, s.hmc_ctr, s.acc, s.a16, s.queue};
+                  s.step, s.imass, s.kin0, s.hmc_ctr, s.acc, s.a16, s.queue, s.curnW, s.curnAhat,
+                  s.curnV, s.curnLd, s.curnQ, s.dlnrc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   s = pta::Scratch{};
@@ -569,7 +589,8 @@ cudaError_t dalloc(T** p, size_t n) {
 int ensure_scratch(pta_ctx* c, int B, bool fp64) {
   pta::Scratch& s = c->sc;
   const pta::DevModel& m = c->dm;
-  if (B <= s.cap && (!fp64 || s.gpart64)) return PTA_OK;
+  const bool curn = m.curn != 0;
+  if (B <= s.cap && (!fp64 || s.gpart64) && (!curn || s.curnW)) return PTA_OK;
   const int cap = std::max(B, s.cap);
   cudaDeviceSynchronize();
   free_scratch(s);
@@ -618,6 +639,14 @@ int ensure_scratch(pta_ctx* c, int B, bool fp64) {
   AL(hmc_ctr, 2);
   AL(acc, cap);
   AL(queue, 1);
+  if (curn) {
+    AL(curnW, (size_t)np * cap * pta::curn_w_doubles(m));
+    AL(curnAhat, np * cap * P);
+    AL(curnV, np * cap * P);
+    AL(curnLd, np * cap);
+    AL(curnQ, (size_t)cap * (m.na + 1));
+    AL(dlnrc, (size_t)cap * np * m.na);
+  }
 #undef AL
   if (e != cudaSuccess) {
     free_scratch(s);
@@ -687,6 +716,7 @@ int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* gr
   const bool gram = c->precision == PTA_PREC_GRAM;
   tm.begin(0);
   if (e == cudaSuccess) e = pta::launch_prior_forward(m, s, B, x, fp64, st);
+  if (e == cudaSuccess && m.curn) e = pta::launch_curn_forward(m, s, B, x, st);
   if (e == cudaSuccess && m.cw) e = pta::launch_cw_forward(m, s, B, x, st);
   if (e == cudaSuccess && !gram) e = pta::launch_tm_prologue(m, s, B, fp64, st);
   tm.end(pta::count_prior_forward(m) + (gram ? 0 : 1) + (m.cw ? 2 : 0));
@@ -709,7 +739,8 @@ int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* gr
   tm.end(gram ? 0 : 1);
   if (grad) {
     tm.begin(3);
-    if (e == cudaSuccess) e = pta::launch_prior_adjoint(m, s, B, x, grad, st);
+    if (e == cudaSuccess)
+      e = m.curn ? pta::launch_curn_adjoint(m, s, B, x, grad, st) : pta::launch_prior_adjoint(m, s, B, x, grad, st);
     if (e == cudaSuccess && m.cw) e = pta::launch_cw_gradient(m, s, B, st);
     tm.end(pta::count_prior_adjoint(m) + (m.cw ? 2 : 0));
   }
@@ -821,6 +852,21 @@ int pta_set_beta(pta_ctx* c, int n, const double* beta, void* stream) {
   if (c->dm.beta != c->beta_dev) drop_graphs(c);
   c->dm.beta = c->beta_dev;
   c->beta_n = n;
+  return PTA_OK;
+}
+
+int pta_set_transform(pta_ctx* c, int transform) {
+  if (!c) return PTA_EINVAL;
+  if (!c->finalized) return fail(c, PTA_ESTATE, "context not finalized");
+  if (transform != PTA_TRANSFORM_PRIOR && transform != PTA_TRANSFORM_CURN)
+    return fail(c, PTA_EINVAL, "set_transform: unknown transform");
+  if (transform == PTA_TRANSFORM_CURN && c->dm.cw)
+    return fail(c, PTA_EINVAL,
+                "the CURN transform with a deterministic signal (Eq. decenter_det_PTA) is not built: use "
+                "PTA_TRANSFORM_PRIOR with the continuous-wave model");
+  if (transform != c->transform) drop_graphs(c);
+  c->transform = transform;
+  c->dm.curn = transform == PTA_TRANSFORM_CURN ? 1 : 0;
   return PTA_OK;
 }
 

@@ -21,8 +21,8 @@ constexpr int kChunk = 2048;     // TOAs per work unit of the TOA kernels
 // The per-frequency Cholesky and its adjoint hold two packed N_p x N_p triangles
 // and 7 N_p vectors in FP64 shared memory: (N_p (N_p + 1) + 7 N_p) x 8 B <= 227 KB.
 constexpr int kMaxPsr = 166;
-constexpr int kLowBins = 4;
-constexpr double kFreeLo = -20.0, kFreeHi = -5.0;  // free-spectrum prior box, log10 (s^2) (Sec. Priors)     // lowest frequencies whose basis columns are projected off the timing model
+constexpr int kLowBins = 4;  // lowest frequencies whose basis columns are projected off the timing model
+constexpr double kFreeLo = -20.0, kFreeHi = -5.0;  // free-spectrum prior box, log10 (s^2) (Sec. Priors)
 
 // Everything a kernel needs about the model and the resident data.  Passed by
 // value; all pointers are device pointers owned by the context.
@@ -91,6 +91,12 @@ struct DevModel {
   const unsigned short* trimap; // packed-lower index -> (row << 8) | col, for npsr <= 256
   const double* Gamma;          // [npsr x npsr]
   const double* LGamma;         // chol(Gamma), lower, [npsr x npsr]
+  const double* LGammaInv;      // chol(Gamma)^-1, lower, [npsr x npsr]
+  // CURN-posterior transform (Eq. PTA_standard_transform_curn), when curn = 1
+  int curn;
+  const double* Grev;           // per pulsar G~ = F^T N~^-1 F, packed lower in reversed order
+                                // (element (i', l') = G~[P-1-i'][P-1-l']), P (P + 1) / 2 each
+  const double* gt;             // [npsr][P] F^T N~^-1 dt (FP64)
 };
 
 // Scratch sized for a batch of up to `cap` chains.
@@ -135,6 +141,13 @@ struct Scratch {
   uint64_t* hmc_ctr = nullptr; // [2] seed, iteration
   int32_t* acc = nullptr;      // [cap] accept flags
   int* queue = nullptr;        // [1] work counter of persistent launches
+  // CURN transform (allocated when it is selected)
+  double* curnW = nullptr;     // [npsr][cap][P (P + 1) / 2] inverse factor Y' (reversed order)
+  double* curnAhat = nullptr;  // [npsr][cap][P] ahat
+  double* curnV = nullptr;     // [npsr][cap][P] phi^-1 a (HD prior)
+  double* curnLd = nullptr;    // [npsr][cap] log det L_CURN
+  double* curnQ = nullptr;     // [cap][na + 1] HD-prior terms per achromatic bin and the DM block
+  double* dlnrc = nullptr;     // [cap][npsr][na] rho d logp / d rho through the transform, per pulsar
 };
 
 // Kernel launchers (defined in the .cu files).
@@ -164,6 +177,10 @@ cudaError_t launch_reduce(const DevModel& m, const Scratch& s, int B, int fp64, 
 cudaError_t launch_prior_adjoint(const DevModel& m, const Scratch& s, int B, const float* x,
                                  float* grad, cudaStream_t st);
 int count_prior_forward(const DevModel& m);
+size_t curn_w_doubles(const DevModel& m);  // P (P + 1) / 2
+cudaError_t launch_curn_forward(const DevModel& m, const Scratch& s, int B, const float* x, cudaStream_t st);
+cudaError_t launch_curn_adjoint(const DevModel& m, const Scratch& s, int B, const float* x, float* grad,
+                                cudaStream_t st);
 int count_prior_adjoint(const DevModel& m);
 cudaError_t launch_final(const DevModel& m, const Scratch& s, int B, const float* x,
                          double* logp, float* grad, int32_t* status, cudaStream_t st);
@@ -206,6 +223,29 @@ __device__ __forceinline__ void sincos_turns64(uint64_t phi, float* s, float* c)
   *c = (((oct + 2u) >> 2) & 1u) ? -c0 : c0;     // octants 2..5
 }
 
+// 1/d in FP64 from an FP32 seed and two Newton steps (r <- r + r (1 - d r)); the
+// relative error squares at each step, 2^-24 -> 2^-48 -> FP64 rounding.  Outside the
+// FP32 normal range the plain FP64 division is used.
+__device__ __forceinline__ double recip64(double d) {
+  const float f = (float)d;
+  if (!(fabsf(f) >= 1.2e-38f && fabsf(f) <= 3.0e38f)) return 1.0 / d;
+  double r = (double)__frcp_rn(f);
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+// 1/sqrt(d) likewise (y <- y (3/2 - d y^2 / 2)), d > 0
+__device__ __forceinline__ double rsqrt64(double d) {
+  const float f = (float)d;
+  if (!(f >= 1.2e-38f && f <= 3.0e38f)) return 1.0 / sqrt(d);
+  double y = (double)rsqrtf(f);
+  const double h = 0.5 * d;
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  return y * fma(-h * y, y, 1.5);
+}
+
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
 }  // namespace pta
@@ -233,6 +273,7 @@ struct pta_ctx {
   double* beta_dev = nullptr;      // pta_set_beta's copy of the inverse temperatures
   int beta_n = 0;                  // chains it covers
   int toa_cfg = -1;                // SIMT tile-shape entry (-1: default), set by the autotuner
+  int transform = PTA_TRANSFORM_PRIOR;
   pta_layout_t lay{};
   // HMC graphs keyed by (B, n_leapfrog)
   struct Graph {

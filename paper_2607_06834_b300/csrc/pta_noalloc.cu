@@ -82,6 +82,10 @@ extern "C" int pta_logp_and_grad_noalloc(pta_ctx* c, int B, const float* x, doub
     c->err = "logp_and_grad_noalloc: tempered evaluation with more chains than pta_set_beta gave";
     return PTA_EINVAL;
   }
+  if (c->dm.curn) {
+    c->err = "logp_and_grad_noalloc: the CURN transform keeps per-chain factors that need the allocating entry point";
+    return PTA_EINVAL;
+  }
   if (c->precision == PTA_PREC_BF16X3) {
     c->err = "logp_and_grad_noalloc: the BF16 tensor-core path needs the allocating entry point";
     return PTA_EINVAL;

@@ -37,6 +37,7 @@ class Engine:
             raise PTAError(f"pta_create failed ({rc})")
         self._h = h
         self.precision = precision
+        self.transform = "prior"
         keep = []
         for p in arr.pulsars:
             arrs = dict(
@@ -106,6 +107,12 @@ class Engine:
         self._beta_keep = b  # alive until the stream has copied it
         self._check(abi.lib.pta_set_beta(self._h, int(b.numel()), C.c_void_p(b.data_ptr()), stream),
                     "pta_set_beta")
+
+    def set_transform(self, transform: str):
+        """Standardizing transform of the coefficients: "prior" (a = L_phi z per
+        frequency bin, the default) or "curn" (a = ahat_CURN + L_CURN z per pulsar)."""
+        self._check(abi.lib.pta_set_transform(self._h, abi.TRANSFORM[transform]), "pta_set_transform")
+        self.transform = transform
 
     def set_toa_config(self, cfg: int):
         self._check(abi.lib.pta_set_toa_config(self._h, int(cfg)), "pta_set_toa_config")

@@ -44,6 +44,12 @@ WORKLOADS = {
     "ng15_cw": dict(npsr=67, ntoa_total=300_000, ntoa_range=(2000, 20000), span_yr=(3.0, 16.0),
                     m_range=(8, 80), n_gwb=14, n_rn=30, n_dm=100, cw=True, chains=64,
                     mode="epochs", nbackend=(1, 4)),
+    # the model of the paper's NANOGrav-15-yr analysis (Sec. "Analyses of real and simulated
+    # datasets"): intrinsic red noise with 30 bins and an HD-correlated GWB with 14, no DM
+    # (P = 60 coefficients per pulsar), on the same 67-pulsar array
+    "ng15_nodm": dict(npsr=67, ntoa_total=300_000, ntoa_range=(2000, 20000), span_yr=(3.0, 16.0),
+                      m_range=(8, 80), n_gwb=14, n_rn=30, n_dm=0, cw=False, chains=64,
+                      mode="epochs", nbackend=(1, 4)),
     "scale150": dict(npsr=150, ntoa_total=1_000_000, ntoa_range=(1000, 30000), span_yr=(5.0, 30.0),
                      m_range=(8, 80), n_gwb=100, n_rn=30, n_dm=150, cw=False, chains=1024,
                      mode="epochs", nbackend=(1, 4)),
@@ -165,8 +171,9 @@ def make_array(name: str, seed: int | None = None) -> Array:
     """Draw the synthetic array named ``name`` (a key of WORKLOADS)."""
     w = WORKLOADS[name]
     if seed is None:
-        # the three 67-pulsar workloads share one array (same seed)
-        seed = {"tiny3": 2607, "ng15": 2608, "ng15_b256": 2608, "ng15_cw": 2608, "scale150": 2611}[name]
+        # the 67-pulsar workloads share one array (same seed; the draws do not depend on n_dm)
+        seed = {"tiny3": 2607, "ng15": 2608, "ng15_b256": 2608, "ng15_cw": 2608, "ng15_nodm": 2608,
+                "scale150": 2611}[name]
     rng = np.random.default_rng(seed)
     npsr = w["npsr"]
     counts = _toa_counts(rng, npsr, w["ntoa_total"], *w["ntoa_range"])
@@ -202,7 +209,7 @@ def make_array(name: str, seed: int | None = None) -> Array:
         common *= 100.0 / max(common.std(), 1e-30)
         rn = _red_process(rng, tr, span, 10.0 ** rng.uniform(0.5, 3.0), rng.uniform(2.0, 5.0))
         dm = _red_process(rng, tr, span, 10.0 ** rng.uniform(1.0, 2.7), rng.uniform(1.0, 4.0))
-        dm *= (1400.0 / nu) ** 2
+        dm *= (1400.0 / nu) ** 2 if w["n_dm"] else 0.0  # no chromatic noise where the model has none
         tm = M @ rng.normal(0.0, 100.0, M.shape[1])
         white = (sigma_ns * efac[backend] * rng.normal(size=n)
                  + equad_ns[backend] * rng.normal(size=n))
