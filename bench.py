@@ -141,6 +141,69 @@ def chol_flops_per_launch(arr, B):
     return float(B * nb * (2 * npsr ** 3 / 3 + 2 * npsr ** 2))
 
 
+def curn_flops_per_launch(arr, B):
+    """FP64 flops of the CURN factorisation per launch: the LDL^T sweep with the inverse
+    (P^3/3 multiply-adds) and the transform's triangular products (3 P^2 flop) per
+    (pulsar, chain)."""
+    P = 2 * max(arr.n_gwb, arr.n_rn) + 2 * arr.n_dm
+    return float(B * arr.npsr * (2.0 * P ** 3 / 3.0 + 3.0 * P ** 2))
+
+
+def curn_variant(dev, steps):
+    """The CURN-posterior transform (Eq. PTA_standard_transform_curn) against the default
+    prior-whitened one on the same batch: the paper's NANOGrav-15-yr model (RN 30 /
+    HD-GWB 14 bins, no DM: P = 60, the factor in shared memory) with 64 and 256 chains,
+    and the 100-DM-bin workload (P = 260, the factor in the global inverse buffer) with
+    256 chains.  CUDA events per step with L2 flushed; the FP64 factorisation stage is
+    the CURN forward stage minus the prior-whitened one."""
+    import ctypes as C
+    import torch
+    from paper_2607_06834_b300 import abi, synth
+    from paper_2607_06834_b300.engine import Engine
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    peak = FP64_PEAK_TFLOPS
+    out = []
+    for name, B in (("ng15_nodm", 64), ("ng15_nodm", 256), ("ng15_b256", 256)):
+        arr = synth.make_array(name)
+        eng = Engine(arr, precision="fp32")
+        x = torch.tensor(synth.make_points(arr, B, seed=6834 + 7), device=dev)
+        rec = {"workload": name, "chains": B, "P": 2 * max(arr.n_gwb, arr.n_rn) + 2 * arr.n_dm}
+        for tr in ("prior", "curn"):
+            eng.set_transform(tr)
+            for _ in range(3):
+                eng.logp_and_grad(x)
+            torch.cuda.synchronize()
+            abi.lib.pta_profile_enable(eng._h, 1)
+            abi.lib.pta_profile_read(eng._h, None, None, 1)
+            n = max(3, min(steps, 10 if name != "ng15_b256" else 3))
+            ev = []
+            for _ in range(n):
+                flush.zero_()
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record()
+                eng.logp_and_grad(x)
+                a1.record()
+                ev.append((a0, a1))
+            torch.cuda.synchronize()
+            sm = (C.c_double * abi.NSTAGES)()
+            abi.lib.pta_profile_read(eng._h, sm, None, 1)
+            abi.lib.pta_profile_enable(eng._h, 0)
+            ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+            rec[tr] = {"value": B / (ms * 1e-3), "unit": "evals/s", "ms_per_step": ms,
+                       "stage_ms": dict(zip(abi.STAGES, [round(v / n, 4) for v in sm]))}
+        fac_ms = rec["curn"]["stage_ms"]["prior_forward"] - rec["prior"]["stage_ms"]["prior_forward"]
+        ach = curn_flops_per_launch(arr, B) / (fac_ms * 1e-3) / 1e12
+        rec["roofline"] = {"kernel": "k_curn_forward + k_curn_whiten (FP64 LDL^T sweep with inverse)",
+                           "bound": "alu", "unit": "TFLOP/s", "achieved": ach, "peak": peak,
+                           "peak_source": "derived: 148 SM x 2 FP64 FMA/clk x 2 flop x 2.032 GHz",
+                           "frac": ach / peak, "stage_ms": fac_ms,
+                           "factor_in": "shared memory" if (rec["P"] * (rec["P"] + 1) // 2 + 8 * rec["P"]) * 8
+                           <= 200 * 1024 else "global inverse buffer"}
+        eng.close()
+        out.append(rec)
+    return out
+
+
 def cpu_baseline(arr, n_eval: int):
     """The FP64 oracle, as it stands, on the host cores: logp + grad of n_eval chains."""
     from oracle import pta_oracle as O
@@ -241,6 +304,52 @@ def hmc_ess(args, dev):
             "ess_estimator": "multi-chain, Geyer initial monotone sequence"}
 
 
+def hmc_ess_transforms(args, dev):
+    """HMC effective samples per second on the model of the paper's NANOGrav-15-yr
+    analysis (67 pulsars, RN 30 / HD-GWB 14 bins, no DM), 64 chains, 20 leapfrog steps,
+    under the CURN-posterior transform (Eq. PTA_standard_transform_curn; z keeps unit
+    mass, z ~ N(0, 1) starts near the posterior) and, as the control, under the
+    prior-whitened transform (z started at its conditional mode).  Same warm-up (step
+    size, diagonal mass of the hyper-parameters, consensus start), same draws."""
+    import torch
+    from paper_2607_06834_b300 import sampler, synth
+    from paper_2607_06834_b300.engine import Engine
+    name = "ng15_nodm"
+    arr = synth.make_array(name)
+    B, L = synth.WORKLOADS[name]["chains"], 20
+    out = {"workload": "paper's NANOGrav-15-yr model (RN 30 / HD-GWB 14 bins, no DM) on the 67-pulsar "
+                       f"array, {B} chains, {L} leapfrog steps per trajectory, FP32 path",
+           "warmup_trajectories": args.hmc_warmup, "sampling_trajectories": args.hmc_samples}
+    for tr in ("curn", "prior"):
+        eng = Engine(arr, precision="fp32")
+        eng.set_transform(tr)
+        lay = eng.layout
+        th0 = lay["d_z"]
+        x0 = torch.tensor(synth.make_points(arr, B, seed=6834 + 3), device=dev)
+        kw = dict(unit_mass=th0, init_dz=0) if tr == "curn" else dict(init_dz=th0)
+        res = sampler.run_hmc(eng, x0, n_warmup=args.hmc_warmup, n_samples=args.hmc_samples, n_leapfrog=L,
+                              record=slice(th0, eng.D), seed=6834 + 3, eps0=0.01,
+                              consensus=args.hmc_warmup // 4, **kw)
+        e = sampler.ess_columns(res.draws)
+        rh = np.array([sampler.split_rhat(res.draws[:, :, k]) for k in range(res.draws.shape[2])])
+        g0 = lay["th_gwb"] - th0
+        t = res.sampling_s
+        out[tr] = {"ess_per_s_gwb_min": float(np.nanmin(e[g0:g0 + 2])) / t,
+                   "ess_per_s_theta_median": float(np.nanmedian(e)) / t,
+                   "ess_gwb_min": float(np.nanmin(e[g0:g0 + 2])), "ess_theta_median": float(np.nanmedian(e)),
+                   "rhat_gwb_max": float(np.nanmax(rh[g0:g0 + 2])), "rhat_theta_median": float(np.nanmedian(rh)),
+                   "rhat_theta_max": float(np.nanmax(rh)), "sampling_s": t, "warmup_s": res.warmup_s,
+                   "ms_per_trajectory": 1e3 * t / max(args.hmc_samples, 1),
+                   "evals_per_s": B * L * args.hmc_samples / t, "accept_rate": res.accept_rate, "step": res.step,
+                   "gwb_posterior_mean": [float(v) for v in res.draws[:, :, g0:g0 + 2].reshape(-1, 2).mean(0)],
+                   "gwb_posterior_std": [float(v) for v in res.draws[:, :, g0:g0 + 2].reshape(-1, 2).std(0)],
+                   "stuck_chains": res.stats["stuck_chains"]}
+        eng.close()
+    out["ess_estimator"] = "multi-chain, Geyer initial monotone sequence"
+    out["bounded_coordinates"] = "hyper-parameters move in logit space inside each trajectory"
+    return out
+
+
 def reduce_timing(ms: float, chains: int, world: int, pg=None, device=None):
     """Max over ranks of the per-step time (ms) and the whole-job throughput: every
     rank evaluates its own ``chains`` chains, so value = world x chains / max time."""
@@ -296,10 +405,12 @@ def run_ours(args):
         pg = dist
     from paper_2607_06834_b300 import abi, synth
     from paper_2607_06834_b300.engine import Engine
-    arr = synth.make_array(WORKLOAD)
-    B = synth.WORKLOADS[WORKLOAD]["chains"]
+    arr = synth.make_array(args.workload)
+    B = args.chains if args.chains > 0 else synth.WORKLOADS[args.workload]["chains"]
     X = synth.make_points(arr, B, seed=6834 + 2 + 1000 * rank)
     eng = Engine(arr, precision=args.precision)
+    if args.transform != "prior":
+        eng.set_transform(args.transform)
     D = eng.D
     tuned = None
     if args.precision == "fp32":  # the autotuner picks the SIMT tile shape (setup, not timed)
@@ -387,6 +498,11 @@ def run_ours(args):
         roof = {"kernel": f"k_toa_simt{shape} (TOA contractions)", "bound": "alu", "unit": "TFLOP/s",
                 "achieved": flops / (stage_ms[dom] * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
                 "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 flop x 2.032 GHz"}
+    elif args.transform == "curn":
+        flops = curn_flops_per_launch(arr, B) + chol_flops_per_launch(arr, B)
+        roof = {"kernel": "prior stage with k_curn_forward (FP64 LDL^T sweep with inverse)", "bound": "alu",
+                "unit": "TFLOP/s", "achieved": flops / (stage_ms[dom] * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "peak_source": "derived: 148 SM x 2 FP64 FMA/clk x 2 flop x 2.032 GHz"}
     else:
         flops = chol_flops_per_launch(arr, B)
         roof = {"kernel": "k_chol_forward (FP64 Cholesky + inverse + transform)", "bound": "alu",
@@ -496,16 +612,20 @@ def run_ours(args):
         eng.set_precision(args.precision)
         if tuned and tuned.get("entry") is not None:
             eng.set_toa_config(tuned["entry"])
+        variants["curn_transform"] = curn_variant(dev, args.steps)
     cpu = None if args.skip_cpu else cpu_baseline(arr, args.cpu_evals)
     hmc = None if args.skip_hmc else hmc_ess(args, dev)
     if hmc is not None:
         hmc["control_small_array"] = hmc_ess_tiny(dev)
+        hmc["transforms_paper_model"] = hmc_ess_transforms(args, dev)
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPE[args.precision],
             "dtype_detail": DTYPE_DETAIL[args.precision] + "; FP64 Cholesky, log-det, timing-model solve and sums",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC, "chains_per_gpu": B, "ntoa": arr.ntoa, "npsr": arr.npsr,
+            "config": {"workload": WORKLOAD_DESC if (args.workload, args.chains) == (WORKLOAD, 0)
+                       else f"{args.workload}, {B} chains", "transform": args.transform,
+                       "chains_per_gpu": B, "ntoa": arr.ntoa, "npsr": arr.npsr,
                        "precision": args.precision, "l2": "flushed between timed steps (512 MB write)",
                        "toa_kernel_autotuned": tuned},
             "roofline": roof, "cpu_baseline": cpu,
@@ -532,6 +652,10 @@ def main():
     ap.add_argument("--skip-hmc", action="store_true")
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--toa-config", type=int, default=-1, help="fixed FP32 TOA kernel entry (default: autotune)")
+    # profiling runs of a single kernel on another shape (the headline keeps the defaults)
+    ap.add_argument("--workload", default=WORKLOAD, help="synthetic workload (synth.WORKLOADS key)")
+    ap.add_argument("--chains", type=int, default=0, help="chains (default: the workload's)")
+    ap.add_argument("--transform", default="prior", choices=["prior", "curn"])
     ap.add_argument("--hmc-warmup", type=int, default=400)
     ap.add_argument("--hmc-samples", type=int, default=200)
     args = ap.parse_args()

@@ -189,6 +189,11 @@ int pta_toa_config_info(int cfg, int* bc, int* tt, int* qpt, int* order);
  * "Priors": log10 A ~ U(-20,-10), gamma ~ U(0,7) by default). */
 int pta_set_hyperprior(pta_ctx* ctx, double log10a_lo, double log10a_hi,
                        double gamma_lo, double gamma_hi);
+/* Prior support of every coordinate of x, into host arrays lo[D], hi[D]: the
+ * (log10 A, gamma) boxes of pta_set_hyperprior, the free-spectrum box (-20, -5), the CW
+ * box and the pulsar phases (0, 2 pi) are finite; z and the pulsar distances get
+ * (-inf, inf).  PTA_ESTATE before pta_finalize. */
+int pta_param_bounds(const pta_ctx* ctx, double* lo, double* hi);
 
 /* Log posterior and gradient for B chains (the hot path).
  *   x_dev      [B x D] float32, row per chain (layout above)
@@ -210,7 +215,13 @@ int pta_logp_and_grad(pta_ctx* ctx, int B, const float* x_dev, double* logp_dev,
  * accept.  x/logp/grad are read as the current state and overwritten with the
  * next state; logp/grad must hold the values at x on entry.
  * accepted_dev[B] receives 1/0.  The leapfrog loop runs as a CUDA graph that is
- * captured on first use for each (B, n_leapfrog) and replayed after. */
+ * captured on first use for each (B, n_leapfrog) and replayed after.
+ * Coordinates with a finite prior box [lo, hi] (pta_param_bounds) move during the
+ * trajectory in u = logit((x - lo) / (hi - lo)), x = lo + (hi - lo) sigmoid(u), with the
+ * log-Jacobian sum of log((hi - lo) s (1 - s)) added to the target (the unconstrained
+ * reparameterisation of a box-bounded parameter; the paper's hyper-priors are uniform
+ * boxes): trajectories never leave the prior support, and inv_mass_dev and the momentum
+ * refer to u for those coordinates.  x, logp and grad on entry and exit are in x. */
 int pta_hmc_trajectory(pta_ctx* ctx, int B, float* x_dev, double* logp_dev, float* grad_dev,
                        const float* step_dev, const float* inv_mass_dev, int n_leapfrog,
                        uint64_t seed, uint64_t iteration, int32_t* accepted_dev, void* stream);

@@ -330,6 +330,34 @@ class Oracle:
             ok = ok and bool(np.all(dist > 0.0)) and box(th_cw[9::2], PRIOR_PPHASE)
         return ok
 
+    def param_bounds(self):
+        """Per-coordinate prior support (lo, hi): the uniform boxes of Sec. "Priors" (and
+        the CW box, pulsar phases in (0, 2 pi)); -inf/inf for z and pulsar distances."""
+        lo = np.full(self.D, -np.inf)
+        hi = np.full(self.D, np.inf)
+        o = self.lay
+        for I in range(self.npsr):
+            if self.rn_free:
+                sl = slice(o["th_rn"] + self.n_rn * I, o["th_rn"] + self.n_rn * (I + 1))
+                lo[sl], hi[sl] = PRIOR_LOG10RHO
+            else:
+                lo[o["th_rn"] + 2 * I], hi[o["th_rn"] + 2 * I] = PRIOR_LOG10A
+                lo[o["th_rn"] + 2 * I + 1], hi[o["th_rn"] + 2 * I + 1] = PRIOR_GAMMA
+            if self.n_dm:
+                lo[o["th_dm"] + 2 * I], hi[o["th_dm"] + 2 * I] = PRIOR_LOG10A
+                lo[o["th_dm"] + 2 * I + 1], hi[o["th_dm"] + 2 * I + 1] = PRIOR_GAMMA
+        if self.gwb_free:
+            lo[o["th_gwb"]: o["th_gwb"] + self.n_gwb], hi[o["th_gwb"]: o["th_gwb"] + self.n_gwb] = PRIOR_LOG10RHO
+        else:
+            lo[o["th_gwb"]], hi[o["th_gwb"]] = PRIOR_LOG10A
+            lo[o["th_gwb"] + 1], hi[o["th_gwb"] + 1] = PRIOR_GAMMA
+        if self.cw:
+            for j in range(8):
+                lo[o["th_cw"] + j], hi[o["th_cw"] + j] = PRIOR_CW[j]
+            for I in range(self.npsr):
+                lo[o["th_cw"] + 9 + 2 * I], hi[o["th_cw"] + 9 + 2 * I] = PRIOR_PPHASE
+        return lo, hi
+
     # -- spectra and prior covariance (Eqs. prior_cov, power_law) -----------------
     def spectra(self, th_rn, th_dm, th_gwb):
         ks = np.arange(1, self.na + 1)
@@ -924,26 +952,59 @@ def hmc_uniform(seed: int, iteration: int, chain: int) -> float:
     return u01(w[0])
 
 
-def hmc_trajectory(logp_grad, x0, logp0, grad0, step, n_leapfrog, p0, u, inv_mass=None):
+def hmc_trajectory(logp_grad, x0, logp0, grad0, step, n_leapfrog, p0, u, inv_mass=None, bounds=None):
     """One HMC transition (App. "Hamiltonian Monte Carlo"): Euclidean-Gaussian kinetic
     energy 1/2 p^T M^-1 p (Eq. Gaussian_momentum), H = -logp + K (Eq. Hamiltonian),
     n_leapfrog leapfrog steps of Hamilton's equations (Eq. Hamilton's_eq), accepted
     with probability min(1, exp(H0 - H1)) (Eq. HMC_acceptance) if u < that.
+    bounds = (lo, hi): the coordinates with a finite box move in
+    v = logit((x - lo) / (hi - lo)), x = lo + (hi - lo) sigmoid(v), and the target there is
+    logp(x(v)) + sum log((hi - lo) s (1 - s)), s = sigmoid(v) (change of variables of a
+    box-bounded parameter); the momentum and inv_mass refer to v for those coordinates.
     Returns (x, logp, grad, accepted)."""
     im = np.ones_like(x0) if inv_mass is None else inv_mass
-    x = x0.copy()
+    if bounds is None:
+        lo = np.full_like(x0, -np.inf)
+        hi = np.full_like(x0, np.inf)
+    else:
+        lo, hi = bounds
+    m = np.isfinite(lo) & np.isfinite(hi)
+    w = hi[m] - lo[m]
+
+    def to_v(x):
+        v = x.copy()
+        t = (x[m] - lo[m]) / w
+        v[m] = np.log(t) - np.log1p(-t)
+        return v
+
+    def to_x(v):
+        x = v.copy()
+        x[m] = lo[m] + w / (1.0 + np.exp(-v[m]))
+        return x
+
+    def log_jac(v):
+        s = 1.0 / (1.0 + np.exp(-v[m]))
+        return float(np.sum(np.log(w) + np.log(s) + np.log1p(-s)))
+
+    def grad_v(g, v):
+        s = 1.0 / (1.0 + np.exp(-v[m]))
+        gv = g.copy()
+        gv[m] = g[m] * w * s * (1.0 - s) + (1.0 - 2.0 * s)
+        return gv
+
+    v = to_v(x0)
     p = p0.copy()
     lp, g = logp0, grad0.copy()
-    H0 = -logp0 + 0.5 * np.sum(p0 * p0 * im)
+    H0 = -(logp0 + log_jac(v)) + 0.5 * np.sum(p0 * p0 * im)
     for _ in range(n_leapfrog):
-        p = p + 0.5 * step * g
-        x = x + step * im * p
-        lp, g = logp_grad(x)
-        p = p + 0.5 * step * g
-    H1 = -lp + 0.5 * np.sum(p * p * im) if math.isfinite(lp) else math.inf
+        p = p + 0.5 * step * grad_v(g, v)
+        v = v + step * im * p
+        lp, g = logp_grad(to_x(v))
+        p = p + 0.5 * step * grad_v(g, v)
+    H1 = -(lp + log_jac(v)) + 0.5 * np.sum(p * p * im) if math.isfinite(lp) else math.inf
     acc = math.log(u) < (H0 - H1)
     if acc:
-        return x, lp, g, True
+        return to_x(v), lp, g, True
     return x0.copy(), logp0, grad0.copy(), False
 
 

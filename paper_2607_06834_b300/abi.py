@@ -18,7 +18,7 @@ EXPORTED = ["pta_create", "pta_add_pulsar", "pta_finalize", "pta_layout", "pta_s
             "pta_set_hyperprior", "pta_logp_and_grad", "pta_hmc_trajectory", "pta_logp_constant",
             "pta_profile_enable", "pta_profile_read", "pta_logp_and_grad_noalloc", "pta_autotune",
             "pta_set_toa_config", "pta_toa_config_info", "pta_debug_inject", "pta_set_beta", "pta_set_transform",
-            "pta_last_error", "pta_destroy"]
+            "pta_param_bounds", "pta_last_error", "pta_destroy"]
 NSTAGES = 5
 STAGES = ["prior_forward", "toa", "epilogue", "adjoint", "final"]
 
@@ -69,6 +69,7 @@ def _load():
     lib.pta_debug_inject.argtypes = [vp, C.c_int]
     lib.pta_set_beta.argtypes = [vp, C.c_int, vp, vp]
     lib.pta_set_transform.argtypes = [vp, C.c_int]
+    lib.pta_param_bounds.argtypes = [vp, vp, vp]
     lib.pta_toa_config_info.argtypes = [C.c_int] + [C.POINTER(C.c_int)] * 4
     lib.pta_last_error.argtypes = [vp]
     lib.pta_last_error.restype = C.c_char_p

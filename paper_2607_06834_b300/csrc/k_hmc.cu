@@ -4,6 +4,13 @@
 // captured on first use and replayed afterwards.  The graph only touches
 // context-owned buffers; the caller's state is copied in and out around it.
 //
+// Bounded coordinates.  Every coordinate with a finite prior box [lo, hi] (the noise
+// and GWB hyper-parameters, the CW box parameters and pulsar phases) moves during a
+// trajectory in u = logit((x - lo) / (hi - lo)), x = lo + (hi - lo) sigmoid(u), with the
+// target's log-Jacobian sum log((hi - lo) s (1 - s)) added to the Hamiltonian, so a
+// trajectory never leaves the prior support (the unconstrained reparameterisation of a
+// box-bounded parameter).  The caller's state, logp and gradient stay in x.
+//
 // Random numbers: Philox4x32-10 (Salmon et al., SC'11) with counter
 // (block j, chain, iteration lo, iteration hi) and key (seed lo, seed hi); each
 // block gives two Box-Muller pairs.  The Metropolis uniform uses block index
@@ -15,6 +22,7 @@
 int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* grad, int32_t* status,
                       cudaStream_t st);
 int pta_prepare_internal(pta_ctx* c, int B);
+int pta_ensure_bounds(pta_ctx* c);
 
 namespace pta {
 namespace {
@@ -74,13 +82,45 @@ __global__ void k_momentum(const uint64_t* ctr, const float* imass, float* p, in
   }
 }
 
-// kinetic energy 1/2 p^T M^-1 p per chain (FP64 accumulation, fixed order)
-__global__ void k_kinetic(const float* p, const float* imass, double* kin, int D) {
+__device__ __forceinline__ bool bounded(double lo, double hi) { return isfinite(lo) && isfinite(hi); }
+
+// log sigmoid(u), stable for either sign
+__device__ __forceinline__ double log_sig(double u) { return u >= 0.0 ? -log1p(exp(-u)) : u - log1p(exp(u)); }
+
+// x = lo + (hi - lo) sigmoid(u) as a float strictly inside (lo, hi)
+__device__ __forceinline__ float u_to_x(double u, double lo, double hi) {
+  const double sg = 1.0 / (1.0 + exp(-u));
+  float xf = (float)fma(hi - lo, sg, lo);
+  for (int t = 0; t < 4 && (double)xf <= lo; ++t) xf = nextafterf(xf, INFINITY);
+  for (int t = 0; t < 4 && (double)xf >= hi; ++t) xf = nextafterf(xf, -INFINITY);
+  return xf;
+}
+
+// d/du of logp(x(u)) + log J(u) from g = d logp / dx
+__device__ __forceinline__ float grad_u(float g, float u, double lo, double hi) {
+  const double sg = 1.0 / (1.0 + exp(-(double)u));
+  return (float)fma((double)g * (hi - lo), sg * (1.0 - sg), 1.0 - 2.0 * sg);
+}
+
+// Start of a trajectory: u from x (bounded coordinates), and K0 - log J(u0) per chain
+// (FP64 accumulation, fixed order), the kinetic energy 1/2 p^T M^-1 p minus the
+// log-Jacobian, so that H0 = -logp0 + kin0.
+__global__ void k_start(const float* x0, const float* p, const float* imass, const double* lo, const double* hi,
+                        float* us, double* kin, int D) {
   const int b = blockIdx.x;
   double s = 0.0;
   for (int j = threadIdx.x; j < D; j += blockDim.x) {
     const double v = p[(size_t)b * D + j];
     s += 0.5 * v * v * imass[j];
+    const double xv = x0[(size_t)b * D + j];
+    if (bounded(lo[j], hi[j])) {
+      const double t = (xv - lo[j]) / (hi[j] - lo[j]);
+      const double u = log(t) - log1p(-t);
+      us[(size_t)b * D + j] = (float)u;
+      s -= log(hi[j] - lo[j]) + log(t) + log1p(-t);
+    } else {
+      us[(size_t)b * D + j] = (float)xv;
+    }
   }
   __shared__ double red[32];
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -93,28 +133,36 @@ __global__ void k_kinetic(const float* p, const float* imass, double* kin, int D
   }
 }
 
-// half kick + drift:  p += eps/2 g;  x += eps M^-1 p
-__global__ void k_kick_drift(float* x, float* p, const float* g, const float* step, const float* imass, int D,
-                             int B) {
+// half kick + drift in u:  p += eps/2 g_u;  u += eps M^-1 p;  x = x(u) for the evaluation
+__global__ void k_kick_drift(float* us, float* x, float* p, const float* g, const float* step, const float* imass,
+                             const double* lo, const double* hi, int D, int B) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)B * D) return;
   const int b = (int)(i / D), j = (int)(i % D);
   const float e = step[b];
-  const float pv = fmaf(0.5f * e, g[i], p[i]);
+  const bool bd = bounded(lo[j], hi[j]);
+  const float gu = bd ? grad_u(g[i], us[i], lo[j], hi[j]) : g[i];
+  const float pv = fmaf(0.5f * e, gu, p[i]);
   p[i] = pv;
-  x[i] = fmaf(e * imass[j], pv, x[i]);
+  const float u = fmaf(e * imass[j], pv, us[i]);
+  us[i] = u;
+  x[i] = bd ? u_to_x(u, lo[j], hi[j]) : u;
 }
 
-__global__ void k_kick(float* p, const float* g, const float* step, int D, int B) {
+__global__ void k_kick(float* p, const float* g, const float* us, const float* step, const double* lo,
+                       const double* hi, int D, int B) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)B * D) return;
-  p[i] = fmaf(0.5f * step[i / D], g[i], p[i]);
+  const int j = (int)(i % D);
+  const float gu = bounded(lo[j], hi[j]) ? grad_u(g[i], us[i], lo[j], hi[j]) : g[i];
+  p[i] = fmaf(0.5f * step[i / D], gu, p[i]);
 }
 
-// Metropolis accept: H = -logp + K; accept if log u < H0 - H1 (finite H1 only).
+// Metropolis accept: H = -logp - log J(u) + K; accept if log u < H0 - H1 (finite H1 only).
 __global__ void k_accept(const uint64_t* ctr, const double* lp0, const double* kin0, const double* lp1,
-                         const float* p, const float* imass, float* x0, float* g0, double* lp0w, const float* x1,
-                         const float* g1, int32_t* accepted, int D) {
+                         const float* p, const float* imass, const float* us, const double* lo, const double* hi,
+                         float* x0, float* g0, double* lp0w, const float* x1, const float* g1, int32_t* accepted,
+                         int D) {
   const int b = blockIdx.x;
   __shared__ double red[32];
   __shared__ int s_acc;
@@ -122,6 +170,10 @@ __global__ void k_accept(const uint64_t* ctr, const double* lp0, const double* k
   for (int j = threadIdx.x; j < D; j += blockDim.x) {
     const double v = p[(size_t)b * D + j];
     s += 0.5 * v * v * imass[j];
+    if (bounded(lo[j], hi[j])) {
+      const double u = us[(size_t)b * D + j];
+      s -= log(hi[j] - lo[j]) + log_sig(u) + log_sig(-u);
+    }
   }
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -162,18 +214,18 @@ static int hmc_record(pta_ctx* c, int B, int L, cudaStream_t st) {
   const int D = c->dm.d;
   const size_t n = (size_t)B * D;
   const unsigned nb = (unsigned)((n + 255) / 256);
+  const double *lo = c->hmc_lo, *hi = c->hmc_hi;
   k_momentum<<<dim3((unsigned)(((D + 3) / 4 + 127) / 128), B), 128, 0, st>>>(s.hmc_ctr, s.imass, s.p, D, B);
-  k_kinetic<<<B, 256, 0, st>>>(s.p, s.imass, s.kin0, D);
-  cudaMemcpyAsync(s.xs, s.x0, n * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  k_start<<<B, 256, 0, st>>>(s.x0, s.p, s.imass, lo, hi, s.us, s.kin0, D);
   cudaMemcpyAsync(s.gs, s.g0, n * sizeof(float), cudaMemcpyDeviceToDevice, st);
   for (int l = 0; l < L; ++l) {
-    k_kick_drift<<<nb, 256, 0, st>>>(s.xs, s.p, s.gs, s.step, s.imass, D, B);
+    k_kick_drift<<<nb, 256, 0, st>>>(s.us, s.xs, s.p, s.gs, s.step, s.imass, lo, hi, D, B);
     int rc = pta_eval_internal(c, B, s.xs, s.lps, s.gs, nullptr, st);
     if (rc != PTA_OK) return rc;
-    k_kick<<<nb, 256, 0, st>>>(s.p, s.gs, s.step, D, B);
+    k_kick<<<nb, 256, 0, st>>>(s.p, s.gs, s.us, s.step, lo, hi, D, B);
   }
-  k_accept<<<B, 256, 0, st>>>(s.hmc_ctr, s.lp0, s.kin0, s.lps, s.p, s.imass, s.x0, s.g0, s.lp0, s.xs, s.gs,
-                              s.acc, D);
+  k_accept<<<B, 256, 0, st>>>(s.hmc_ctr, s.lp0, s.kin0, s.lps, s.p, s.imass, s.us, lo, hi, s.x0, s.g0, s.lp0,
+                              s.xs, s.gs, s.acc, D);
   return cudaGetLastError() == cudaSuccess ? PTA_OK : PTA_ECUDA;
 }
 
@@ -191,6 +243,7 @@ extern "C" int pta_hmc_trajectory(pta_ctx* c, int B, float* x, double* logp, flo
     return PTA_EINVAL;
   }
   int rc = pta_prepare_internal(c, B);
+  if (rc == PTA_OK) rc = pta_ensure_bounds(c);
   if (rc != PTA_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const Scratch& s = c->sc;

@@ -573,7 +573,7 @@ void free_scratch(pta::Scratch& s) {
   void* ptrs[] = {s.a32, s.a64, s.Lpk, s.Lipk, s.gpart, s.gpart64, s.c2part, s.ghat, s.chi2,
                   s.dlnk, s.dlnkd, s.dlnr, s.stat, s.sk, s.skd, s.srho, s.cwc, s.cwjac, s.cwsig,
                   s.cwbs, s.cwwt, s.cwgp, s.cwg, s.x0, s.g0, s.p, s.lp0, s.xs, s.gs, s.lps,
-                  s.step, s.imass, s.kin0, s.hmc_ctr, s.acc, s.a16, s.queue, s.curnW, s.curnAhat,
+                  s.step, s.imass, s.kin0, s.hmc_ctr, s.acc, s.a16, s.queue, s.us, s.curnW, s.curnAhat,
                   s.curnV, s.curnLd, s.curnQ, s.dlnrc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -631,6 +631,7 @@ int ensure_scratch(pta_ctx* c, int B, bool fp64) {
   AL(p, (size_t)cap * m.d);
   AL(lp0, cap);
   AL(xs, (size_t)cap * m.d);
+  AL(us, (size_t)cap * m.d);
   AL(gs, (size_t)cap * m.d);
   AL(lps, cap);
   AL(step, cap);
@@ -769,6 +770,61 @@ static int ensure_bf16(pta_ctx* c) {
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(c, PTA_ECUDA, std::string("BF16 basis build: ") + cudaGetErrorString(e));
   m.xmlo = p;
+  return PTA_OK;
+}
+
+// Prior support of every coordinate of x (Sec. "Priors"; CW box and pulsar phases):
+// finite [lo, hi] for box-bounded ones, (-inf, inf) for z and the pulsar distances.
+static void param_bounds(const pta_ctx* c, double* lo, double* hi) {
+  const pta::DevModel& m = c->dm;
+  const pta_layout_t& L = c->lay;
+  for (int j = 0; j < L.d; ++j) {
+    lo[j] = -INFINITY;
+    hi[j] = INFINITY;
+  }
+  auto box = [&](int j, double a, double b) {
+    lo[j] = a;
+    hi[j] = b;
+  };
+  for (int I = 0; I < m.npsr; ++I) {
+    if (m.rn_free) {
+      for (int k = 0; k < m.n_rn; ++k) box(L.th_rn + m.n_rn * I + k, pta::kFreeLo, pta::kFreeHi);
+    } else {
+      box(L.th_rn + 2 * I, m.la_lo, m.la_hi);
+      box(L.th_rn + 2 * I + 1, m.g_lo, m.g_hi);
+    }
+    if (m.nd) {
+      box(L.th_dm + 2 * I, m.la_lo, m.la_hi);
+      box(L.th_dm + 2 * I + 1, m.g_lo, m.g_hi);
+    }
+  }
+  if (m.gwb_free) {
+    for (int k = 0; k < m.n_gwb; ++k) box(L.th_gwb + k, pta::kFreeLo, pta::kFreeHi);
+  } else {
+    box(L.th_gwb, m.la_lo, m.la_hi);
+    box(L.th_gwb + 1, m.g_lo, m.g_hi);
+  }
+  if (m.cw) {
+    for (int i = 0; i < 8; ++i) box(L.th_cw + i, m.cw_lo[i], m.cw_hi[i]);
+    for (int I = 0; I < m.npsr; ++I) box(L.th_cw + 9 + 2 * I, 0.0, 2.0 * pta::kPi);
+  }
+}
+
+int pta_ensure_bounds(pta_ctx* c) {
+  const int D = c->dm.d;
+  if (!c->hmc_lo) {
+    if (cudaMalloc(&c->hmc_lo, D * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->hmc_hi, D * sizeof(double)) != cudaSuccess)
+      return fail(c, PTA_ENOMEM, "bounds allocation failed");
+    c->bounds_dirty = true;
+  }
+  if (!c->bounds_dirty) return PTA_OK;
+  std::vector<double> lo(D), hi(D);
+  param_bounds(c, lo.data(), hi.data());
+  if (cudaMemcpy(c->hmc_lo, lo.data(), D * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->hmc_hi, hi.data(), D * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(c, PTA_ECUDA, "bounds upload failed");
+  c->bounds_dirty = false;
   return PTA_OK;
 }
 
@@ -951,6 +1007,14 @@ int pta_set_hyperprior(pta_ctx* c, double la_lo, double la_hi, double g_lo, doub
   c->dm.la_hi = la_hi;
   c->dm.g_lo = g_lo;
   c->dm.g_hi = g_hi;
+  c->bounds_dirty = true;
+  return PTA_OK;
+}
+
+int pta_param_bounds(const pta_ctx* c, double* lo, double* hi) {
+  if (!c || !lo || !hi) return PTA_EINVAL;
+  if (!c->finalized) return PTA_ESTATE;
+  param_bounds(c, lo, hi);
   return PTA_OK;
 }
 
@@ -1010,6 +1074,8 @@ void pta_destroy(pta_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
   if (c->beta_dev) cudaFree(c->beta_dev);
+  if (c->hmc_lo) cudaFree(c->hmc_lo);
+  if (c->hmc_hi) cudaFree(c->hmc_hi);
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   free_scratch(c->sc);

@@ -132,7 +132,8 @@ struct Scratch {
   float* g0 = nullptr;
   float* p = nullptr;
   double* lp0 = nullptr;
-  float* xs = nullptr;         // working state
+  float* xs = nullptr;         // working state (x, evaluated)
+  float* us = nullptr;         // working state with bounded coordinates in u = logit((x - lo)/(hi - lo))
   float* gs = nullptr;
   double* lps = nullptr;
   float* step = nullptr;       // [cap]
@@ -274,6 +275,10 @@ struct pta_ctx {
   int beta_n = 0;                  // chains it covers
   int toa_cfg = -1;                // SIMT tile-shape entry (-1: default), set by the autotuner
   int transform = PTA_TRANSFORM_PRIOR;
+  // prior support box per coordinate (HMC moves bounded coordinates in logit space)
+  double* hmc_lo = nullptr;
+  double* hmc_hi = nullptr;
+  bool bounds_dirty = true;
   pta_layout_t lay{};
   // HMC graphs keyed by (B, n_leapfrog)
   struct Graph {

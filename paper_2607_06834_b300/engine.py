@@ -114,6 +114,15 @@ class Engine:
         self._check(abi.lib.pta_set_transform(self._h, abi.TRANSFORM[transform]), "pta_set_transform")
         self.transform = transform
 
+    def param_bounds(self):
+        """(lo, hi) float64 arrays of the prior support of each coordinate (+-inf where
+        unbounded); the HMC trajectory moves the bounded ones in logit space."""
+        lo = np.empty(self.D, dtype=np.float64)
+        hi = np.empty(self.D, dtype=np.float64)
+        self._check(abi.lib.pta_param_bounds(self._h, C.c_void_p(lo.ctypes.data), C.c_void_p(hi.ctypes.data)),
+                    "pta_param_bounds")
+        return lo, hi
+
     def set_toa_config(self, cfg: int):
         self._check(abi.lib.pta_set_toa_config(self._h, int(cfg)), "pta_set_toa_config")
 

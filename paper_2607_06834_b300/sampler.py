@@ -272,7 +272,7 @@ class HMCResult:
 def run_hmc(engine, x0: torch.Tensor, n_warmup: int, n_samples: int, n_leapfrog: int,
             record=None, seed: int = 1, eps0: float = 0.05, target_accept: float = 0.8,
             jitter: float = 0.1, timer=None, init_dz: int = 0, init_iters: int = 100,
-            consensus: int = 0) -> HMCResult:
+            consensus: int = 0, unit_mass: int = 0) -> HMCResult:
     """Warm up and sample ``x0.shape[0]`` chains.  ``engine`` provides ``D``,
     ``logp_and_grad(x)`` and ``hmc_trajectory(x, logp, grad, step, L, seed, it, inv_mass)``
     working on tensors of x0's device.  ``record`` (a slice or an index tensor) selects
@@ -283,7 +283,11 @@ def run_hmc(engine, x0: torch.Tensor, n_warmup: int, n_samples: int, n_leapfrog:
     chains first run that many warm-up trajectories from their own starts, then all
     restart from the state of the chain with the highest log posterior (the rest of
     the warm-up and the Philox momenta then separate them): chains that start in
-    regions far apart would otherwise need far longer to meet than the run allows."""
+    regions far apart would otherwise need far longer to meet than the run allows.
+    With ``unit_mass`` > 0 the first unit_mass coordinates keep inverse mass 1 through
+    the adaptation (coordinates that the transform standardizes by construction).
+    Box-bounded coordinates (``engine.param_bounds()``) get their mass from the variance
+    of u = logit((x - lo)/(hi - lo)), the coordinate the trajectory moves them in."""
     import time
 
     if timer is None:
@@ -309,6 +313,15 @@ def run_hmc(engine, x0: torch.Tensor, n_warmup: int, n_samples: int, n_leapfrog:
     step = torch.empty(B, dtype=torch.float32, device=dev)
     windows = warmup_schedule(n_warmup)
     wi = 0
+    # the trajectory moves box-bounded coordinates in u = logit((x - lo)/(hi - lo)): their
+    # mass is adapted from the variance of u
+    bnd = None
+    if hasattr(engine, "param_bounds"):
+        lo, hi = engine.param_bounds()
+        m = np.isfinite(lo) & np.isfinite(hi)
+        if m.any():
+            idx = torch.tensor(np.nonzero(m)[0], device=dev)
+            bnd = (idx, torch.tensor(lo[m], device=dev), torch.tensor(hi[m], device=dev))
     s1 = torch.zeros((B, D), dtype=torch.float64, device=dev)
     s2 = torch.zeros((B, D), dtype=torch.float64, device=dev)
     cnt = 0
@@ -328,6 +341,9 @@ def run_hmc(engine, x0: torch.Tensor, n_warmup: int, n_samples: int, n_leapfrog:
             da.restart(eps)
         if wi < len(windows) and windows[wi][0] <= i < windows[wi][1]:
             xd = x.double()
+            if bnd is not None:
+                t = ((xd[:, bnd[0]] - bnd[1]) / (bnd[2] - bnd[1])).clamp(1e-12, 1.0 - 1e-12)
+                xd[:, bnd[0]] = torch.log(t) - torch.log1p(-t)
             s1 += xd
             s2 += xd * xd
             cnt += 1
@@ -338,6 +354,8 @@ def run_hmc(engine, x0: torch.Tensor, n_warmup: int, n_samples: int, n_leapfrog:
                 var = ((s2 / cnt - mean * mean).clamp_min(0.0) * cnt / max(cnt - 1, 1)).median(0).values
                 n = cnt * B  # draws behind the estimate
                 var = (n / (n + 5.0)) * var + 1e-3 * (5.0 / (n + 5.0))
+                if unit_mass > 0:  # coordinates standardized by construction keep unit mass
+                    var[:unit_mass] = 1.0
                 inv_mass = var.float().contiguous()
                 s1.zero_()
                 s2.zero_()

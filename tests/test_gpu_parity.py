@@ -388,9 +388,14 @@ def test_hmc_trajectory_matches_oracle(tiny):
         lp0, g0 = lgf(x0)
         p0 = O.hmc_normals(seed, it, b, orc.D)
         u = O.hmc_uniform(seed, it, b)
-        xo, lpo, go, acco = O.hmc_trajectory(lgf, x0, lp0, g0, step, L, p0, u)
+        xo, lpo, go, acco = O.hmc_trajectory(lgf, x0, lp0, g0, step, L, p0, u, bounds=orc.param_bounds())
         assert bool(accg[b]) == acco
         np.testing.assert_allclose(xg[b], xo, rtol=1e-3, atol=1e-4)
+    # the library's prior support is the oracle's
+    lo, hi = eng.param_bounds()
+    olo, ohi = orc.param_bounds()
+    np.testing.assert_array_equal(lo, olo)
+    np.testing.assert_array_equal(hi, ohi)
     # graph replay with a new iteration counter moves the state again
     acc2 = eng.hmc_trajectory(x, lp, g, steps, L, seed, it + 1)
     torch.cuda.synchronize()

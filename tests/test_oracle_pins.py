@@ -343,6 +343,32 @@ def test_hmc_reversibility_and_gaussian_target():
     assert np.abs(xs.mean(0)).max() < 0.1
 
 
+def test_hmc_bounded_coordinates_sample_the_box():
+    """Box-bounded coordinates moved in logit space: a flat target on [lo, hi] (logp = 0
+    inside) must be sampled uniformly (mean (lo + hi)/2, variance (hi - lo)^2 / 12), next
+    to an unbounded Gaussian coordinate (N(1, 0.5^2)); no proposal leaves the box."""
+    lo = np.array([-20.0, 0.0, -np.inf])
+    hi = np.array([-10.0, 7.0, np.inf])
+
+    def lg(x):
+        if not (lo[0] < x[0] < hi[0] and lo[1] < x[1] < hi[1]):
+            return -math.inf, np.zeros(3)
+        return -0.5 * ((x[2] - 1.0) / 0.5) ** 2, np.array([0.0, 0.0, -(x[2] - 1.0) / 0.25])
+    x = np.array([-12.0, 6.5, 0.0])
+    lp, g = lg(x)
+    xs = []
+    for it in range(6000):
+        p0 = O.hmc_normals(13, it, 0, 3)
+        u = O.hmc_uniform(13, it, 0)
+        x, lp, g, _ = O.hmc_trajectory(lg, x, lp, g, 0.4, 6, p0, u, bounds=(lo, hi))
+        assert math.isfinite(lp)
+        xs.append(x)
+    xs = np.array(xs[500:])
+    assert abs(xs[:, 0].mean() - (-15.0)) < 0.3 and abs(xs[:, 1].mean() - 3.5) < 0.25
+    np.testing.assert_allclose(xs[:, :2].var(0), [100.0 / 12, 49.0 / 12], rtol=0.12)
+    assert abs(xs[:, 2].mean() - 1.0) < 0.05 and abs(xs[:, 2].std() - 0.5) < 0.05
+
+
 
 def test_tempered_posterior_limits_and_linearity():
     """Eq. (tempered_post): beta = 0 leaves the prior alone (closed form: logp = -|z|^2/2
