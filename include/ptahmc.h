@@ -230,15 +230,17 @@ int pta_hmc_trajectory(pta_ctx* ctx, int B, float* x_dev, double* logp_dev, floa
  * workspace is a fixed 32 MiB array compiled into the library (held on every GPU
  * that loads the library until exit) instead of context-owned device memory.  The
  * paper has no counterpart; it exists for callers that cannot call cudaMalloc when
- * they evaluate (work recorded into a stream capture, or a host framework that
- * owns every device allocation).  The context still holds the data uploaded by
- * pta_finalize.
+ * they evaluate: a host framework that owns every device allocation and forbids
+ * allocations outside its own allocator, or a sampler loop that must not pay for or
+ * risk an allocation failure in the middle of a run.  The context still holds the
+ * data uploaded by pta_finalize.
  *   - B chains must fit in the array: otherwise PTA_EINVAL with the needed size in
  *     pta_last_error (about 1.2 MB per chain for 67 pulsars, 3e5 TOAs).
  *   - The first call on a device looks up the array's device address (with that
- *     device current) and caches it; make that first call before any capture.
+ *     device current) and caches it; make that first call before any stream capture.
  *   - All calls share the array and it keeps the last call's contents: calls that
- *     overlap on the GPU race.  The status flags are cleared on `stream` per call.
+ *     overlap on the GPU race.  What must start at zero (the per-chain status flags
+ *     and the work counter of persistent launches) is cleared on `stream` per call.
  *   - PTA_PREC_FP64 needs the stored FP64 basis, which pta_logp_and_grad builds on
  *     its first FP64 call; without it the call returns PTA_ESTATE.
  *   - PTA_PREC_BF16X3 (its packed coefficients need their own buffer) and the

@@ -2,9 +2,10 @@
 // per-call scratch buffer carved out of one file-scope device array instead of
 // context-owned allocations.
 //
-// Who needs it: callers that must not call cudaMalloc at evaluation time, e.g. code
-// that records the call into a stream capture, or a host framework that owns all
-// device allocation and forbids allocations outside its own allocator.  The
+// Who needs it: callers that must not call cudaMalloc at evaluation time, e.g. a host
+// framework that owns all device allocation and forbids allocations outside its own
+// allocator, or a long sampler loop that must not pay for, or risk the failure of, an
+// allocation in the middle of a run.  The
 // context's resident data (uploaded by pta_finalize) is still used as is; only
 // the per-call workspace moves here.
 //
@@ -14,9 +15,9 @@
 // asks the runtime for the device address with cudaGetSymbolAddress, with that
 // device current, and caches it; make that first call before any stream capture.
 // All calls share the array: calls that overlap on the GPU (different streams,
-// devices excluded) race on it.  The array keeps the last call's contents; the one
-// buffer that must start at zero (per-chain status flags) is cleared on the
-// caller's stream at the start of every call.
+// devices excluded) race on it.  The array keeps the last call's contents; what must
+// start at zero (the per-chain status flags, and the work counter of persistent TOA
+// launches) is cleared on the caller's stream within every call.
 #include <mutex>
 
 #include "pta_internal.cuh"
