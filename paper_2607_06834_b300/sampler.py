@@ -270,7 +270,7 @@ class HMCResult:
 
 
 def run_hmc(engine, x0: torch.Tensor, n_warmup: int, n_samples: int, n_leapfrog: int,
-            record=None, seed: int = 1, eps0: float = 0.05, target_accept: float = 0.8,
+            record=None, seed: int = 1, eps0: float = 0.05, target_accept: float = 0.651,
             jitter: float = 0.1, timer=None, init_dz: int = 0, init_iters: int = 100,
             consensus: int = 0, unit_mass: int = 0) -> HMCResult:
     """Warm up and sample ``x0.shape[0]`` chains.  ``engine`` provides ``D``,
@@ -284,6 +284,10 @@ def run_hmc(engine, x0: torch.Tensor, n_warmup: int, n_samples: int, n_leapfrog:
     restart from the state of the chain with the highest log posterior (the rest of
     the warm-up and the Philox momenta then separate them): chains that start in
     regions far apart would otherwise need far longer to meet than the run allows.
+    The step size targets acceptance 0.651, the asymptotically optimal rate of HMC with a
+    fixed number of leapfrog steps (Beskos, Pillai, Roberts, Sanz-Serna & Stuart 2013); the
+    0.8 that NUTS implementations use left the accepted fraction near 0.93 here and halved
+    the ESS of a 40-dimensional Gaussian test.
     With ``unit_mass`` > 0 the first unit_mass coordinates keep inverse mass 1 through
     the adaptation (coordinates that the transform standardizes by construction).
     Box-bounded coordinates (``engine.param_bounds()``) get their mass from the variance
