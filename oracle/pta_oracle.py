@@ -247,8 +247,6 @@ class Oracle:
     def __init__(self, arr, store_basis: bool = True, transform: str = "prior"):
         if transform not in ("prior", "curn"):
             raise ValueError("transform must be 'prior' or 'curn'")
-        if transform == "curn" and arr.cw:
-            raise NotImplementedError("CURN transform with a deterministic signal (Eq. decenter_det_PTA)")
         self.transform_kind = transform
         self._curn_fixed = None
         self.arr = arr
@@ -433,9 +431,12 @@ class Oracle:
             phi[2 * self.na + 2 * k: 2 * self.na + 2 * k + 2] = kdm[I, k]
         return phi
 
-    def curn_moments(self, I, phiC, beta):
-        """ahat_I, L_I (lower Cholesky factor of Sigma_I) and Sigma_I."""
+    def curn_moments(self, I, phiC, beta, h=None):
+        """ahat_I, L_I (lower Cholesky factor of Sigma_I) and Sigma_I.  With a deterministic
+        signal h_I (Eq. decenter_det_PTA) the mean is abar_I = beta Sigma_I F^T N~^-1 (dt - h)."""
         FNF, FNd = self.curn_fixed(I)
+        if h is not None:
+            FNd = FNd - self.get_F(I).T @ ntilde_inv_woodbury(self.Nvar[I], self.psrs[I].M, h)
         Sigma = np.linalg.inv(beta * FNF + np.diag(1.0 / phiC))
         Sigma = 0.5 * (Sigma + Sigma.T)
         return beta * Sigma @ FNd, np.linalg.cholesky(Sigma), Sigma
@@ -454,13 +455,15 @@ class Oracle:
                     Z[I, 2 * self.na + 2 * k + c] = z_dm[I, k, c]
         return Z
 
-    def curn_transform(self, z_ach, z_dm, rho, kappa, kdm, beta: float = 1.0):
-        """a_I = ahat_I + L_I z_I for every pulsar; returns (a, [L_I])."""
+    def curn_transform(self, z_ach, z_dm, rho, kappa, kdm, beta: float = 1.0, th_cw=None):
+        """a_I = ahat_I + L_I z_I for every pulsar (abar_I with the deterministic signal,
+        Eq. decenter_det_PTA); returns (a, [L_I])."""
         Z = self.z_per_pulsar(z_ach, z_dm)
         a = np.zeros((self.npsr, self.P))
         Ls = []
         for I in range(self.npsr):
-            ahat, L, _ = self.curn_moments(I, self.curn_prior_var(I, rho, kappa, kdm), beta)
+            h = self.signal(th_cw, I) if self.cw else None
+            ahat, L, _ = self.curn_moments(I, self.curn_prior_var(I, rho, kappa, kdm), beta, h)
             a[I] = ahat + L @ Z[I]
             Ls.append(L)
         return a, Ls
@@ -476,12 +479,12 @@ class Oracle:
         return ld
 
     def _logp_curn(self, x, beta, lpt):
-        z_ach, z_dm, th_rn, th_dm, th_gwb, _ = self.unpack(x)
+        z_ach, z_dm, th_rn, th_dm, th_gwb, th_cw = self.unpack(x)
         rho, kappa, kdm = self.spectra(th_rn, th_dm, th_gwb)
-        a, Ls = self.curn_transform(z_ach, z_dm, rho, kappa, kdm, beta)
+        a, Ls = self.curn_transform(z_ach, z_dm, rho, kappa, kdm, beta, th_cw)
         chi2 = 0.0
         for I in range(self.npsr):
-            r = self.dt_ns[I] - self.get_F(I) @ a[I]
+            r = self.dt_ns[I] - self.get_F(I) @ a[I] - self.signal(th_cw, I)
             chi2 += r @ ntilde_inv_woodbury(self.Nvar[I], self.psrs[I].M, r)
         logdetL = sum(float(np.sum(np.log(np.diag(L)))) for L in Ls)
         return (-0.5 * beta * chi2 - 0.5 * self._a_phi_a(a, rho, kappa, kdm)
@@ -521,11 +524,15 @@ class Oracle:
         at fixed a, 1/2 v^T dphi v - 1/2 tr(phi^-1 dphi) (v = phi^-1 a); through
         a(eta) = ahat + L z, gbar . da with dSigma = -Sigma dSigma^-1 Sigma,
         dL = chol_tangent(L, dSigma), dahat = beta dSigma F^T N~^-1 dt; and
-        d log det L = tr(L^-1 dL)."""
+        d log det L = tr(L^-1 dL).
+        With the deterministic signal (Eq. decenter_det_PTA) the mean abar_I depends on the
+        CW parameters too: d logp = beta w~ . dh + gbar_I . dabar_I with
+        dabar_I = -beta Sigma_I F_I^T N~_I^-1 dh_I, dh by complex-step differentiation of
+        ``cw_signal``; the mean's spectral tangent uses F^T N~^-1 (dt - h)."""
         g = np.zeros(self.D)
         if not math.isfinite(self.log_prior_theta(x)):
             return g
-        z_ach, z_dm, th_rn, th_dm, th_gwb, _ = self.unpack(x)
+        z_ach, z_dm, th_rn, th_dm, th_gwb, th_cw = self.unpack(x)
         rho, kappa, kdm = self.spectra(th_rn, th_dm, th_gwb)
         npsr, na, nd, P = self.npsr, self.na, self.n_dm, self.P
         Z = self.z_per_pulsar(z_ach, z_dm)
@@ -533,13 +540,19 @@ class Oracle:
         a = np.zeros((npsr, P))
         for I in range(npsr):
             phiC = self.curn_prior_var(I, rho, kappa, kdm)
-            ahat, L, Sigma = self.curn_moments(I, phiC, beta)
+            h = self.signal(th_cw, I) if self.cw else None
+            ahat, L, Sigma = self.curn_moments(I, phiC, beta, h)
             a[I] = ahat + L @ Z[I]
-            mom.append((phiC, L, Sigma))
+            FNd = self.curn_fixed(I)[1]
+            if h is not None:
+                FNd = FNd - self.get_F(I).T @ ntilde_inv_woodbury(self.Nvar[I], self.psrs[I].M, h)
+            mom.append((phiC, L, Sigma, FNd))
         gbar = np.zeros((npsr, P))
+        wts = []
         for I in range(npsr):
-            r = self.dt_ns[I] - self.get_F(I) @ a[I]
-            gbar[I] = beta * (self.get_F(I).T @ ntilde_inv_woodbury(self.Nvar[I], self.psrs[I].M, r))
+            r = self.dt_ns[I] - self.get_F(I) @ a[I] - self.signal(th_cw, I)
+            wts.append(ntilde_inv_woodbury(self.Nvar[I], self.psrs[I].M, r))
+            gbar[I] = beta * (self.get_F(I).T @ wts[I])
         Phis = [self.phi_bin(rho[k], kappa[:, k]) for k in range(na)]
         v = np.zeros((npsr, P))
         for k in range(na):
@@ -581,14 +594,34 @@ class Oracle:
                 dphiC = self.curn_prior_var(I, drho, dkap, dkdm)
                 if not np.any(dphiC):
                     continue
-                phiC, L, Sigma = mom[I]
+                phiC, L, Sigma, FNd = mom[I]
                 dSinv = -dphiC / phiC ** 2                 # d(phi_CURN^-1), diagonal
                 dSigma = -(Sigma * dSinv[None, :]) @ Sigma
                 dL = chol_tangent(L, dSigma)
-                FNd = self.curn_fixed(I)[1]
                 da = beta * dSigma @ FNd + dL @ Z[I]
                 d += gbar[I] @ da + np.trace(sla.solve_triangular(L, dL, lower=True))
             g[j] = d
+        if self.cw:
+            hstep = 1e-30
+            for j in range(8 + 2 * npsr):
+                pulsars = range(npsr) if j < 8 else [(j - 8) // 2]
+                acc = 0.0
+                for I in pulsars:
+                    th8, dist, pph = self.cw_th(th_cw, I)
+                    th8c = np.array(th8, dtype=complex)
+                    dist_c, pph_c = complex(dist), complex(pph)
+                    if j < 8:
+                        th8c[j] += 1j * hstep
+                    elif (j - 8) % 2 == 0:
+                        dist_c += 1j * hstep
+                    else:
+                        pph_c += 1j * hstep
+                    ds = np.imag(cw_signal(self.t_rel[I], self.psrs[I].pos, th8c, dist_c, pph_c)) / hstep
+                    Fds = self.get_F(I).T @ ntilde_inv_woodbury(self.Nvar[I], self.psrs[I].M, ds)
+                    acc += beta * (wts[I] @ ds) - beta * (gbar[I] @ (mom[I][2] @ Fds))
+                g[o["th_cw"] + j] = acc
+            for I in range(npsr):
+                g[o["th_cw"] + 8 + 2 * I] += -(th_cw[8 + 2 * I] - self.psrs[I].dist_kpc) / DIST_SIGMA_KPC ** 2
         return g
 
     # -- deterministic signal ---------------------------------------------------
@@ -608,7 +641,7 @@ class Oracle:
         z_ach, z_dm, th_rn, th_dm, th_gwb, th_cw = self.unpack(x)
         rho, kappa, kdm = self.spectra(th_rn, th_dm, th_gwb)
         if self.transform_kind == "curn":
-            a, Ls = self.curn_transform(z_ach, z_dm, rho, kappa, kdm, beta)
+            a, Ls = self.curn_transform(z_ach, z_dm, rho, kappa, kdm, beta, th_cw)
         else:
             a, Ls = self.transform(z_ach, z_dm, rho, kappa, kdm)
         rs = [self.dt_ns[I] - self.get_F(I) @ a[I] - self.signal(th_cw, I) for I in range(self.npsr)]

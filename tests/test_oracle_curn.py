@@ -13,6 +13,8 @@ against things other than itself.  CPU only.
   Jacobian det L_CURN and the prior normalisation are both checked by this.
 * beta = 0: the transform is a = sqrt(phi_CURN) z; for one pulsar this is the
   prior-whitened transform, so the two oracles agree.
+* With a circular binary (Eq. decenter_det_PTA) the same exactness and integral hold with
+  the mean abar = Sigma F^T N~^-1 (dt - h).
 * The gradient against central differences, power-law and free spectra, tempered."""
 import math
 
@@ -124,7 +126,37 @@ def test_gradient_central_differences(kw, beta):
     assert np.all(err <= 1e-6 * np.abs(g) + 1e-7 * scale), (np.argmax(err / (np.abs(g) + 1e-7 * scale)), err.max())
 
 
-def test_rejects_deterministic_signal():
-    arr = synth.small_array(npsr=2, ntoa=40, m=3, n_gwb=2, n_rn=2, n_dm=0, seed=13, cw=True)
-    with pytest.raises(NotImplementedError):
-        O.Oracle(arr, transform="curn")
+def _cw_point(orc, arr, seed):
+    x = synth.make_points(arr, 1, seed=seed)[0].astype(np.float64)
+    c = orc.lay["th_cw"]
+    x[c: c + 8] = [9.5, -7.8, -13.5, 0.3, 1.0, 0.2, 2.0, 1.0]
+    return x
+
+
+def test_deterministic_signal_single_pulsar_exact_whitening():
+    """Eq. decenter_det_PTA: with a circular binary the conditional posterior of a is still
+    Gaussian with the CURN covariance and mean abar = Sigma F^T N~^-1 (dt - h); for one pulsar
+    logp(z) + |z|^2/2 is independent of z and equals the dense marginal likelihood of dt - h
+    (minus the dropped constant) plus the CW prior."""
+    arr = synth.small_array(npsr=1, ntoa=60, m=3, n_gwb=3, n_rn=3, n_dm=1, seed=8, cw=True)
+    orc = O.Oracle(arr, transform="curn")
+    x = _cw_point(orc, arr, 3)
+    ref = orc.dense_marginal(x) - orc.data_constant() + orc.log_prior_theta(x)
+    for y in _z_variants(orc, x, 4, seed=5):
+        v = orc.logp(y) + 0.5 * y[: orc.Dz] @ y[: orc.Dz]
+        assert abs(v - ref) <= 1e-9 * abs(ref), (v, ref)
+
+
+def test_deterministic_signal_integral_and_gradient():
+    arr = synth.small_array(npsr=2, ntoa=40, m=3, n_gwb=2, n_rn=2, n_dm=1, seed=13, cw=True)
+    orc = O.Oracle(arr, transform="curn")
+    x = _cw_point(orc, arr, 21)
+    a = _closed_form_logZ(orc, x)
+    b = orc.dense_marginal(x) + orc.log_prior_theta(x)
+    assert abs(a - b) <= 1e-9 * abs(b), (a, b)
+    for beta in (1.0, 0.6):
+        g = orc.grad(x, beta=beta)
+        fd = _fd_grad(orc, x, beta)
+        scale = np.abs(g).max()
+        err = np.abs(fd - g)
+        assert np.all(err <= 1e-6 * np.abs(g) + 1e-7 * scale), (np.argmax(err / (np.abs(g) + 1e-7 * scale)), err.max())
