@@ -164,9 +164,11 @@ int pta_set_beta(pta_ctx* ctx, int n, const double* beta, void* stream);
  *     matrix per (pulsar, chain), about P^3/3 FP64 multiply-adds, and keeps
  *     B N_p P (P + 1) / 2 doubles of inverse factors between the value and the gradient
  *     (PTA_ENOMEM from the evaluation if they do not fit).
- * PTA_EINVAL for an unknown value and, for PTA_TRANSFORM_CURN, for models with the
- * continuous-wave signal (the deterministic generalisation, Eq. decenter_det_PTA, is not
- * built).  pta_logp_and_grad_noalloc rejects the CURN transform.  Recaptures HMC graphs. */
+ * With the continuous-wave signal h(theta) the mean is abar_I = beta Sigma_I F_I^T N~_I^-1
+ * (dt_I - h_I) (Eq. decenter_det_PTA) and the CW gradient includes its dependence on theta;
+ * this costs one extra TOA pass per evaluation and one more when the gradient is asked for.
+ * PTA_EINVAL for an unknown value.  pta_logp_and_grad_noalloc rejects the CURN transform.
+ * Recaptures HMC graphs. */
 #define PTA_TRANSFORM_PRIOR 0
 #define PTA_TRANSFORM_CURN 1
 int pta_set_transform(pta_ctx* ctx, int transform);

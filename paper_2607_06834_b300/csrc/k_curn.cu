@@ -83,7 +83,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 __global__ void __launch_bounds__(kCT)
     k_curn_forward(DevModel m, const float* __restrict__ x, const double* __restrict__ sk,
                    const double* __restrict__ skd, const double* __restrict__ srho, double* a64, double* Wg,
-                   double* ahat, double* ld, int32_t* stat, int B, int in_smem) {
+                   double* ahat, double* ld, int32_t* stat, const double* __restrict__ g0, int B, int in_smem) {
   extern __shared__ double sm[];
   __shared__ int s_bad;
   __shared__ double red[kCT / 32];
@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(kCT)
   double* up = zp + P;                    // Y' g'
   double* tp = up + P;                    // beta Y' g' + z'
   const double bt = m.beta ? m.beta[b] : 1.0;
+  const double gsc = g0 ? 1.0 : bt;  // factor of Y'^T Y' g in the mean
   const float* xb = x + (size_t)b * m.d;
   const double* G = m.Grev + (size_t)I * ntri;
   if (tid == 0) s_bad = 0;
@@ -114,7 +115,9 @@ __global__ void __launch_bounds__(kCT)
     else
       s_bad = 1;
     rd[i] = dv;
-    gp[i] = m.gt[(size_t)I * P + p];
+    // g = F^T N~^-1 dt, or with the deterministic signal the already beta-scaled
+    // beta F^T N~^-1 (dt - h) = g0 + beta G~ a_ref (Eq. decenter_det_PTA)
+    gp[i] = g0 ? fma(bt, m.ga[(size_t)I * P + p], g0[o * P + p]) : m.gt[(size_t)I * P + p];
     zp[i] = (double)xb[zidx(m, I, p)];
   }
   __syncthreads();
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(kCT)
     double sacc = 0.0;
     for (int c = 0; c <= i; ++c) sacc = fma(row[c], gp[c], sacc);
     up[i] = sacc;
-    tp[i] = fma(bt, sacc, zp[i]);
+    tp[i] = fma(gsc, sacc, zp[i]);
   }
   __syncthreads();
   for (int c = tid; c < P; c += kCT) {
@@ -205,7 +208,7 @@ __global__ void __launch_bounds__(kCT)
     }
     const int p = P - 1 - c;
     a64[o * m.PM + p] = sa;
-    ahat[o * P + p] = bt * sh;
+    ahat[o * P + p] = gsc * sh;
   }
   double acc = 0.0;
   for (int i = tid; i < P; i += kCT) acc += log(d[i]);
@@ -337,7 +340,7 @@ __global__ void __launch_bounds__(kCT)
     k_curn_adjoint(DevModel m, const float* __restrict__ x, const double* __restrict__ ghat,
                    const double* __restrict__ Wg, const double* __restrict__ vbuf, const double* __restrict__ ahat,
                    const double* __restrict__ sk, const double* __restrict__ skd, const double* __restrict__ srho,
-                   float* grad, double* dlnk, double* dlnkd, double* dlnrc, int B, int in_smem) {
+                   float* grad, double* dlnk, double* dlnkd, double* dlnrc, double* v2, int B, int in_smem) {
   extern __shared__ double sm[];
   const int I = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, P = m.P, np = m.npsr;
   const int ntri = P * (P + 1) / 2;
@@ -381,6 +384,7 @@ __global__ void __launch_bounds__(kCT)
     }
     const double ab = -h * ah[c] - Tc - 0.5 * Dg;  // d logp / d d_p
     const int p = P - 1 - c;
+    if (v2) v2[o * P + p] = h;  // A^-1 gbar, for the CW gradient through the mean
     pd[p] = -ab / phic(m, sk, skd, srho, b, I, p);  // phi d/dphi = -d_p d/dd_p
   }
   __syncthreads();
@@ -393,6 +397,23 @@ __global__ void __launch_bounds__(kCT)
   }
   for (int k = tid; k < m.nd; k += kCT)
     dlnkd[((size_t)b * np + I) * m.nd + k] += pd[2 * m.na + 2 * k] + pd[2 * m.na + 2 * k + 1];
+}
+
+// Auxiliary passes of the deterministic-signal transform: a = a_ref - v per (pulsar,
+// chain), and the difference of two per-TOA weight arrays.
+__global__ void k_set_a(DevModel m, double* a64, const double* __restrict__ v, int B) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)m.npsr * B * m.P) return;
+  const int p = (int)(i % m.P);
+  const size_t o = i / m.P;           // I * B + b
+  const int I = (int)(o / B);
+  const double a = m.aref[(size_t)I * m.P + p];
+  a64[o * m.PM + p] = v ? a - v[i] : a;
+}
+
+__global__ void k_sub(float* out, const float* __restrict__ w, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] -= w[i];
 }
 
 size_t fwd_smem(const DevModel& m, bool tri) {
@@ -415,7 +436,7 @@ cudaError_t launch_curn_forward(const DevModel& m, const Scratch& s, int B, cons
   cudaError_t e = cudaFuncSetAttribute(k_curn_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k_curn_forward<<<dim3(m.npsr, B), kCT, sm, st>>>(m, x, s.sk, s.skd, s.srho, s.a64, s.curnW, s.curnAhat, s.curnLd,
-                                                    s.stat, B, tri ? 1 : 0);
+                                                    s.stat, m.cw ? s.curnG0 : nullptr, B, tri ? 1 : 0);
   const size_t ws = ((size_t)m.npsr * (m.npsr + 1) / 2 + 4 * m.npsr) * sizeof(double);
   e = cudaFuncSetAttribute(k_curn_whiten, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws);
   if (e != cudaSuccess) return e;
@@ -431,7 +452,19 @@ cudaError_t launch_curn_adjoint(const DevModel& m, const Scratch& s, int B, cons
   cudaError_t e = cudaFuncSetAttribute(k_curn_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k_curn_adjoint<<<dim3(m.npsr, B), kCT, sm, st>>>(m, x, s.ghat, s.curnW, s.curnV, s.curnAhat, s.sk, s.skd, s.srho,
-                                                    grad, s.dlnk, s.dlnkd, s.dlnrc, B, tri ? 1 : 0);
+                                                    grad, s.dlnk, s.dlnkd, s.dlnrc, m.cw ? s.curnV2 : nullptr, B,
+                                                    tri ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_curn_set_a(const DevModel& m, const Scratch& s, int B, const double* v, cudaStream_t st) {
+  const size_t n = (size_t)m.npsr * B * m.P;
+  k_set_a<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m, s.a64, v, B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub(float* out, const float* w, size_t n, cudaStream_t st) {
+  k_sub<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, w, n);
   return cudaGetLastError();
 }
 

@@ -284,6 +284,7 @@ int pta_finalize(pta_ctx* c, void* stream) {
   std::vector<double> gg2((size_t)npsr * m.P, 0.0), cc2(npsr, 0.0);
   const size_t ntriP = (size_t)m.P * (m.P + 1) / 2;
   std::vector<double> Grev((size_t)npsr * ntriP, 0.0), gtv((size_t)npsr * m.P, 0.0);  // CURN transform
+  std::vector<double> gav((size_t)npsr * m.P, 0.0);  // G~ a_ref (CURN mean with the deterministic signal)
   const double nu_ref = d.nu_ref_mhz;
   const int P = m.P, kmax = std::max(m.na, m.nd);
   double logc = 0.0;
@@ -445,6 +446,15 @@ int pta_finalize(pta_ctx* c, void* stream) {
       }
     }
     std::copy(ar.begin(), ar.end(), aref.begin() + (size_t)I * P);
+    for (int q = 0; q < P; ++q) {  // G~ a_ref from the reversed packed copy of G~
+      double acc = 0.0;
+      for (int r = 0; r < P; ++r) {
+        const size_t i1 = (size_t)(P - 1 - q), i2 = (size_t)(P - 1 - r);
+        const size_t hi = std::max(i1, i2), lo = std::min(i1, i2);
+        acc += Grev[(size_t)I * ntriP + hi * (hi + 1) / 2 + lo] * ar[r];
+      }
+      gav[(size_t)I * P + q] = acc;
+    }
     // c_ref = K^-1 (b0 - H^T a_ref); dt'' = dt - F a_ref - M c_ref (projected reference residual)
     std::vector<double> cref(mI);
     for (int j = 0; j < mI; ++j) {
@@ -548,6 +558,7 @@ int pta_finalize(pta_ctx* c, void* stream) {
   UP(LGi, LGammaInv);
   UP(Grev, Grev);
   UP(gtv, gt);
+  UP(gav, ga);
   {
     std::vector<double> lnk(kmax + 1, 0.0);
     for (int k = 1; k <= kmax; ++k) lnk[k] = std::log((double)k);
@@ -574,7 +585,8 @@ void free_scratch(pta::Scratch& s) {
                   s.dlnk, s.dlnkd, s.dlnr, s.stat, s.sk, s.skd, s.srho, s.cwc, s.cwjac, s.cwsig,
                   s.cwbs, s.cwwt, s.cwgp, s.cwg, s.x0, s.g0, s.p, s.lp0, s.xs, s.gs, s.lps,
                   s.step, s.imass, s.kin0, s.hmc_ctr, s.acc, s.a16, s.queue, s.us, s.curnW, s.curnAhat,
-                  s.curnV, s.curnLd, s.curnQ, s.dlnrc};
+                  s.curnV, s.curnLd, s.curnQ, s.dlnrc, s.curnG0, s.curnV2, s.cwwt2,
+                  s.chi2b, s.zeros};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   s = pta::Scratch{};
@@ -647,6 +659,14 @@ int ensure_scratch(pta_ctx* c, int B, bool fp64) {
     AL(curnLd, np * cap);
     AL(curnQ, (size_t)cap * (m.na + 1));
     AL(dlnrc, (size_t)cap * np * m.na);
+    if (m.cw) {
+      AL(curnG0, np * cap * P);
+      AL(curnV2, np * cap * P);
+      AL(cwwt2, (size_t)cap * m.ntoa_pad);
+      AL(chi2b, np * cap);
+      AL(zeros, m.ntoa_pad);
+      if (e == cudaSuccess) e = cudaMemset(s.zeros, 0, sizeof(float) * m.ntoa_pad);
+    }
   }
 #undef AL
   if (e != cudaSuccess) {
@@ -717,10 +737,21 @@ int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* gr
   const bool gram = c->precision == PTA_PREC_GRAM;
   tm.begin(0);
   if (e == cudaSuccess) e = pta::launch_prior_forward(m, s, B, x, fp64, st);
-  if (e == cudaSuccess && m.curn) e = pta::launch_curn_forward(m, s, B, x, st);
   if (e == cudaSuccess && m.cw) e = pta::launch_cw_forward(m, s, B, x, st);
+  if (e == cudaSuccess && m.curn && m.cw) {
+    // Eq. decenter_det_PTA: the mean needs beta F^T N~^-1 (dt'' - s) per chain, the TOA
+    // pass at a = a_ref (its chi2 is discarded)
+    pta::Scratch s0 = s;
+    s0.ghat = s.curnG0;
+    s0.chi2 = s.chi2b;
+    e = pta::launch_curn_set_a(m, s, B, nullptr, st);
+    if (e == cudaSuccess) e = pta::launch_tm_prologue(m, s0, B, 0, st);
+    if (e == cudaSuccess) e = pta::launch_toa_fp32_cfg(m, s0, B, c->toa_cfg, st);
+    if (e == cudaSuccess) e = pta::launch_reduce(m, s0, B, 0, st);
+  }
+  if (e == cudaSuccess && m.curn) e = pta::launch_curn_forward(m, s, B, x, st);
   if (e == cudaSuccess && !gram) e = pta::launch_tm_prologue(m, s, B, fp64, st);
-  tm.end(pta::count_prior_forward(m) + (gram ? 0 : 1) + (m.cw ? 2 : 0));
+  tm.end(pta::count_prior_forward(m) + (gram ? 0 : 1) + (m.cw ? 2 : 0) + (m.curn && m.cw ? 4 : 0));
   tm.begin(1);
   if (e == cudaSuccess && gram) {
     e = pta::launch_gram(m, s, B, st);  // writes ghat and chi2 directly
@@ -742,8 +773,24 @@ int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* gr
     tm.begin(3);
     if (e == cudaSuccess)
       e = m.curn ? pta::launch_curn_adjoint(m, s, B, x, grad, st) : pta::launch_prior_adjoint(m, s, B, x, grad, st);
+    if (e == cudaSuccess && m.curn && m.cw) {
+      // CW gradient through the mean: weights w~ - N~^-1 F A^-1 gbar at every TOA, the
+      // second from a TOA pass with a = a_ref - A^-1 gbar, zero residual and no signal
+      pta::Scratch s2 = s;
+      s2.ghat = s.curnG0;
+      s2.chi2 = s.chi2b;
+      s2.cwsig = nullptr;
+      s2.cwbs = nullptr;
+      s2.cwwt = s.cwwt2;
+      pta::DevModel m2 = m;
+      m2.dt = s.zeros;
+      e = pta::launch_curn_set_a(m, s, B, s.curnV2, st);
+      if (e == cudaSuccess) e = pta::launch_tm_prologue(m2, s2, B, 0, st);
+      if (e == cudaSuccess) e = pta::launch_toa_fp32_cfg(m2, s2, B, c->toa_cfg, st);
+      if (e == cudaSuccess) e = pta::launch_sub(s.cwwt, s.cwwt2, (size_t)B * m.ntoa_pad, st);
+    }
     if (e == cudaSuccess && m.cw) e = pta::launch_cw_gradient(m, s, B, st);
-    tm.end(pta::count_prior_adjoint(m) + (m.cw ? 2 : 0));
+    tm.end(pta::count_prior_adjoint(m) + (m.cw ? 2 : 0) + (m.curn && m.cw ? 4 : 0));
   }
   tm.begin(4);
   if (e == cudaSuccess) e = pta::launch_final(m, s, B, x, logp, grad, status, st);
@@ -916,10 +963,6 @@ int pta_set_transform(pta_ctx* c, int transform) {
   if (!c->finalized) return fail(c, PTA_ESTATE, "context not finalized");
   if (transform != PTA_TRANSFORM_PRIOR && transform != PTA_TRANSFORM_CURN)
     return fail(c, PTA_EINVAL, "set_transform: unknown transform");
-  if (transform == PTA_TRANSFORM_CURN && c->dm.cw)
-    return fail(c, PTA_EINVAL,
-                "the CURN transform with a deterministic signal (Eq. decenter_det_PTA) is not built: use "
-                "PTA_TRANSFORM_PRIOR with the continuous-wave model");
   if (transform != c->transform) drop_graphs(c);
   c->transform = transform;
   c->dm.curn = transform == PTA_TRANSFORM_CURN ? 1 : 0;

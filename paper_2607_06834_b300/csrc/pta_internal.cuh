@@ -97,6 +97,7 @@ struct DevModel {
   const double* Grev;           // per pulsar G~ = F^T N~^-1 F, packed lower in reversed order
                                 // (element (i', l') = G~[P-1-i'][P-1-l']), P (P + 1) / 2 each
   const double* gt;             // [npsr][P] F^T N~^-1 dt (FP64)
+  const double* ga;             // [npsr][P] G~ a_ref (mean with the deterministic signal)
 };
 
 // Scratch sized for a batch of up to `cap` chains.
@@ -149,6 +150,12 @@ struct Scratch {
   double* curnLd = nullptr;    // [npsr][cap] log det L_CURN
   double* curnQ = nullptr;     // [cap][na + 1] HD-prior terms per achromatic bin and the DM block
   double* dlnrc = nullptr;     // [cap][npsr][na] rho d logp / d rho through the transform, per pulsar
+  // CURN transform with the deterministic signal (Eq. decenter_det_PTA)
+  double* curnG0 = nullptr;    // [npsr][cap][P] beta F^T N~^-1 (dt'' - s) from the pass at a = a_ref
+  double* curnV2 = nullptr;    // [npsr][cap][P] A^-1 gbar (CW gradient through the mean)
+  float* cwwt2 = nullptr;      // [cap][ntoa_pad] N~^-1 F A^-1 gbar at every TOA
+  double* chi2b = nullptr;     // [npsr][cap] chi2 of the auxiliary passes (unused)
+  float* zeros = nullptr;      // [ntoa_pad] zero residual for the auxiliary pass
 };
 
 // Kernel launchers (defined in the .cu files).
@@ -182,6 +189,9 @@ size_t curn_w_doubles(const DevModel& m);  // P (P + 1) / 2
 cudaError_t launch_curn_forward(const DevModel& m, const Scratch& s, int B, const float* x, cudaStream_t st);
 cudaError_t launch_curn_adjoint(const DevModel& m, const Scratch& s, int B, const float* x, float* grad,
                                 cudaStream_t st);
+// a64 = a_ref - v (v == nullptr: a_ref) for every chain; out -= w elementwise
+cudaError_t launch_curn_set_a(const DevModel& m, const Scratch& s, int B, const double* v, cudaStream_t st);
+cudaError_t launch_sub(float* out, const float* w, size_t n, cudaStream_t st);
 int count_prior_adjoint(const DevModel& m);
 cudaError_t launch_final(const DevModel& m, const Scratch& s, int B, const float* x,
                          double* logp, float* grad, int32_t* status, cudaStream_t st);

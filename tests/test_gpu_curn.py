@@ -127,7 +127,6 @@ def test_curn_ng15_global_factor():
 
 def test_curn_hmc_trajectory_and_rejections():
     from paper_2607_06834_b300 import sampler
-    from paper_2607_06834_b300.engine import Engine, PTAError
     arr = synth.small_array(**CASES[1])
     eng = _engine(arr, "fp32")
     X = torch.tensor(synth.make_points(arr, 8, seed=65), device="cuda")
@@ -135,10 +134,6 @@ def test_curn_hmc_trajectory_and_rejections():
     lp_end, _, st = eng.logp_and_grad(res.state.x.contiguous())
     assert np.all(st.cpu().numpy() == 0) and np.all(np.isfinite(lp_end.cpu().numpy()))
     assert 0.2 < res.accept_rate <= 1.0
-    # continuous-wave model: the deterministic generalisation is not built
-    cw = Engine(synth.small_array(npsr=2, ntoa=100, m=3, n_gwb=2, n_rn=2, cw=True, seed=5), precision="fp32")
-    with pytest.raises(PTAError):
-        cw.set_transform("curn")
     # the allocation-free entry point keeps no per-chain factors
     B = 4
     x = torch.tensor(synth.make_points(arr, B, seed=66), device="cuda")
@@ -153,3 +148,50 @@ def test_curn_hmc_trajectory_and_rejections():
     a, _, _ = _eval(eng, x.cpu().numpy())
     b, _, _ = _eval(ref, x.cpu().numpy())
     np.testing.assert_array_equal(a, b)
+
+
+CW_CASE = dict(npsr=3, ntoa=[150, 700, 2300], m=[3, 9, 12], n_gwb=4, n_rn=5, n_dm=3, seed=41, nbackend=2, cw=True)
+
+
+def _cw_points(orc, arr, B, seed):
+    X = synth.make_points(arr, B, seed=seed)
+    c = orc.lay["th_cw"]
+    X[0, c: c + 8] = [9.5, -7.8, -13.5, 0.3, 1.0, 0.2, 2.0, 1.0]  # a loud binary in one chain
+    return X
+
+
+@pytest.mark.parametrize("tempered", [False, True])
+def test_curn_deterministic_signal_matches_oracle(tempered):
+    """Eq. decenter_det_PTA on the FP32 path: the mean abar = Sigma F^T N~^-1 (dt - h) from an
+    extra TOA pass, and the CW gradient through it from another; every block of the gradient
+    (z, noise, GWB, CW) against the oracle, with and without per-chain temperatures."""
+    arr = synth.small_array(**CW_CASE)
+    orc = O.Oracle(arr, transform="curn")
+    B = 8
+    X = _cw_points(orc, arr, B, 67)
+    beta = np.array([1.0, 0.5, 0.1, 0.0, 0.3, 0.9, 0.05, 0.7]) if tempered else np.ones(B)
+    eng = _engine(arr, "fp32")
+    if tempered:
+        eng.set_beta(torch.tensor(beta, device="cuda"))
+    lp, g, st = _eval(eng, X)
+    assert np.all(st == 0)
+    Xd = X.astype(np.float64)
+    lo = np.array([orc.logp(x, beta=b) for x, b in zip(Xd, beta)])
+    go = np.array([orc.grad(x, beta=b) for x, b in zip(Xd, beta)])
+    _check("fp32", lp, g, lo, go, "curn cw" + (" tempered" if tempered else ""))
+    c = orc.lay["th_cw"]
+    relcw = _grad_rel(g[:, c:], go[:, c:])
+    print(f"cw block grad rel {relcw.max():.2e}")
+    assert relcw.max() < GRAD_REL
+
+
+def test_curn_deterministic_signal_hmc():
+    from paper_2607_06834_b300 import sampler
+    arr = synth.small_array(**CW_CASE)
+    orc = O.Oracle(arr, transform="curn")
+    eng = _engine(arr, "fp32")
+    X = torch.tensor(_cw_points(orc, arr, 8, 68), device="cuda")
+    res = sampler.run_hmc(eng, X, n_warmup=30, n_samples=10, n_leapfrog=6, seed=4, unit_mass=eng.layout["d_z"])
+    lp_end, _, st = eng.logp_and_grad(res.state.x.contiguous())
+    assert np.all(st.cpu().numpy() == 0) and np.all(np.isfinite(lp_end.cpu().numpy()))
+    assert 0.2 < res.accept_rate <= 1.0
