@@ -50,6 +50,10 @@ WORKLOADS = {
     "ng15_nodm": dict(npsr=67, ntoa_total=300_000, ntoa_range=(2000, 20000), span_yr=(3.0, 16.0),
                       m_range=(8, 80), n_gwb=14, n_rn=30, n_dm=0, cw=False, chains=64,
                       mode="epochs", nbackend=(1, 4)),
+    # the same model with a circular binary (the paper's joint GWB + RN + CW analysis shape)
+    "ng15_nodm_cw": dict(npsr=67, ntoa_total=300_000, ntoa_range=(2000, 20000), span_yr=(3.0, 16.0),
+                         m_range=(8, 80), n_gwb=14, n_rn=30, n_dm=0, cw=True, chains=64,
+                         mode="epochs", nbackend=(1, 4)),
     "scale150": dict(npsr=150, ntoa_total=1_000_000, ntoa_range=(1000, 30000), span_yr=(5.0, 30.0),
                      m_range=(8, 80), n_gwb=100, n_rn=30, n_dm=150, cw=False, chains=1024,
                      mode="epochs", nbackend=(1, 4)),
@@ -173,7 +177,7 @@ def make_array(name: str, seed: int | None = None) -> Array:
     if seed is None:
         # the 67-pulsar workloads share one array (same seed; the draws do not depend on n_dm)
         seed = {"tiny3": 2607, "ng15": 2608, "ng15_b256": 2608, "ng15_cw": 2608, "ng15_nodm": 2608,
-                "scale150": 2611}[name]
+                "ng15_nodm_cw": 2608, "scale150": 2611}[name]
     rng = np.random.default_rng(seed)
     npsr = w["npsr"]
     counts = _toa_counts(rng, npsr, w["ntoa_total"], *w["ntoa_range"])
