@@ -171,6 +171,23 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
                "l"(src)
                : "memory");
 }
+// Packed FP32 pairs: one fma.rn.f32x2 does two independent FP32 multiply-adds (same
+// rounding as two fmaf), halving the issue slots of the register-blocked products.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2dup(float v) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ void f2unpack(f32x2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 f2fma(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
@@ -248,11 +265,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     prefetch(0);
   }
   const int cg = tid % C::CG, rg = tid / C::CG;
-  float acc[QPT][4];
+  f32x2 acc[QPT][2];  // ghat pairs (chains 4cg, 4cg+1) and (4cg+2, 4cg+3)
 #pragma unroll
   for (int i = 0; i < QPT; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < 2; ++j) acc[i][j] = 0ull;
   double c2acc = 0.0;
 
   for (int t0 = 0; t0 < len; t0 += TT) {
@@ -303,15 +320,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncthreads();
     // --- y[t][c] = sum_p [F | M | F~_lo][t][p] coef[p][c]
-    float y[C::RPT][4];
+    f32x2 y2[C::RPT][2];
 #pragma unroll
-    for (int r = 0; r < C::RPT; ++r)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) y[r][j] = 0.f;
+    for (int r = 0; r < C::RPT; ++r) y2[r][0] = y2[r][1] = 0ull;
     const float* xrow = Xs + rg * C::RPT;
     const float* arow = As + 4 * cg;
     auto g1 = [&](int p) {
-      const float4 av = *reinterpret_cast<const float4*>(arow + p * C::AS);
+      const ulonglong2 av = *reinterpret_cast<const ulonglong2*>(arow + p * C::AS);
       float fv[C::RPT];
       if constexpr (C::RPT % 4 == 0) {
 #pragma unroll
@@ -328,10 +343,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
 #pragma unroll
       for (int r = 0; r < C::RPT; ++r) {
-        y[r][0] = fmaf(fv[r], av.x, y[r][0]);
-        y[r][1] = fmaf(fv[r], av.y, y[r][1]);
-        y[r][2] = fmaf(fv[r], av.z, y[r][2]);
-        y[r][3] = fmaf(fv[r], av.w, y[r][3]);
+        const f32x2 f = f2dup(fv[r]);
+        y2[r][0] = f2fma(f, av.x, y2[r][0]);
+        y2[r][1] = f2fma(f, av.y, y2[r][1]);
       }
     };
     if constexpr (PF) {
@@ -342,6 +356,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
 #pragma unroll(ORD == 0 ? 2 : 4)
       for (int p = 0; p < KA; ++p) g1(p);
+    }
+    float y[C::RPT][4];
+#pragma unroll
+    for (int r = 0; r < C::RPT; ++r) {
+      f2unpack(y2[r][0], y[r][0], y[r][1]);
+      f2unpack(y2[r][1], y[r][2], y[r][3]);
     }
     // --- projected residual, whitened residual, chi2 pieces
     float q4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -378,17 +398,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     // so each basis row is one 16-byte load
 #pragma unroll 1
     for (int t = 0; t < TT; t += 4) {
-      float4 wv[4];
+      ulonglong2 wv[4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) wv[r] = *reinterpret_cast<const float4*>(Ws + (t + r) * C::WS + 4 * cg);
+      for (int r = 0; r < 4; ++r) wv[r] = *reinterpret_cast<const ulonglong2*>(Ws + (t + r) * C::WS + 4 * cg);
       if constexpr (ORD == 0) {
 #pragma unroll
         for (int i = 0; i < QPT; ++i) {
           const float4 xv = *reinterpret_cast<const float4*>(Xs + (rg + C::RG * i) * C::XS + t);
-          acc[i][0] = fmaf(xv.x, wv[0].x, fmaf(xv.y, wv[1].x, fmaf(xv.z, wv[2].x, fmaf(xv.w, wv[3].x, acc[i][0]))));
-          acc[i][1] = fmaf(xv.x, wv[0].y, fmaf(xv.y, wv[1].y, fmaf(xv.z, wv[2].y, fmaf(xv.w, wv[3].y, acc[i][1]))));
-          acc[i][2] = fmaf(xv.x, wv[0].z, fmaf(xv.y, wv[1].z, fmaf(xv.z, wv[2].z, fmaf(xv.w, wv[3].z, acc[i][2]))));
-          acc[i][3] = fmaf(xv.x, wv[0].w, fmaf(xv.y, wv[1].w, fmaf(xv.z, wv[2].w, fmaf(xv.w, wv[3].w, acc[i][3]))));
+          const f32x2 dx = f2dup(xv.x), dy = f2dup(xv.y), dz = f2dup(xv.z), dw = f2dup(xv.w);
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const f32x2 w0 = j ? wv[0].y : wv[0].x, w1 = j ? wv[1].y : wv[1].x;
+            const f32x2 w2 = j ? wv[2].y : wv[2].x, w3 = j ? wv[3].y : wv[3].x;
+            acc[i][j] = f2fma(dx, w0, f2fma(dy, w1, f2fma(dz, w2, f2fma(dw, w3, acc[i][j]))));
+          }
         }
       } else {
         float4 xv[QPT];
@@ -399,10 +422,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int i = 0; i < QPT; ++i) {
             const float xr = r == 0 ? xv[i].x : (r == 1 ? xv[i].y : (r == 2 ? xv[i].z : xv[i].w));
-            acc[i][0] = fmaf(xr, wv[r].x, acc[i][0]);
-            acc[i][1] = fmaf(xr, wv[r].y, acc[i][1]);
-            acc[i][2] = fmaf(xr, wv[r].z, acc[i][2]);
-            acc[i][3] = fmaf(xr, wv[r].w, acc[i][3]);
+            const f32x2 d = f2dup(xr);
+            acc[i][0] = f2fma(d, wv[r].x, acc[i][0]);
+            acc[i][1] = f2fma(d, wv[r].y, acc[i][1]);
           }
         }
       }
@@ -412,10 +434,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int i = 0; i < QPT; ++i) {
     const int q = rg + C::RG * i;
     if (q < P) {
+      float g4[4];
+      f2unpack(acc[i][0], g4[0], g4[1]);
+      f2unpack(acc[i][1], g4[2], g4[3]);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int b = b0 + 4 * cg + j;
-        if (b < B) gpart[((size_t)u * B + b) * m.Qs + q] = acc[i][j];
+        if (b < B) gpart[((size_t)u * B + b) * m.Qs + q] = g4[j];
       }
     }
   }
