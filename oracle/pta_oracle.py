@@ -40,7 +40,10 @@ C = N + F phi F^T; the log-det cancellation of the prior-whitened transform;
 the Gram-form (Eq. stochastic_posterior) equivalence; central finite
 differences of every gradient block; CW invariants (h -> 0, L -> 0 with equal
 phases, psi -> psi + pi/2, dPhi/dt = omega(t), antenna-pattern identity);
-Philox4x32-10 known-answer vectors; HMC reversibility and Gaussian moments.
+Philox4x32-10 known-answer vectors; HMC reversibility and Gaussian moments;
+hand-worked golden values (tests/golden/) for the white-noise variance, the DM
+weight and the circular-binary delay at special geometries, and the quadrupole-
+formula chirp rate for Eq. (CW_evolve).
 """
 from __future__ import annotations
 

@@ -90,14 +90,39 @@ def test_power_law_invariants():
 
 
 # --------------------------------------------------------------- Eq. (WN_cov)
-def test_white_noise_definition():
-    arr = synth.small_array(npsr=1, ntoa=50, nbackend=3, seed=3)
-    p = arr.pulsars[0]
-    N = O.white_noise_var(p)
-    for i in range(p.n):
-        b = p.backend[i]
-        assert N[i] == pytest.approx((p.efac[b] * p.sigma_s[i] * 1e9) ** 2 + (p.equad_s[b] * 1e9) ** 2,
-                                     rel=1e-14)
+def _golden_rows(name):
+    return [[float(v) for v in l.split()] for l in open(os.path.join(GOLDEN, name))
+            if l.strip() and not l.startswith("#")]
+
+
+def test_white_noise_golden_values():
+    """N_ii against values worked by hand from Eq. (WN_cov) (tests/golden/white_noise.txt);
+    each TOA has its own backend so EFAC/EQUAD are picked per row."""
+    from types import SimpleNamespace
+    rows = _golden_rows("white_noise.txt")
+    psr = SimpleNamespace(sigma_s=np.array([r[0] * 1e-6 for r in rows]),
+                          backend=np.arange(len(rows), dtype=np.int32),
+                          efac=np.array([r[1] for r in rows]),
+                          equad_s=np.array([r[2] * 1e-6 for r in rows]))
+    np.testing.assert_allclose(O.white_noise_var(psr), [r[3] for r in rows], rtol=1e-12)
+    # backend selection: the same sigma under two backends takes each backend's EFAC/EQUAD
+    psr2 = SimpleNamespace(sigma_s=np.array([1e-6, 1e-6]), backend=np.array([1, 0], dtype=np.int32),
+                           efac=np.array([1.2, 0.8]), equad_s=np.array([0.5e-6, 0.1e-6]))
+    np.testing.assert_allclose(O.white_noise_var(psr2), [0.64e6 + 1e4, 1.69e6], rtol=1e-12)
+
+
+def test_chromatic_weight_golden_values():
+    """DM basis weight (nu_ref/nu)^2, nu_ref = 1400 MHz, against hand values
+    (tests/golden/chromatic_weight.txt): 4 at 700 MHz, 1/4 at 2800 MHz."""
+    rows = _golden_rows("chromatic_weight.txt")
+    nu = np.array([r[0] for r in rows])
+    np.testing.assert_allclose(O.chromatic_weight(nu), [r[1] for r in rows], rtol=1e-14)
+    # and the oracle's DM columns are the achromatic ones times that weight, row by row
+    arr = synth.small_array(npsr=1, ntoa=40, n_gwb=2, n_rn=3, n_dm=2, seed=8)
+    orc = O.Oracle(arr)
+    F = orc.get_F(0)
+    w = (1400.0 / arr.pulsars[0].freqs_mhz) ** 2
+    np.testing.assert_allclose(F[:, 2 * orc.na:], F[:, :4] * w[:, None], rtol=1e-13)
 
 
 # --------------------------------------------------------------- Eq. (Fourier_series)
@@ -271,7 +296,7 @@ def test_cw_phase_derivative_is_frequency():
     for t in (0.0, 3e8, 9e8):
         h = 1e3
         d = (O.cw_phase(t + h, mc, w0)[0] - O.cw_phase(t - h, mc, w0)[0]) / (2 * h)
-        assert d == pytest.approx(O.cw_phase(t, mc, w0)[1], rel=1e-6)
+        assert d == pytest.approx(O.cw_phase(t, mc, w0)[1], rel=1e-6, abs=0)
 
 
 def test_cw_taylor_form_small_x():
@@ -289,6 +314,34 @@ def test_cw_antenna_pattern_identity():
         p /= np.linalg.norm(p)
         fp, fx, op = O.cw_geometry(rng.uniform(-1, 1), rng.uniform(0, 2 * math.pi), p)
         assert fp * fp + fx * fx == pytest.approx(0.25 * (1 - op) ** 2, rel=1e-12)
+
+
+def test_cw_special_geometry_golden_values():
+    """Earth-term delay at t = 0 for geometries where the antenna pattern and the
+    polarisation factors reduce to closed form (tests/golden/cw_special_geometry.txt,
+    derived by hand from the circular-binary model of Sec. "Deterministic signals and
+    continuous waves"): pins the amplitude h/(2 w0^(2/3) w^(1/3)), the inclination
+    factors (1 + cos^2 i) and 2 cos i, the polarisation rotation and both patterns."""
+    for line in open(os.path.join(GOLDEN, "cw_special_geometry.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        case, *v = line.split()
+        px, py, pz, cosi, psi, phi0, phiI, s_ns = map(float, v)
+        th = np.array([9.0, -8.0, -14.0, cosi, psi, 1.0, 0.0, phi0])
+        s = O.cw_signal(np.array([0.0]), np.array([px, py, pz]), th, 1.3, phiI)
+        assert abs(s[0] - s_ns) <= 1e-9 * abs(s_ns), (case, s[0], s_ns)
+
+
+def test_cw_chirp_rate_is_quadrupole_formula():
+    """Eq. (CW_evolve) at t = 0 must reproduce the quadrupole-formula chirp of a circular
+    binary, d omega/dt = (96/5) Mc^(5/3) omega^(11/3) (Peters & Mathews 1963, with
+    omega = pi f_gw and Mc in seconds), for several masses and frequencies."""
+    for lmc, lf in ((8.5, -8.3), (9.4, -7.9), (10.0, -7.6)):
+        mc = 10 ** lmc * O.TSUN_S
+        w0 = math.pi * 10 ** lf
+        h = 1e4
+        dw = (O.cw_phase(h, mc, w0)[1] - O.cw_phase(-h, mc, w0)[1]) / (2 * h)
+        assert dw == pytest.approx(96.0 / 5.0 * mc ** (5.0 / 3.0) * w0 ** (11.0 / 3.0), rel=1e-6, abs=0)
 
 
 # --------------------------------------------------------------- Philox + HMC
