@@ -53,6 +53,11 @@ extern "C" {
  * in compensated FP32 (error-free products and sums) with FP64 dot products.  No
  * continuous-wave signal (PTA_EINVAL). */
 #define PTA_PREC_GRAM 5
+/* tcgen05 tensor cores at FP32 accuracy: both operands of F a and F^T w~ scaled to a
+ * power-of-two grid and cut into fp16 pieces whose leading products sum exactly in
+ * the FP32 accumulator (six MMAs per K step), w~ staged in device memory between the
+ * two contractions.  PTA_EINVAL when P + max m_I + n_low > 480. */
+#define PTA_PREC_F16X6 6
 
 typedef struct pta_ctx pta_ctx;
 
@@ -237,7 +242,8 @@ int pta_hmc_trajectory(pta_ctx* ctx, int B, float* x_dev, double* logp_dev, floa
  * risk an allocation failure in the middle of a run.  The context still holds the
  * data uploaded by pta_finalize.
  *   - B chains must fit in the array: otherwise PTA_EINVAL with the needed size in
- *     pta_last_error (about 1.2 MB per chain for 67 pulsars, 3e5 TOAs).
+ *     pta_last_error (for 67 pulsars and 3e5 TOAs: 1.24 MB per chain, 27 chains; the
+ *     FP64 path also keeps FP64 partial sums, 1.62 MB per chain, 20 chains).
  *   - The first call on a device looks up the array's device address (with that
  *     device current) and caches it; make that first call before any stream capture.
  *   - All calls share the array and it keeps the last call's contents: calls that
@@ -245,7 +251,8 @@ int pta_hmc_trajectory(pta_ctx* ctx, int B, float* x_dev, double* logp_dev, floa
  *     and the work counter of persistent launches) is cleared on `stream` per call.
  *   - PTA_PREC_FP64 needs the stored FP64 basis, which pta_logp_and_grad builds on
  *     its first FP64 call; without it the call returns PTA_ESTATE.
- *   - PTA_PREC_BF16X3 (its packed coefficients need their own buffer) and the
+ *   - PTA_PREC_BF16X3 and PTA_PREC_F16X6 (their packed coefficients and, for the
+ *     latter, the staged w~ need their own buffers) and the
  *     continuous-wave model return PTA_EINVAL. */
 int pta_logp_and_grad_noalloc(pta_ctx* ctx, int B, const float* x_dev, double* logp_dev,
                               float* grad_dev, int32_t* status_dev, void* stream);

@@ -48,7 +48,7 @@ __device__ __forceinline__ int low_col(const DevModel& m, int q) {
 
 __global__ void __launch_bounds__(128)
     k_tm_prologue(DevModel m, double* __restrict__ a64, float* __restrict__ a32, const double* __restrict__ cwbs,
-                  int B, int fp64) {
+                  int B, int fp64) {  // fp64: 0 FP32 packed rows, 1 FP64 path, 2 FP64 packed rows
   extern __shared__ double smp[];
   const int I = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int P = m.P, mI = m.m[I];
@@ -114,20 +114,26 @@ __global__ void __launch_bounds__(128)
     }
   }
   __syncthreads();
-  if (fp64) {
+  if (fp64 == 1) {
     for (int p = tid; p < P; p += 128) row[p] = da[p];
     for (int j = tid; j < mI; j += 128) row[P + j] = cv[j];
   } else {
+    // packed row [da (low columns zero) | c | da of the low columns | 0]: FP32 for the
+    // FP32-operand kernels, FP64 in place for the exact-split tensor-core path (its
+    // fp16 pieces are cut from the FP64 values)
     float* r32 = a32 + ((size_t)I * B + b) * m.PM;
     for (int q = tid; q < m.PM; q += 128) {
-      float v = 0.f;
+      double v = 0.0;
       if (q < P)
-        v = is_low_col(m, q) ? 0.f : (float)da[q];
+        v = is_low_col(m, q) ? 0.0 : da[q];
       else if (q < P + mI)
-        v = (float)cv[q - P];
+        v = cv[q - P];
       else if (q < P + mI + m.NL)
-        v = (float)da[low_col(m, q - P - mI)];
-      r32[q] = v;
+        v = da[low_col(m, q - P - mI)];
+      if (fp64 == 2)
+        row[q] = v;
+      else
+        r32[q] = (float)v;
     }
   }
 }
@@ -386,10 +392,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     *reinterpret_cast<float4*>(C2 + rg * BC + 4 * cg) = make_float4(q4[0], q4[1], q4[2], q4[3]);
     __syncthreads();
-    if (tid < BC) {  // fixed-order chi2 reduction over row groups: thread c owns chain c
-      float s = 0.f;
-      for (int g = 0; g < C::RG; ++g) s += C2[g * BC + tid];
-      c2acc += (double)s;
+    if (tid < BC) {  // fixed-order chi2 reduction over row groups: thread c owns chain c; FP64, so
+                     // the rounding of a 64-term FP32 running sum does not accumulate over tiles
+      double s = 0.0;
+      for (int g = 0; g < C::RG; ++g) s += (double)C2[g * BC + tid];
+      c2acc += s;
     }
     // F a of this tile is done with the timing-model rows: fetch the next tile's
     if constexpr (PF)

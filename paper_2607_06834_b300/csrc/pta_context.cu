@@ -101,7 +101,7 @@ int pta_create(pta_ctx** out, const pta_model_desc* d) {
   if (d->n_gwb < 0 || d->n_rn < 0 || d->n_dm < 0 || (d->n_gwb == 0 && d->n_rn == 0) ||
       d->n_gwb > 512 || d->n_rn > 512 || d->n_dm > 512)
     return PTA_EINVAL;
-  if (d->precision < PTA_PREC_FP64 || d->precision > PTA_PREC_GRAM) return PTA_EINVAL;
+  if (d->precision < PTA_PREC_FP64 || d->precision > PTA_PREC_F16X6) return PTA_EINVAL;
   if (d->precision == PTA_PREC_GRAM && d->cw) return PTA_EINVAL;
   if (d->spectrum < 0 || d->spectrum > (PTA_FREE_GWB | PTA_FREE_RN)) return PTA_EINVAL;
   pta_ctx* c = new (std::nothrow) pta_ctx();
@@ -507,6 +507,20 @@ int pta_finalize(pta_ctx* c, void* stream) {
     }
   }
 
+  // per pulsar: largest |M| and |F~_lo| per column and the largest chromatic weight over
+  // its TOAs (scales of the exact-split tensor-core path)
+  std::vector<float> colmaxf((size_t)npsr * (m_max + m.NL), 0.f), wmaxp(npsr, 0.f);
+  for (int I = 0; I < npsr; ++I) {
+    const int n = c->psrs[I].n, mI = mm[I];
+    float* cm = &colmaxf[(size_t)I * (m_max + m.NL)];
+    for (int i = 0; i < n; ++i) {
+      for (int j = 0; j < mI; ++j) cm[j] = std::fmax(cm[j], std::fabs(M32[m_off[I] + (long long)i * mI + j]));
+      for (int j = 0; j < m.NL; ++j)
+        cm[m_max + j] = std::fmax(cm[m_max + j], std::fabs(Flo[flo_off[I] + (long long)i * m.NL + j]));
+      wmaxp[I] = std::fmax(wmaxp[I], chrom[toa_off[I] + i]);
+    }
+  }
+
   int rc;
 #define UP(vec, field)                                  \
   if ((rc = upload(c, vec, &m.field)) != PTA_OK) return rc;
@@ -569,6 +583,8 @@ int pta_finalize(pta_ctx* c, void* stream) {
     UP(tm, trimap);
   }
   UP(nuw64, chrom64);
+  UP(colmaxf, colmaxf);
+  UP(wmaxp, wmaxp);
 #undef UP
   c->finalized = true;
   (void)stream;
@@ -586,7 +602,7 @@ void free_scratch(pta::Scratch& s) {
                   s.cwbs, s.cwwt, s.cwgp, s.cwg, s.x0, s.g0, s.p, s.lp0, s.xs, s.gs, s.lps,
                   s.step, s.imass, s.kin0, s.hmc_ctr, s.acc, s.a16, s.queue, s.us, s.curnW, s.curnAhat,
                   s.curnV, s.curnLd, s.curnQ, s.dlnrc, s.curnG0, s.curnV2, s.cwwt2,
-                  s.chi2b, s.zeros};
+                  s.chi2b, s.zeros, s.c16, s.spf, s.yexp, s.wres, s.wmx};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   s = pta::Scratch{};
@@ -602,7 +618,8 @@ int ensure_scratch(pta_ctx* c, int B, bool fp64) {
   pta::Scratch& s = c->sc;
   const pta::DevModel& m = c->dm;
   const bool curn = m.curn != 0;
-  if (B <= s.cap && (!fp64 || s.gpart64) && (!curn || s.curnW)) return PTA_OK;
+  const bool f16 = c->precision == PTA_PREC_F16X6;
+  if (B <= s.cap && (!fp64 || s.gpart64) && (!curn || s.curnW) && (!f16 || s.c16)) return PTA_OK;
   const int cap = std::max(B, s.cap);
   cudaDeviceSynchronize();
   free_scratch(s);
@@ -652,6 +669,13 @@ int ensure_scratch(pta_ctx* c, int B, bool fp64) {
   AL(hmc_ctr, 2);
   AL(acc, cap);
   AL(queue, 1);
+  if (f16) {
+    AL(c16, pta::f16_pack_bytes(m, cap));
+    AL(spf, pta::f16_scale_floats(m, cap));
+    AL(yexp, np * cap);
+    if (!m.cw) AL(wres, (size_t)cap * m.ntoa_pad);
+    AL(wmx, (size_t)m.n_units * cap);
+  }
   if (curn) {
     AL(curnW, (size_t)np * cap * pta::curn_w_doubles(m));
     AL(curnAhat, np * cap * P);
@@ -726,11 +750,12 @@ struct StageTimer {
 };
 }  // namespace
 
-// One full evaluation on `st` (used by pta_logp_and_grad and the HMC driver).
-int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* grad, int32_t* status,
-                      cudaStream_t st, bool profile) {
+// One full evaluation on `st` with the per-call workspace `s` (the context's own
+// scratch for pta_logp_and_grad and the HMC driver, the fixed array for the
+// allocation-free entry point).
+int pta_eval_scratch(pta_ctx* c, const pta::Scratch& s, int B, const float* x, double* logp, float* grad,
+                     int32_t* status, cudaStream_t st, bool profile) {
   const pta::DevModel& m = c->dm;
-  const pta::Scratch& s = c->sc;
   const bool fp64 = c->precision == PTA_PREC_FP64;
   StageTimer tm{c, st, profile && c->prof};
   cudaError_t e = cudaMemsetAsync(s.stat, 0, sizeof(int32_t) * B, st);
@@ -762,6 +787,8 @@ int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* gr
       e = pta::launch_toa_tc(m, s, B, c->precision == PTA_PREC_TF32X3 ? 3 : 1, st);
     else if (c->precision == PTA_PREC_BF16X3)
       e = pta::launch_toa_bf16(m, s, B, st);
+    else if (c->precision == PTA_PREC_F16X6)
+      e = pta::launch_toa_f16(m, s, B, st);
     else
       e = pta::launch_toa_fp32_cfg(m, s, B, c->toa_cfg, st);
   }
@@ -800,8 +827,13 @@ int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* gr
 }
 
 int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* grad, int32_t* status,
+                      cudaStream_t st, bool profile) {
+  return pta_eval_scratch(c, c->sc, B, x, logp, grad, status, st, profile);
+}
+
+int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* grad, int32_t* status,
                       cudaStream_t st) {
-  return pta_eval_internal(c, B, x, logp, grad, status, st, false);
+  return pta_eval_scratch(c, c->sc, B, x, logp, grad, status, st, false);
 }
 
 // Fixed timing-model / low-frequency part of the BF16 tensor-core basis, built on
@@ -900,8 +932,11 @@ int pta_layout(const pta_ctx* c, pta_layout_t* out) {
 int pta_set_precision(pta_ctx* c, int precision) {
   if (!c) return PTA_EINVAL;
   if (precision != PTA_PREC_FP64 && precision != PTA_PREC_FP32 && precision != PTA_PREC_TF32X3 &&
-      precision != PTA_PREC_TF32 && precision != PTA_PREC_BF16X3 && precision != PTA_PREC_GRAM)
+      precision != PTA_PREC_TF32 && precision != PTA_PREC_BF16X3 && precision != PTA_PREC_GRAM &&
+      precision != PTA_PREC_F16X6)
     return fail(c, PTA_EINVAL, "precision mode not available in this build");
+  if (precision == PTA_PREC_F16X6 && c->finalized && !pta::f16_supported(c->dm))
+    return fail(c, PTA_EINVAL, "exact-split tensor-core path needs P + m_max + 2 (low bins) <= 480");
   if (precision == PTA_PREC_GRAM && c->dm.cw)
     return fail(c, PTA_EINVAL, "the Gram form has no deterministic signal: use a TOA-form mode with CW");
   if (precision == PTA_PREC_BF16X3 && c->finalized && !pta::bf16_supported(c->dm))

@@ -98,6 +98,9 @@ struct DevModel {
                                 // (element (i', l') = G~[P-1-i'][P-1-l']), P (P + 1) / 2 each
   const double* gt;             // [npsr][P] F^T N~^-1 dt (FP64)
   const double* ga;             // [npsr][P] G~ a_ref (mean with the deterministic signal)
+  // exact-split fp16 tensor-core path (PTA_PREC_F16X6)
+  const float* colmaxf;         // [npsr][m_max + NL] max |.| over the pulsar's TOAs of M and F~_lo columns
+  const float* wmaxp;           // [npsr] largest chromatic weight (nu_ref/nu)^2 of the pulsar
 };
 
 // Scratch sized for a batch of up to `cap` chains.
@@ -156,6 +159,12 @@ struct Scratch {
   float* cwwt2 = nullptr;      // [cap][ntoa_pad] N~^-1 F A^-1 gbar at every TOA
   double* chi2b = nullptr;     // [npsr][cap] chi2 of the auxiliary passes (unused)
   float* zeros = nullptr;      // [ntoa_pad] zero residual for the auxiliary pass
+  // exact-split fp16 tensor-core path (allocated when it is selected)
+  unsigned char* c16 = nullptr; // [npsr][chain blocks] 4 fp16 pieces of the scaled coefficients
+  float* spf = nullptr;         // [npsr][chain blocks][PM] basis column factors
+  int* yexp = nullptr;          // [npsr][cap] exponent of F a per chain
+  float* wres = nullptr;        // [cap][ntoa_pad] whitened projected residual w~
+  float* wmx = nullptr;         // [units][cap] max |w~| of the unit
 };
 
 // Kernel launchers (defined in the .cu files).
@@ -177,6 +186,10 @@ size_t bf16_xmlo_bytes(const DevModel& m);
 cudaError_t build_bf16_xmlo(const DevModel& m, unsigned char* out, cudaStream_t st);
 cudaError_t launch_toa_bf16(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
 cudaError_t launch_gram(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
+bool f16_supported(const DevModel& m);
+size_t f16_pack_bytes(const DevModel& m, int cap);
+size_t f16_scale_floats(const DevModel& m, int cap);
+cudaError_t launch_toa_f16(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
 size_t cw_const_bytes();
 cudaError_t launch_cw_forward(const DevModel& m, const Scratch& s, int B, const float* x, cudaStream_t st);
 cudaError_t launch_cw_gradient(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
