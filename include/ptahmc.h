@@ -53,11 +53,15 @@ extern "C" {
  * in compensated FP32 (error-free products and sums) with FP64 dot products.  No
  * continuous-wave signal (PTA_EINVAL). */
 #define PTA_PREC_GRAM 5
-/* tcgen05 tensor cores at FP32 accuracy: both operands of F a and F^T w~ scaled to a
- * power-of-two grid and cut into fp16 pieces whose leading products sum exactly in
- * the FP32 accumulator (six MMAs per K step), w~ staged in device memory between the
- * two contractions.  PTA_EINVAL when P + max m_I + n_low > 480. */
-#define PTA_PREC_F16X6 6
+/* tcgen05 tensor cores at better than FP32 accuracy (the exact-split path): the
+ * residual is formed with the projected basis F~ = F - M (M^T N^-1 M)^-1 M^T N^-1 F,
+ * stored once per model (built in FP64 on the first call in this mode; 8 bytes per
+ * TOA and column, 0.7 GB for 67 pulsars, 3e5 TOAs and P = 260) as four fp16 pieces
+ * on fixed power-of-two grids, and the FP64 coefficients are cut the same way, so the
+ * leading products sum exactly in the FP32 accumulator (ten MMAs per K step for F a,
+ * six for F^T w~); w~ is staged in device memory between the two contractions.
+ * PTA_EINVAL when P (+ max m_I with the continuous-wave signal) > 512 or m_I > 128. */
+#define PTA_PREC_F16SPLIT 6
 
 typedef struct pta_ctx pta_ctx;
 
@@ -251,7 +255,7 @@ int pta_hmc_trajectory(pta_ctx* ctx, int B, float* x_dev, double* logp_dev, floa
  *     and the work counter of persistent launches) is cleared on `stream` per call.
  *   - PTA_PREC_FP64 needs the stored FP64 basis, which pta_logp_and_grad builds on
  *     its first FP64 call; without it the call returns PTA_ESTATE.
- *   - PTA_PREC_BF16X3 and PTA_PREC_F16X6 (their packed coefficients and, for the
+ *   - PTA_PREC_BF16X3 and PTA_PREC_F16SPLIT (their packed coefficients and, for the
  *     latter, the staged w~ need their own buffers) and the
  *     continuous-wave model return PTA_EINVAL. */
 int pta_logp_and_grad_noalloc(pta_ctx* ctx, int B, const float* x_dev, double* logp_dev,

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libptahmc.so")
 
 PTA_OK, PTA_EINVAL, PTA_ESTATE, PTA_ECUDA, PTA_ENOMEM, PTA_ETIMEOUT = 0, -1, -2, -3, -4, -5
-PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2, "tf32": 3, "bf16x3": 4, "gram": 5, "f16x6": 6}
+PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2, "tf32": 3, "bf16x3": 4, "gram": 5, "f16split": 6}
 TRANSFORM = {"prior": 0, "curn": 1}
 
 EXPORTED = ["pta_create", "pta_add_pulsar", "pta_finalize", "pta_layout", "pta_set_precision",

@@ -48,7 +48,7 @@ __device__ __forceinline__ int low_col(const DevModel& m, int q) {
 
 __global__ void __launch_bounds__(128)
     k_tm_prologue(DevModel m, double* __restrict__ a64, float* __restrict__ a32, const double* __restrict__ cwbs,
-                  int B, int fp64) {  // fp64: 0 FP32 packed rows, 1 FP64 path, 2 FP64 packed rows
+                  int B, int fp64) {  // fp64: 0 FP32 packed rows, 1 FP64 path, 2 exact-split path
   extern __shared__ double smp[];
   const int I = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int P = m.P, mI = m.m[I];
@@ -70,7 +70,9 @@ __global__ void __launch_bounds__(128)
   __syncthreads();
   for (int j0 = 0; j0 < mI; j0 += 32) {
     const int j = j0 + lane;
-    if (j < mI) {
+    if (j < mI && fp64 == 2) {
+      part[warp * mI + j] = 0.0;  // projected basis: c carries only the signal's projection
+    } else if (j < mI) {
       if (fp64) {
         const double* H = m.H + m.h_off[I];
         double s = 0.0;
@@ -114,26 +116,24 @@ __global__ void __launch_bounds__(128)
     }
   }
   __syncthreads();
-  if (fp64 == 1) {
+  if (fp64) {
+    // FP64 rows in place: [da | c] for the FP64 path; [da | c_s] for the exact-split
+    // tensor-core path, whose basis is fully projected (c_s only with a signal)
     for (int p = tid; p < P; p += 128) row[p] = da[p];
-    for (int j = tid; j < mI; j += 128) row[P + j] = cv[j];
+    if (fp64 == 1 || cwbs)
+      for (int j = tid; j < mI; j += 128) row[P + j] = cv[j];
   } else {
-    // packed row [da (low columns zero) | c | da of the low columns | 0]: FP32 for the
-    // FP32-operand kernels, FP64 in place for the exact-split tensor-core path (its
-    // fp16 pieces are cut from the FP64 values)
+    // FP32 packed row [da (low columns zero) | c | da of the low columns | 0]
     float* r32 = a32 + ((size_t)I * B + b) * m.PM;
     for (int q = tid; q < m.PM; q += 128) {
-      double v = 0.0;
+      float v = 0.f;
       if (q < P)
-        v = is_low_col(m, q) ? 0.0 : da[q];
+        v = is_low_col(m, q) ? 0.f : (float)da[q];
       else if (q < P + mI)
-        v = cv[q - P];
+        v = (float)cv[q - P];
       else if (q < P + mI + m.NL)
-        v = da[low_col(m, q - P - mI)];
-      if (fp64 == 2)
-        row[q] = v;
-      else
-        r32[q] = (float)v;
+        v = (float)da[low_col(m, q - P - mI)];
+      r32[q] = v;
     }
   }
 }

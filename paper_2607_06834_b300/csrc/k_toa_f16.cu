@@ -1,47 +1,52 @@
-// TOA contractions on the tcgen05 tensor cores at FP32 accuracy, same quantities as
-// k_toa_simt (the projected residual of Eq. raw_det_posterior with N~^-1 of Eq.
-// Gmatrix_proj, whitened by Eq. WN_cov):
-//   y  = [F | M | F~_lo] coef,  r~ = dt'' - y,  w~ = N^-1 r~,  chi2 = sum r~ w~,
-//   ghat = F^T w~.
+// TOA contractions on the tcgen05 tensor cores at FP32 accuracy or better, same
+// quantities as k_toa_simt (the projected residual of Eq. raw_det_posterior with N~^-1
+// of Eq. Gmatrix_proj, whitened by Eq. WN_cov), written with the fully projected basis
+//   F~ = F - M (M^T N^-1 M)^-1 M^T N^-1 F   (N^-1-orthogonal to the timing model):
+//   y  = F~ (a - a_ref) [+ M c_s],  r~ = dt'' - y,  w~ = N^-1 r~,  chi2 = sum r~ w~,
+//   ghat = F~^T w~ = F^T w~   (M^T w~ = 0).
+// With a deterministic signal s the projection of s enters through the timing-model
+// columns, c_s = -(M^T N^-1 M)^-1 M^T N^-1 s, and the kernel subtracts s itself.
 //
 // Why an exact split.  The tensor cores accumulate in FP32 without round-to-nearest,
-// and the products of one residual cancel 16-100 fold (the coefficients of low
-// frequencies, the timing model and DM are nearly degenerate), so an FP32-accuracy
-// result needs most of the sum to be computed without rounding at all.  Both operands
-// are scaled to a common power-of-two grid and cut into fp16 pieces:
-//   v = v0 + v1 + r2,  v0 on the 2^7 grid, v1 on the 2^-1 grid (|v0/2^7|, |2 v1| <= 128),
-//   r = v - v0 and r2 = v - v0 - v1 rounded to fp16,
-// for |v| <= 2^14.  Products of grid pieces are integers times a fixed quantum, so
+// and the terms of one residual cancel 20-400 fold, so an FP32-accuracy result needs
+// most of the sum formed without rounding.  Both operands are scaled to a common
+// power-of-two grid (|v| < 2^14) and cut into fp16 pieces, three on fixed grids and
+// the rest:
+//   v = v0 + v1 + v2 + v3,  v0, v1, v2 on the 2^7, 2^-1, 2^-9 grids (round to nearest),
+//   v3 the fp16 of what is left (|v3| <= 2^-10),
+// so |v0| <= 2^14, |v1| <= 2^6, |v2| <= 2^-2 are exact fp16 numbers of at most 8
+// significant bits.  Products of grid pieces are integers times a fixed quantum, so
 //   L0 = sum X0 C0            (quantum 2^14, at most K 2^14 quanta)
 //   L1 = sum X1 C0 + X0 C1    (quantum 2^6,  at most 2 K 2^14 quanta)
-// stay below 2^24 quanta for K <= 511 columns and are exact in the FP32 accumulator
+// stay within 2^24 quanta for K <= 512 columns and are exact in the FP32 accumulator
 // whatever its rounding; the rest,
-//   L2 = sum X2 C0 + X0 C2 + Xr Cr   (2^-16 of the leading terms),
-// carries rounding relative to its own small size.  Six MMAs per K step represent
-// both operands to about 2^-27 of their scale.  y = (L0 + L1 + L2) 2^(scale).
+//   L2 = X2 C0 + X1 C1 + X0 C2 + X3 C0 + X0 C3 + X2 C1 + X1 C2   (2^-16 of the scale),
+// carries rounding relative to its own small size.  Ten MMAs per K step represent the
+// product to about 2^-35 of its largest term.  y = (L0 + L1 + L2) 2^(scale).
 //
-// Scaling (k_f16_pack): basis column q is normalised to 2^14 by a power of two from
-// its largest value over the pulsar's TOAs (|sin|, |cos| <= 1, the largest DM weight,
-// stored maxima of the timing-model and projected low-frequency columns); the
-// coefficients carry the inverse factor and each chain row is normalised to 2^14 by
-// its own exponent, so a chain's accuracy does not depend on the other chains.
+// The basis is fixed, so it is built once per model in FP64 (k_f16_image): F~ from
+// FP64 sines and cosines of the exactly reduced phases minus the FP64 timing-model
+// projection, each column normalised by a power of two from its largest value over
+// the pulsar's TOAs, cut into the four pieces and stored in the order the residual
+// kernel reads it.  The coefficients are cut from the FP64 rows of the prior stage,
+// each chain normalised to 2^14 by its own exponent (k_f16_pack), so a chain's accuracy
+// does not depend on the other chains.
 //
-// k_f16_res: F a, the residual, chi2 and w~.  One CTA per (work unit, block of NC
-// chains).  The MMA's M is 128 TOAs and its A operand (the basis, 32 columns per
-// chunk) is written into tensor memory by generator warps with tcgen05.st; its N is
-// the NC chains and its B operand (the block's coefficients, all columns) is resident
+// k_f16_res: F~ a, the residual, chi2 and w~.  One CTA per (block of NC chains, work
+// unit).  The MMA's M is 128 TOAs and its A operand (32 basis columns per chunk) sits
+// in tensor memory, written there by loader warps from the stored pieces; its N is the
+// NC chains and its B operand (the block's coefficient pieces, all columns) is resident
 // in shared memory.  Accumulators and basis chunks are double-buffered in tensor
-// memory.  Epilogue warps read the three accumulators per TOA lane, form the
-// residual, write w~ to global memory (TOA-major per chain) and reduce chi2 over the
-// TOAs in FP64.
+// memory.  Epilogue warps read the three accumulators per TOA lane, form the residual
+// with error-free sums, write w~ (TOA-major per chain) and reduce chi2 in FP64.
 //
-// k_f16_ftw: ghat = F^T w~ over the unit.  One CTA per (work unit, block of 128
-// chains, chunk of <= 144 basis columns).  M = 128 chains with A = w~ in tensor memory
-// (scaled per chain and unit by its largest |w~|, from k_f16_res), N = the chunk's
-// columns with B = the basis in shared memory (MN-major), K = TOAs, 32 per stage.
-// w~ = W0 + Wr (Wr as fp16 hi + lo), basis likewise; L0 = sum W0 X0 is exact (7-bit
-// grid pieces: at most 2048 2^12 quanta), the other five products go to a second
-// accumulator.
+// k_f16_ftw: ghat = F~^T w~ over the unit.  One CTA per (chunk of <= 144 basis columns,
+// block of 128 chains, work unit).  M = 128 chains with A = w~ in tensor memory (scaled
+// per chain and unit by its largest |w~|), N = the chunk's columns with B = the pieces
+// X0, X1, X2 in shared memory (MN-major), K = TOAs, 32 per stage.  w~ = W0 + Wh + Wl
+// (W0 on the 2^7 grid for |w~| < 2^12, Wh and Wl fp16); L0 = sum W0 X0 is exact (at most
+// 2048 2^12 quanta), W0 X1 + Wh X0 + W0 X2 + Wh X1 + Wl X0 go to a second accumulator
+// (about 2^-23 of the largest term: the gradient's tolerance is 1e-4).
 //
 // Every mbarrier wait is bounded; a wait that gives up marks the CTA's chains with
 // status bit 4 and the CTA drains its own MMAs before it frees tensor memory.
@@ -53,11 +58,12 @@
 namespace pta {
 namespace {
 
-constexpr int TTA = 128;   // TOAs per tile in k_f16_res (MMA M)
-constexpr int KCA = 32;    // basis columns per chunk in k_f16_res
-constexpr int KWB = 32;    // TOAs per stage in k_f16_ftw
-constexpr int QWB = 144;   // basis columns per chunk in k_f16_ftw (MMA N)
-constexpr int NSB = 4;     // stages in k_f16_ftw
+constexpr int TTA = 128;                  // TOAs per tile in k_f16_res (MMA M) and per stored basis tile
+constexpr int KCA = 32;                   // basis columns per chunk
+constexpr int XCW = 4 * (KCA / 2) * TTA;  // 32-bit words of one stored (tile, chunk): 4 pieces
+constexpr int KWB = 32;                   // TOAs per stage in k_f16_ftw
+constexpr int QWB = 144;                  // basis columns per chunk in k_f16_ftw (MMA N)
+constexpr int NSB = 4;                    // stages in k_f16_ftw
 constexpr uint32_t kWaitLimit = 4000000u;
 constexpr uint32_t kDrainLimit = 4000000u;
 
@@ -118,15 +124,6 @@ __device__ __forceinline__ uint32_t h2(float lo, float hi) {
 }
 __device__ __forceinline__ float f16r(float v) { return __half2float(__float2half_rn(v)); }
 
-// |v| <= 2^14: v0 on the 2^7 grid, v1 on the 2^-1 grid (round to nearest by the
-// magic-number additions), r = v - v0, r2 = v - v0 - v1 (all exact in FP32)
-__device__ __forceinline__ void split_grid(float v, float& v0, float& v1, float& r, float& r2) {
-  v0 = __fsub_rn(__fadd_rn(v, 1610612736.f), 1610612736.f);  // 1.5 x 2^30: ulp 2^7
-  r = __fsub_rn(v, v0);
-  v1 = __fsub_rn(__fadd_rn(r, 6291456.f), 6291456.f);        // 1.5 x 2^22: ulp 2^-1
-  r2 = __fsub_rn(r, v1);
-}
-
 // 2^e as a float for -126 <= e <= 127 (exact)
 __device__ __forceinline__ float pow2f(int e) {
   e = max(-126, min(127, e));
@@ -141,70 +138,201 @@ __device__ __forceinline__ float two_sum(float a, float b, float& e) {
   return s;
 }
 
-// sin and cos of harmonic k+1 from those of harmonic k by one rotation with the
-// fundamental (s1, c1): two FMA-rounded products, so a run of three rotations after an
-// exactly reduced anchor stays within a few ulp of the exact values
-__device__ __forceinline__ void rotate(float& s, float& c, float s1, float c1) {
-  const float sn = fmaf(s, c1, c * s1);
-  c = fmaf(c, c1, -(s * s1));
-  s = sn;
-}
-
-// exponent e with |v| <= 2^e (frexp); 0 for v == 0
+// exponent e with |v| < 2^e (frexp); 0 for v == 0
 __device__ __forceinline__ int exp_up(float v) {
   int e = 0;
   frexpf(v, &e);
   return v == 0.f ? 0 : e;
 }
+__device__ __forceinline__ int exp_up64(double v) {
+  int e = 0;
+  frexp(v, &e);
+  return v == 0.0 ? 0 : e;
+}
 
-__device__ __forceinline__ int round_up_d(int a, int b) { return (a + b - 1) / b * b; }
-__device__ __forceinline__ int kx_of(const DevModel& m, int I) { return round_up_d(m.P + m.m[I] + m.NL, KCA); }
+// |v| < 2^14 (FP64): v0, v1, v2 on the 2^7, 2^-1, 2^-9 grids, each rounded to nearest
+// from what the previous ones leave (exact in FP64), v3 the rest; as floats (v0, v1, v2
+// exact, fp16-exact too; v3 is rounded to fp16 when packed)
+__device__ __forceinline__ void split4(double v, float& v0, float& v1, float& v2, float& v3) {
+  const double a0 = rint(v * 0x1p-7) * 0x1p7;
+  double r = v - a0;
+  const double a1 = rint(r * 2.0) * 0.5;
+  r -= a1;
+  const double a2 = rint(r * 0x1p9) * 0x1p-9;
+  r -= a2;
+  v0 = (float)a0;
+  v1 = (float)a1;
+  v2 = (float)a2;
+  v3 = (float)r;
+}
 
-// Column maxima of the basis over pulsar I's TOAs (sin/cos: 1; DM: largest weight;
-// fixed columns: stored)
-__device__ __forceinline__ float basis_colmax(const DevModel& m, int I, int q) {
-  if (q < 2 * m.na) return 1.f;
-  if (q < m.P) return m.wmaxp[I];
-  const int j = q - m.P;
-  return j < m.m[I] + m.NL ? m.colmaxf[(size_t)I * (m.m_max + m.NL) + (j < m.m[I] ? j : m.m_max + j - m.m[I])] : 0.f;
+// |v| < 2^12: v0 on the 2^7 grid (round to nearest by the magic-number addition),
+// rh = fp16(v - v0), rl = the rest (exact in FP32; rounded to fp16 when packed)
+__device__ __forceinline__ void split_w(float v, float& v0, float& rh, float& rl) {
+  v0 = __fsub_rn(__fadd_rn(v, 1610612736.f), 1610612736.f);  // 1.5 x 2^30: ulp 2^7
+  const float r = __fsub_rn(v, v0);
+  rh = f16r(r);
+  rl = __fsub_rn(r, rh);
+}
+
+__host__ __device__ __forceinline__ int round_up_hd(int a, int b) { return (a + b - 1) / b * b; }
+// stored basis columns of pulsar I: P Fourier columns, then its timing-model columns
+// when a deterministic signal is modelled, padded to whole chunks
+__host__ __device__ __forceinline__ int kx_cols(int P, int mI, int cw) { return round_up_hd(P + (cw ? mI : 0), KCA); }
+__device__ __forceinline__ int kx_of(const DevModel& m, int I) { return kx_cols(m.P, m.m[I], m.cw); }
+
+// ---------------------------------------------------------------------------
+// Stored basis.  Pulsar I's pieces start at word x16_off[I]; its tile tau (TOAs
+// 128 tau .. 128 tau + 127 of the pulsar) and chunk c (columns 32 c .. 32 c + 31) form
+// one block of XCW words at x16_off[I] + (tau nch + c) XCW.  Inside it, piece a, TOA t
+// and word j (columns 32 c + 2 j (low half) and 32 c + 2 j + 1 (high half)) is word
+//   ((4 a + j / 4) 128 + t) 4 + j % 4:
+// the 4 words of 8 consecutive columns are one 16-byte row per TOA, and a warp's 32 TOAs
+// of one such row are 512 contiguous bytes.  Word j of a piece lands in tensor-memory
+// column j of that piece's block (the A-operand layout of kind::f16), and the 16-byte
+// rows are the core-matrix rows of the MN-major B operand of k_f16_ftw.
+// ---------------------------------------------------------------------------
+
+// Column q of pulsar I's stored basis at padded TOA ta (FP64).  F~ = F - M K^-1 H^T for
+// q < P (DM columns weighted by (nu_ref/nu)^2), the normalised timing-model column
+// q - P beyond (signal models only); 0 on padding rows.  kih: this chunk's 32 columns
+// of K^-1 H^T as kih[32 j + (q mod 32)].
+__device__ double basis64(const DevModel& m, int I, int ta, int q, const double* kih, double s, double c) {
+  if (m.ninv64[ta] == 0.0) return 0.0;
+  const int mI = m.m[I], P = m.P;
+  const long long row = ta - m.toa_off[I];
+  const double* Mr = m.M64 + m.m_off[I] + row * mI;
+  if (q >= P) return q - P < mI ? Mr[q - P] : 0.0;
+  double v = (q & 1) ? c : s;
+  if (q >= 2 * m.na) v *= m.chrom64[ta];
+  const double* kq = kih + (q & (KCA - 1));
+  for (int j = 0; j < mI; ++j) v = fma(-Mr[j], kq[KCA * j], v);
+  return v;
+}
+
+// sin and cos of column pair (q, q + 1) at TOA ta: harmonic k of the exactly reduced
+// phase, FP64 sincospi (zero beyond the Fourier columns)
+__device__ __forceinline__ void pair_sincos(const DevModel& m, int ta, int q, double& s, double& c) {
+  s = 0.0;
+  c = 0.0;
+  if (q >= m.P) return;
+  const int k = q < 2 * m.na ? q / 2 + 1 : (q - 2 * m.na) / 2 + 1;
+  const uint64_t ph = m.phase[ta] * (uint64_t)k;  // mod 2^64: the fraction of a turn
+  sincospi(2.0 * ((double)(ph >> 11) * 0x1p-53), &s, &c);
+}
+
+__device__ void load_kih(const DevModel& m, int I, int c, double* kih) {
+  const int mI = m.m[I], P = m.P;
+  for (int e = threadIdx.x; e < KCA * mI; e += blockDim.x) {
+    const int j = e / KCA, q = KCA * c + e % KCA;
+    kih[e] = q < P ? m.KiH[m.h_off[I] + (size_t)j * P + q] : 0.0;
+  }
+}
+
+// Pass 1: largest |column| over each pulsar's TOAs (as the bits of a non-negative
+// double, which order like the values).  Grid (unit, chunk), 128 threads (one TOA each).
+__global__ void __launch_bounds__(128) k_f16_colmax(DevModel m, unsigned long long* cmax, int kxm) {
+  __shared__ double kih[KCA * 128];
+  const int u = blockIdx.x, c = blockIdx.y, t = threadIdx.x, lane = t & 31;
+  const int I = m.unit_psr[u], start = m.unit_start[u], len = m.unit_len[u];
+  if (c >= kx_of(m, I) / KCA) return;
+  load_kih(m, I, c, kih);
+  __syncthreads();
+#pragma unroll 1
+  for (int j = 0; j < KCA; j += 2) {
+    const int q = KCA * c + j;
+    double m0 = 0.0, m1 = 0.0;
+    for (int i = t; i < len; i += 128) {
+      const int ta = start + i;
+      double s, cs;
+      pair_sincos(m, ta, q, s, cs);
+      m0 = fmax(m0, fabs(basis64(m, I, ta, q, kih, s, cs)));
+      m1 = fmax(m1, fabs(basis64(m, I, ta, q + 1, kih, s, cs)));
+    }
+    for (int o = 16; o; o >>= 1) {
+      m0 = fmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+      m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+    }
+    if (lane == 0) {
+      atomicMax(&cmax[(size_t)I * kxm + q], (unsigned long long)__double_as_longlong(m0));
+      atomicMax(&cmax[(size_t)I * kxm + q + 1], (unsigned long long)__double_as_longlong(m1));
+    }
+  }
+}
+
+// Pass 2: the column exponents and the four pieces of every stored word.
+__global__ void __launch_bounds__(128)
+    k_f16_image(DevModel m, const unsigned long long* __restrict__ cmax, int kxm, uint32_t* __restrict__ img,
+                int* __restrict__ cexp) {
+  __shared__ double kih[KCA * 128];
+  __shared__ double fac[KCA];
+  const int u = blockIdx.x, c = blockIdx.y, t = threadIdx.x;
+  const int I = m.unit_psr[u], start = m.unit_start[u], len = m.unit_len[u];
+  const int nch = kx_of(m, I) / KCA;
+  if (c >= nch) return;
+  load_kih(m, I, c, kih);
+  if (t < KCA) {
+    const int e = exp_up64(__longlong_as_double((long long)cmax[(size_t)I * kxm + KCA * c + t]));
+    fac[t] = ldexp(1.0, 14 - e);  // |column| < 2^e: scaled columns stay below 2^14
+    if (u == m.unit0[I]) cexp[(size_t)I * kxm + KCA * c + t] = e;
+  }
+  __syncthreads();
+  const int tau0 = (start - m.toa_off[I]) / TTA;
+  for (int i = 0; i < len / TTA; ++i) {
+    const int ta = start + i * TTA + t;
+    uint4* dst = reinterpret_cast<uint4*>(img + m.x16_off[I] + ((size_t)(tau0 + i) * nch + c) * XCW) + t;
+#pragma unroll 1
+    for (int g = 0; g < KCA / 8; ++g) {  // 8 columns: one 16-byte row per piece
+      uint32_t w[4][4];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int q = KCA * c + 8 * g + 2 * jj;
+        double s, cs;
+        pair_sincos(m, ta, q, s, cs);
+        float a0, a1, a2, a3, b0, b1, b2, b3;
+        split4(basis64(m, I, ta, q, kih, s, cs) * fac[8 * g + 2 * jj], a0, a1, a2, a3);
+        split4(basis64(m, I, ta, q + 1, kih, s, cs) * fac[8 * g + 2 * jj + 1], b0, b1, b2, b3);
+        w[0][jj] = h2(a0, b0);
+        w[1][jj] = h2(a1, b1);
+        w[2][jj] = h2(a2, b2);
+        w[3][jj] = h2(a3, b3);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a) dst[(4 * a + g) * TTA] = make_uint4(w[a][0], w[a][1], w[a][2], w[a][3]);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
-// Pack: per (pulsar, block of NC chains) the basis column factors, the chain
-// exponents and the four fp16 pieces of the scaled coefficients in the MMA's K-major
-// layout: element (chain n, column k) of piece a at a PM NC 2 + (k/8) NC 16 + (n/8) 128
-// + (n%8) 16 + (k%8) 2 bytes.  Pieces: 0 C0, 1 C1, 2 C2 (fp16 of r2), 3 Cr.
-// Column q of the basis is normalised by its own largest value over the pulsar's TOAs,
-// X' = X 2^(14 - c_q), and the coefficients carry the inverse factor, C' = C 2^c_q,
-// each chain row normalised to 2^14 by its own exponent E_n: so every chain's accuracy
-// is relative to its own largest term, independent of the other chains of the block.
+// Pack: per (pulsar, block of NC chains) the chain exponents and the four fp16 pieces
+// of the scaled coefficients in the MMA's K-major layout: element (chain n, column k) of
+// piece a at a PM NC 2 + (k/8) NC 16 + (n/8) 128 + (n%8) 16 + (k%8) 2 bytes.  The rows
+// are the FP64 coefficient rows [a - a_ref | c_s] of the prior stage.  Stored basis
+// column q carries 2^(14 - c_q), so coefficient q carries 2^c_q, and each chain row is
+// normalised to 2^14 by its own exponent E_n (y = L 2^(E_n - 28)).
 // ---------------------------------------------------------------------------
 template <int NC>
 __global__ void __launch_bounds__(256)
-    k_f16_pack(DevModel m, const float* __restrict__ a32, unsigned char* __restrict__ c16, float* __restrict__ spf,
-               int* __restrict__ yexp, int B, int nCB) {
-  extern __shared__ float sh[];
-  float* cf = sh;                 // [PM] coefficient factors 2^c_q
-  __shared__ int s_e[NC];
+    k_f16_pack(DevModel m, const double* __restrict__ a64, unsigned char* __restrict__ c16, int* __restrict__ yexp,
+               int B, int nCB) {
+  extern __shared__ double cf[];  // [KX] 2^c_q
+  __shared__ double s_f[NC];      // 2^(14 - E_n)
   const int I = blockIdx.x, cb = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int b0 = cb * NC, nvalid = min(NC, B - b0), KX = kx_of(m, I), PM = m.PM;
-  const float* rows = a32 + ((size_t)I * B + b0) * PM;
-  float* spo = spf + ((size_t)I * nCB + cb) * PM;
-  for (int q = tid; q < KX; q += 256) {
-    const int c = exp_up(basis_colmax(m, I, q));
-    cf[q] = ldexpf(1.f, c);
-    spo[q] = ldexpf(1.f, 14 - c);
-  }
+  const int ncol = m.P + (m.cw ? m.m[I] : 0);  // columns with coefficients; the rest of the chunk is 0
+  const double* rows = a64 + ((size_t)I * B + b0) * PM;
+  for (int q = tid; q < KX; q += 256) cf[q] = ldexp(1.0, m.x16_cexp[(size_t)I * m.x16_kxm + q]);
   __syncthreads();
   // per-chain exponent of max_q |C_nq 2^c_q| (one warp per chain)
   for (int n = warp; n < NC; n += 8) {
-    float mx = 0.f;
+    double mx = 0.0;
     if (n < nvalid)
-      for (int q = lane; q < KX; q += 32) mx = fmaxf(mx, fabsf(rows[(size_t)n * PM + q]) * cf[q]);
-    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      for (int q = lane; q < ncol; q += 32) mx = fmax(mx, fabs(rows[(size_t)n * PM + q]) * cf[q]);
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) {
-      s_e[n] = exp_up(mx);
-      if (n < nvalid) yexp[(size_t)I * B + b0 + n] = exp_up(mx) - 28;
+      const int e = exp_up64(mx);
+      s_f[n] = ldexp(1.0, 14 - e);
+      if (n < nvalid) yexp[(size_t)I * B + b0 + n] = e - 28;
     }
   }
   __syncthreads();
@@ -212,14 +340,12 @@ __global__ void __launch_bounds__(256)
   const size_t asz = (size_t)PM * NC * 2;
   for (int e = tid; e < NC * (KX / 8); e += 256) {
     const int n = e % NC, g = e / NC;  // consecutive threads: consecutive chains
-    float c0[8], c1[8], c2[8], cr[8];
+    float c0[8], c1[8], c2[8], c3[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int q = 8 * g + i;
-      const float v = n < nvalid ? ldexpf(rows[(size_t)n * PM + q] * cf[q], 14 - s_e[n]) : 0.f;
-      float r;
-      split_grid(v, c0[i], c1[i], r, c2[i]);
-      cr[i] = r;
+      const double v = (n < nvalid && q < ncol) ? rows[(size_t)n * PM + q] * cf[q] * s_f[n] : 0.0;
+      split4(v, c0[i], c1[i], c2[i], c3[i]);
     }
     const size_t off = (size_t)g * NC * 16 + (n >> 3) * 128 + (n & 7) * 16;
     *reinterpret_cast<uint4*>(out + off) = make_uint4(h2(c0[0], c0[1]), h2(c0[2], c0[3]), h2(c0[4], c0[5]), h2(c0[6], c0[7]));
@@ -228,7 +354,7 @@ __global__ void __launch_bounds__(256)
     *reinterpret_cast<uint4*>(out + 2 * asz + off) =
         make_uint4(h2(c2[0], c2[1]), h2(c2[2], c2[3]), h2(c2[4], c2[5]), h2(c2[6], c2[7]));
     *reinterpret_cast<uint4*>(out + 3 * asz + off) =
-        make_uint4(h2(cr[0], cr[1]), h2(cr[2], cr[3]), h2(cr[4], cr[5]), h2(cr[6], cr[7]));
+        make_uint4(h2(c3[0], c3[1]), h2(c3[2], c3[3]), h2(c3[4], c3[5]), h2(c3[6], c3[7]));
   }
 }
 
@@ -237,35 +363,34 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------------
 template <int NC>
 struct ResCfg {
-  static constexpr int DB = 3 * NC;               // tensor-memory columns of one accumulator set
-  static constexpr int XBASE = 2 * DB;            // first basis-chunk column
-  static constexpr int XST = 4 * (KCA / 2);       // columns of one basis chunk (4 pieces)
-  static constexpr int NXS = (512 - XBASE) / XST; // basis-chunk stages
+  static constexpr int DB = 3 * NC;                // tensor-memory columns of one accumulator set
+  static constexpr int XBASE = 2 * DB;             // first basis-chunk column
+  static constexpr int XST = 4 * (KCA / 2);        // columns of one basis chunk (4 pieces)
+  static constexpr int NXS = (512 - XBASE) / XST;  // basis-chunk stages
   static_assert(NXS >= 2, "tensor memory");
 };
 
 template <int NC>
 __global__ void __launch_bounds__(448, 1)
-    k_f16_res(DevModel m, const unsigned char* __restrict__ c16, const float* __restrict__ spf,
-              const int* __restrict__ yexp, float* __restrict__ wres, float* __restrict__ wmx,
-              double* __restrict__ c2part, int32_t* __restrict__ stat, const float* __restrict__ cwsig, int B,
-              int nCB) {
+    k_f16_res(DevModel m, const unsigned char* __restrict__ c16, const int* __restrict__ yexp,
+              float* __restrict__ wres, float* __restrict__ wmx, double* __restrict__ c2part,
+              int32_t* __restrict__ stat, const float* __restrict__ cwsig, int B, int nCB) {
   using CF = ResCfg<NC>;
   constexpr int NXS = CF::NXS;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t cfull, xfull[NXS], xfree[NXS], dfull[2], dempty[2], drain;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_bad;
-  const int u = blockIdx.x, cb = blockIdx.y, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // chain block fastest: the blocks of one unit run together and share its basis in L2
+  const int cb = blockIdx.x, u = blockIdx.y, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int I = m.unit_psr[u], start = m.unit_start[u], len = m.unit_len[u];
-  const int mI = m.m[I], PM = m.PM, KX = kx_of(m, I), nch = KX / KCA, ntile = len / TTA;
+  const int PM = m.PM, KX = kx_of(m, I), nch = KX / KCA, ntile = len / TTA;
   const int b0 = cb * NC, nvalid = min(NC, B - b0);
   const size_t asz = (size_t)PM * NC * 2;
-  unsigned char* Cs = smem;                                            // 4 pieces x PM x NC fp16
-  float* sp = reinterpret_cast<float*>(smem + 4 * asz);               // [PM] basis column factors
-  double* redc = reinterpret_cast<double*>(sp + round_up_d(PM, 2));   // [4][NC] chi2 partials
-  float* redm = reinterpret_cast<float*>(redc + 4 * NC);              // [4][NC] max |w|
-  float* ysc = redm + 4 * NC;                                         // [NC] 2^(exponent of y) per chain
+  unsigned char* Cs = smem;                                        // 4 pieces x PM x NC fp16
+  double* redc = reinterpret_cast<double*>(smem + 4 * asz);        // [4][NC] chi2 partials
+  float* redm = reinterpret_cast<float*>(redc + 4 * NC);           // [4][NC] max |w|
+  float* ysc = redm + 4 * NC;                                      // [NC] 2^(exponent of y) per chain
 
   if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
   if (tid == 0) {
@@ -282,8 +407,6 @@ __global__ void __launch_bounds__(448, 1)
     s_bad = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  const float* spg = spf + ((size_t)I * nCB + cb) * PM;
-  for (int q = tid; q < KX; q += blockDim.x) sp[q] = spg[q];
   for (int n = tid; n < NC; n += blockDim.x) ysc[n] = pow2f(n < nvalid ? yexp[(size_t)I * B + b0 + n] : 0);
   tc::fence_before();
   __syncthreads();
@@ -320,14 +443,18 @@ __global__ void __launch_bounds__(448, 1)
             uint64_t bd[4];
 #pragma unroll
             for (int a = 0; a < 4; ++a) bd[a] = tc::desc(cbase + a * (uint32_t)asz + kg * NC * 16, NC * 16, 128);
-            const uint32_t ax0 = xa + 8 * ks, ax1 = ax0 + KCA / 2, ax2 = ax0 + KCA, ax3 = ax0 + 3 * (KCA / 2);
+            const uint32_t x0 = xa + 8 * ks, x1 = x0 + KCA / 2, x2 = x0 + KCA, x3 = x0 + 3 * (KCA / 2);
             const uint32_t acc = (c | ks) ? 1u : 0u;
-            mma_ts(d0, ax0, bd[0], ID, acc);  // L0 = X0 C0
-            mma_ts(d1, ax1, bd[0], ID, acc);  // L1 = X1 C0 + X0 C1
-            mma_ts(d1, ax0, bd[1], ID, 1u);
-            mma_ts(d2, ax2, bd[0], ID, acc);  // L2 = X2 C0 + X0 C2 + Xr Cr
-            mma_ts(d2, ax0, bd[2], ID, 1u);
-            mma_ts(d2, ax3, bd[3], ID, 1u);
+            mma_ts(d0, x0, bd[0], ID, acc);  // L0 = X0 C0
+            mma_ts(d1, x1, bd[0], ID, acc);  // L1 = X1 C0 + X0 C1
+            mma_ts(d1, x0, bd[1], ID, 1u);
+            mma_ts(d2, x2, bd[0], ID, acc);  // L2: the 2^-16 and 2^-24 terms
+            mma_ts(d2, x1, bd[1], ID, 1u);
+            mma_ts(d2, x0, bd[2], ID, 1u);
+            mma_ts(d2, x3, bd[0], ID, 1u);
+            mma_ts(d2, x0, bd[3], ID, 1u);
+            mma_ts(d2, x2, bd[1], ID, 1u);
+            mma_ts(d2, x1, bd[2], ID, 1u);
           }
           tc::commit(&xfree[s]);
         }
@@ -349,71 +476,44 @@ __global__ void __launch_bounds__(448, 1)
     }
     __syncwarp();
   } else if (warp < 10) {
-    // ------------------------------------------------ basis generation into tensor memory
-    // Harmonics come in runs of consecutive k along the columns: each run of four
-    // pairs starts from an exactly reduced sin/cos and rotates by the fundamental.
-    // Column factors: every achromatic column shares one (|sin|, |cos| <= 1), every DM
-    // column another (the pulsar's largest weight), fixed columns their own.
+    // ------------------------------------------------ stored basis into tensor memory
+    // Warp (quarter qw, half hf): TOAs 32 qw .. 32 qw + 31, words 8 hf .. 8 hf + 7 of every
+    // piece (16-byte rows 2 hf and 2 hf + 1).  Chunk g + 1 is fetched into registers
+    // while chunk g is stored.
     const int qw = warp & 3, hf = (warp - 2) >> 2, t = 32 * qw + lane;
     const uint32_t lanef = (uint32_t)(32 * qw) << 16;
-    const int na2 = 2 * m.na, P = m.P, NL = m.NL;
-    const float fa = sp[0], fd = m.nd ? sp[na2] : 0.f;
-    int g = 0;
-    bool ok = true;
-    for (int i = 0; i < ntile && ok; ++i) {
-      const int ta = start + i * TTA + t;
-      const uint64_t U = m.phase[ta];
-      const float wd = m.chrom[ta] * fd;  // DM weight times the DM column factor (a power of two)
-      float s1, c1;
-      sincos_turns64(U, &s1, &c1);
-      const long long row = (long long)(start - m.toa_off[I] + i * TTA + t);
-      const float* Mr = m.M32 + m.m_off[I] + row * mI;
-      const float* Lr = m.Flo + m.flo_off[I] + row * NL;
-      for (int c = 0; c < nch; ++c, ++g) {
-        const int s = g % NXS;
-        if (g >= NXS && !(ok = __all_sync(0xffffffffu, wait(&xfree[s], ((g / NXS) - 1) & 1)))) break;
-        uint32_t w0[8], w1[8], w2[8], wr[8];
-        const int q0 = c * KCA + hf * (KCA / 2);
-        float sn = 0.f, cs = 1.f;
-        int kprev = -8;
+    const int tau0 = (start - m.toa_off[I]) / TTA;
+    // (tile i, chunk c) of this unit is block i nch + c after the unit's first one
+    const uint4* xb = reinterpret_cast<const uint4*>(m.x16 + m.x16_off[I] + (size_t)tau0 * nch * XCW) + t;
+    const int G = ntile * nch;
+    auto fetch = [&](int g, uint32_t (&r)[4][8]) {
+      const uint4* p = xb + (size_t)g * (XCW / 4);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int q = q0 + 2 * j;  // warp-uniform: every branch below is uniform
-          float xa, xb;
-          if (q < P) {
-            const bool dm = q >= na2;
-            const int k = dm ? (q - na2) / 2 + 1 : q / 2 + 1;
-            if ((j & 3) == 0 || k != kprev + 1)
-              sincos_turns64(U * (uint64_t)k, &sn, &cs);
-            else
-              rotate(sn, cs, s1, c1);
-            kprev = k;
-            const float f = dm ? wd : fa;
-            xa = sn * f;
-            xb = cs * f;
-          } else {
-            const int j0 = q - P, j1 = j0 + 1;
-            xa = (j0 < mI ? Mr[j0] : (j0 < mI + NL ? Lr[j0 - mI] : 0.f)) * sp[q];
-            xb = (j1 < mI ? Mr[j1] : (j1 < mI + NL ? Lr[j1 - mI] : 0.f)) * sp[q + 1];
-          }
-          float a0, a1, ar, a2, b0_, b1, br, b2;
-          split_grid(xa, a0, a1, ar, a2);
-          split_grid(xb, b0_, b1, br, b2);
-          w0[j] = h2(a0, b0_);
-          w1[j] = h2(a1, b1);
-          w2[j] = h2(a2, b2);
-          wr[j] = h2(ar, br);
-        }
-        const uint32_t col = tmem + lanef + CF::XBASE + s * CF::XST + hf * 8;
-        st8(col, w0);
-        st8(col + KCA / 2, w1);
-        st8(col + KCA, w2);
-        st8(col + 3 * (KCA / 2), wr);
-        wait_st();
-        tc::fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&xfull[s]);
+      for (int a = 0; a < 4; ++a) {
+        const uint4 lo = __ldg(p + (4 * a + 2 * hf) * TTA), hi = __ldg(p + (4 * a + 2 * hf + 1) * TTA);
+        r[a][0] = lo.x; r[a][1] = lo.y; r[a][2] = lo.z; r[a][3] = lo.w;
+        r[a][4] = hi.x; r[a][5] = hi.y; r[a][6] = hi.z; r[a][7] = hi.w;
       }
+    };
+    auto put = [&](int g, const uint32_t (&r)[4][8]) -> bool {
+      const int s = g % NXS;
+      if (g >= NXS && !__all_sync(0xffffffffu, wait(&xfree[s], ((g / NXS) - 1) & 1))) return false;
+      const uint32_t col = tmem + lanef + CF::XBASE + s * CF::XST + hf * 8;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) st8(col + a * (KCA / 2), r[a]);
+      wait_st();
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&xfull[s]);
+      return true;
+    };
+    uint32_t ra[4][8], rb[4][8];
+    if (G > 0) fetch(0, ra);
+    for (int g = 0; g < G; g += 2) {
+      if (g + 1 < G) fetch(g + 1, rb);
+      if (!put(g, ra) || g + 1 >= G) break;
+      if (g + 2 < G) fetch(g + 2, ra);
+      if (!put(g + 1, rb)) break;
     }
   } else {
     // ------------------------------------------------ epilogue (lane = TOA)
@@ -516,13 +616,6 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
-__device__ __forceinline__ void split_w(float v, float& v0, float& rh, float& rl) {
-  v0 = __fsub_rn(__fadd_rn(v, 1610612736.f), 1610612736.f);
-  const float r = __fsub_rn(v, v0);
-  rh = f16r(r);
-  rl = __fsub_rn(r, rh);
-}
-
 __global__ void __launch_bounds__(416, 1)
     k_f16_ftw(DevModel m, const float* __restrict__ wres, const float* __restrict__ wmx, float* __restrict__ gpart,
               int32_t* __restrict__ stat, int B) {
@@ -535,9 +628,7 @@ __global__ void __launch_bounds__(416, 1)
   const int qc = blockIdx.x, cb = blockIdx.y, u = blockIdx.z, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int I = m.unit_psr[u], start = m.unit_start[u], len = m.unit_len[u], nst = len / KWB;
   const int b0 = cb * 128, nvalid = min(128, B - b0);
-  const int q0 = qc * QWB, qw = min(QWB, m.P - q0), NQ = round_up_d(qw, 16);
-  // column exponent: |F| <= 1 (achromatic), <= the largest DM weight (DM columns)
-  const int cdm = exp_up(m.wmaxp[I]);
+  const int q0 = qc * QWB, qw = min(QWB, m.P - q0), NQ = round_up_hd(qw, 16);
 
   if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
   if (tid == 0) {
@@ -584,11 +675,11 @@ __global__ void __launch_bounds__(416, 1)
           const uint32_t a0 = wa + 8 * ks, ah = a0 + KWB / 2, al = a0 + KWB;
           const uint32_t acc = (g | ks) ? 1u : 0u;
           mma_ts(tmem + FW_D0, a0, bx[0], ID, acc);  // L0 = W0 X0
-          mma_ts(tmem + FW_DR, a0, bx[1], ID, acc);  // rest
+          mma_ts(tmem + FW_DR, a0, bx[1], ID, acc);  // rest: W0 X1 + Wh X0 + W0 X2 + Wh X1 + Wl X0
           mma_ts(tmem + FW_DR, ah, bx[0], ID, 1u);
           mma_ts(tmem + FW_DR, a0, bx[2], ID, 1u);
-          mma_ts(tmem + FW_DR, al, bx[0], ID, 1u);
           mma_ts(tmem + FW_DR, ah, bx[1], ID, 1u);
+          mma_ts(tmem + FW_DR, al, bx[0], ID, 1u);
         }
         tc::commit(&wfree[s]);
         tc::commit(&xfree[s]);
@@ -604,7 +695,7 @@ __global__ void __launch_bounds__(416, 1)
     const uint32_t lanef = (uint32_t)(32 * qwp) << 16;
     const bool valid = n < nvalid;
     const int ew = valid ? exp_up(wmx[(size_t)u * B + b0 + n]) : 0;
-    const float wsc = pow2f(13 - ew);
+    const float wsc = pow2f(12 - ew);  // |w~| < 2^ew: scaled below 2^12
     const float* wrow = wres + (size_t)(valid ? b0 + n : 0) * m.ntoa_pad + start;
     // w~ rows stream in through cp.async, NSB stages ahead; each thread copies and reads
     // only its own chain's row, so its own wait_group orders them
@@ -649,9 +740,9 @@ __global__ void __launch_bounds__(416, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&wfull[s]);
     }
-    // ghat rows of this unit and column chunk
+    // ghat rows of this unit and column chunk: undo 2^(12 - ew) and 2^(14 - c_q)
     asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy in flight at exit
-    const float sa = pow2f(ew - 26), sd = pow2f(ew + cdm - 26);  // undo the w~ and column scales
+    const int* ce = m.x16_cexp + (size_t)I * m.x16_kxm + q0;
     if (ok && __all_sync(0xffffffffu, wait(&dfull, 0))) {
       tc::fence_after();
       for (int c0 = 0; c0 < NQ; c0 += 16) {
@@ -663,60 +754,46 @@ __global__ void __launch_bounds__(416, 1)
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int q = c0 + j;
-            if (q < qw)
-              dst[q] = __fadd_rn(__uint_as_float(l0[j]), __uint_as_float(lr[j])) * (q0 + q >= 2 * m.na ? sd : sa);
+            if (q < qw) dst[q] = __fadd_rn(__uint_as_float(l0[j]), __uint_as_float(lr[j])) * pow2f(ew + ce[q] - 26);
           }
         }
       }
     }
   } else {
-    // ------------------------------------------------ basis chunk into shared memory (MN-major)
-    const int gw = warp - 5;  // 8 warps; lane = TOA of the stage
-    const int na2 = 2 * m.na, P = m.P;
-    const float fa = 8192.f, fd = pow2f(13 - cdm);  // |sin|, |cos| <= 1; DM columns <= 2^cdm
-    for (int g = 0; g < nst; ++g) {
-      const int s = g % NSB;
-      if (g >= NSB && !__all_sync(0xffffffffu, wait(&xfree[s], ((g / NSB) - 1) & 1))) break;
-      const int ta = start + g * KWB + lane;
-      const uint64_t U = m.phase[ta];
-      const float wd = m.chrom[ta] * fd;
-      float s1, c1;
-      sincos_turns64(U, &s1, &c1);
-      unsigned char* xs = smem + s * FW_XST;
-      for (int grp = gw; grp < NQ / 8; grp += 8) {
-        float v0[8], vh[8], vl[8];
-        float sn = 0.f, cs = 1.f;
-        int kprev = -8;
+    // ------------------------------------------------ stored basis rows into shared memory (MN-major)
+    // 8 warps; lane = TOA of the stage; one 16-byte row (8 columns) of a piece per
+    // cp.async.  Stage g + NSB - 1 is requested while stage g lands.
+    const int gw = warp - 5;
+    const int tau0 = (start - m.toa_off[I]) / TTA, nch = kx_of(m, I) / KCA;
+    const uint4* xb = reinterpret_cast<const uint4*>(m.x16 + m.x16_off[I]);
+    auto issue = [&](int g) -> bool {
+      if (g < nst) {
+        const int s = g % NSB;
+        if (g >= NSB && !__all_sync(0xffffffffu, wait(&xfree[s], ((g / NSB) - 1) & 1))) return false;
+        const int toa = g * KWB + lane;  // TOA of the unit
+        const size_t blk = ((size_t)(tau0 + toa / TTA) * nch) * (XCW / 4) + (toa % TTA);
+        unsigned char* xs = smem + s * FW_XST;
+        for (int grp = gw; grp < NQ / 8; grp += 8) {
+          const int q = q0 + 8 * grp, c = q / KCA, r8 = (q % KCA) / 8;
+          const uint4* src = xb + blk + (size_t)c * (XCW / 4);
+          const int off = grp * ((KWB / 8) * 128) + (lane >> 3) * 128 + (lane & 7) * 16;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int q = q0 + 8 * grp + 2 * j;  // warp-uniform
-          float xa = 0.f, xb = 0.f;
-          if (q < P) {
-            const bool dm = q >= na2;
-            const int k = dm ? (q - na2) / 2 + 1 : q / 2 + 1;
-            if (j == 0 || k != kprev + 1)
-              sincos_turns64(U * (uint64_t)k, &sn, &cs);
-            else
-              rotate(sn, cs, s1, c1);
-            kprev = k;
-            const float f = dm ? wd : fa;
-            xa = sn * f;
-            xb = cs * f;
-          }
-          split_w(xa, v0[2 * j], vh[2 * j], vl[2 * j]);
-          split_w(xb, v0[2 * j + 1], vh[2 * j + 1], vl[2 * j + 1]);
+          for (int a = 0; a < 3; ++a) cp_async16(xs + a * FW_XARR + off, src + (4 * a + r8) * TTA);
         }
-        const int off = grp * ((KWB / 8) * 128) + (lane >> 3) * 128 + (lane & 7) * 16;
-        *reinterpret_cast<uint4*>(xs + off) = make_uint4(h2(v0[0], v0[1]), h2(v0[2], v0[3]), h2(v0[4], v0[5]), h2(v0[6], v0[7]));
-        *reinterpret_cast<uint4*>(xs + FW_XARR + off) =
-            make_uint4(h2(vh[0], vh[1]), h2(vh[2], vh[3]), h2(vh[4], vh[5]), h2(vh[6], vh[7]));
-        *reinterpret_cast<uint4*>(xs + 2 * FW_XARR + off) =
-            make_uint4(h2(vl[0], vl[1]), h2(vl[2], vl[3]), h2(vl[4], vl[5]), h2(vl[6], vl[7]));
       }
+      cp_async_commit();
+      return true;
+    };
+    bool ok = true;
+    for (int g = 0; g < NSB - 1; ++g) issue(g);
+    for (int g = 0; g < nst && ok; ++g) {
+      ok = issue(g + NSB - 1);
+      asm volatile("cp.async.wait_group %0;" ::"n"(NSB - 1) : "memory");  // stage g has landed
       tc::fence_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&xfull[s]);
+      if (lane == 0) mbar_arrive(&xfull[g % NSB]);
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy in flight at exit
   }
   tc::fence_before();
   __syncthreads();
@@ -729,8 +806,7 @@ __global__ void __launch_bounds__(416, 1)
 
 template <int NC>
 size_t res_smem(const DevModel& m) {
-  return 4 * (size_t)m.PM * NC * 2 + sizeof(float) * round_up(m.PM, 2) + 4 * NC * (sizeof(double) + sizeof(float)) +
-         NC * sizeof(int);
+  return 4 * (size_t)m.PM * NC * 2 + 4 * NC * (sizeof(double) + sizeof(float)) + NC * sizeof(float);
 }
 
 // chains per CTA of k_f16_res: 64 when the coefficient block fits in shared memory
@@ -739,13 +815,13 @@ int res_nc(const DevModel& m) { return res_smem<64>(m) <= 200 * 1024 ? 64 : 32; 
 template <int NC>
 cudaError_t launch_f16_nc(const DevModel& m, const Scratch& s, int B, cudaStream_t st) {
   const int nCB = (B + NC - 1) / NC;
-  k_f16_pack<NC><<<dim3(m.npsr, nCB), 256, sizeof(float) * m.PM, st>>>(m, s.a32, s.c16, s.spf, s.yexp, B, nCB);
+  k_f16_pack<NC><<<dim3(m.npsr, nCB), 256, sizeof(double) * m.x16_kxm, st>>>(m, s.a64, s.c16, s.yexp, B, nCB);
   const size_t sm = res_smem<NC>(m);
   if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(k_f16_res<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   float* w = m.cw ? s.cwwt : s.wres;
-  k_f16_res<NC><<<dim3(m.n_units, nCB), 448, sm, st>>>(m, s.c16, s.spf, s.yexp, w, s.wmx, s.c2part, s.stat,
+  k_f16_res<NC><<<dim3(nCB, m.n_units), 448, sm, st>>>(m, s.c16, s.yexp, w, s.wmx, s.c2part, s.stat,
                                                       m.cw ? s.cwsig : nullptr, B, nCB);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -758,21 +834,64 @@ cudaError_t launch_f16_nc(const DevModel& m, const Scratch& s, int B, cudaStream
 
 }  // namespace
 
-// The exact levels need K = P + m + n_low <= 480 columns per tile (2 K 2^14 < 2^24 quanta
-// with margin) and the coefficient block of 32 chains in shared memory.
-bool f16_supported(const DevModel& m) { return res_smem<32>(m) <= 227 * 1024 && m.PM <= 480; }
+// The exact levels need at most 512 basis columns per pulsar (2 K 2^14 <= 2^24 quanta),
+// the timing-model projection at most 128 columns (its shared-memory cache) and the
+// coefficient block of 32 chains in shared memory.
+bool f16_supported(const DevModel& m) {
+  return m.P + (m.cw ? m.m_max : 0) <= 512 && m.m_max <= 128 && res_smem<32>(m) <= 227 * 1024;
+}
 
 size_t f16_pack_bytes(const DevModel& m, int cap) {
   const int nc = res_nc(m), nCB = (cap + nc - 1) / nc;
   return (size_t)m.npsr * nCB * 4 * m.PM * nc * 2;
 }
-size_t f16_scale_floats(const DevModel& m, int cap) {
-  const int nc = res_nc(m), nCB = (cap + nc - 1) / nc;
-  return (size_t)m.npsr * nCB * m.PM;
+
+// The stored basis, built once per model: per-pulsar word offsets, column maxima
+// (pass 1), column exponents and the pieces (pass 2).  Sets m.x16, m.x16_off,
+// m.x16_cexp and m.x16_kxm; the device allocations are appended to `allocs`.
+cudaError_t build_f16_basis(DevModel& m, const std::vector<int>& n_pad, const std::vector<int>& mI,
+                            std::vector<void*>& allocs) {
+  int kxm = KCA;
+  std::vector<long long> off(m.npsr);
+  long long words = 0;
+  for (int I = 0; I < m.npsr; ++I) {
+    const int kx = kx_cols(m.P, mI[I], m.cw);
+    kxm = std::max(kxm, kx);
+    off[I] = words;
+    words += (long long)(n_pad[I] / TTA) * (kx / KCA) * XCW;
+  }
+  uint32_t* img = nullptr;
+  long long* doff = nullptr;
+  int* cexp = nullptr;
+  unsigned long long* cmax = nullptr;
+  cudaError_t e = cudaMalloc(&img, sizeof(uint32_t) * std::max<long long>(words, 4));
+  if (e == cudaSuccess) allocs.push_back(img);
+  if (e == cudaSuccess && (e = cudaMalloc(&doff, sizeof(long long) * m.npsr)) == cudaSuccess) allocs.push_back(doff);
+  if (e == cudaSuccess && (e = cudaMalloc(&cexp, sizeof(int) * (size_t)m.npsr * kxm)) == cudaSuccess)
+    allocs.push_back(cexp);
+  if (e == cudaSuccess) e = cudaMalloc(&cmax, sizeof(unsigned long long) * (size_t)m.npsr * kxm);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(doff, off.data(), sizeof(long long) * m.npsr, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(cmax, 0, sizeof(unsigned long long) * (size_t)m.npsr * kxm);
+  if (e == cudaSuccess) e = cudaMemset(cexp, 0, sizeof(int) * (size_t)m.npsr * kxm);
+  if (e == cudaSuccess) {
+    m.x16_off = doff;
+    m.x16_kxm = kxm;
+    const dim3 grid(m.n_units, kxm / KCA);
+    k_f16_colmax<<<grid, 128>>>(m, cmax, kxm);
+    k_f16_image<<<grid, 128>>>(m, cmax, kxm, img, cexp);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  cudaFree(cmax);
+  if (e != cudaSuccess) return e;
+  m.x16 = img;
+  m.x16_cexp = cexp;
+  return cudaSuccess;
 }
 
 cudaError_t launch_toa_f16(const DevModel& m, const Scratch& s, int B, cudaStream_t st) {
-  if (!f16_supported(m) || !s.c16 || !s.spf || !s.yexp || !s.wmx || (!m.cw && !s.wres)) return cudaErrorInvalidValue;
+  if (!f16_supported(m) || !m.x16 || !s.c16 || !s.yexp || !s.wmx || (!m.cw && !s.wres)) return cudaErrorInvalidValue;
   return res_nc(m) == 64 ? launch_f16_nc<64>(m, s, B, st) : launch_f16_nc<32>(m, s, B, st);
 }
 

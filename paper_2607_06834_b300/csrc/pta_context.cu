@@ -101,7 +101,7 @@ int pta_create(pta_ctx** out, const pta_model_desc* d) {
   if (d->n_gwb < 0 || d->n_rn < 0 || d->n_dm < 0 || (d->n_gwb == 0 && d->n_rn == 0) ||
       d->n_gwb > 512 || d->n_rn > 512 || d->n_dm > 512)
     return PTA_EINVAL;
-  if (d->precision < PTA_PREC_FP64 || d->precision > PTA_PREC_F16X6) return PTA_EINVAL;
+  if (d->precision < PTA_PREC_FP64 || d->precision > PTA_PREC_F16SPLIT) return PTA_EINVAL;
   if (d->precision == PTA_PREC_GRAM && d->cw) return PTA_EINVAL;
   if (d->spectrum < 0 || d->spectrum > (PTA_FREE_GWB | PTA_FREE_RN)) return PTA_EINVAL;
   pta_ctx* c = new (std::nothrow) pta_ctx();
@@ -279,6 +279,7 @@ int pta_finalize(pta_ctx* c, void* stream) {
   std::vector<double> LK(lkoff, 0.0), KI(lkoff, 0.0), H(hoff, 0.0), aref((size_t)npsr * m.P, 0.0), pos(3 * npsr),
       dist(npsr);
   std::vector<float> Hhi(hoff, 0.f), Hlo(hoff, 0.f);
+  std::vector<double> kih(hoff, 0.0);  // (M^T N^-1 M)^-1 H^T per pulsar [m_I x P]
   const int P4 = (m.P + 3) & ~3;
   std::vector<float> Gth((size_t)npsr * m.P * P4, 0.f), Gtl((size_t)npsr * m.P * P4, 0.f);
   std::vector<double> gg2((size_t)npsr * m.P, 0.0), cc2(npsr, 0.0);
@@ -408,6 +409,7 @@ int pta_finalize(pta_ctx* c, void* stream) {
       kinv(col);
       for (int j = 0; j < mI; ++j) KiH[(size_t)j * P + q] = col[j];
     }
+    std::copy(KiH.begin(), KiH.end(), kih.begin() + h_off[I]);
     std::vector<double> A((size_t)P * P), rhs(P);
     for (int q = 0; q < P; ++q) {
       double s2 = g[q];
@@ -507,20 +509,6 @@ int pta_finalize(pta_ctx* c, void* stream) {
     }
   }
 
-  // per pulsar: largest |M| and |F~_lo| per column and the largest chromatic weight over
-  // its TOAs (scales of the exact-split tensor-core path)
-  std::vector<float> colmaxf((size_t)npsr * (m_max + m.NL), 0.f), wmaxp(npsr, 0.f);
-  for (int I = 0; I < npsr; ++I) {
-    const int n = c->psrs[I].n, mI = mm[I];
-    float* cm = &colmaxf[(size_t)I * (m_max + m.NL)];
-    for (int i = 0; i < n; ++i) {
-      for (int j = 0; j < mI; ++j) cm[j] = std::fmax(cm[j], std::fabs(M32[m_off[I] + (long long)i * mI + j]));
-      for (int j = 0; j < m.NL; ++j)
-        cm[m_max + j] = std::fmax(cm[m_max + j], std::fabs(Flo[flo_off[I] + (long long)i * m.NL + j]));
-      wmaxp[I] = std::fmax(wmaxp[I], chrom[toa_off[I] + i]);
-    }
-  }
-
   int rc;
 #define UP(vec, field)                                  \
   if ((rc = upload(c, vec, &m.field)) != PTA_OK) return rc;
@@ -583,8 +571,7 @@ int pta_finalize(pta_ctx* c, void* stream) {
     UP(tm, trimap);
   }
   UP(nuw64, chrom64);
-  UP(colmaxf, colmaxf);
-  UP(wmaxp, wmaxp);
+  UP(kih, KiH);
 #undef UP
   c->finalized = true;
   (void)stream;
@@ -602,7 +589,7 @@ void free_scratch(pta::Scratch& s) {
                   s.cwbs, s.cwwt, s.cwgp, s.cwg, s.x0, s.g0, s.p, s.lp0, s.xs, s.gs, s.lps,
                   s.step, s.imass, s.kin0, s.hmc_ctr, s.acc, s.a16, s.queue, s.us, s.curnW, s.curnAhat,
                   s.curnV, s.curnLd, s.curnQ, s.dlnrc, s.curnG0, s.curnV2, s.cwwt2,
-                  s.chi2b, s.zeros, s.c16, s.spf, s.yexp, s.wres, s.wmx};
+                  s.chi2b, s.zeros, s.c16, s.yexp, s.wres, s.wmx};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   s = pta::Scratch{};
@@ -618,7 +605,7 @@ int ensure_scratch(pta_ctx* c, int B, bool fp64) {
   pta::Scratch& s = c->sc;
   const pta::DevModel& m = c->dm;
   const bool curn = m.curn != 0;
-  const bool f16 = c->precision == PTA_PREC_F16X6;
+  const bool f16 = c->precision == PTA_PREC_F16SPLIT;
   if (B <= s.cap && (!fp64 || s.gpart64) && (!curn || s.curnW) && (!f16 || s.c16)) return PTA_OK;
   const int cap = std::max(B, s.cap);
   cudaDeviceSynchronize();
@@ -671,7 +658,6 @@ int ensure_scratch(pta_ctx* c, int B, bool fp64) {
   AL(queue, 1);
   if (f16) {
     AL(c16, pta::f16_pack_bytes(m, cap));
-    AL(spf, pta::f16_scale_floats(m, cap));
     AL(yexp, np * cap);
     if (!m.cw) AL(wres, (size_t)cap * m.ntoa_pad);
     AL(wmx, (size_t)m.n_units * cap);
@@ -775,7 +761,8 @@ int pta_eval_scratch(pta_ctx* c, const pta::Scratch& s, int B, const float* x, d
     if (e == cudaSuccess) e = pta::launch_reduce(m, s0, B, 0, st);
   }
   if (e == cudaSuccess && m.curn) e = pta::launch_curn_forward(m, s, B, x, st);
-  if (e == cudaSuccess && !gram) e = pta::launch_tm_prologue(m, s, B, fp64, st);
+  if (e == cudaSuccess && !gram)
+    e = pta::launch_tm_prologue(m, s, B, fp64 ? 1 : (c->precision == PTA_PREC_F16SPLIT ? 2 : 0), st);
   tm.end(pta::count_prior_forward(m) + (gram ? 0 : 1) + (m.cw ? 2 : 0) + (m.curn && m.cw ? 4 : 0));
   tm.begin(1);
   if (e == cudaSuccess && gram) {
@@ -787,7 +774,7 @@ int pta_eval_scratch(pta_ctx* c, const pta::Scratch& s, int B, const float* x, d
       e = pta::launch_toa_tc(m, s, B, c->precision == PTA_PREC_TF32X3 ? 3 : 1, st);
     else if (c->precision == PTA_PREC_BF16X3)
       e = pta::launch_toa_bf16(m, s, B, st);
-    else if (c->precision == PTA_PREC_F16X6)
+    else if (c->precision == PTA_PREC_F16SPLIT)
       e = pta::launch_toa_f16(m, s, B, st);
     else
       e = pta::launch_toa_fp32_cfg(m, s, B, c->toa_cfg, st);
@@ -849,6 +836,20 @@ static int ensure_bf16(pta_ctx* c) {
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(c, PTA_ECUDA, std::string("BF16 basis build: ") + cudaGetErrorString(e));
   m.xmlo = p;
+  return PTA_OK;
+}
+
+// Stored basis of the exact-split fp16 tensor-core path, built on its first evaluation.
+static int ensure_f16(pta_ctx* c) {
+  pta::DevModel& m = c->dm;
+  if (m.x16) return PTA_OK;
+  std::vector<int> n_pad(m.npsr), mI(m.npsr);
+  for (int I = 0; I < m.npsr; ++I) {
+    n_pad[I] = pta::round_up(c->psrs[I].n, pta::kTile);
+    mI[I] = c->psrs[I].m;
+  }
+  cudaError_t e = pta::build_f16_basis(m, n_pad, mI, c->dev_allocs);
+  if (e != cudaSuccess) return fail(c, PTA_ECUDA, std::string("fp16 basis build: ") + cudaGetErrorString(e));
   return PTA_OK;
 }
 
@@ -917,6 +918,7 @@ int pta_prepare_internal(pta_ctx* c, int B) {
   if (rc != PTA_OK) return rc;
   if (fp64) rc = ensure_f64(c);
   if (rc == PTA_OK && c->precision == PTA_PREC_BF16X3) rc = ensure_bf16(c);
+  if (rc == PTA_OK && c->precision == PTA_PREC_F16SPLIT) rc = ensure_f16(c);
   return rc;
 }
 
@@ -933,10 +935,10 @@ int pta_set_precision(pta_ctx* c, int precision) {
   if (!c) return PTA_EINVAL;
   if (precision != PTA_PREC_FP64 && precision != PTA_PREC_FP32 && precision != PTA_PREC_TF32X3 &&
       precision != PTA_PREC_TF32 && precision != PTA_PREC_BF16X3 && precision != PTA_PREC_GRAM &&
-      precision != PTA_PREC_F16X6)
+      precision != PTA_PREC_F16SPLIT)
     return fail(c, PTA_EINVAL, "precision mode not available in this build");
-  if (precision == PTA_PREC_F16X6 && c->finalized && !pta::f16_supported(c->dm))
-    return fail(c, PTA_EINVAL, "exact-split tensor-core path needs P + m_max + 2 (low bins) <= 480");
+  if (precision == PTA_PREC_F16SPLIT && c->finalized && !pta::f16_supported(c->dm))
+    return fail(c, PTA_EINVAL, "exact-split tensor-core path needs P (+ m_max with a signal) <= 512 and m_max <= 128");
   if (precision == PTA_PREC_GRAM && c->dm.cw)
     return fail(c, PTA_EINVAL, "the Gram form has no deterministic signal: use a TOA-form mode with CW");
   if (precision == PTA_PREC_BF16X3 && c->finalized && !pta::bf16_supported(c->dm))

@@ -98,9 +98,13 @@ struct DevModel {
                                 // (element (i', l') = G~[P-1-i'][P-1-l']), P (P + 1) / 2 each
   const double* gt;             // [npsr][P] F^T N~^-1 dt (FP64)
   const double* ga;             // [npsr][P] G~ a_ref (mean with the deterministic signal)
-  // exact-split fp16 tensor-core path (PTA_PREC_F16X6)
-  const float* colmaxf;         // [npsr][m_max + NL] max |.| over the pulsar's TOAs of M and F~_lo columns
-  const float* wmaxp;           // [npsr] largest chromatic weight (nu_ref/nu)^2 of the pulsar
+  // exact-split fp16 tensor-core path (PTA_PREC_F16SPLIT)
+  const double* KiH;            // (M^T N^-1 M)^-1 H^T per pulsar [m_I x P] FP64, offsets h_off
+  // exact-split fp16 tensor-core path: the stored basis pieces (built on first use)
+  const uint32_t* x16;          // pieces; pulsar I's start at word x16_off[I]
+  const long long* x16_off;
+  const int* x16_cexp;          // [npsr][x16_kxm] column exponents c_q: |column q| < 2^c_q
+  int x16_kxm;                  // stored columns per pulsar, largest (row length of x16_cexp)
 };
 
 // Scratch sized for a batch of up to `cap` chains.
@@ -161,7 +165,6 @@ struct Scratch {
   float* zeros = nullptr;      // [ntoa_pad] zero residual for the auxiliary pass
   // exact-split fp16 tensor-core path (allocated when it is selected)
   unsigned char* c16 = nullptr; // [npsr][chain blocks] 4 fp16 pieces of the scaled coefficients
-  float* spf = nullptr;         // [npsr][chain blocks][PM] basis column factors
   int* yexp = nullptr;          // [npsr][cap] exponent of F a per chain
   float* wres = nullptr;        // [cap][ntoa_pad] whitened projected residual w~
   float* wmx = nullptr;         // [units][cap] max |w~| of the unit
@@ -188,7 +191,8 @@ cudaError_t launch_toa_bf16(const DevModel& m, const Scratch& s, int B, cudaStre
 cudaError_t launch_gram(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
 bool f16_supported(const DevModel& m);
 size_t f16_pack_bytes(const DevModel& m, int cap);
-size_t f16_scale_floats(const DevModel& m, int cap);
+cudaError_t build_f16_basis(DevModel& m, const std::vector<int>& n_pad, const std::vector<int>& mI,
+                            std::vector<void*>& allocs);
 cudaError_t launch_toa_f16(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
 size_t cw_const_bytes();
 cudaError_t launch_cw_forward(const DevModel& m, const Scratch& s, int B, const float* x, cudaStream_t st);

@@ -1,4 +1,4 @@
-"""GPU parity of the exact-split fp16 tensor-core path (PTA_PREC_F16X6) against the FP64
+"""GPU parity of the exact-split fp16 tensor-core path (PTA_PREC_F16SPLIT) against the FP64
 oracle, held to the FP32 bar: |dlogp| <= 1e-3 nats at near-posterior points (the
 CURN-conditional draw of the coefficients, Eq. PTA_standard_transform_curn) and
 relative gradient-norm error <= 1e-4; at prior-random points, where chi2 is orders of
@@ -50,10 +50,10 @@ def test_tiny_1000_points():
     X = synth.make_points(arr, 1000, seed=6834)
     X[:16] = np.array([O.curn_point(orc, x.astype(np.float64), 1.0, seed=i) for i, x in enumerate(X[:16])])
     lo, go = _oracle(orc, X)
-    lp, g, st = _eval(_engine(arr, "f16x6"), X)
+    lp, g, st = _eval(_engine(arr, "f16split"), X)
     assert np.all(st == 0)
     err = np.abs(lp - lo)
-    print(f"tiny f16x6: max |dlogp| near {err[:16].max():.2e}, random {err[16:].max():.2e}; "
+    print(f"tiny f16split: max |dlogp| near {err[:16].max():.2e}, random {err[16:].max():.2e}; "
           f"max grad rel {_grad_rel(g, go).max():.2e}")
     assert err[:16].max() < LOGP_ABS
     assert np.all(err <= LOGP_ABS + REL_RANDOM * np.abs(lo))
@@ -71,12 +71,12 @@ def test_ragged_arrays(kw, B):
     X[:6] = np.array([O.curn_point(orc, x.astype(np.float64), 1.0, seed=i) for i, x in enumerate(X[:6])])
     sample = list(range(6)) + [B // 2, 64, B - 1]
     lo, go = _oracle(orc, X[sample])
-    eng = _engine(arr, "f16x6")
+    eng = _engine(arr, "f16split")
     lp, g, st = _eval(eng, X)
     assert np.all(st == 0)
     err = np.abs(lp[sample] - lo)
     rel = _grad_rel(g[sample], go)
-    print(f"f16x6 ragged B={B}: max |dlogp| near {err[:6].max():.2e} random {err[6:].max():.2e}; "
+    print(f"f16split ragged B={B}: max |dlogp| near {err[:6].max():.2e} random {err[6:].max():.2e}; "
           f"max grad rel {rel.max():.2e}")
     assert err[:6].max() < LOGP_ABS
     assert np.all(err <= LOGP_ABS + REL_RANDOM * np.abs(lo))
@@ -95,14 +95,14 @@ def test_ng15_batch256_sampled():
     near = [5 + 16 * j for j in range(16)]
     for j, i in enumerate(near):
         X[i] = O.curn_point(orc, X[i].astype(np.float64), 1.0, seed=j)
-    eng = _engine(arr, "f16x6")
+    eng = _engine(arr, "f16split")
     lp, g, st = _eval(eng, X)
     assert np.all(st == 0)
     sample = [0, 77, 255] + near
     lo, go = _oracle(orc, X[sample])
     err = np.abs(lp[sample] - lo)
     rel = _grad_rel(g[sample], go)
-    print(f"f16x6 ng15: 16 near-posterior chains: max |dlogp| {err[3:].max():.2e}, max grad rel "
+    print(f"f16split ng15: 16 near-posterior chains: max |dlogp| {err[3:].max():.2e}, max grad rel "
           f"{rel[3:].max():.2e}; random: {err[:3].max():.2e} at |logp| {np.abs(lo[:3]).max():.3g}")
     assert err[3:].max() < LOGP_ABS
     assert np.all(err[:3] <= LOGP_ABS + REL_RANDOM * np.abs(lo[:3]))

@@ -291,9 +291,9 @@ def test_tensor_core_paths_against_simt(ng15):
 
 
 # ------------------------------------------------------------------ continuous-wave signal
-def _cw_check(arr, orc, X, near):
+def _cw_check(arr, orc, X, near, prec="fp32"):
     lo, go = _oracle(orc, X)
-    eng = _engine(arr, "fp32")
+    eng = _engine(arr, prec)
     lp, g, st = _eval(eng, X)
     assert np.all(st == 0)
     c = orc.lay["th_cw"]
@@ -301,7 +301,7 @@ def _cw_check(arr, orc, X, near):
         err = abs(lp[i] - lo[i])
         rel = _grad_rel(g[i], go[i])
         relcw = _grad_rel(g[i, c:], go[i, c:])
-        print(f"cw chain {i}: logp {lo[i]:.3f} |d| {err:.2e} grad rel {rel:.2e} cw-block rel {relcw:.2e}")
+        print(f"cw {prec} chain {i}: logp {lo[i]:.3f} |d| {err:.2e} grad rel {rel:.2e} cw-block rel {relcw:.2e}")
         if i in near:
             assert err < LOGP_ABS
         else:
@@ -309,7 +309,8 @@ def _cw_check(arr, orc, X, near):
         assert rel < GRAD_REL and relcw < GRAD_REL
 
 
-def test_cw_small_array():
+@pytest.mark.parametrize("prec", ["fp32", "f16split"])
+def test_cw_small_array(prec):
     arr = synth.small_array(npsr=3, ntoa=[150, 700, 2300], m=[3, 9, 12], n_gwb=4, n_rn=5, n_dm=3, seed=41,
                             nbackend=2, cw=True)
     orc = O.Oracle(arr)
@@ -317,10 +318,11 @@ def test_cw_small_array():
     near = [0, 1, 2]
     for i in near:
         X[i] = O.curn_point(orc, X[i].astype(np.float64), 1.0, seed=i)
-    _cw_check(arr, orc, X, near)
+    _cw_check(arr, orc, X, near, prec)
 
 
-def test_cw_ng15_sampled():
+@pytest.mark.parametrize("prec", ["fp32", "f16split"])
+def test_cw_ng15_sampled(prec):
     """Config with the 67-pulsar array plus a circular binary (64-chain batch sampled):
     16 near-posterior chains (the coefficients' conditional draw given the binary) held
     to the absolute bar, 2 prior-random ones to the relative bound."""
@@ -330,7 +332,7 @@ def test_cw_ng15_sampled():
     near = [2 + 4 * j for j in range(16)]
     for j, i in enumerate(near):
         X[i] = O.curn_point(orc, X[i].astype(np.float64), 1.0, seed=4 + j)
-    eng = _engine(arr, "fp32")
+    eng = _engine(arr, prec)
     lp, g, st = _eval(eng, X)
     assert np.all(st == 0)
     errs, rels = [], []
@@ -344,7 +346,8 @@ def test_cw_ng15_sampled():
         if i in near:
             errs.append(err)
             rels.append(rel)
-    print(f"ng15 cw: {len(near)} near-posterior chains: max |dlogp| {max(errs):.2e}, max grad rel {max(rels):.2e}")
+    print(f"ng15 cw {prec}: {len(near)} near-posterior chains: max |dlogp| {max(errs):.2e}, "
+          f"max grad rel {max(rels):.2e}")
 
 
 # ------------------------------------------------------------------ edge cases
