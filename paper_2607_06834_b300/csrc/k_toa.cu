@@ -116,12 +116,12 @@ __global__ void __launch_bounds__(128)
     }
   }
   __syncthreads();
-  if (fp64) {
-    // FP64 rows in place: [da | c] for the FP64 path; [da | c_s] for the exact-split
-    // tensor-core path, whose basis is fully projected (c_s only with a signal)
+  if (fp64 == 1) {
     for (int p = tid; p < P; p += 128) row[p] = da[p];
-    if (fp64 == 1 || cwbs)
-      for (int j = tid; j < mI; j += 128) row[P + j] = cv[j];
+    for (int j = tid; j < mI; j += 128) row[P + j] = cv[j];
+  } else if (fp64 == 2) {
+    // exact-split tensor-core path (fully projected basis): a stays in place, c_s follows
+    for (int j = tid; j < mI; j += 128) row[P + j] = cv[j];
   } else {
     // FP32 packed row [da (low columns zero) | c | da of the low columns | 0]
     float* r32 = a32 + ((size_t)I * B + b) * m.PM;

@@ -50,6 +50,8 @@
 //
 // Every mbarrier wait is bounded; a wait that gives up marks the CTA's chains with
 // status bit 4 and the CTA drains its own MMAs before it frees tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
 #include "pta_internal.cuh"
@@ -60,7 +62,9 @@ namespace {
 
 constexpr int TTA = 128;                  // TOAs per tile in k_f16_res (MMA M) and per stored basis tile
 constexpr int KCA = 32;                   // basis columns per chunk
-constexpr int XCW = 4 * (KCA / 2) * TTA;  // 32-bit words of one stored (tile, chunk): 4 pieces
+constexpr int KCB = 16;                   // basis columns per stored block (one MMA K step)
+constexpr int XBW = 4 * (KCB / 2) * TTA;  // 32-bit words of one stored (tile, column block): 4 pieces
+constexpr int RES_XSB = XBW * 4;          // bytes of one stored block (16 KB)
 constexpr int KWB = 32;                   // TOAs per stage in k_f16_ftw
 constexpr int QWB = 144;                  // basis columns per chunk in k_f16_ftw (MMA N)
 constexpr int NSB = 4;                    // stages in k_f16_ftw
@@ -79,11 +83,6 @@ __device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t b, uint3
       "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d),
       "r"(a), "l"(b), "r"(idesc), "r"(acc));
 }
-__device__ __forceinline__ void st8(uint32_t taddr, const uint32_t (&r)[8]) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
-               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
-               : "memory");
-}
 __device__ __forceinline__ void st16(uint32_t taddr, const uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
@@ -91,6 +90,22 @@ __device__ __forceinline__ void st16(uint32_t taddr, const uint32_t (&r)[16]) {
       "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
       "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
       : "memory");
+}
+// 32 lanes x 16 columns of 32-bit values, completion awaited by wait_ld
+__device__ __forceinline__ void ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// ties registers written by ld16_nw to a point after wait_ld, so that no use of them is
+// scheduled before the wait
+template <int N>
+__device__ __forceinline__ void after_wait(uint32_t (&r)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) asm volatile("" : "+r"(r[i]));
 }
 __device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 // 32 lanes x 16 columns of 32-bit values (waits for completion)
@@ -183,14 +198,15 @@ __device__ __forceinline__ int kx_of(const DevModel& m, int I) { return kx_cols(
 
 // ---------------------------------------------------------------------------
 // Stored basis.  Pulsar I's pieces start at word x16_off[I]; its tile tau (TOAs
-// 128 tau .. 128 tau + 127 of the pulsar) and chunk c (columns 32 c .. 32 c + 31) form
-// one block of XCW words at x16_off[I] + (tau nch + c) XCW.  Inside it, piece a, TOA t
-// and word j (columns 32 c + 2 j (low half) and 32 c + 2 j + 1 (high half)) is word
-//   ((4 a + j / 4) 128 + t) 4 + j % 4:
-// the 4 words of 8 consecutive columns are one 16-byte row per TOA, and a warp's 32 TOAs
-// of one such row are 512 contiguous bytes.  Word j of a piece lands in tensor-memory
-// column j of that piece's block (the A-operand layout of kind::f16), and the 16-byte
-// rows are the core-matrix rows of the MN-major B operand of k_f16_ftw.
+// 128 tau .. 128 tau + 127 of the pulsar) and column block kc (columns 16 kc ..
+// 16 kc + 15) form one block of XBW words (16 KB) at x16_off[I] + (tau nkc + kc) XBW.
+// Inside it, piece a, 8-column half h, TOA t and word w (columns 16 kc + 8 h + 2 w (low
+// half) and + 1 (high half)) is word  ((2 a + h) 128 + t) 4 + w:  one 16-byte row per
+// (piece, half, TOA).  Piece a of a block is then the K-major, unswizzled A operand of
+// one M = 128, K = 16 MMA in shared memory as it stands (8 x 16-byte core matrices,
+// 128 bytes between 8-TOA groups, 2048 bytes between the two 8-column halves), and the
+// 16-byte rows of 32 consecutive TOAs (512 bytes) are the core-matrix rows of the
+// MN-major B operand of k_f16_ftw.
 // ---------------------------------------------------------------------------
 
 // Column q of pulsar I's stored basis at padded TOA ta (FP64).  F~ = F - M K^-1 H^T for
@@ -277,10 +293,10 @@ __global__ void __launch_bounds__(128)
     if (u == m.unit0[I]) cexp[(size_t)I * kxm + KCA * c + t] = e;
   }
   __syncthreads();
-  const int tau0 = (start - m.toa_off[I]) / TTA;
+  const int tau0 = (start - m.toa_off[I]) / TTA, nkc = nch * (KCA / KCB);
   for (int i = 0; i < len / TTA; ++i) {
     const int ta = start + i * TTA + t;
-    uint4* dst = reinterpret_cast<uint4*>(img + m.x16_off[I] + ((size_t)(tau0 + i) * nch + c) * XCW) + t;
+    uint4* dst = reinterpret_cast<uint4*>(img + m.x16_off[I] + (size_t)(tau0 + i) * nkc * XBW) + t;
 #pragma unroll 1
     for (int g = 0; g < KCA / 8; ++g) {  // 8 columns: one 16-byte row per piece
       uint32_t w[4][4];
@@ -297,63 +313,92 @@ __global__ void __launch_bounds__(128)
         w[2][jj] = h2(a2, b2);
         w[3][jj] = h2(a3, b3);
       }
+      const int kc = (KCA * c + 8 * g) / KCB, h = g & 1;
 #pragma unroll
-      for (int a = 0; a < 4; ++a) dst[(4 * a + g) * TTA] = make_uint4(w[a][0], w[a][1], w[a][2], w[a][3]);
+      for (int a = 0; a < 4; ++a)
+        dst[(size_t)kc * (XBW / 4) + (2 * a + h) * TTA] = make_uint4(w[a][0], w[a][1], w[a][2], w[a][3]);
     }
   }
 }
 
 // ---------------------------------------------------------------------------
 // Pack: per (pulsar, block of NC chains) the chain exponents and the four fp16 pieces
-// of the scaled coefficients in the MMA's K-major layout: element (chain n, column k) of
-// piece a at a PM NC 2 + (k/8) NC 16 + (n/8) 128 + (n%8) 16 + (k%8) 2 bytes.  The rows
-// are the FP64 coefficient rows [a - a_ref | c_s] of the prior stage.  Stored basis
-// column q carries 2^(14 - c_q), so coefficient q carries 2^c_q, and each chain row is
-// normalised to 2^14 by its own exponent E_n (y = L 2^(E_n - 28)).
+// of the scaled coefficients as one K-major B operand of 4 NC rows, the pieces stacked
+// along N (row a NC + n is piece a of chain n): element (row r, column k) at
+// (k/8) 4 NC 16 + (r/8) 128 + (r%8) 16 + (k%8) 2 bytes.  Rows [0, j NC) are then the
+// pieces c0 .. c(j-1), so one MMA with A = X_i and N = (4 - i) NC forms X_i c0 ..
+// X_i c(3-i) at once.  Coefficient q is a_q - a_ref,q for q < P and, with a signal,
+// the FP64 c_s that k_tm_prologue wrote after them.  Stored basis column q carries
+// 2^(14 - c_q), so coefficient q carries 2^c_q, and each chain row is normalised to
+// 2^14 by its own exponent E_n (y = L 2^(E_n - 28)).  The FP64 value is carried as an
+// unevaluated float pair and cut with FP32 operations (B300's FP64 rate is 1/64 of FP32).
 // ---------------------------------------------------------------------------
+
+// hi + lo (|hi| <= 2^14, |lo| <= ulp(hi) / 2) = v0 + v1 + v2 + v3: v0, v1 on the 2^7 and
+// 2^-1 grids (from hi alone, so |v0| <= 2^14 and |v1| <= 2^6 as in the exact split), v2 on
+// the 2^-9 grid, v3 the rest; every step is exact except the one rounding that adds lo
+// (2^-26 of 2^-2, far below v3's fp16 rounding)
+__device__ __forceinline__ void split4_ff(float hi, float lo, float& v0, float& v1, float& v2, float& v3) {
+  v0 = __fsub_rn(__fadd_rn(hi, 1610612736.f), 1610612736.f);  // 1.5 x 2^30: ulp 2^7
+  float r = __fsub_rn(hi, v0);
+  v1 = __fsub_rn(__fadd_rn(r, 6291456.f), 6291456.f);         // 1.5 x 2^22: ulp 2^-1
+  r = __fadd_rn(__fsub_rn(r, v1), lo);
+  v2 = __fsub_rn(__fadd_rn(r, 24576.f), 24576.f);             // 1.5 x 2^14: ulp 2^-9
+  v3 = __fsub_rn(r, v2);
+}
+
 template <int NC>
 __global__ void __launch_bounds__(256)
     k_f16_pack(DevModel m, const double* __restrict__ a64, unsigned char* __restrict__ c16, int* __restrict__ yexp,
                int B, int nCB) {
-  extern __shared__ double cf[];  // [KX] 2^c_q
-  __shared__ double s_f[NC];      // 2^(14 - E_n)
+  extern __shared__ int ce[];  // [KX] column exponents c_q
+  __shared__ int s_e[NC];
   const int I = blockIdx.x, cb = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int b0 = cb * NC, nvalid = min(NC, B - b0), KX = kx_of(m, I), PM = m.PM;
-  const int ncol = m.P + (m.cw ? m.m[I] : 0);  // columns with coefficients; the rest of the chunk is 0
+  const int b0 = cb * NC, nvalid = min(NC, B - b0), KX = kx_of(m, I), PM = m.PM, P = m.P, KXM = m.x16_kxm;
+  const int ncol = P + (m.cw ? m.m[I] : 0);  // columns with coefficients; the rest of the block is 0
   const double* rows = a64 + ((size_t)I * B + b0) * PM;
-  for (int q = tid; q < KX; q += 256) cf[q] = ldexp(1.0, m.x16_cexp[(size_t)I * m.x16_kxm + q]);
+  const double* ar = m.aref + (size_t)I * P;
+  for (int q = tid; q < KX; q += 256) ce[q] = m.x16_cexp[(size_t)I * KXM + q];
   __syncthreads();
-  // per-chain exponent of max_q |C_nq 2^c_q| (one warp per chain)
+  auto coef = [&](int n, int q) -> double { return q < P ? rows[(size_t)n * PM + q] - ar[q] : rows[(size_t)n * PM + q]; };
+  // per-chain exponent of max_q |C_nq 2^c_q| (one warp per chain).  The FP32 rounding of
+  // |C| can only raise the maximum to the next power of two, which keeps |v| < 2^14.
   for (int n = warp; n < NC; n += 8) {
-    double mx = 0.0;
+    float mx = 0.f;
     if (n < nvalid)
-      for (int q = lane; q < ncol; q += 32) mx = fmax(mx, fabs(rows[(size_t)n * PM + q]) * cf[q]);
-    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      for (int q = lane; q < ncol; q += 32) mx = fmaxf(mx, fabsf((float)coef(n, q)) * pow2f(ce[q]));
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) {
-      const int e = exp_up64(mx);
-      s_f[n] = ldexp(1.0, 14 - e);
-      if (n < nvalid) yexp[(size_t)I * B + b0 + n] = e - 28;
+      s_e[n] = exp_up(mx);
+      if (n < nvalid) yexp[(size_t)I * B + b0 + n] = exp_up(mx) - 28;
     }
   }
   __syncthreads();
-  unsigned char* out = c16 + ((size_t)I * nCB + cb) * 4 * (size_t)PM * NC * 2;
-  const size_t asz = (size_t)PM * NC * 2;
+  unsigned char* out = c16 + ((size_t)I * nCB + cb) * 4 * (size_t)KXM * NC * 2;
+  constexpr int PS = NC * 16;  // bytes between the pieces' row blocks within one K group
   for (int e = tid; e < NC * (KX / 8); e += 256) {
     const int n = e % NC, g = e / NC;  // consecutive threads: consecutive chains
     float c0[8], c1[8], c2[8], c3[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int q = 8 * g + i;
-      const double v = (n < nvalid && q < ncol) ? rows[(size_t)n * PM + q] * cf[q] * s_f[n] : 0.0;
-      split4(v, c0[i], c1[i], c2[i], c3[i]);
+      float hi = 0.f, lo = 0.f;
+      if (n < nvalid && q < ncol) {
+        const double d = coef(n, q);
+        const float sc = pow2f(ce[q] + 14 - s_e[n]);  // exact: a power of two
+        hi = (float)d;
+        lo = (float)(d - (double)hi) * sc;
+        hi *= sc;
+      }
+      split4_ff(hi, lo, c0[i], c1[i], c2[i], c3[i]);
     }
-    const size_t off = (size_t)g * NC * 16 + (n >> 3) * 128 + (n & 7) * 16;
+    const size_t off = (size_t)g * 4 * NC * 16 + (n >> 3) * 128 + (n & 7) * 16;
     *reinterpret_cast<uint4*>(out + off) = make_uint4(h2(c0[0], c0[1]), h2(c0[2], c0[3]), h2(c0[4], c0[5]), h2(c0[6], c0[7]));
-    *reinterpret_cast<uint4*>(out + asz + off) =
+    *reinterpret_cast<uint4*>(out + PS + off) =
         make_uint4(h2(c1[0], c1[1]), h2(c1[2], c1[3]), h2(c1[4], c1[5]), h2(c1[6], c1[7]));
-    *reinterpret_cast<uint4*>(out + 2 * asz + off) =
+    *reinterpret_cast<uint4*>(out + 2 * PS + off) =
         make_uint4(h2(c2[0], c2[1]), h2(c2[2], c2[3]), h2(c2[4], c2[5]), h2(c2[6], c2[7]));
-    *reinterpret_cast<uint4*>(out + 3 * asz + off) =
+    *reinterpret_cast<uint4*>(out + 3 * PS + off) =
         make_uint4(h2(c3[0], c3[1]), h2(c3[2], c3[3]), h2(c3[4], c3[5]), h2(c3[6], c3[7]));
   }
 }
@@ -361,22 +406,27 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------------
 // k_f16_res
 // ---------------------------------------------------------------------------
+constexpr int RES_NXS = 4;             // shared-memory stages of stored basis blocks
+constexpr int RES_THREADS = 320;       // warp 0 MMA, warp 1 copies, warps 2-9 epilogue
+constexpr int RES_EPI0 = 64;           // first epilogue thread
+
+// Accumulator blocks (NC columns each) of one tile: after every K step
+//   block 0 = X0 c0 (L0, exact), block 1 = X0 c1 + X1 c0 (L1, exact),
+//   block 2 = X0 c2 + X1 c1 + X2 c0, block 3 = X0 c3 + X1 c2 + X2 c1 + X3 c0 (L2 = 2 + 3),
+// from four MMAs: A = X_i, B = the first 4 - i pieces, D = blocks i .. 3.
 template <int NC>
 struct ResCfg {
-  static constexpr int DB = 3 * NC;                // tensor-memory columns of one accumulator set
-  static constexpr int XBASE = 2 * DB;             // first basis-chunk column
-  static constexpr int XST = 4 * (KCA / 2);        // columns of one basis chunk (4 pieces)
-  static constexpr int NXS = (512 - XBASE) / XST;  // basis-chunk stages
-  static_assert(NXS >= 2, "tensor memory");
+  static constexpr int DB = 4 * NC;  // tensor-memory columns of one accumulator set (double-buffered)
+  static_assert(2 * DB <= 512, "tensor memory");
 };
 
 template <int NC>
-__global__ void __launch_bounds__(448, 1)
+__global__ void __launch_bounds__(RES_THREADS, 1)
     k_f16_res(DevModel m, const unsigned char* __restrict__ c16, const int* __restrict__ yexp,
               float* __restrict__ wres, float* __restrict__ wmx, double* __restrict__ c2part,
               int32_t* __restrict__ stat, const float* __restrict__ cwsig, int B, int nCB) {
   using CF = ResCfg<NC>;
-  constexpr int NXS = CF::NXS;
+  constexpr int NXS = RES_NXS;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t cfull, xfull[NXS], xfree[NXS], dfull[2], dempty[2], drain;
   __shared__ uint32_t tmem_base;
@@ -384,24 +434,25 @@ __global__ void __launch_bounds__(448, 1)
   // chain block fastest: the blocks of one unit run together and share its basis in L2
   const int cb = blockIdx.x, u = blockIdx.y, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int I = m.unit_psr[u], start = m.unit_start[u], len = m.unit_len[u];
-  const int PM = m.PM, KX = kx_of(m, I), nch = KX / KCA, ntile = len / TTA;
+  const int KXM = m.x16_kxm, KX = kx_of(m, I), nkc = KX / KCB, ntile = len / TTA, G = ntile * nkc;
   const int b0 = cb * NC, nvalid = min(NC, B - b0);
-  const size_t asz = (size_t)PM * NC * 2;
-  unsigned char* Cs = smem;                                        // 4 pieces x PM x NC fp16
-  double* redc = reinterpret_cast<double*>(smem + 4 * asz);        // [4][NC] chi2 partials
-  float* redm = reinterpret_cast<float*>(redc + 4 * NC);           // [4][NC] max |w|
-  float* ysc = redm + 4 * NC;                                      // [NC] 2^(exponent of y) per chain
+  const size_t csz = 4 * (size_t)KXM * NC * 2;
+  unsigned char* Xs = smem;                                         // NXS stored blocks (16 KB each)
+  unsigned char* Cs = smem + NXS * RES_XSB;                         // 4 NC rows x KXM fp16 (pieces stacked)
+  double* redc = reinterpret_cast<double*>(Cs + csz);               // [8][NC/2] chi2 partials
+  float* redm = reinterpret_cast<float*>(redc + 4 * NC);            // [8][NC/2] max |w|
+  float* ysc = redm + 4 * NC;                                       // [NC] 2^(exponent of y) per chain
 
-  if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 2 * CF::DB <= 256 ? 256 : 512);
   if (tid == 0) {
     tc::mbar_init(&cfull, 1);
     for (int s = 0; s < NXS; ++s) {
-      tc::mbar_init(&xfull[s], 8);
+      tc::mbar_init(&xfull[s], 1);
       tc::mbar_init(&xfree[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&dfull[b], 1);
-      tc::mbar_init(&dempty[b], 4);
+      tc::mbar_init(&dempty[b], 8);
     }
     tc::mbar_init(&drain, 1);
     s_bad = 0;
@@ -422,40 +473,24 @@ __global__ void __launch_bounds__(448, 1)
   if (warp == 0) {
     // ------------------------------------------------ MMA issue (lane 0)
     if (lane == 0) {
-      constexpr uint32_t ID = idesc_f16(TTA, NC, 0);
       bool ok = wait(&cfull, 0);
       if (ok) tc::fence_after();
-      const uint32_t cbase = tc::smem_u32(Cs);
+      const uint32_t cbase = tc::smem_u32(Cs), xbase = tc::smem_u32(Xs);
       int g = 0;
       for (int i = 0; i < ntile && ok; ++i) {
         const int buf = i & 1;
         if (i >= 2 && !(ok = wait(&dempty[buf], ((i >> 1) - 1) & 1))) break;
         tc::fence_after();
-        const uint32_t d0 = tmem + buf * CF::DB, d1 = d0 + NC, d2 = d0 + 2 * NC;
-        for (int c = 0; c < nch; ++c, ++g) {
+        const uint32_t dbase = tmem + buf * CF::DB;
+        for (int kc = 0; kc < nkc; ++kc, ++g) {
           const int s = g % NXS;
           if (!(ok = wait(&xfull[s], (g / NXS) & 1))) break;
           tc::fence_after();
-          const uint32_t xa = tmem + CF::XBASE + s * CF::XST;
+          const uint64_t cd = tc::desc(cbase + kc * 2 * (4 * NC * 16), 4 * NC * 16, 128);
 #pragma unroll
-          for (int ks = 0; ks < KCA / 16; ++ks) {
-            const uint32_t kg = (uint32_t)(c * (KCA / 8) + 2 * ks);
-            uint64_t bd[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) bd[a] = tc::desc(cbase + a * (uint32_t)asz + kg * NC * 16, NC * 16, 128);
-            const uint32_t x0 = xa + 8 * ks, x1 = x0 + KCA / 2, x2 = x0 + KCA, x3 = x0 + 3 * (KCA / 2);
-            const uint32_t acc = (c | ks) ? 1u : 0u;
-            mma_ts(d0, x0, bd[0], ID, acc);  // L0 = X0 C0
-            mma_ts(d1, x1, bd[0], ID, acc);  // L1 = X1 C0 + X0 C1
-            mma_ts(d1, x0, bd[1], ID, 1u);
-            mma_ts(d2, x2, bd[0], ID, acc);  // L2: the 2^-16 and 2^-24 terms
-            mma_ts(d2, x1, bd[1], ID, 1u);
-            mma_ts(d2, x0, bd[2], ID, 1u);
-            mma_ts(d2, x3, bd[0], ID, 1u);
-            mma_ts(d2, x0, bd[3], ID, 1u);
-            mma_ts(d2, x2, bd[1], ID, 1u);
-            mma_ts(d2, x1, bd[2], ID, 1u);
-          }
+          for (int a = 0; a < 4; ++a)
+            tc::mma_f16(dbase + a * NC, tc::desc(xbase + s * RES_XSB + a * (RES_XSB / 4), 2048, 128), cd,
+                        idesc_f16(TTA, (4 - a) * NC, 0), (kc | a) ? 1u : 0u);
           tc::commit(&xfree[s]);
         }
         if (!ok) break;
@@ -466,67 +501,45 @@ __global__ void __launch_bounds__(448, 1)
     }
     __syncwarp();
   } else if (warp == 1) {
-    // ------------------------------------------------ resident coefficient block
+    // ------------------------------------------------ bulk copies: coefficient block, basis blocks
     if (lane == 0) {
-      const unsigned char* src = c16 + ((size_t)I * nCB + cb) * 4 * asz;
-      const uint32_t bytes = (uint32_t)KX * NC * 2;
-      mbar_expect_tx(&cfull, 4 * bytes);
-      for (int a = 0; a < 4; ++a) bulk_g2s(Cs + a * asz, src + a * asz, bytes, &cfull);
-      if (!tc::mbar_wait(&cfull, 0, kDrainLimit)) s_bad = 1;  // landed before the CTA may exit
+      const unsigned char* src = c16 + ((size_t)I * nCB + cb) * csz;
+      const uint32_t bytes = (uint32_t)KX * 4 * NC * 2;  // the K groups this pulsar uses
+      mbar_expect_tx(&cfull, bytes);
+      bulk_g2s(Cs, src, bytes, &cfull);
+      // the unit's blocks are consecutive: (tile i, column block kc) is block i nkc + kc
+      const unsigned char* xsrc = reinterpret_cast<const unsigned char*>(
+          m.x16 + m.x16_off[I] + (size_t)((start - m.toa_off[I]) / TTA) * nkc * XBW);
+      int g = 0;
+      for (; g < G; ++g) {
+        const int s = g % NXS;
+        if (g >= NXS && !wait(&xfree[s], ((g / NXS) - 1) & 1)) break;
+        mbar_expect_tx(&xfull[s], RES_XSB);
+        bulk_g2s(Xs + s * RES_XSB, xsrc + (size_t)g * RES_XSB, RES_XSB, &xfull[s]);
+      }
+      // no copy in flight into this CTA's shared memory at exit (bounded waits)
+      if (!tc::mbar_wait(&cfull, 0, kDrainLimit)) s_bad = 1;
+      for (int h = max(0, g - NXS); h < g; ++h)
+        if (!tc::mbar_wait(&xfull[h % NXS], (h / NXS) & 1, kDrainLimit)) s_bad = 1;
     }
     __syncwarp();
-  } else if (warp < 10) {
-    // ------------------------------------------------ stored basis into tensor memory
-    // Warp (quarter qw, half hf): TOAs 32 qw .. 32 qw + 31, words 8 hf .. 8 hf + 7 of every
-    // piece (16-byte rows 2 hf and 2 hf + 1).  Chunk g + 1 is fetched into registers
-    // while chunk g is stored.
-    const int qw = warp & 3, hf = (warp - 2) >> 2, t = 32 * qw + lane;
-    const uint32_t lanef = (uint32_t)(32 * qw) << 16;
-    const int tau0 = (start - m.toa_off[I]) / TTA;
-    // (tile i, chunk c) of this unit is block i nch + c after the unit's first one
-    const uint4* xb = reinterpret_cast<const uint4*>(m.x16 + m.x16_off[I] + (size_t)tau0 * nch * XCW) + t;
-    const int G = ntile * nch;
-    auto fetch = [&](int g, uint32_t (&r)[4][8]) {
-      const uint4* p = xb + (size_t)g * (XCW / 4);
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const uint4 lo = __ldg(p + (4 * a + 2 * hf) * TTA), hi = __ldg(p + (4 * a + 2 * hf + 1) * TTA);
-        r[a][0] = lo.x; r[a][1] = lo.y; r[a][2] = lo.z; r[a][3] = lo.w;
-        r[a][4] = hi.x; r[a][5] = hi.y; r[a][6] = hi.z; r[a][7] = hi.w;
-      }
-    };
-    auto put = [&](int g, const uint32_t (&r)[4][8]) -> bool {
-      const int s = g % NXS;
-      if (g >= NXS && !__all_sync(0xffffffffu, wait(&xfree[s], ((g / NXS) - 1) & 1))) return false;
-      const uint32_t col = tmem + lanef + CF::XBASE + s * CF::XST + hf * 8;
-#pragma unroll
-      for (int a = 0; a < 4; ++a) st8(col + a * (KCA / 2), r[a]);
-      wait_st();
-      tc::fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&xfull[s]);
-      return true;
-    };
-    uint32_t ra[4][8], rb[4][8];
-    if (G > 0) fetch(0, ra);
-    for (int g = 0; g < G; g += 2) {
-      if (g + 1 < G) fetch(g + 1, rb);
-      if (!put(g, ra) || g + 1 >= G) break;
-      if (g + 2 < G) fetch(g + 2, ra);
-      if (!put(g + 1, rb)) break;
-    }
   } else {
     // ------------------------------------------------ epilogue (lane = TOA)
-    const int qe = warp & 3, t = 32 * qe + lane;
+    // Eight warps: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its 32 TOAs) and
+    // chains NH h .. NH h + NH - 1 of the block (h = (w - 2) / 4), 16 at a time.
+    constexpr int NH = NC / 2;
+    const int qe = warp & 3, hq = (warp - 2) >> 2, t = 32 * qe + lane, n0 = NH * hq;
     const uint32_t lanef = (uint32_t)(32 * qe) << 16;
     // per-warp partials in this warp's own slots of redc / redm (even lanes write)
-    double* myc = redc + qe * NC;
-    float* mym = redm + qe * NC;
-    for (int n = lane; n < NC; n += 32) {
+    double* myc = redc + (warp - 2) * NH;
+    float* mym = redm + (warp - 2) * NH;
+    for (int n = lane; n < NH; n += 32) {
       myc[n] = 0.0;
       mym[n] = 0.f;
     }
     __syncwarp();
+    double d64n = m.dt64[start + t];
+    float nin = m.ninv[start + t];
     for (int i = 0; i < ntile; ++i) {
       const int buf = i & 1;
       if (!__all_sync(0xffffffffu, wait(&dfull[buf], (i >> 1) & 1))) break;
@@ -535,25 +548,36 @@ __global__ void __launch_bounds__(448, 1)
       // dt'' as an unevaluated float pair: the residual dt'' - y is formed with
       // error-free sums from the exact level sums L0 and L1, so it is accurate to its
       // own size, not to the size of dt'' or y
-      const double d64 = m.dt64[ta];
-      const float dh = (float)d64, dl = (float)(d64 - (double)dh), ni = m.ninv[ta];
-      const uint32_t d0 = tmem + lanef + buf * CF::DB;
+      const double d64 = d64n;
+      const float dh = (float)d64, dl = (float)(d64 - (double)dh), ni = nin;
+      if (i + 1 < ntile) {  // the next tile's TOA data, in flight during this one
+        d64n = m.dt64[ta + TTA];
+        nin = m.ninv[ta + TTA];
+      }
+      const uint32_t d0 = tmem + lanef + buf * CF::DB + n0;
 #pragma unroll 1
-      for (int gq = 0; gq < NC / 16; ++gq) {
-        uint32_t l0[16], l1[16], l2[16];
-        ld16(d0 + 16 * gq, l0);
-        ld16(d0 + NC + 16 * gq, l1);
-        ld16(d0 + 2 * NC + 16 * gq, l2);
+      for (int gq = 0; gq < NH / 16; ++gq) {
+        uint32_t l0[16], l1[16], l2[16], l3[16];
+        ld16_nw(d0 + 16 * gq, l0);
+        ld16_nw(d0 + NC + 16 * gq, l1);
+        ld16_nw(d0 + 2 * NC + 16 * gq, l2);
+        ld16_nw(d0 + 3 * NC + 16 * gq, l3);
+        wait_ld();
+        after_wait(l0);
+        after_wait(l1);
+        after_wait(l2);
+        after_wait(l3);
         float ch[16], am[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const int n = 16 * gq + j;
+          const int nl = 16 * gq + j, n = n0 + nl;
           const int bb = b0 + n;
           const float sc = ysc[n];  // 2^(exponent of y): the products below are exact
           float ea, eb;
           const float a = two_sum(dh, -__uint_as_float(l0[j]) * sc, ea);
           const float b = two_sum(a, -__uint_as_float(l1[j]) * sc, eb);
-          float r = __fadd_rn(b, __fadd_rn(__fadd_rn(ea, eb), __fsub_rn(dl, __uint_as_float(l2[j]) * sc)));
+          const float l2s = __fadd_rn(__uint_as_float(l2[j]), __uint_as_float(l3[j]));
+          float r = __fadd_rn(b, __fadd_rn(__fadd_rn(ea, eb), __fsub_rn(dl, l2s * sc)));
           if (cwsig && n < nvalid) r -= cwsig[(size_t)bb * m.ntoa_pad + ta];
           const float w = r * ni;
           if (n < nvalid) wres[(size_t)bb * m.ntoa_pad + ta] = w;
@@ -584,11 +608,14 @@ __global__ void __launch_bounds__(448, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&dempty[buf]);
     }
-    // fixed-order combination of the four epilogue warps
-    named_bar(1, 128);
-    for (int n = tid - 320; n < nvalid; n += 128) {
-      c2part[(size_t)u * B + b0 + n] = ((redc[n] + redc[NC + n]) + redc[2 * NC + n]) + redc[3 * NC + n];
-      wmx[(size_t)u * B + b0 + n] = fmaxf(fmaxf(redm[n], redm[NC + n]), fmaxf(redm[2 * NC + n], redm[3 * NC + n]));
+    // fixed-order combination of the four warps of each chain half
+    named_bar(1, RES_THREADS - RES_EPI0);
+    for (int n = tid - RES_EPI0; n < nvalid; n += RES_THREADS - RES_EPI0) {
+      const int h = n / NH, j = n % NH;
+      const double* c = redc + 4 * h * NH + j;
+      const float* mm = redm + 4 * h * NH + j;
+      c2part[(size_t)u * B + b0 + n] = ((c[0] + c[NH]) + c[2 * NH]) + c[3 * NH];
+      wmx[(size_t)u * B + b0 + n] = fmaxf(fmaxf(mm[0], mm[NH]), fmaxf(mm[2 * NH], mm[3 * NH]));
     }
   }
   tc::fence_before();
@@ -596,9 +623,10 @@ __global__ void __launch_bounds__(448, 1)
   if (s_bad && tid < nvalid) atomicOr(&stat[b0 + tid], 4);
   if (warp == 0) {
     tc::fence_after();
-    tc::tmem_dealloc(tmem, 512);
+    tc::tmem_dealloc(tmem, 2 * CF::DB <= 256 ? 256 : 512);
   }
 }
+
 
 // ---------------------------------------------------------------------------
 // k_f16_ftw
@@ -607,20 +635,40 @@ constexpr int FW_D0 = 0, FW_DR = QWB, FW_WB = 2 * QWB;  // tensor-memory columns
 constexpr int FW_WST = 3 * (KWB / 2);                   // columns of one w~ stage (3 pieces)
 static_assert(FW_WB + NSB * FW_WST <= 512, "tensor memory");
 constexpr int FW_XARR = KWB * QWB * 2;                  // bytes of one basis piece per stage
-constexpr int FW_XST = 3 * FW_XARR;
-constexpr int FW_WROW = KWB + 4;                        // floats per staged w~ row (padded: no bank conflicts)
-constexpr int FW_SMEM = NSB * FW_XST + NSB * 128 * FW_WROW * 4;
+constexpr int FW_XST = 3 * FW_XARR;                     // one stage: pieces X0, X1, X2
+constexpr int FW_WSB = 128 * KWB * 4;                   // w~ stage: 128 chains x 32 TOAs (128-byte swizzled rows)
+constexpr int FW_SMEM = NSB * FW_XST + NSB * FW_WSB;
+constexpr int FW_THREADS = 192;                         // warp 0 MMA, warps 1-4 w~ and epilogue, warp 5 copies
+static_assert((NSB * FW_XST) % 1024 == 0, "swizzled w~ stages start on 1024-byte boundaries");
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+// TMA tile loads (tensor maps built on the host; coordinates innermost first)
+__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(tc::smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(tc::smem_u32(mbar))
+      : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void tma_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+                                       uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5, %6}], [%7];" ::"r"(tc::smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(tc::smem_u32(mbar))
+      : "memory");
+}
 
-__global__ void __launch_bounds__(416, 1)
-    k_f16_ftw(DevModel m, const float* __restrict__ wres, const float* __restrict__ wmx, float* __restrict__ gpart,
-              int32_t* __restrict__ stat, int B) {
+// Tensor maps: tw over w~ [chains][ntoa_pad] (FP32, box 32 TOAs x 128 chains, 128-byte
+// swizzle: 16-byte chunk j of chain row n sits at chunk j ^ (n % 8)); tx over the stored
+// basis as (8 halves, TOA 128, half h 2, block, piece a 4) with byte strides 16, 2048,
+// 16384, 4096 (box 8 x 32 x 2 x 9 x 3: one stage's X0, X1, X2 rows of 144 columns, in
+// the MN-major order [a][column group][TOA][8 columns]).
+__global__ void __launch_bounds__(FW_THREADS, 1)
+    k_f16_ftw(DevModel m, const __grid_constant__ CUtensorMap tw, const __grid_constant__ CUtensorMap tx,
+              const float* __restrict__ wmx, float* __restrict__ gpart, int32_t* __restrict__ stat, int B) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t wfull[NSB], xfull[NSB], wfree[NSB], xfree[NSB], dfull, drain;
+  __shared__ __align__(8) uint64_t wland[NSB], wread[NSB], wfull[NSB], wfree[NSB], xfull[NSB], xfree[NSB], dfull,
+      drain;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_bad;
   // column chunk fastest: the chunks of one (unit, chain block) run together and the
@@ -629,13 +677,16 @@ __global__ void __launch_bounds__(416, 1)
   const int I = m.unit_psr[u], start = m.unit_start[u], len = m.unit_len[u], nst = len / KWB;
   const int b0 = cb * 128, nvalid = min(128, B - b0);
   const int q0 = qc * QWB, qw = min(QWB, m.P - q0), NQ = round_up_hd(qw, 16);
+  unsigned char* wsm = smem + NSB * FW_XST;
 
   if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
   if (tid == 0) {
     for (int s = 0; s < NSB; ++s) {
+      tc::mbar_init(&wland[s], 1);
+      tc::mbar_init(&wread[s], 4);
       tc::mbar_init(&wfull[s], 4);
-      tc::mbar_init(&xfull[s], 8);
       tc::mbar_init(&wfree[s], 1);
+      tc::mbar_init(&xfull[s], 1);
       tc::mbar_init(&xfree[s], 1);
     }
     tc::mbar_init(&dfull, 1);
@@ -696,29 +747,16 @@ __global__ void __launch_bounds__(416, 1)
     const bool valid = n < nvalid;
     const int ew = valid ? exp_up(wmx[(size_t)u * B + b0 + n]) : 0;
     const float wsc = pow2f(12 - ew);  // |w~| < 2^ew: scaled below 2^12
-    const float* wrow = wres + (size_t)(valid ? b0 + n : 0) * m.ntoa_pad + start;
-    // w~ rows stream in through cp.async, NSB stages ahead; each thread copies and reads
-    // only its own chain's row, so its own wait_group orders them
-    float* wsm = reinterpret_cast<float*>(smem + NSB * FW_XST);
-    auto issue = [&](int g) {
-      if (valid && g < nst) {
-        float* dst = wsm + ((g % NSB) * 128 + n) * FW_WROW;
-#pragma unroll
-        for (int j = 0; j < KWB / 4; ++j) cp_async16(dst + 4 * j, wrow + g * KWB + 4 * j);
-      }
-      cp_async_commit();
-    };
-    for (int g = 0; g < NSB; ++g) issue(g);
     bool ok = true;
     for (int g = 0; g < nst; ++g) {
       const int s = g % NSB;
-      if (g >= NSB && !(ok = __all_sync(0xffffffffu, wait(&wfree[s], ((g / NSB) - 1) & 1)))) break;
-      asm volatile("cp.async.wait_group %0;" ::"n"(NSB - 1) : "memory");
-      const float* src = wsm + (s * 128 + n) * FW_WROW;
+      if (!(ok = __all_sync(0xffffffffu, wait(&wland[s], (g / NSB) & 1)))) break;
+      // row n of the swizzled stage: 16-byte chunk j at chunk j ^ (n % 8)
+      const unsigned char* row = wsm + s * FW_WSB + n * (KWB * 4);
       uint32_t p0[16], ph[16], pl[16];
 #pragma unroll
       for (int j = 0; j < KWB / 4; ++j) {
-        const float4 v = valid ? *reinterpret_cast<const float4*>(src + 4 * j) : make_float4(0, 0, 0, 0);
+        const float4 v = *reinterpret_cast<const float4*>(row + 16 * (j ^ (n & 7)));
         const float vv[4] = {v.x, v.y, v.z, v.w};
         float a0[4], ah[4], al[4];
 #pragma unroll
@@ -730,7 +768,9 @@ __global__ void __launch_bounds__(416, 1)
         pl[2 * j] = h2(al[0], al[1]);
         pl[2 * j + 1] = h2(al[2], al[3]);
       }
-      issue(g + NSB);  // into the buffer just read
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&wread[s]);  // the staged rows may be refilled
+      if (g >= NSB && !(ok = __all_sync(0xffffffffu, wait(&wfree[s], ((g / NSB) - 1) & 1)))) break;
       const uint32_t col = tmem + lanef + FW_WB + s * FW_WST;
       st16(col, p0);
       st16(col + KWB / 2, ph);
@@ -741,7 +781,6 @@ __global__ void __launch_bounds__(416, 1)
       if (lane == 0) mbar_arrive(&wfull[s]);
     }
     // ghat rows of this unit and column chunk: undo 2^(12 - ew) and 2^(14 - c_q)
-    asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy in flight at exit
     const int* ce = m.x16_cexp + (size_t)I * m.x16_kxm + q0;
     if (ok && __all_sync(0xffffffffu, wait(&dfull, 0))) {
       tc::fence_after();
@@ -759,41 +798,25 @@ __global__ void __launch_bounds__(416, 1)
         }
       }
     }
-  } else {
-    // ------------------------------------------------ stored basis rows into shared memory (MN-major)
-    // 8 warps; lane = TOA of the stage; one 16-byte row (8 columns) of a piece per
-    // cp.async.  Stage g + NSB - 1 is requested while stage g lands.
-    const int gw = warp - 5;
-    const int tau0 = (start - m.toa_off[I]) / TTA, nch = kx_of(m, I) / KCA;
-    const uint4* xb = reinterpret_cast<const uint4*>(m.x16 + m.x16_off[I]);
-    auto issue = [&](int g) -> bool {
-      if (g < nst) {
-        const int s = g % NSB;
-        if (g >= NSB && !__all_sync(0xffffffffu, wait(&xfree[s], ((g / NSB) - 1) & 1))) return false;
-        const int toa = g * KWB + lane;  // TOA of the unit
-        const size_t blk = ((size_t)(tau0 + toa / TTA) * nch) * (XCW / 4) + (toa % TTA);
-        unsigned char* xs = smem + s * FW_XST;
-        for (int grp = gw; grp < NQ / 8; grp += 8) {
-          const int q = q0 + 8 * grp, c = q / KCA, r8 = (q % KCA) / 8;
-          const uint4* src = xb + blk + (size_t)c * (XCW / 4);
-          const int off = grp * ((KWB / 8) * 128) + (lane >> 3) * 128 + (lane & 7) * 16;
-#pragma unroll
-          for (int a = 0; a < 3; ++a) cp_async16(xs + a * FW_XARR + off, src + (4 * a + r8) * TTA);
-        }
-      }
-      cp_async_commit();
-      return true;
-    };
-    bool ok = true;
-    for (int g = 0; g < NSB - 1; ++g) issue(g);
-    for (int g = 0; g < nst && ok; ++g) {
-      ok = issue(g + NSB - 1);
-      asm volatile("cp.async.wait_group %0;" ::"n"(NSB - 1) : "memory");  // stage g has landed
-      tc::fence_async_smem();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&xfull[g % NSB]);
+  } else if (lane == 0) {
+    // ------------------------------------------------ TMA: w~ rows and stored basis rows per stage
+    const int tau0 = (start - m.toa_off[I]) / TTA, nkc = kx_of(m, I) / KCB;
+    const int blk0 = (int)(m.x16_off[I] / XBW) + q0 / KCB;
+    int g = 0;
+    for (; g < nst; ++g) {
+      const int s = g % NSB;
+      if (g >= NSB && !(wait(&wread[s], ((g / NSB) - 1) & 1) && wait(&xfree[s], ((g / NSB) - 1) & 1))) break;
+      const int toa = g * KWB, tau = tau0 + toa / TTA, tsub = toa % TTA;
+      mbar_expect_tx(&wland[s], FW_WSB);
+      tma_2d(wsm + s * FW_WSB, &tw, start + toa, b0, &wland[s]);
+      mbar_expect_tx(&xfull[s], FW_XST);
+      tma_5d(smem + s * FW_XST, &tx, 0, tsub, 0, blk0 + tau * nkc, 0, &xfull[s]);
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy in flight at exit
+    // no copy in flight into this CTA's shared memory at exit (bounded waits)
+    for (int h = max(0, g - NSB); h < g; ++h) {
+      tc::mbar_wait(&wland[h % NSB], (h / NSB) & 1, kDrainLimit);
+      tc::mbar_wait(&xfull[h % NSB], (h / NSB) & 1, kDrainLimit);
+    }
   }
   tc::fence_before();
   __syncthreads();
@@ -804,31 +827,67 @@ __global__ void __launch_bounds__(416, 1)
   }
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
+using EncodeTiled = PFN_cuTensorMapEncodeTiled_v12000;
+EncodeTiled encode_tiled() {
+  static EncodeTiled fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  }
+  return fn;
+}
+
 template <int NC>
 size_t res_smem(const DevModel& m) {
-  return 4 * (size_t)m.PM * NC * 2 + 4 * NC * (sizeof(double) + sizeof(float)) + NC * sizeof(float);
+  return (size_t)RES_NXS * RES_XSB + 4 * (size_t)m.x16_kxm * NC * 2 + 4 * NC * (sizeof(double) + sizeof(float)) +
+         NC * sizeof(float);
 }
 
 // chains per CTA of k_f16_res: 64 when the coefficient block fits in shared memory
-int res_nc(const DevModel& m) { return res_smem<64>(m) <= 200 * 1024 ? 64 : 32; }
+int res_nc(const DevModel& m) { return res_smem<64>(m) <= 227 * 1024 ? 64 : 32; }
 
 template <int NC>
 cudaError_t launch_f16_nc(const DevModel& m, const Scratch& s, int B, cudaStream_t st) {
   const int nCB = (B + NC - 1) / NC;
-  k_f16_pack<NC><<<dim3(m.npsr, nCB), 256, sizeof(double) * m.x16_kxm, st>>>(m, s.a64, s.c16, s.yexp, B, nCB);
+  k_f16_pack<NC><<<dim3(m.npsr, nCB), 256, sizeof(int) * m.x16_kxm, st>>>(m, s.a64, s.c16, s.yexp, B, nCB);
   const size_t sm = res_smem<NC>(m);
   if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(k_f16_res<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   float* w = m.cw ? s.cwwt : s.wres;
-  k_f16_res<NC><<<dim3(nCB, m.n_units), 448, sm, st>>>(m, s.c16, s.yexp, w, s.wmx, s.c2part, s.stat,
-                                                      m.cw ? s.cwsig : nullptr, B, nCB);
+  k_f16_res<NC><<<dim3(nCB, m.n_units), RES_THREADS, sm, st>>>(m, s.c16, s.yexp, w, s.wmx, s.c2part, s.stat,
+                                                              m.cw ? s.cwsig : nullptr, B, nCB);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_f16_ftw, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_SMEM);
   if (e != cudaSuccess) return e;
-  k_f16_ftw<<<dim3((m.P + QWB - 1) / QWB, (B + 127) / 128, m.n_units), 416, FW_SMEM, st>>>(m, w, s.wmx, s.gpart,
-                                                                                           s.stat, B);
+  EncodeTiled enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap tw, tx;
+  {
+    const cuuint64_t dim[2] = {(cuuint64_t)m.ntoa_pad, (cuuint64_t)B};
+    const cuuint64_t stride[1] = {(cuuint64_t)m.ntoa_pad * 4};
+    const cuuint32_t box[2] = {KWB, 128}, es[2] = {1, 1};
+    if (enc(&tw, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, w, dim, stride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  {
+    const cuuint64_t dim[5] = {8, TTA, 2, (cuuint64_t)m.x16_blocks, 4};
+    const cuuint64_t stride[4] = {16, 2048, (cuuint64_t)RES_XSB, 4096};
+    const cuuint32_t box[5] = {8, KWB, 2, QWB / KCB, 3}, es[5] = {1, 1, 1, 1, 1};
+    if (enc(&tx, CU_TENSOR_MAP_DATA_TYPE_UINT16, 5, const_cast<uint32_t*>(m.x16), dim, stride, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  k_f16_ftw<<<dim3((m.P + QWB - 1) / QWB, (B + 127) / 128, m.n_units), FW_THREADS, FW_SMEM, st>>>(m, tw, tx, s.wmx,
+                                                                                                  s.gpart, s.stat, B);
   return cudaGetLastError();
 }
 
@@ -836,14 +895,19 @@ cudaError_t launch_f16_nc(const DevModel& m, const Scratch& s, int B, cudaStream
 
 // The exact levels need at most 512 basis columns per pulsar (2 K 2^14 <= 2^24 quanta),
 // the timing-model projection at most 128 columns (its shared-memory cache) and the
-// coefficient block of 32 chains in shared memory.
+// coefficient block of 32 chains in shared memory beside the basis stages.
 bool f16_supported(const DevModel& m) {
-  return m.P + (m.cw ? m.m_max : 0) <= 512 && m.m_max <= 128 && res_smem<32>(m) <= 227 * 1024;
+  const int kxm = round_up_hd(m.P + (m.cw ? m.m_max : 0), KCA);
+  DevModel t = m;
+  t.x16_kxm = kxm;
+  return m.P + (m.cw ? m.m_max : 0) <= 512 && m.m_max <= 128 && res_smem<32>(t) <= 227 * 1024;
 }
 
 size_t f16_pack_bytes(const DevModel& m, int cap) {
-  const int nc = res_nc(m), nCB = (cap + nc - 1) / nc;
-  return (size_t)m.npsr * nCB * 4 * m.PM * nc * 2;
+  DevModel t = m;
+  t.x16_kxm = round_up_hd(m.P + (m.cw ? m.m_max : 0), KCA);
+  const int nc = res_nc(t), nCB = (cap + nc - 1) / nc;
+  return (size_t)m.npsr * nCB * 4 * t.x16_kxm * nc * 2;
 }
 
 // The stored basis, built once per model: per-pulsar word offsets, column maxima
@@ -858,7 +922,7 @@ cudaError_t build_f16_basis(DevModel& m, const std::vector<int>& n_pad, const st
     const int kx = kx_cols(m.P, mI[I], m.cw);
     kxm = std::max(kxm, kx);
     off[I] = words;
-    words += (long long)(n_pad[I] / TTA) * (kx / KCA) * XCW;
+    words += (long long)(n_pad[I] / TTA) * (kx / KCB) * XBW;
   }
   uint32_t* img = nullptr;
   long long* doff = nullptr;
@@ -887,6 +951,7 @@ cudaError_t build_f16_basis(DevModel& m, const std::vector<int>& n_pad, const st
   if (e != cudaSuccess) return e;
   m.x16 = img;
   m.x16_cexp = cexp;
+  m.x16_blocks = words / XBW;
   return cudaSuccess;
 }
 

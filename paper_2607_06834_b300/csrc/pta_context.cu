@@ -761,9 +761,11 @@ int pta_eval_scratch(pta_ctx* c, const pta::Scratch& s, int B, const float* x, d
     if (e == cudaSuccess) e = pta::launch_reduce(m, s0, B, 0, st);
   }
   if (e == cudaSuccess && m.curn) e = pta::launch_curn_forward(m, s, B, x, st);
-  if (e == cudaSuccess && !gram)
-    e = pta::launch_tm_prologue(m, s, B, fp64 ? 1 : (c->precision == PTA_PREC_F16SPLIT ? 2 : 0), st);
-  tm.end(pta::count_prior_forward(m) + (gram ? 0 : 1) + (m.cw ? 2 : 0) + (m.curn && m.cw ? 4 : 0));
+  // the exact-split path reads a - a_ref itself; its prologue only adds the signal's c_s
+  const bool f16 = c->precision == PTA_PREC_F16SPLIT;
+  if (e == cudaSuccess && !gram && (!f16 || m.cw))
+    e = pta::launch_tm_prologue(m, s, B, fp64 ? 1 : (f16 ? 2 : 0), st);
+  tm.end(pta::count_prior_forward(m) + (gram || (f16 && !m.cw) ? 0 : 1) + (m.cw ? 2 : 0) + (m.curn && m.cw ? 4 : 0));
   tm.begin(1);
   if (e == cudaSuccess && gram) {
     e = pta::launch_gram(m, s, B, st);  // writes ghat and chi2 directly
@@ -779,7 +781,7 @@ int pta_eval_scratch(pta_ctx* c, const pta::Scratch& s, int B, const float* x, d
     else
       e = pta::launch_toa_fp32_cfg(m, s, B, c->toa_cfg, st);
   }
-  tm.end(1);
+  tm.end(f16 ? 3 : (c->precision == PTA_PREC_BF16X3 ? 2 : 1));  // pack + kernels
   tm.begin(2);
   if (e == cudaSuccess && !gram) e = pta::launch_reduce(m, s, B, fp64, st);
   tm.end(gram ? 0 : 1);

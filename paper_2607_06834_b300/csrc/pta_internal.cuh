@@ -105,6 +105,7 @@ struct DevModel {
   const long long* x16_off;
   const int* x16_cexp;          // [npsr][x16_kxm] column exponents c_q: |column q| < 2^c_q
   int x16_kxm;                  // stored columns per pulsar, largest (row length of x16_cexp)
+  long long x16_blocks;         // stored 16 KB blocks in all
 };
 
 // Scratch sized for a batch of up to `cap` chains.
