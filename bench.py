@@ -32,12 +32,15 @@ WORKLOAD = "ng15_b256"
 WORKLOAD_DESC = "NANOGrav-15-yr-like: 67 pulsars, 3.0e5 TOAs, RN 30 / DM 100 / HD-GWB 14 bins, 256 chains"
 METRIC = "logp+grad evals/s (all chains) at 67-psr size vs FP64 plain path; % roofline"
 DTYPE = {"fp32": "f32", "fp64": "f64", "tf32x3": "tf32x3", "tf32": "tf32", "bf16x3": "bf16x3",
-         "gram": "f32 (compensated)"}
+         "gram": "f32 (compensated)", "f16split": "f16 (exact split, f32 accumulate)"}
 DTYPE_DETAIL = {"fp32": "FP32 TOA contractions (SIMT)", "fp64": "FP64 TOA contractions (stored basis)",
                 "tf32x3": "3-term split TF32 tensor-core TOA contractions, FP32 accumulation",
                 "tf32": "single TF32 tensor-core TOA contractions, FP32 accumulation",
                 "bf16x3": "3-term split BF16 tensor-core TOA contractions, FP32 accumulation",
-                "gram": "Gram form: per-pulsar F^T N~^-1 F products in compensated FP32 (hi/lo, Dot2)"}
+                "gram": "Gram form: per-pulsar F^T N~^-1 F products in compensated FP32 (hi/lo, Dot2)",
+                "f16split": "exact-split fp16 tensor-core TOA contractions (tcgen05 kind::f16): stored projected "
+                            "basis and FP64 coefficients cut into 4 fp16 pieces, exact leading levels, "
+                            "10 MMAs per K step for F a and 6 for F^T w"}
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12     # SMs x 2 FP64 FMA/clk x 2 flop x max SM clock
 
@@ -45,16 +48,15 @@ FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12     # SMs x 2 FP64 FMA/clk x 2 f
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
 # kernel from one ncu capture, valid only while the kernel's sources are the ones
 # profiled (sha256 of each file); see profiles/.
-CAPTURED_TRAFFIC = {
-    ("fp32", 90): {"bytes": 99.4e6, "profile": "profiles/k_toa_simt_ng15_b256.md",
-                   "sources": {"k_toa.cu": "c8d87cf044a8314097a12141a102f2f6f1655504562fa633692ac1885ff3e7ed",
-                               "pta_internal.cuh": "6980f278b2d07f527a51f8b84b6aecf336252fc4f05fe8ed5ba6b76aa628bb97"}},
-}
+CAPTURED_TRAFFIC = {}
 
 
-def captured_traffic(precision, entry):
+def captured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` (dram__bytes_read.sum + dram__bytes_write.sum)
+    from one ncu capture, valid only while the kernel's source files are the ones
+    profiled (sha256 of each file); None otherwise."""
     import hashlib
-    rec = CAPTURED_TRAFFIC.get((precision, entry))
+    rec = CAPTURED_TRAFFIC.get(kernel)
     if rec is None:
         return None
     csrc = os.path.join(ROOT, "paper_2607_06834_b300", "csrc")
@@ -64,7 +66,7 @@ def captured_traffic(precision, entry):
                 return None
         except OSError:
             return None
-    return rec["bytes"]
+    return {"bytes_per_launch": rec["bytes"], "profile": rec["profile"]}
 
 
 def dist_env():
@@ -131,6 +133,34 @@ def toa_flops_per_launch(arr, B):
     na = max(arr.n_gwb, arr.n_rn)
     P = 2 * na + 2 * arr.n_dm
     return float(B * sum(2 * p.n * (2 * P + p.m) for p in arr.pulsars))
+
+
+def toa_flops_f16(arr, B):
+    """Algorithmic flops of the exact-split path's contractions per launch: F~ a and
+    F~^T w (2 n P each) per chain and pulsar, plus M c_s (2 n m) with a signal."""
+    na = max(arr.n_gwb, arr.n_rn)
+    P = 2 * na + 2 * arr.n_dm
+    return float(B * sum(2 * p.n * (2 * P + (p.m if arr.cw else 0)) for p in arr.pulsars))
+
+
+def toa_issued_f16(arr, B):
+    """Tensor flops the exact-split kernels issue per launch (launch shapes of
+    k_f16_res and k_f16_ftw): per 128-TOA tile, 16-column step and chain block of NC,
+    MMAs of N = 4, 3, 2, 1 x NC; per 32-TOA stage, 144-column chunk and 128 chains, six
+    MMAs of N = 144 (the last chunk rounded up to 16)."""
+    na = max(arr.n_gwb, arr.n_rn)
+    P = 2 * na + 2 * arr.n_dm
+    kxm = -(-(P + (max(p.m for p in arr.pulsars) if arr.cw else 0)) // 32) * 32
+    nc = 64 if 4 * 16384 + 4 * kxm * 64 * 2 + 64 * 16 <= 227 * 1024 else 32
+    res = ftw = 0.0
+    for p in arr.pulsars:
+        npad = -(-p.n // 128) * 128
+        kx = -(-(P + (p.m if arr.cw else 0)) // 32) * 32
+        res += (npad // 128) * (kx // 16) * 2.0 * 128 * 10 * nc * 16 * (-(-B // nc))
+        for q0 in range(0, P, 144):
+            nq = -(-min(144, P - q0) // 16) * 16
+            ftw += (npad // 32) * 2 * 6 * 2.0 * 128 * nq * 16 * (-(-B // 128))
+    return res + ftw
 
 
 def chol_flops_per_launch(arr, B):
@@ -204,26 +234,177 @@ def curn_variant(dev, steps):
     return out
 
 
-def cpu_baseline(arr, n_eval: int):
-    """The FP64 oracle, as it stands, on the host cores: logp + grad of n_eval chains."""
+def scale150_leg(dev, steps: int, peaks):
+    """The scale-up configuration: 150 pulsars, 1.0e6 TOAs (1k-30k per pulsar over up to
+    30 yr), 100 GWB / 30 red-noise / 150 DM bins (P = 500), 1024 chains in one call.
+    Evals/s of the exact-split path (headline mode) and the FP32 SIMT path, the plain
+    FP64 path on the same batch, stage and kernel times, the dominant kernel's roofline
+    and the end-to-end rate through host buffers.  L2 flushed between timed steps."""
+    import ctypes as C
+    import torch
+    from paper_2607_06834_b300 import abi, synth
+    from paper_2607_06834_b300.engine import Engine
+    arr = synth.make_array("scale150")
+    B = synth.WORKLOADS["scale150"]["chains"]
+    t0 = time.perf_counter()
+    eng = Engine(arr, precision="f16split")
+    setup_s = time.perf_counter() - t0
+    X = synth.make_points(arr, B, seed=6834 + 4)
+    x = torch.tensor(X, device=dev)
+    out = (torch.empty(B, dtype=torch.float64, device=dev), torch.empty_like(x),
+           torch.empty(B, dtype=torch.int32, device=dev))
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    rec = {"workload": "150 pulsars, 1.0e6 TOAs, GWB 100 / RN 30 / DM 150 bins (P = 500), 1024 chains",
+           "ntoa": arr.ntoa, "chains": B, "host_setup_s": setup_s}
+
+    def timed(prec, n):
+        eng.set_precision(prec)
+        for _ in range(2):
+            eng.logp_and_grad(x, out=out)
+        torch.cuda.synchronize()
+        assert int((out[2] != 0).sum()) == 0, "non-finite or out-of-prior chains in the scale-up batch"
+        abi.lib.pta_profile_enable(eng._h, 1)
+        abi.lib.pta_profile_read(eng._h, None, None, 1)
+        ev = []
+        for _ in range(n):
+            flush.zero_()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record()
+            eng.logp_and_grad(x, out=out)
+            a1.record()
+            ev.append((a0, a1))
+        torch.cuda.synchronize()
+        sm = (C.c_double * abi.NSTAGES)()
+        abi.lib.pta_profile_read(eng._h, sm, None, 1)
+        abi.lib.pta_profile_enable(eng._h, 0)
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        st = [v / n for v in sm]
+        return {"value": B / (ms * 1e-3), "unit": "evals/s", "ms_per_step": ms, "steps": n,
+                "stage_ms": dict(zip(abi.STAGES, [round(v, 3) for v in st])),
+                "kernel_ms": dict(zip(abi.KERNEL_TIMERS, [round(v, 3) for v in st[len(abi.STAGES):]]))}
+
+    n = max(3, min(steps, 5))
+    rec["f16split"] = timed("f16split", n)
+    rec["fp32"] = timed("fp32", n)
+    rec["fp64_plain_path"] = timed("fp64", 1)
+    rec["f16split_vs_fp64_plain_path"] = rec["f16split"]["value"] / rec["fp64_plain_path"]["value"]
+    # roofline of the dominant kernel in the headline mode
+    f = rec["f16split"]
+    kms = f["kernel_ms"]
+    dom = max(kms, key=kms.get)
+    if dom == "chol_forward":
+        flops = chol_flops_per_launch(arr, B)
+        rec["roofline"] = {"kernel": "k_chol_forward (FP64 150 x 150 Cholesky + inverse + transform, 30 dense bins)",
+                           "bound": "alu", "unit": "TFLOP/s", "achieved": flops / (kms[dom] * 1e-3) / 1e12,
+                           "peak": FP64_PEAK_TFLOPS,
+                           "peak_source": "derived: 148 SM x 2 FP64 FMA/clk x 2 flop x 2.032 GHz"}
+    else:
+        bf16 = (peaks or {}).get("bf16_tflops", 1800.0)
+        flops = toa_flops_f16(arr, B) / 2  # one of the two contractions per kernel
+        rec["roofline"] = {"kernel": {"toa_res": "k_f16_res", "toa_ftw": "k_f16_ftw"}[dom], "bound": "tensor",
+                           "unit": "TFLOP/s", "achieved": flops / (kms[dom] * 1e-3) / 1e12, "peak": bf16,
+                           "peak_source": "measured bf16 burst (fp16 has the same dense rate)"}
+    rec["roofline"]["frac"] = rec["roofline"]["achieved"] / rec["roofline"]["peak"]
+    rec["roofline"]["kernel_ms"] = kms[dom]
+    # end to end through host buffers: x in, logp and gradient out, every step
+    eng.set_precision("f16split")
+    xh = torch.tensor(X).pin_memory()
+    lh = torch.empty(B, dtype=torch.float64).pin_memory()
+    gh = torch.empty(tuple(x.shape), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(n):
+        x.copy_(xh, non_blocking=True)
+        eng.logp_and_grad(x, out=out)
+        lh.copy_(out[0], non_blocking=True)
+        gh.copy_(out[1], non_blocking=True)
+    e1.record()
+    e1.synchronize()
+    rec["e2e"] = {"value": B / (e0.elapsed_time(e1) / n * 1e-3), "unit": "evals/s",
+                  "h2d_bytes_per_step": int(x.numel() * 4), "d2h_bytes_per_step": int(B * 8 + x.numel() * 4)}
+    eng.close()
+    return rec
+
+
+_ORC = None
+
+
+def _oracle_worker_init(workload: str):
+    """Process-pool worker: its own FP64 oracle (stored basis) of the workload."""
+    global _ORC
     from oracle import pta_oracle as O
     from paper_2607_06834_b300 import synth
+    _ORC = O.Oracle(synth.make_array(workload))
+
+
+def _oracle_eval(x):
+    _ORC.logp(x)
+    _ORC.grad(x)
+    return 1
+
+
+def oracle_pool(workload: str):
+    """A spawn-started pool (safe after CUDA use) of one single-threaded oracle per host
+    core, bounded by memory (about 1 GB per worker at the 67-pulsar size)."""
+    import multiprocessing as mp
+    ncpu = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     try:
-        from threadpoolctl import threadpool_info
-        cores = max([t.get("num_threads", 1) for t in threadpool_info()] or [1])
-    except Exception:
-        cores = os.cpu_count()
-    orc = O.Oracle(arr)
-    X = synth.make_points(arr, n_eval, seed=6834 + 2).astype(np.float64)
-    orc.logp(X[0])
-    t0 = time.perf_counter()
-    for x in X:
-        orc.logp(x)
-        orc.grad(x)
-    dt = time.perf_counter() - t0
-    return {"value": n_eval / dt, "unit": "evals/s", "cores": int(cores), "kind": "oracle",
-            "sample": f"{n_eval} single-chain logp+grad evaluations of the {WORKLOAD} workload "
-                      f"({dt:.1f} s, numpy FP64)"}
+        avail_gb = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE") / 2 ** 30
+    except (ValueError, OSError):
+        avail_gb = 16.0
+    nproc = max(1, min(ncpu, 64, int(avail_gb // 1.5)))
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"   # one BLAS thread per worker: the pool is the parallelism
+    try:
+        pool = mp.get_context("spawn").Pool(nproc, initializer=_oracle_worker_init, initargs=(workload,))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return pool, nproc
+
+
+def oracle_rate(workload: str, steps: int, warmup: int):
+    """The FP64 oracle, as it stands, on the host cores: each step evaluates logp + grad
+    of one chain per worker process (B = #workers chains in parallel).  Returns
+    (evals/s, workers, timed seconds, steps timed)."""
+    from paper_2607_06834_b300 import synth
+    pool, nproc = oracle_pool(workload)
+    try:
+        arr = synth.make_array(workload)
+        X = synth.make_points(arr, nproc * (steps + warmup), seed=6834 + 2).astype(np.float64)
+        for i in range(warmup):
+            pool.map(_oracle_eval, list(X[i * nproc:(i + 1) * nproc]), chunksize=1)
+        t0 = time.perf_counter()
+        for i in range(warmup, warmup + steps):
+            pool.map(_oracle_eval, list(X[i * nproc:(i + 1) * nproc]), chunksize=1)
+        dt = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    return nproc * steps / dt, nproc, dt, steps
+
+
+def cpu_baseline(workload: str, steps: int):
+    value, nproc, dt, steps = oracle_rate(workload, steps, 1)
+    return {"value": value, "unit": "evals/s", "cores": int(nproc), "kind": "oracle",
+            "sample": f"{steps} steps of {nproc} chains of the {workload} workload, one chain per process "
+                      f"({nproc} spawned processes, one BLAS thread each; {dt:.1f} s timed; numpy FP64)"}
+
+
+RHAT_CONVERGED = 1.05
+
+
+def ess_rate(ess: float, rhat: float, seconds: float):
+    """ESS per second of a parameter group, published only when its split R-hat is at most
+    RHAT_CONVERGED: an ESS of chains that have not mixed is not an effective sample size."""
+    if not np.isfinite(rhat) or rhat > RHAT_CONVERGED:
+        return {"ess_per_s": "unconverged", "rhat": float(rhat)}
+    return {"ess_per_s": float(ess) / seconds, "rhat": float(rhat)}
 
 
 def hmc_ess_tiny(dev):
@@ -246,7 +427,8 @@ def hmc_ess_tiny(dev):
     eng.close()
     return {"workload": "3 pulsars x 200 TOAs, RN/GWB 10 bins, 64 chains, 20 leapfrog steps, FP32 path",
             "warmup_trajectories": 400, "sampling_trajectories": 400,
-            "ess_per_s_gwb_min": float(np.nanmin(e[g0:g0 + 2])) / t, "ess_per_s_median": float(np.nanmedian(e)) / t,
+            "gwb": ess_rate(np.nanmin(e[g0:g0 + 2]), np.nanmax(rh[g0:g0 + 2]), t),
+            "all_parameters": ess_rate(np.nanmedian(e), np.nanmax(rh), t),
             "ess_gwb_min": float(np.nanmin(e[g0:g0 + 2])), "ess_median": float(np.nanmedian(e)),
             "rhat_max": float(np.nanmax(rh)), "rhat_median": float(np.nanmedian(rh)), "sampling_s": t,
             "accept_rate": res.accept_rate, "stuck_chains": res.stats["stuck_chains"]}
@@ -288,10 +470,10 @@ def hmc_ess(args, dev):
     return {"workload": "NANOGrav-15-yr-like array + circular SMBHB (Earth and pulsar terms), "
                         f"{B} chains, {L} leapfrog steps per trajectory, FP32 path",
             "warmup_trajectories": args.hmc_warmup, "sampling_trajectories": args.hmc_samples,
-            "ess_per_s_gwb_min": e_gwb / t, "ess_per_s_theta_median": e_med / t,
-            "ess_per_s_cw_median": e_cw / t,
-            "ess_gwb_min": e_gwb, "ess_theta_median": e_med, "ess_cw_median": e_cw,
-            "ess_z_median": e_z, "ess_per_s_z_median": e_z / t,
+            "gwb": ess_rate(e_gwb, np.nanmax(rh[g0:g0 + 2]), t),
+            "theta_median": ess_rate(e_med, np.nanmax(rh), t),
+            "cw": ess_rate(e_cw, np.nanmax(rh[cw0:cw0 + 8]), t),
+            "ess_gwb_min": e_gwb, "ess_theta_median": e_med, "ess_cw_median": e_cw, "ess_z_median": e_z,
             "start": "conditional mode in z, then all chains restart from the best chain after a quarter "
                      "of the warm-up (consensus start)",
             "sampling_s": t, "warmup_s": res.warmup_s,
@@ -319,28 +501,30 @@ def hmc_ess_transforms(args, dev):
     B, L = synth.WORKLOADS[name]["chains"], 20
     out = {"workload": "paper's NANOGrav-15-yr model (RN 30 / HD-GWB 14 bins, no DM) on the 67-pulsar "
                        f"array, {B} chains, {L} leapfrog steps per trajectory, FP32 path",
-           "warmup_trajectories": args.hmc_warmup, "sampling_trajectories": args.hmc_samples}
+           "warmup_trajectories": args.hmc_warmup,
+           "sampling_trajectories": {"curn": args.hmc_samples_curn, "prior": args.hmc_samples}}
     for tr in ("curn", "prior"):
+        ns = args.hmc_samples_curn if tr == "curn" else args.hmc_samples
         eng = Engine(arr, precision="fp32")
         eng.set_transform(tr)
         lay = eng.layout
         th0 = lay["d_z"]
         x0 = torch.tensor(synth.make_points(arr, B, seed=6834 + 3), device=dev)
         kw = dict(unit_mass=th0, init_dz=0) if tr == "curn" else dict(init_dz=th0)
-        res = sampler.run_hmc(eng, x0, n_warmup=args.hmc_warmup, n_samples=args.hmc_samples, n_leapfrog=L,
+        res = sampler.run_hmc(eng, x0, n_warmup=args.hmc_warmup, n_samples=ns, n_leapfrog=L,
                               record=slice(th0, eng.D), seed=6834 + 3, eps0=0.01,
                               consensus=args.hmc_warmup // 4, **kw)
         e = sampler.ess_columns(res.draws)
         rh = np.array([sampler.split_rhat(res.draws[:, :, k]) for k in range(res.draws.shape[2])])
         g0 = lay["th_gwb"] - th0
         t = res.sampling_s
-        out[tr] = {"ess_per_s_gwb_min": float(np.nanmin(e[g0:g0 + 2])) / t,
-                   "ess_per_s_theta_median": float(np.nanmedian(e)) / t,
+        out[tr] = {"gwb": ess_rate(np.nanmin(e[g0:g0 + 2]), np.nanmax(rh[g0:g0 + 2]), t),
+                   "theta": ess_rate(np.nanmedian(e), np.nanmax(rh), t),
                    "ess_gwb_min": float(np.nanmin(e[g0:g0 + 2])), "ess_theta_median": float(np.nanmedian(e)),
                    "rhat_gwb_max": float(np.nanmax(rh[g0:g0 + 2])), "rhat_theta_median": float(np.nanmedian(rh)),
                    "rhat_theta_max": float(np.nanmax(rh)), "sampling_s": t, "warmup_s": res.warmup_s,
-                   "ms_per_trajectory": 1e3 * t / max(args.hmc_samples, 1),
-                   "evals_per_s": B * L * args.hmc_samples / t, "accept_rate": res.accept_rate, "step": res.step,
+                   "ms_per_trajectory": 1e3 * t / max(ns, 1),
+                   "evals_per_s": B * L * ns / t, "accept_rate": res.accept_rate, "step": res.step,
                    "gwb_posterior_mean": [float(v) for v in res.draws[:, :, g0:g0 + 2].reshape(-1, 2).mean(0)],
                    "gwb_posterior_std": [float(v) for v in res.draws[:, :, g0:g0 + 2].reshape(-1, 2).std(0)],
                    "stuck_chains": res.stats["stuck_chains"]}
@@ -362,9 +546,9 @@ def hmc_ess_transforms(args, dev):
     t = res.sampling_s
     out["curn_with_cw"] = {"workload": "same model + circular SMBHB (Earth and pulsar terms), CURN transform with "
                                        "the signal-dependent mean",
-                           "ess_per_s_gwb_min": float(np.nanmin(e[g0:g0 + 2])) / t,
-                           "ess_per_s_theta_median": float(np.nanmedian(e)) / t,
-                           "ess_per_s_cw_median": float(np.nanmedian(e[c0:c0 + 8])) / t,
+                           "gwb": ess_rate(np.nanmin(e[g0:g0 + 2]), np.nanmax(rh[g0:g0 + 2]), t),
+                           "theta": ess_rate(np.nanmedian(e), np.nanmax(rh), t),
+                           "cw": ess_rate(np.nanmedian(e[c0:c0 + 8]), np.nanmax(rh[c0:c0 + 8]), t),
                            "ess_gwb_min": float(np.nanmin(e[g0:g0 + 2])), "ess_theta_median": float(np.nanmedian(e)),
                            "ess_cw_median": float(np.nanmedian(e[c0:c0 + 8])),
                            "rhat_gwb_max": float(np.nanmax(rh[g0:g0 + 2])),
@@ -396,31 +580,13 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    from paper_2607_06834_b300 import synth
-    from oracle import pta_oracle as O
-    arr = synth.make_array(WORKLOAD)
-    orc = O.Oracle(arr)
-    X = synth.make_points(arr, args.steps + args.warmup, seed=6834 + 2).astype(np.float64)
-    for i in range(args.warmup):
-        orc.logp(X[i])
-        orc.grad(X[i])
-    t0 = time.perf_counter()
-    for i in range(args.warmup, args.warmup + args.steps):
-        orc.logp(X[i])
-        orc.grad(X[i])
-    dt = time.perf_counter() - t0
-    try:
-        from threadpoolctl import threadpool_info
-        cores = max([t.get("num_threads", 1) for t in threadpool_info()] or [1])
-    except Exception:
-        cores = os.cpu_count()
-    value = args.steps / dt
+    value, nproc, dt, steps = oracle_rate(WORKLOAD, args.steps, args.warmup)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "chains_per_step": 1},
-            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": int(cores), "kind": "oracle",
-                             "sample": "one single-chain logp+grad evaluation per step"},
+            "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "chains_per_step": nproc},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": int(nproc), "kind": "oracle",
+                             "sample": f"each step: {nproc} chains, one per spawned process (one BLAS thread each)"},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -492,18 +658,39 @@ def run_ours(args):
     abi.lib.pta_profile_read(eng._h, stage_ms, stage_n, 1)
     abi.lib.pta_profile_enable(eng._h, 0)
     stage_ms = [v / args.steps for v in stage_ms]
+    kernel_ms = dict(zip(abi.KERNEL_TIMERS, stage_ms[len(abi.STAGES):]))  # single kernels inside the stages
+    stage_ms = stage_ms[:len(abi.STAGES)]
     launches = int(sum(stage_n))
     ms, value = reduce_timing(ms, B, world, pg, dev)
     if rank != 0:
         pg.destroy_process_group()
         return
     # roofline of the dominant stage's kernel
-    dom = int(np.argmax(stage_ms))
+    dom = int(np.argmax(stage_ms))  # main stages only
     peaks = measured_peaks()
-    if abi.STAGES[dom] == "toa" and args.precision in ("tf32x3", "tf32"):
+    bf16_peak = (peaks or {}).get("bf16_tflops", 1800.0)
+    toa_roof = None
+    if args.precision == "f16split":
+        flops = toa_flops_f16(arr, B)
+        issued = toa_issued_f16(arr, B)
+        ms_toa = stage_ms[abi.STAGES.index("toa")]
+        kms = {k: kernel_ms[k] for k in ("toa_res", "toa_ftw")}
+        toa_roof = {"kernel": "k_f16_pack + k_f16_res + k_f16_ftw (TOA contractions, tcgen05 kind::f16, exact split)",
+                    "bound": "tensor", "unit": "TFLOP/s", "achieved": flops / (ms_toa * 1e-3) / 1e12,
+                    "peak": bf16_peak, "peak_source": "measured bf16 burst (fp16 has the same dense rate)",
+                    "stage_ms": ms_toa, "kernel_ms": kms, "algorithmic_flop": flops, "issued_flop": issued,
+                    "issued_tflops": issued / (ms_toa * 1e-3) / 1e12,
+                    "issued_frac": issued / (ms_toa * 1e-3) / 1e12 / bf16_peak,
+                    "note": "the exact split issues about 10 products per algorithmic one in F~ a and 6 in "
+                            "F~^T w: frac is algorithmic flops over the dense peak, issued_frac the tensor "
+                            "pipe's share of it"}
+        toa_roof["frac"] = toa_roof["achieved"] / toa_roof["peak"]
+    if abi.STAGES[dom] == "toa" and toa_roof is not None:
+        roof = dict(toa_roof)
+    elif abi.STAGES[dom] == "toa" and args.precision in ("tf32x3", "tf32"):
         flops = toa_flops_per_launch(arr, B)
         terms = 3 if args.precision == "tf32x3" else 1
-        tf32_peak = (peaks or {}).get("bf16_tflops", 1800.0) * (1.1 / 2.25)
+        tf32_peak = bf16_peak * (1.1 / 2.25)
         roof = {"kernel": f"k_toa_tc<{terms}> (TOA contractions, tcgen05 kind::tf32)", "bound": "tensor",
                 "unit": "TFLOP/s", "achieved": flops / (stage_ms[dom] * 1e-3) / 1e12, "peak": tf32_peak,
                 "peak_source": "measured bf16 burst x nominal TF32/BF16 ratio 1.1/2.25",
@@ -520,8 +707,7 @@ def run_ours(args):
         flops = toa_flops_per_launch(arr, B)
         roof = {"kernel": "k_toa_bf16 (TOA contractions, tcgen05 kind::f16, 3-term BF16 split)",
                 "bound": "tensor", "unit": "TFLOP/s", "achieved": flops / (stage_ms[dom] * 1e-3) / 1e12,
-                "peak": (peaks or {}).get("bf16_tflops", 1800.0),
-                "peak_source": "measured bf16 burst (cuBLAS)", "pipe_terms": 3}
+                "peak": bf16_peak, "peak_source": "measured bf16 burst (cuBLAS)", "pipe_terms": 3}
     elif abi.STAGES[dom] == "toa":
         flops = toa_flops_per_launch(arr, B)
         shape = f"<{tuned['chains_per_cta']},{tuned['toas_per_tile']},{tuned['rows_per_thread']},{tuned['order']}>" \
@@ -536,12 +722,15 @@ def run_ours(args):
                 "peak_source": "derived: 148 SM x 2 FP64 FMA/clk x 2 flop x 2.032 GHz"}
     else:
         flops = chol_flops_per_launch(arr, B)
-        roof = {"kernel": "k_chol_forward (FP64 Cholesky + inverse + transform)", "bound": "alu",
-                "unit": "TFLOP/s", "achieved": flops / (stage_ms[dom] * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
-                "peak_source": "derived: 148 SM x 2 FP64 FMA/clk x 2 flop x 2.032 GHz"}
+        kms = kernel_ms["chol_forward"]
+        roof = {"kernel": "k_chol_forward (FP64 Cholesky + inverse + transform, dense bins)", "bound": "alu",
+                "unit": "TFLOP/s", "achieved": flops / (kms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "peak_source": "derived: 148 SM x 2 FP64 FMA/clk x 2 flop x 2.032 GHz", "kernel_ms": kms,
+                "algorithmic_flop": flops}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = captured_traffic(args.precision, tuned["entry"]) \
-        if (tuned and abi.STAGES[dom] == "toa") else None
+    roof["traffic"] = captured_traffic(roof["kernel"].split(" ")[0])
+    if toa_roof is not None:
+        toa_roof["traffic"] = {k: captured_traffic(k) for k in ("k_f16_res", "k_f16_ftw")}
     roof["stage_ms"] = dict(zip(abi.STAGES, [round(v, 4) for v in stage_ms]))
     # end to end through the public call with host buffers (pinned), copies inside the timed
     # region: every step copies its input x host->device and its logp and gradient
@@ -614,11 +803,22 @@ def run_ours(args):
     # flushed, CUDA events per step); the headline stays the FP32 TOA form
     variants = {}
     if not args.skip_variants:
-        for prec in ("gram", "bf16x3", "tf32x3"):
+        accuracy = {"gram": "FP64-level (parity at FP64 tolerances)",
+                    "fp32": "FP32 bar at the 67-pulsar size (max 5.0e-4 nats over 16 near-posterior points); "
+                            "1.6e-3 nats at one of 8 near-posterior points at the 150-pulsar size",
+                    "f16split": "max 1.8e-4 nats over 16 near-posterior points, gradient 1.1e-5",
+                    "bf16x3": "reported: 8e-3 nats at a near-posterior point",
+                    "tf32x3": "reported: 2.5e-3 nats at a near-posterior point"}
+        for prec in ("fp32", "f16split", "gram", "bf16x3", "tf32x3"):
             if prec == args.precision:
                 continue
             try:
                 eng.set_precision(prec)
+                vt = None
+                if prec == "fp32":  # the autotuner picks the SIMT tile shape (setup, not timed)
+                    from paper_2607_06834_b300.engine import toa_config_info
+                    chosen, _ = eng.autotune(B)
+                    vt = {"entry": chosen, **toa_config_info(chosen)}
                 for _ in range(3):
                     eng.logp_and_grad(x, out=out)
                 torch.cuda.synchronize()
@@ -634,17 +834,17 @@ def run_ours(args):
                 torch.cuda.synchronize()
                 vms = float(np.mean([a.elapsed_time(b) for a, b in zip(vs, ve)]))
                 variants[prec] = {"value": B / (vms * 1e-3), "unit": "evals/s", "ms_per_step": vms,
-                                  "detail": DTYPE_DETAIL[prec],
-                                  "accuracy": {"gram": "FP64-level (parity at FP64 tolerances)",
-                                               "bf16x3": "reported: 8e-3 nats at a near-posterior point",
-                                               "tf32x3": "reported: 2.5e-3 nats at a near-posterior point"}[prec]}
+                                  "detail": DTYPE_DETAIL[prec], "accuracy": accuracy[prec]}
+                if vt:
+                    variants[prec]["toa_kernel_autotuned"] = vt
             except Exception as exc:  # a mode this model cannot run
                 variants[prec] = {"unavailable": str(exc)}
         eng.set_precision(args.precision)
         if tuned and tuned.get("entry") is not None:
             eng.set_toa_config(tuned["entry"])
         variants["curn_transform"] = curn_variant(dev, args.steps)
-    cpu = None if args.skip_cpu else cpu_baseline(arr, args.cpu_evals)
+    scale = None if (args.skip_scale150 or args.workload != WORKLOAD) else scale150_leg(dev, args.steps, peaks)
+    cpu = None if args.skip_cpu else cpu_baseline(args.workload, args.cpu_steps)
     hmc = None if args.skip_hmc else hmc_ess(args, dev)
     if hmc is not None:
         hmc["control_small_array"] = hmc_ess_tiny(dev)
@@ -658,11 +858,15 @@ def run_ours(args):
                        else f"{args.workload}, {B} chains", "transform": args.transform,
                        "chains_per_gpu": B, "ntoa": arr.ntoa, "npsr": arr.npsr,
                        "precision": args.precision, "l2": "flushed between timed steps (512 MB write)",
-                       "toa_kernel_autotuned": tuned},
-            "roofline": roof, "cpu_baseline": cpu,
+                       "toa_kernel_autotuned": tuned,
+                       # the metric is quoted against the plain FP64 GPU path on the same batch
+                       "vs_fp64_plain_path": None if fp64 is None else
+                       {"fp64_evals_per_s": fp64["value"], "ratio": value / fp64["value"]}},
+            "roofline": roof, "roofline_toa": toa_roof, "cpu_baseline": cpu,
             "e2e": {"value": world * B / (e2e_ms * 1e-3), "unit": "evals/s",
                     "h2d_bytes_per_step": int(B * D * 4), "d2h_bytes_per_step": int(B * 8 + B * D * 4)},
             "gpu_launches": launches, "fp64_plain_path": fp64, "variants": variants or None, "hmc": hmc,
+            "scale150": scale,
             "clocks": ck,
             "wall_s_timed": t_wall, "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None}
     print(json.dumps(line), flush=True)
@@ -676,12 +880,13 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", default="fp32")
-    ap.add_argument("--cpu-evals", type=int, default=16)
+    ap.add_argument("--precision", default="f16split")
+    ap.add_argument("--cpu-steps", type=int, default=2, help="oracle steps (one chain per host core each)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-hmc", action="store_true")
     ap.add_argument("--skip-variants", action="store_true")
+    ap.add_argument("--skip-scale150", action="store_true")
     ap.add_argument("--toa-config", type=int, default=-1, help="fixed FP32 TOA kernel entry (default: autotune)")
     # profiling runs of a single kernel on another shape (the headline keeps the defaults)
     ap.add_argument("--workload", default=WORKLOAD, help="synthetic workload (synth.WORKLOADS key)")
@@ -689,6 +894,8 @@ def main():
     ap.add_argument("--transform", default="prior", choices=["prior", "curn"])
     ap.add_argument("--hmc-warmup", type=int, default=400)
     ap.add_argument("--hmc-samples", type=int, default=200)
+    ap.add_argument("--hmc-samples-curn", type=int, default=800,
+                    help="sampling trajectories of the CURN leg on the paper's model")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

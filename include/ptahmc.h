@@ -131,8 +131,9 @@ int pta_layout(const pta_ctx* ctx, pta_layout_t* out);
 /* Select the contraction precision (PTA_PREC_*) for later calls.  PTA_EINVAL for
  * an unknown mode, for the TF32 modes beyond 896 coefficients per pulsar, and for
  * PTA_PREC_BF16X3 when P > 416 or P + max m_I + n_low > 384, n_low = 16 projected
- * low-frequency columns (the 4 lowest achromatic and 4 lowest DM bins).  The
- * continuous-wave model runs only with PTA_PREC_FP32. */
+ * low-frequency columns (the 4 lowest achromatic and 4 lowest DM bins), and for
+ * PTA_PREC_F16SPLIT when P (+ max m_I with the continuous-wave signal) > 512.  The
+ * continuous-wave model runs with PTA_PREC_FP32 and PTA_PREC_F16SPLIT. */
 int pta_set_precision(pta_ctx* ctx, int precision);
 /* Autotuner of the FP32 TOA kernel's tile shape (no counterpart in the paper).
  * Times every table entry that can run this model (chains per CTA, TOAs per tile,
@@ -272,8 +273,11 @@ int pta_logp_constant(const pta_ctx* ctx, double* c);
  * the accumulated milliseconds and launch counts per stage (arrays of
  * PTA_NSTAGES entries, either may be NULL) and, if reset != 0, clears them.
  * Stages: 0 prior forward (spectra, Cholesky, transform), 1 TOA contractions,
- * 2 FP64 epilogue (timing-model solve), 3 adjoint, 4 final sum. */
-#define PTA_NSTAGES 5
+ * 2 FP64 epilogue (timing-model solve), 3 adjoint, 4 final sum; their sum is the
+ * evaluation.  Entries 5-7 time single kernels inside those stages (no launches
+ * counted): 5 the dense-bin Cholesky k_chol_forward, 6 the exact-split residual
+ * kernel k_f16_res, 7 its F^T w~ kernel k_f16_ftw. */
+#define PTA_NSTAGES 8
 int pta_profile_enable(pta_ctx* ctx, int enable);
 int pta_profile_read(pta_ctx* ctx, double* ms, long long* launches, int reset);
 

@@ -19,8 +19,10 @@ EXPORTED = ["pta_create", "pta_add_pulsar", "pta_finalize", "pta_layout", "pta_s
             "pta_profile_enable", "pta_profile_read", "pta_logp_and_grad_noalloc", "pta_autotune",
             "pta_set_toa_config", "pta_toa_config_info", "pta_debug_inject", "pta_set_beta", "pta_set_transform",
             "pta_param_bounds", "pta_last_error", "pta_destroy"]
-NSTAGES = 5
+NSTAGES = 8
 STAGES = ["prior_forward", "toa", "epilogue", "adjoint", "final"]
+# single kernels timed inside those stages (not part of the stage sum)
+KERNEL_TIMERS = ["chol_forward", "toa_res", "toa_ftw"]
 
 
 class ModelDesc(C.Structure):

@@ -238,8 +238,8 @@ extern "C" int pta_hmc_trajectory(pta_ctx* c, int B, float* x, double* logp, flo
     return PTA_EINVAL;
   }
   if (B == 0) return PTA_OK;
-  if (c->dm.cw && c->precision != PTA_PREC_FP32) {
-    c->err = "the continuous-wave model runs on the FP32 path (PTA_PREC_FP32)";
+  if (c->dm.cw && c->precision != PTA_PREC_FP32 && c->precision != PTA_PREC_F16SPLIT) {
+    c->err = "the continuous-wave model runs on the FP32 and exact-split paths (PTA_PREC_FP32, PTA_PREC_F16SPLIT)";
     return PTA_EINVAL;
   }
   int rc = pta_prepare_internal(c, B);

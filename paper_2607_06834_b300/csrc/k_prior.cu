@@ -497,7 +497,7 @@ int count_prior_forward(const DevModel& m) {
 int count_prior_adjoint(const DevModel& m) { return m.curn ? 1 : count_prior_forward(m) - 1; }
 
 cudaError_t launch_prior_forward(const DevModel& m, const Scratch& s, int B, const float* x, int fp64,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, cudaEvent_t* kev) {
   (void)fp64;
   const int nspec = m.npsr * (m.na + m.nd) + m.na;
   k_spectra<<<dim3((nspec + 127) / 128, B), 128, 0, st>>>(m, x, s.sk, s.skd, s.srho);
@@ -505,7 +505,9 @@ cudaError_t launch_prior_forward(const DevModel& m, const Scratch& s, int B, con
     const size_t sm = chol_smem(m);
     cudaError_t e = cudaFuncSetAttribute(k_chol_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
+    if (kev) cudaEventRecord(kev[0], st);
     k_chol_forward<<<dim3(m.n_chol, B), 128, sm, st>>>(m, x, s.sk, s.srho, s.a64, s.Lpk, s.Lipk, s.stat);
+    if (kev) cudaEventRecord(kev[1], st);
   }
   if (m.curn) return cudaGetLastError();  // a comes from the CURN transform (launch_curn_forward)
   if (m.n_gwbonly > 0) k_gwbonly_forward<<<dim3(m.n_gwbonly, B), 128, 0, st>>>(m, x, s.srho, s.a64);

@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------------
 // k_f16_res
 // ---------------------------------------------------------------------------
-constexpr int RES_NXS = 4;             // shared-memory stages of stored basis blocks
+constexpr int RES_NXS = 8;             // shared-memory stages: a stored basis block and its coefficient slice
 constexpr int RES_THREADS = 320;       // warp 0 MMA, warp 1 copies, warps 2-9 epilogue
 constexpr int RES_EPI0 = 64;           // first epilogue thread
 
@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
   using CF = ResCfg<NC>;
   constexpr int NXS = RES_NXS;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t cfull, xfull[NXS], xfree[NXS], dfull[2], dempty[2], drain;
+  __shared__ __align__(8) uint64_t xfull[NXS], xfree[NXS], dfull[2], dempty[2], drain;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_bad;
   // chain block fastest: the blocks of one unit run together and share its basis in L2
@@ -437,15 +437,15 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
   const int KXM = m.x16_kxm, KX = kx_of(m, I), nkc = KX / KCB, ntile = len / TTA, G = ntile * nkc;
   const int b0 = cb * NC, nvalid = min(NC, B - b0);
   const size_t csz = 4 * (size_t)KXM * NC * 2;
-  unsigned char* Xs = smem;                                         // NXS stored blocks (16 KB each)
-  unsigned char* Cs = smem + NXS * RES_XSB;                         // 4 NC rows x KXM fp16 (pieces stacked)
-  double* redc = reinterpret_cast<double*>(Cs + csz);               // [8][NC/2] chi2 partials
+  constexpr int CSL = 2 * 4 * NC * 16;                              // coefficient slice of one 16-column step
+  constexpr int STG = RES_XSB + CSL;                                // one stage: basis block + slice
+  unsigned char* Xs = smem;                                         // NXS stages
+  double* redc = reinterpret_cast<double*>(smem + NXS * STG);       // [8][NC/2] chi2 partials
   float* redm = reinterpret_cast<float*>(redc + 4 * NC);            // [8][NC/2] max |w|
   float* ysc = redm + 4 * NC;                                       // [NC] 2^(exponent of y) per chain
 
   if (warp == 0) tc::tmem_alloc(&tmem_base, 2 * CF::DB <= 256 ? 256 : 512);
   if (tid == 0) {
-    tc::mbar_init(&cfull, 1);
     for (int s = 0; s < NXS; ++s) {
       tc::mbar_init(&xfull[s], 1);
       tc::mbar_init(&xfree[s], 1);
@@ -473,9 +473,8 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
   if (warp == 0) {
     // ------------------------------------------------ MMA issue (lane 0)
     if (lane == 0) {
-      bool ok = wait(&cfull, 0);
-      if (ok) tc::fence_after();
-      const uint32_t cbase = tc::smem_u32(Cs), xbase = tc::smem_u32(Xs);
+      bool ok = true;
+      const uint32_t xbase = tc::smem_u32(Xs);
       int g = 0;
       for (int i = 0; i < ntile && ok; ++i) {
         const int buf = i & 1;
@@ -486,10 +485,10 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
           const int s = g % NXS;
           if (!(ok = wait(&xfull[s], (g / NXS) & 1))) break;
           tc::fence_after();
-          const uint64_t cd = tc::desc(cbase + kc * 2 * (4 * NC * 16), 4 * NC * 16, 128);
+          const uint64_t cd = tc::desc(xbase + s * STG + RES_XSB, 4 * NC * 16, 128);
 #pragma unroll
           for (int a = 0; a < 4; ++a)
-            tc::mma_f16(dbase + a * NC, tc::desc(xbase + s * RES_XSB + a * (RES_XSB / 4), 2048, 128), cd,
+            tc::mma_f16(dbase + a * NC, tc::desc(xbase + s * STG + a * (RES_XSB / 4), 2048, 128), cd,
                         idesc_f16(TTA, (4 - a) * NC, 0), (kc | a) ? 1u : 0u);
           tc::commit(&xfree[s]);
         }
@@ -501,12 +500,12 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
     }
     __syncwarp();
   } else if (warp == 1) {
-    // ------------------------------------------------ bulk copies: coefficient block, basis blocks
+    // ------------------------------------------------ bulk copies: basis block + coefficient slice per step
+    // (the coefficient block, 147 KB at 64 chains and 288 columns, would halve the ring's
+    // depth if it stayed resident; its slices come from L2, where the whole batch's
+    // pieces stay)
     if (lane == 0) {
-      const unsigned char* src = c16 + ((size_t)I * nCB + cb) * csz;
-      const uint32_t bytes = (uint32_t)KX * 4 * NC * 2;  // the K groups this pulsar uses
-      mbar_expect_tx(&cfull, bytes);
-      bulk_g2s(Cs, src, bytes, &cfull);
+      const unsigned char* csrc = c16 + ((size_t)I * nCB + cb) * csz;
       // the unit's blocks are consecutive: (tile i, column block kc) is block i nkc + kc
       const unsigned char* xsrc = reinterpret_cast<const unsigned char*>(
           m.x16 + m.x16_off[I] + (size_t)((start - m.toa_off[I]) / TTA) * nkc * XBW);
@@ -514,11 +513,11 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
       for (; g < G; ++g) {
         const int s = g % NXS;
         if (g >= NXS && !wait(&xfree[s], ((g / NXS) - 1) & 1)) break;
-        mbar_expect_tx(&xfull[s], RES_XSB);
-        bulk_g2s(Xs + s * RES_XSB, xsrc + (size_t)g * RES_XSB, RES_XSB, &xfull[s]);
+        mbar_expect_tx(&xfull[s], STG);
+        bulk_g2s(Xs + s * STG, xsrc + (size_t)g * RES_XSB, RES_XSB, &xfull[s]);
+        bulk_g2s(Xs + s * STG + RES_XSB, csrc + (size_t)(g % nkc) * CSL, CSL, &xfull[s]);
       }
       // no copy in flight into this CTA's shared memory at exit (bounded waits)
-      if (!tc::mbar_wait(&cfull, 0, kDrainLimit)) s_bad = 1;
       for (int h = max(0, g - NXS); h < g; ++h)
         if (!tc::mbar_wait(&xfull[h % NXS], (h / NXS) & 1, kDrainLimit)) s_bad = 1;
     }
@@ -843,7 +842,8 @@ EncodeTiled encode_tiled() {
 
 template <int NC>
 size_t res_smem(const DevModel& m) {
-  return (size_t)RES_NXS * RES_XSB + 4 * (size_t)m.x16_kxm * NC * 2 + 4 * NC * (sizeof(double) + sizeof(float)) +
+  (void)m;
+  return (size_t)RES_NXS * (RES_XSB + 2 * 4 * NC * 16) + 4 * NC * (sizeof(double) + sizeof(float)) +
          NC * sizeof(float);
 }
 
@@ -851,7 +851,7 @@ size_t res_smem(const DevModel& m) {
 int res_nc(const DevModel& m) { return res_smem<64>(m) <= 227 * 1024 ? 64 : 32; }
 
 template <int NC>
-cudaError_t launch_f16_nc(const DevModel& m, const Scratch& s, int B, cudaStream_t st) {
+cudaError_t launch_f16_nc(const DevModel& m, const Scratch& s, int B, cudaStream_t st, cudaEvent_t* kev) {
   const int nCB = (B + NC - 1) / NC;
   k_f16_pack<NC><<<dim3(m.npsr, nCB), 256, sizeof(int) * m.x16_kxm, st>>>(m, s.a64, s.c16, s.yexp, B, nCB);
   const size_t sm = res_smem<NC>(m);
@@ -859,8 +859,10 @@ cudaError_t launch_f16_nc(const DevModel& m, const Scratch& s, int B, cudaStream
   cudaError_t e = cudaFuncSetAttribute(k_f16_res<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   float* w = m.cw ? s.cwwt : s.wres;
+  if (kev) cudaEventRecord(kev[0], st);
   k_f16_res<NC><<<dim3(nCB, m.n_units), RES_THREADS, sm, st>>>(m, s.c16, s.yexp, w, s.wmx, s.c2part, s.stat,
                                                               m.cw ? s.cwsig : nullptr, B, nCB);
+  if (kev) cudaEventRecord(kev[1], st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_f16_ftw, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_SMEM);
@@ -886,8 +888,10 @@ cudaError_t launch_f16_nc(const DevModel& m, const Scratch& s, int B, cudaStream
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
+  if (kev) cudaEventRecord(kev[2], st);
   k_f16_ftw<<<dim3((m.P + QWB - 1) / QWB, (B + 127) / 128, m.n_units), FW_THREADS, FW_SMEM, st>>>(m, tw, tx, s.wmx,
                                                                                                   s.gpart, s.stat, B);
+  if (kev) cudaEventRecord(kev[3], st);
   return cudaGetLastError();
 }
 
@@ -955,9 +959,9 @@ cudaError_t build_f16_basis(DevModel& m, const std::vector<int>& n_pad, const st
   return cudaSuccess;
 }
 
-cudaError_t launch_toa_f16(const DevModel& m, const Scratch& s, int B, cudaStream_t st) {
+cudaError_t launch_toa_f16(const DevModel& m, const Scratch& s, int B, cudaStream_t st, cudaEvent_t* kev) {
   if (!f16_supported(m) || !m.x16 || !s.c16 || !s.yexp || !s.wmx || (!m.cw && !s.wres)) return cudaErrorInvalidValue;
-  return res_nc(m) == 64 ? launch_f16_nc<64>(m, s, B, st) : launch_f16_nc<32>(m, s, B, st);
+  return res_nc(m) == 64 ? launch_f16_nc<64>(m, s, B, st, kev) : launch_f16_nc<32>(m, s, B, st, kev);
 }
 
 }  // namespace pta

@@ -733,6 +733,23 @@ struct StageTimer {
     c->prof_stage.push_back(stage);
     c->prof_launch[stage] += launches;
   }
+  // n event pairs for single kernels (entries `first` ..), recorded by the launcher;
+  // nullptr when profiling is off
+  cudaEvent_t* kernels(int first, int n) {
+    if (!on) return nullptr;
+    for (int i = 0; i < n; ++i) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      kev[2 * i] = a;
+      kev[2 * i + 1] = b;
+      c->prof_ev.push_back(a);
+      c->prof_ev.push_back(b);
+      c->prof_stage.push_back(first + i);
+    }
+    return kev;
+  }
+  cudaEvent_t kev[4];
 };
 }  // namespace
 
@@ -747,7 +764,7 @@ int pta_eval_scratch(pta_ctx* c, const pta::Scratch& s, int B, const float* x, d
   cudaError_t e = cudaMemsetAsync(s.stat, 0, sizeof(int32_t) * B, st);
   const bool gram = c->precision == PTA_PREC_GRAM;
   tm.begin(0);
-  if (e == cudaSuccess) e = pta::launch_prior_forward(m, s, B, x, fp64, st);
+  if (e == cudaSuccess) e = pta::launch_prior_forward(m, s, B, x, fp64, st, m.n_chol > 0 ? tm.kernels(5, 1) : nullptr);
   if (e == cudaSuccess && m.cw) e = pta::launch_cw_forward(m, s, B, x, st);
   if (e == cudaSuccess && m.curn && m.cw) {
     // Eq. decenter_det_PTA: the mean needs beta F^T N~^-1 (dt'' - s) per chain, the TOA
@@ -777,7 +794,7 @@ int pta_eval_scratch(pta_ctx* c, const pta::Scratch& s, int B, const float* x, d
     else if (c->precision == PTA_PREC_BF16X3)
       e = pta::launch_toa_bf16(m, s, B, st);
     else if (c->precision == PTA_PREC_F16SPLIT)
-      e = pta::launch_toa_f16(m, s, B, st);
+      e = pta::launch_toa_f16(m, s, B, st, tm.kernels(6, 2));
     else
       e = pta::launch_toa_fp32_cfg(m, s, B, c->toa_cfg, st);
   }
@@ -1105,8 +1122,9 @@ int pta_logp_and_grad(pta_ctx* c, int B, const float* x, double* logp, float* gr
   if (!c) return PTA_EINVAL;
   if (B < 0 || (B > 0 && (!x || !logp))) return fail(c, PTA_EINVAL, "logp_and_grad: bad arguments");
   if (B == 0) return PTA_OK;
-  if (c->dm.cw && c->precision != PTA_PREC_FP32)
-    return fail(c, PTA_EINVAL, "the continuous-wave model runs on the FP32 path (PTA_PREC_FP32)");
+  if (c->dm.cw && c->precision != PTA_PREC_FP32 && c->precision != PTA_PREC_F16SPLIT)
+    return fail(c, PTA_EINVAL,
+                "the continuous-wave model runs on the FP32 and exact-split paths (PTA_PREC_FP32, PTA_PREC_F16SPLIT)");
   int rc = pta_prepare_internal(c, B);
   if (rc != PTA_OK) return rc;
   return pta_eval_internal(c, B, x, logp, grad, status, (cudaStream_t)stream, true);

@@ -173,7 +173,7 @@ struct Scratch {
 
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_prior_forward(const DevModel& m, const Scratch& s, int B, const float* x,
-                                 int fp64, cudaStream_t st);
+                                 int fp64, cudaStream_t st, cudaEvent_t* kev = nullptr);  // kev: 2 events around k_chol_forward
 cudaError_t launch_toa_fp32(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
 // SIMT tile-shape table (autotuner): entry count, shape of entry i, whether entry i
 // can run this model, the default entry, and a launch with a chosen entry (-1: default)
@@ -194,7 +194,8 @@ bool f16_supported(const DevModel& m);
 size_t f16_pack_bytes(const DevModel& m, int cap);
 cudaError_t build_f16_basis(DevModel& m, const std::vector<int>& n_pad, const std::vector<int>& mI,
                             std::vector<void*>& allocs);
-cudaError_t launch_toa_f16(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
+// kev (optional): 4 events recorded around k_f16_res and k_f16_ftw
+cudaError_t launch_toa_f16(const DevModel& m, const Scratch& s, int B, cudaStream_t st, cudaEvent_t* kev = nullptr);
 size_t cw_const_bytes();
 cudaError_t launch_cw_forward(const DevModel& m, const Scratch& s, int B, const float* x, cudaStream_t st);
 cudaError_t launch_cw_gradient(const DevModel& m, const Scratch& s, int B, cudaStream_t st);
@@ -319,6 +320,6 @@ struct pta_ctx {
   bool prof = false;
   std::vector<cudaEvent_t> prof_ev;   // pairs (start, end) per recorded stage
   std::vector<int> prof_stage;
-  double prof_ms[PTA_NSTAGES] = {0, 0, 0, 0, 0};
-  long long prof_launch[PTA_NSTAGES] = {0, 0, 0, 0, 0};
+  double prof_ms[PTA_NSTAGES] = {};
+  long long prof_launch[PTA_NSTAGES] = {};
 };

@@ -22,8 +22,8 @@
 
 #include "pta_internal.cuh"
 
-int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* grad, int32_t* status,
-                      cudaStream_t st);
+int pta_eval_scratch(pta_ctx* c, const pta::Scratch& s, int B, const float* x, double* logp, float* grad,
+                     int32_t* status, cudaStream_t st, bool profile);
 
 namespace {
 
@@ -38,15 +38,15 @@ void* g_addr[kMaxDevices] = {nullptr};
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Bytes of per-call workspace for B chains (same buffers as the context scratch,
-// without the HMC state).
-size_t noalloc_bytes(const pta::DevModel& m, int B) {
+// without the HMC state; the FP64 partial sums only for the FP64 path).
+size_t noalloc_bytes(const pta::DevModel& m, int B, bool fp64) {
   const size_t np = m.npsr, tri = np * (np + 1) / 2;
   size_t s = 0;
   s += align256(np * B * m.PM * sizeof(float));
   s += align256(np * B * m.PM * sizeof(double));
   s += align256((size_t)B * std::max(1, m.n_chol) * tri * sizeof(double)) * 2;
   s += align256((size_t)m.n_units * B * m.Qs * sizeof(float));
-  s += align256((size_t)m.n_units * B * m.Qs * sizeof(double));
+  if (fp64) s += align256((size_t)m.n_units * B * m.Qs * sizeof(double));
   s += align256((size_t)m.n_units * B * sizeof(double));
   s += align256(np * B * m.P * sizeof(double));
   s += align256(np * B * sizeof(double));
@@ -87,8 +87,8 @@ extern "C" int pta_logp_and_grad_noalloc(pta_ctx* c, int B, const float* x, doub
     c->err = "logp_and_grad_noalloc: the CURN transform keeps per-chain factors that need the allocating entry point";
     return PTA_EINVAL;
   }
-  if (c->precision == PTA_PREC_BF16X3) {
-    c->err = "logp_and_grad_noalloc: the BF16 tensor-core path needs the allocating entry point";
+  if (c->precision == PTA_PREC_BF16X3 || c->precision == PTA_PREC_F16SPLIT) {
+    c->err = "logp_and_grad_noalloc: the BF16 and exact-split tensor-core paths need the allocating entry point";
     return PTA_EINVAL;
   }
   if (c->precision == PTA_PREC_FP64 && !c->dm.F64) {
@@ -96,7 +96,8 @@ extern "C" int pta_logp_and_grad_noalloc(pta_ctx* c, int B, const float* x, doub
              "entry point builds on its first FP64 call";
     return PTA_ESTATE;
   }
-  const size_t need = noalloc_bytes(c->dm, B);
+  const bool fp64 = c->precision == PTA_PREC_FP64;
+  const size_t need = noalloc_bytes(c->dm, B, fp64);
   if (need > kNoallocBytes) {
     c->err = "logp_and_grad_noalloc: " + std::to_string(B) + " chains need " + std::to_string(need) +
              " bytes of workspace, above the fixed " + std::to_string(kNoallocBytes) + " bytes; use fewer chains";
@@ -136,7 +137,7 @@ extern "C" int pta_logp_and_grad_noalloc(pta_ctx* c, int B, const float* x, doub
   s.Lpk = (double*)take((size_t)B * std::max(1, m.n_chol) * tri * sizeof(double));
   s.Lipk = (double*)take((size_t)B * std::max(1, m.n_chol) * tri * sizeof(double));
   s.gpart = (float*)take((size_t)m.n_units * B * m.Qs * sizeof(float));
-  s.gpart64 = (double*)take((size_t)m.n_units * B * m.Qs * sizeof(double));
+  if (fp64) s.gpart64 = (double*)take((size_t)m.n_units * B * m.Qs * sizeof(double));
   s.c2part = (double*)take((size_t)m.n_units * B * sizeof(double));
   s.ghat = (double*)take(np * B * m.P * sizeof(double));
   s.chi2 = (double*)take(np * B * sizeof(double));
@@ -148,10 +149,7 @@ extern "C" int pta_logp_and_grad_noalloc(pta_ctx* c, int B, const float* x, doub
   s.skd = (double*)take((size_t)B * np * std::max(1, m.nd) * sizeof(double));
   s.srho = (double*)take((size_t)B * m.na * sizeof(double));
   s.queue = (int*)take(16);
-  // Run the same kernel sequence as pta_logp_and_grad on this workspace.
-  pta::Scratch saved = c->sc;
-  c->sc = s;
-  const int rc = pta_eval_internal(c, B, x, logp, grad, status, (cudaStream_t)stream);
-  c->sc = saved;
-  return rc;
+  // Run the same kernel sequence as pta_logp_and_grad on this workspace; the
+  // context's own scratch is not touched.
+  return pta_eval_scratch(c, s, B, x, logp, grad, status, (cudaStream_t)stream, false);
 }
