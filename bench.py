@@ -501,19 +501,20 @@ def hmc_ess_transforms(args, dev):
     B, L = synth.WORKLOADS[name]["chains"], 20
     out = {"workload": "paper's NANOGrav-15-yr model (RN 30 / HD-GWB 14 bins, no DM) on the 67-pulsar "
                        f"array, {B} chains, {L} leapfrog steps per trajectory, FP32 path",
-           "warmup_trajectories": args.hmc_warmup,
+           "warmup_trajectories": {"curn": args.hmc_warmup_curn, "prior": args.hmc_warmup},
            "sampling_trajectories": {"curn": args.hmc_samples_curn, "prior": args.hmc_samples}}
     for tr in ("curn", "prior"):
         ns = args.hmc_samples_curn if tr == "curn" else args.hmc_samples
+        nw = args.hmc_warmup_curn if tr == "curn" else args.hmc_warmup
         eng = Engine(arr, precision="fp32")
         eng.set_transform(tr)
         lay = eng.layout
         th0 = lay["d_z"]
         x0 = torch.tensor(synth.make_points(arr, B, seed=6834 + 3), device=dev)
         kw = dict(unit_mass=th0, init_dz=0) if tr == "curn" else dict(init_dz=th0)
-        res = sampler.run_hmc(eng, x0, n_warmup=args.hmc_warmup, n_samples=ns, n_leapfrog=L,
+        res = sampler.run_hmc(eng, x0, n_warmup=nw, n_samples=ns, n_leapfrog=L,
                               record=slice(th0, eng.D), seed=6834 + 3, eps0=0.01,
-                              consensus=args.hmc_warmup // 4, **kw)
+                              consensus=nw // 4, **kw)
         e = sampler.ess_columns(res.draws)
         rh = np.array([sampler.split_rhat(res.draws[:, :, k]) for k in range(res.draws.shape[2])])
         g0 = lay["th_gwb"] - th0
@@ -896,6 +897,8 @@ def main():
     ap.add_argument("--hmc-samples", type=int, default=200)
     ap.add_argument("--hmc-samples-curn", type=int, default=800,
                     help="sampling trajectories of the CURN leg on the paper's model")
+    ap.add_argument("--hmc-warmup-curn", type=int, default=1000,
+                    help="warm-up trajectories of the CURN leg on the paper's model")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -60,7 +60,7 @@ __global__ void k_spectra(DevModel m, const float* __restrict__ x, double* sk, d
 // sits on the column-to-column path; sqrt(d) for all pivots at once at the end
 // gives the Cholesky factor L D^(1/2), its inverse D^(-1/2) X and the transform.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(512)
     k_chol_forward(DevModel m, const float* __restrict__ x, const double* __restrict__ sk,
                    const double* __restrict__ srho, double* a64, double* Lpk, double* Lipk, int32_t* stat) {
   extern __shared__ double sm[];
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(128)
 // with u = column I of L^-1 (from dL = L tril_half(L^-1 dPhi L^-T), dPhi = e_I e_I^T); and
 // rho d logp / d rho = 1/2 sum_c gt.z - sum_I kappa_I d logp/d kappa_I (scaling identity:
 // Phi -> s Phi gives a -> sqrt(s) a).
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(512)
     k_chol_adjoint(DevModel m, const float* __restrict__ x, const double* __restrict__ ghat,
                    const double* __restrict__ Lpk, const double* __restrict__ Lipk, const double* __restrict__ sk,
                    float* grad, double* dlnk, double* dlnr, int B) {
@@ -210,6 +210,8 @@ __global__ void __launch_bounds__(128)
     grad[(size_t)b * m.d + m.z_ach + (2 * k) * np + i] = (float)(s - zs[i]);
   }
   __syncthreads();
+  // kappa_I d logp/d kappa_I, one thread per I (each walk is a short dependent FP64 chain;
+  // spreading it over a warp with prefix scans costs several times the FP64 operations)
   for (int I = tid; I < np; I += nt) {
     double p0 = 0.0, p1 = 0.0, acc = 0.0;
     for (int a = I; a < np; ++a) {
@@ -481,6 +483,11 @@ __global__ void k_final(DevModel m, const float* __restrict__ x, const double* _
 
 }  // namespace
 
+// Threads per CTA of the dense-bin kernels: their two packed triangles allow 5-6 CTAs per
+// SM at 67 pulsars, but only one at 150 (181 KB), where 4 warps would leave the FP64
+// latency exposed: 16 warps per CTA there.
+static int chol_threads(const DevModel& m) { return m.npsr >= 96 ? 512 : 128; }
+
 static size_t chol_smem(const DevModel& m) {
   const size_t np = m.npsr, ntri = np * (np + 1) / 2;
   return (2 * ntri + 4 * np) * sizeof(double);
@@ -506,7 +513,7 @@ cudaError_t launch_prior_forward(const DevModel& m, const Scratch& s, int B, con
     cudaError_t e = cudaFuncSetAttribute(k_chol_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     if (kev) cudaEventRecord(kev[0], st);
-    k_chol_forward<<<dim3(m.n_chol, B), 128, sm, st>>>(m, x, s.sk, s.srho, s.a64, s.Lpk, s.Lipk, s.stat);
+    k_chol_forward<<<dim3(m.n_chol, B), chol_threads(m), sm, st>>>(m, x, s.sk, s.srho, s.a64, s.Lpk, s.Lipk, s.stat);
     if (kev) cudaEventRecord(kev[1], st);
   }
   if (m.curn) return cudaGetLastError();  // a comes from the CURN transform (launch_curn_forward)
@@ -522,7 +529,7 @@ cudaError_t launch_prior_adjoint(const DevModel& m, const Scratch& s, int B, con
     const size_t sm = adj_smem(m);
     cudaError_t e = cudaFuncSetAttribute(k_chol_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_chol_adjoint<<<dim3(m.n_chol, B), 128, sm, st>>>(m, x, s.ghat, s.Lpk, s.Lipk, s.sk, grad, s.dlnk, s.dlnr,
+    k_chol_adjoint<<<dim3(m.n_chol, B), chol_threads(m), sm, st>>>(m, x, s.ghat, s.Lpk, s.Lipk, s.sk, grad, s.dlnk, s.dlnr,
                                                        B);
   }
   if (m.n_gwbonly > 0)
