@@ -483,10 +483,10 @@ __global__ void k_final(DevModel m, const float* __restrict__ x, const double* _
 
 }  // namespace
 
-// Threads per CTA of the dense-bin kernels: their two packed triangles allow 5-6 CTAs per
-// SM at 67 pulsars, but only one at 150 (181 KB), where 4 warps would leave the FP64
-// latency exposed: 16 warps per CTA there.
-static int chol_threads(const DevModel& m) { return m.npsr >= 96 ? 512 : 128; }
+// Threads per CTA of the dense-bin kernels: their two packed triangles allow 5 CTAs per SM
+// at 67 pulsars (8 warps each), but only one at 150 (181 KB), where few warps would leave
+// the FP64 latency exposed: 16 warps per CTA there.
+static int chol_threads(const DevModel& m) { return m.npsr >= 96 ? 512 : 256; }
 
 static size_t chol_smem(const DevModel& m) {
   const size_t np = m.npsr, ntri = np * (np + 1) / 2;
