@@ -67,7 +67,8 @@ constexpr int XBW = 4 * (KCB / 2) * TTA;  // 32-bit words of one stored (tile, c
 constexpr int RES_XSB = XBW * 4;          // bytes of one stored block (16 KB)
 constexpr int KWB = 32;                   // TOAs per stage in k_f16_ftw
 constexpr int QWB = 144;                  // basis columns per chunk in k_f16_ftw (MMA N)
-constexpr int NSB = 4;                    // stages in k_f16_ftw
+constexpr int NSB = 4;                    // tensor-memory (w~) stages in k_f16_ftw
+constexpr int NSM = 5;                    // shared-memory (TMA landing) stages in k_f16_ftw
 constexpr uint32_t kWaitLimit = 4000000u;
 constexpr uint32_t kDrainLimit = 4000000u;
 
@@ -406,7 +407,7 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------------
 // k_f16_res
 // ---------------------------------------------------------------------------
-constexpr int RES_NXS = 8;             // shared-memory stages: a stored basis block and its coefficient slice
+constexpr int RES_NXS = 4;             // shared-memory stages: two stored basis blocks and their coefficient slices
 constexpr int RES_THREADS = 320;       // warp 0 MMA, warp 1 copies, warps 2-9 epilogue
 constexpr int RES_EPI0 = 64;           // first epilogue thread
 
@@ -438,7 +439,9 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
   const int b0 = cb * NC, nvalid = min(NC, B - b0);
   const size_t csz = 4 * (size_t)KXM * NC * 2;
   constexpr int CSL = 2 * 4 * NC * 16;                              // coefficient slice of one 16-column step
-  constexpr int STG = RES_XSB + CSL;                                // one stage: basis block + slice
+  constexpr int STB = RES_XSB + CSL;                                // one step: basis block + slice
+  constexpr int STG = 2 * STB;                                      // one stage: two steps
+  const int G2 = G / 2;                                             // stages (nkc is even: KX is a multiple of 32)
   unsigned char* Xs = smem;                                         // NXS stages
   double* redc = reinterpret_cast<double*>(smem + NXS * STG);       // [8][NC/2] chi2 partials
   float* redm = reinterpret_cast<float*>(redc + 4 * NC);            // [8][NC/2] max |w|
@@ -481,15 +484,19 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
         if (i >= 2 && !(ok = wait(&dempty[buf], ((i >> 1) - 1) & 1))) break;
         tc::fence_after();
         const uint32_t dbase = tmem + buf * CF::DB;
-        for (int kc = 0; kc < nkc; ++kc, ++g) {
+        for (int kc = 0; kc < nkc; kc += 2, ++g) {
           const int s = g % NXS;
           if (!(ok = wait(&xfull[s], (g / NXS) & 1))) break;
           tc::fence_after();
-          const uint64_t cd = tc::desc(xbase + s * STG + RES_XSB, 4 * NC * 16, 128);
 #pragma unroll
-          for (int a = 0; a < 4; ++a)
-            tc::mma_f16(dbase + a * NC, tc::desc(xbase + s * STG + a * (RES_XSB / 4), 2048, 128), cd,
-                        idesc_f16(TTA, (4 - a) * NC, 0), (kc | a) ? 1u : 0u);
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t sb = xbase + s * STG + h * STB;
+            const uint64_t cd = tc::desc(sb + RES_XSB, 4 * NC * 16, 128);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+              tc::mma_f16(dbase + a * NC, tc::desc(sb + a * (RES_XSB / 4), 2048, 128), cd,
+                          idesc_f16(TTA, (4 - a) * NC, 0), (kc | h | a) ? 1u : 0u);
+          }
           tc::commit(&xfree[s]);
         }
         if (!ok) break;
@@ -510,12 +517,16 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
       const unsigned char* xsrc = reinterpret_cast<const unsigned char*>(
           m.x16 + m.x16_off[I] + (size_t)((start - m.toa_off[I]) / TTA) * nkc * XBW);
       int g = 0;
-      for (; g < G; ++g) {
+      for (; g < G2; ++g) {
         const int s = g % NXS;
         if (g >= NXS && !wait(&xfree[s], ((g / NXS) - 1) & 1)) break;
         mbar_expect_tx(&xfull[s], STG);
-        bulk_g2s(Xs + s * STG, xsrc + (size_t)g * RES_XSB, RES_XSB, &xfull[s]);
-        bulk_g2s(Xs + s * STG + RES_XSB, csrc + (size_t)(g % nkc) * CSL, CSL, &xfull[s]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int gb = 2 * g + h;  // stored block: (tile gb / nkc, column block gb % nkc)
+          bulk_g2s(Xs + s * STG + h * STB, xsrc + (size_t)gb * RES_XSB, RES_XSB, &xfull[s]);
+          bulk_g2s(Xs + s * STG + h * STB + RES_XSB, csrc + (size_t)(gb % nkc) * CSL, CSL, &xfull[s]);
+        }
       }
       // no copy in flight into this CTA's shared memory at exit (bounded waits)
       for (int h = max(0, g - NXS); h < g; ++h)
@@ -635,10 +646,12 @@ constexpr int FW_WST = 3 * (KWB / 2);                   // columns of one w~ sta
 static_assert(FW_WB + NSB * FW_WST <= 512, "tensor memory");
 constexpr int FW_XARR = KWB * QWB * 2;                  // bytes of one basis piece per stage
 constexpr int FW_XST = 3 * FW_XARR;                     // one stage: pieces X0, X1, X2
-constexpr int FW_WSB = 128 * KWB * 4;                   // w~ stage: 128 chains x 32 TOAs (128-byte swizzled rows)
-constexpr int FW_SMEM = NSB * FW_XST + NSB * FW_WSB;
+constexpr int FW_WSB = 128 * KWB * 4;                   // w~ stage: two halves of 128 chains x 32 TOAs (128-byte swizzled rows)
+constexpr int FW_WHB = 128 * 32 * 4;                    // one half
+constexpr int FW_SMEM = NSM * FW_XST + NSM * FW_WSB;
 constexpr int FW_THREADS = 192;                         // warp 0 MMA, warps 1-4 w~ and epilogue, warp 5 copies
-static_assert((NSB * FW_XST) % 1024 == 0, "swizzled w~ stages start on 1024-byte boundaries");
+static_assert((NSM * FW_XST) % 1024 == 0, "swizzled w~ stages start on 1024-byte boundaries");
+static_assert(FW_SMEM + 2048 <= 227 * 1024, "shared memory");
 
 // TMA tile loads (tensor maps built on the host; coordinates innermost first)
 __device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* mbar) {
@@ -648,25 +661,27 @@ __device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int c0
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(tc::smem_u32(mbar))
       : "memory");
 }
-__device__ __forceinline__ void tma_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+__device__ __forceinline__ void tma_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                        uint64_t* mbar) {
   asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-      "%5, %6}], [%7];" ::"r"(tc::smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(tc::smem_u32(mbar))
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(tc::smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(tc::smem_u32(mbar))
       : "memory");
 }
 
-// Tensor maps: tw over w~ [chains][ntoa_pad] (FP32, box 32 TOAs x 128 chains, 128-byte
+// Tensor maps: tw over w~ [chains][ntoa_pad] (FP32, box 32 TOAs x 128 chains per 32-TOA half, 128-byte
 // swizzle: 16-byte chunk j of chain row n sits at chunk j ^ (n % 8)); tx over the stored
-// basis as (8 halves, TOA 128, half h 2, block, piece a 4) with byte strides 16, 2048,
-// 16384, 4096 (box 8 x 32 x 2 x 9 x 3: one stage's X0, X1, X2 rows of 144 columns, in
-// the MN-major order [a][column group][TOA][8 columns]).
+// basis as (TOA x 8 halves 1024, half h 2, block, piece a 4) with byte strides 2048,
+// 16384, 4096 (box 256 x 2 x 9 x 3: one stage's X0, X1, X2 rows of 144 columns as 512-byte
+// runs of 32 TOAs, in the MN-major order [a][column group][TOA][8 columns]).
 __global__ void __launch_bounds__(FW_THREADS, 1)
     k_f16_ftw(DevModel m, const __grid_constant__ CUtensorMap tw, const __grid_constant__ CUtensorMap tx,
               const float* __restrict__ wmx, float* __restrict__ gpart, int32_t* __restrict__ stat, int B) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t wland[NSB], wread[NSB], wfull[NSB], wfree[NSB], xfull[NSB], xfree[NSB], dfull,
+  // shared-memory stages (NSM: TMA landings of w~ and basis rows) and tensor-memory stages
+  // (NSB: w~ pieces) run as separate rings
+  __shared__ __align__(8) uint64_t wland[NSM], wread[NSM], xfull[NSM], xfree[NSM], wfull[NSB], wfree[NSB], dfull,
       drain;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_bad;
@@ -676,17 +691,19 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
   const int I = m.unit_psr[u], start = m.unit_start[u], len = m.unit_len[u], nst = len / KWB;
   const int b0 = cb * 128, nvalid = min(128, B - b0);
   const int q0 = qc * QWB, qw = min(QWB, m.P - q0), NQ = round_up_hd(qw, 16);
-  unsigned char* wsm = smem + NSB * FW_XST;
+  unsigned char* wsm = smem + NSM * FW_XST;
 
   if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
   if (tid == 0) {
-    for (int s = 0; s < NSB; ++s) {
+    for (int s = 0; s < NSM; ++s) {
       tc::mbar_init(&wland[s], 1);
       tc::mbar_init(&wread[s], 4);
-      tc::mbar_init(&wfull[s], 4);
-      tc::mbar_init(&wfree[s], 1);
       tc::mbar_init(&xfull[s], 1);
       tc::mbar_init(&xfree[s], 1);
+    }
+    for (int s = 0; s < NSB; ++s) {
+      tc::mbar_init(&wfull[s], 4);
+      tc::mbar_init(&wfree[s], 1);
     }
     tc::mbar_init(&dfull, 1);
     tc::mbar_init(&drain, 1);
@@ -711,9 +728,9 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
       const uint32_t xbase = tc::smem_u32(smem);
       bool ok = true;
       for (int g = 0; g < nst && ok; ++g) {
-        const int s = g % NSB;
+        const int s = g % NSB, sx = g % NSM;
         if (!(ok = wait(&wfull[s], (g / NSB) & 1))) break;
-        if (!(ok = wait(&xfull[s], (g / NSB) & 1))) break;
+        if (!(ok = wait(&xfull[sx], (g / NSM) & 1))) break;
         tc::fence_after();
         const uint32_t wa = tmem + FW_WB + s * FW_WST;
 #pragma unroll
@@ -721,7 +738,7 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
           uint64_t bx[3];
 #pragma unroll
           for (int j = 0; j < 3; ++j)
-            bx[j] = tc::desc(xbase + s * FW_XST + j * FW_XARR + ks * 256, 128, (KWB / 8) * 128);
+            bx[j] = tc::desc(xbase + sx * FW_XST + j * FW_XARR + ks * 256, 128, (KWB / 8) * 128);
           const uint32_t a0 = wa + 8 * ks, ah = a0 + KWB / 2, al = a0 + KWB;
           const uint32_t acc = (g | ks) ? 1u : 0u;
           mma_ts(tmem + FW_D0, a0, bx[0], ID, acc);  // L0 = W0 X0
@@ -732,7 +749,7 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
           mma_ts(tmem + FW_DR, al, bx[0], ID, 1u);
         }
         tc::commit(&wfree[s]);
-        tc::commit(&xfree[s]);
+        tc::commit(&xfree[sx]);
       }
       if (ok) tc::commit(&dfull);
       tc::commit(&drain);
@@ -748,14 +765,14 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
     const float wsc = pow2f(12 - ew);  // |w~| < 2^ew: scaled below 2^12
     bool ok = true;
     for (int g = 0; g < nst; ++g) {
-      const int s = g % NSB;
-      if (!(ok = __all_sync(0xffffffffu, wait(&wland[s], (g / NSB) & 1)))) break;
-      // row n of the swizzled stage: 16-byte chunk j at chunk j ^ (n % 8)
-      const unsigned char* row = wsm + s * FW_WSB + n * (KWB * 4);
-      uint32_t p0[16], ph[16], pl[16];
+      const int s = g % NSB, sx = g % NSM;
+      if (!(ok = __all_sync(0xffffffffu, wait(&wland[sx], (g / NSM) & 1)))) break;
+      // row n of each swizzled half: 16-byte chunk j at chunk j ^ (n % 8)
+      const unsigned char* row = wsm + sx * FW_WSB + n * 128;
+      uint32_t p0[KWB / 2], ph[KWB / 2], pl[KWB / 2];
 #pragma unroll
       for (int j = 0; j < KWB / 4; ++j) {
-        const float4 v = *reinterpret_cast<const float4*>(row + 16 * (j ^ (n & 7)));
+        const float4 v = *reinterpret_cast<const float4*>(row + (j / 8) * FW_WHB + 16 * ((j % 8) ^ (n & 7)));
         const float vv[4] = {v.x, v.y, v.z, v.w};
         float a0[4], ah[4], al[4];
 #pragma unroll
@@ -768,12 +785,15 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
         pl[2 * j + 1] = h2(al[2], al[3]);
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&wread[s]);  // the staged rows may be refilled
+      if (lane == 0) mbar_arrive(&wread[sx]);  // the staged rows may be refilled
       if (g >= NSB && !(ok = __all_sync(0xffffffffu, wait(&wfree[s], ((g / NSB) - 1) & 1)))) break;
       const uint32_t col = tmem + lanef + FW_WB + s * FW_WST;
-      st16(col, p0);
-      st16(col + KWB / 2, ph);
-      st16(col + KWB, pl);
+#pragma unroll
+      for (int h = 0; h < KWB / 32; ++h) {
+        st16(col + 16 * h, *reinterpret_cast<uint32_t(*)[16]>(p0 + 16 * h));
+        st16(col + KWB / 2 + 16 * h, *reinterpret_cast<uint32_t(*)[16]>(ph + 16 * h));
+        st16(col + KWB + 16 * h, *reinterpret_cast<uint32_t(*)[16]>(pl + 16 * h));
+      }
       wait_st();
       tc::fence_before();
       __syncwarp();
@@ -803,18 +823,18 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
     const int blk0 = (int)(m.x16_off[I] / XBW) + q0 / KCB;
     int g = 0;
     for (; g < nst; ++g) {
-      const int s = g % NSB;
-      if (g >= NSB && !(wait(&wread[s], ((g / NSB) - 1) & 1) && wait(&xfree[s], ((g / NSB) - 1) & 1))) break;
+      const int s = g % NSM;
+      if (g >= NSM && !(wait(&wread[s], ((g / NSM) - 1) & 1) && wait(&xfree[s], ((g / NSM) - 1) & 1))) break;
       const int toa = g * KWB, tau = tau0 + toa / TTA, tsub = toa % TTA;
       mbar_expect_tx(&wland[s], FW_WSB);
-      tma_2d(wsm + s * FW_WSB, &tw, start + toa, b0, &wland[s]);
+      for (int h = 0; h < KWB / 32; ++h) tma_2d(wsm + s * FW_WSB + h * FW_WHB, &tw, start + toa + 32 * h, b0, &wland[s]);
       mbar_expect_tx(&xfull[s], FW_XST);
-      tma_5d(smem + s * FW_XST, &tx, 0, tsub, 0, blk0 + tau * nkc, 0, &xfull[s]);
+      tma_4d(smem + s * FW_XST, &tx, 8 * tsub, 0, blk0 + tau * nkc, 0, &xfull[s]);
     }
     // no copy in flight into this CTA's shared memory at exit (bounded waits)
-    for (int h = max(0, g - NSB); h < g; ++h) {
-      tc::mbar_wait(&wland[h % NSB], (h / NSB) & 1, kDrainLimit);
-      tc::mbar_wait(&xfull[h % NSB], (h / NSB) & 1, kDrainLimit);
+    for (int h = max(0, g - NSM); h < g; ++h) {
+      tc::mbar_wait(&wland[h % NSM], (h / NSM) & 1, kDrainLimit);
+      tc::mbar_wait(&xfull[h % NSM], (h / NSM) & 1, kDrainLimit);
     }
   }
   tc::fence_before();
@@ -843,7 +863,7 @@ EncodeTiled encode_tiled() {
 template <int NC>
 size_t res_smem(const DevModel& m) {
   (void)m;
-  return (size_t)RES_NXS * (RES_XSB + 2 * 4 * NC * 16) + 4 * NC * (sizeof(double) + sizeof(float)) +
+  return (size_t)RES_NXS * 2 * (RES_XSB + 2 * 4 * NC * 16) + 4 * NC * (sizeof(double) + sizeof(float)) +
          NC * sizeof(float);
 }
 
@@ -870,20 +890,20 @@ cudaError_t launch_f16_nc(const DevModel& m, const Scratch& s, int B, cudaStream
   EncodeTiled enc = encode_tiled();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap tw, tx;
-  {
+  {  // [B][ntoa_pad]: box 32 TOAs x 128 chains, 128-byte swizzle
     const cuuint64_t dim[2] = {(cuuint64_t)m.ntoa_pad, (cuuint64_t)B};
     const cuuint64_t stride[1] = {(cuuint64_t)m.ntoa_pad * 4};
-    const cuuint32_t box[2] = {KWB, 128}, es[2] = {1, 1};
+    const cuuint32_t box[2] = {32, 128}, es[2] = {1, 1};
     if (enc(&tw, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, w, dim, stride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
         CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
   {
-    const cuuint64_t dim[5] = {8, TTA, 2, (cuuint64_t)m.x16_blocks, 4};
-    const cuuint64_t stride[4] = {16, 2048, (cuuint64_t)RES_XSB, 4096};
-    const cuuint32_t box[5] = {8, KWB, 2, QWB / KCB, 3}, es[5] = {1, 1, 1, 1, 1};
-    if (enc(&tx, CU_TENSOR_MAP_DATA_TYPE_UINT16, 5, const_cast<uint32_t*>(m.x16), dim, stride, box, es,
+    const cuuint64_t dim[4] = {8 * TTA, 2, (cuuint64_t)m.x16_blocks, 4};
+    const cuuint64_t stride[3] = {2048, (cuuint64_t)RES_XSB, 4096};
+    const cuuint32_t box[4] = {8 * KWB, 2, QWB / KCB, 3}, es[4] = {1, 1, 1, 1};
+    if (enc(&tx, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<uint32_t*>(m.x16), dim, stride, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
