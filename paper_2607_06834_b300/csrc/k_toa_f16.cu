@@ -407,7 +407,8 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------------
 // k_f16_res
 // ---------------------------------------------------------------------------
-constexpr int RES_NXS = 4;             // shared-memory stages: two stored basis blocks and their coefficient slices
+constexpr int RES_NXS = 3;             // shared-memory stages: up to three stored basis blocks and their coefficient slices
+constexpr int RES_KB = 3;              // stored blocks per stage, at most
 constexpr int RES_THREADS = 320;       // warp 0 MMA, warp 1 copies, warps 2-9 epilogue
 constexpr int RES_EPI0 = 64;           // first epilogue thread
 
@@ -440,8 +441,9 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
   const size_t csz = 4 * (size_t)KXM * NC * 2;
   constexpr int CSL = 2 * 4 * NC * 16;                              // coefficient slice of one 16-column step
   constexpr int STB = RES_XSB + CSL;                                // one step: basis block + slice
-  constexpr int STG = 2 * STB;                                      // one stage: two steps
-  const int G2 = G / 2;                                             // stages (nkc is even: KX is a multiple of 32)
+  constexpr int STG = RES_KB * STB;                                 // one stage: up to RES_KB steps
+  const int kb = nkc % 3 == 0 ? 3 : 2;                              // steps per stage (nkc is even)
+  const int G2 = G / kb;                                            // stages; a tile is nkc / kb of them
   unsigned char* Xs = smem;                                         // NXS stages
   double* redc = reinterpret_cast<double*>(smem + NXS * STG);       // [8][NC/2] chi2 partials
   float* redm = reinterpret_cast<float*>(redc + 4 * NC);            // [8][NC/2] max |w|
@@ -484,12 +486,12 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
         if (i >= 2 && !(ok = wait(&dempty[buf], ((i >> 1) - 1) & 1))) break;
         tc::fence_after();
         const uint32_t dbase = tmem + buf * CF::DB;
-        for (int kc = 0; kc < nkc; kc += 2, ++g) {
+        for (int kc = 0; kc < nkc; kc += kb, ++g) {
           const int s = g % NXS;
           if (!(ok = wait(&xfull[s], (g / NXS) & 1))) break;
           tc::fence_after();
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
+#pragma unroll 1
+          for (int h = 0; h < kb; ++h) {
             const uint32_t sb = xbase + s * STG + h * STB;
             const uint64_t cd = tc::desc(sb + RES_XSB, 4 * NC * 16, 128);
 #pragma unroll
@@ -520,10 +522,9 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
       for (; g < G2; ++g) {
         const int s = g % NXS;
         if (g >= NXS && !wait(&xfree[s], ((g / NXS) - 1) & 1)) break;
-        mbar_expect_tx(&xfull[s], STG);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int gb = 2 * g + h;  // stored block: (tile gb / nkc, column block gb % nkc)
+        mbar_expect_tx(&xfull[s], kb * STB);
+        for (int h = 0; h < kb; ++h) {
+          const int gb = kb * g + h;  // stored block: (tile gb / nkc, column block gb % nkc)
           bulk_g2s(Xs + s * STG + h * STB, xsrc + (size_t)gb * RES_XSB, RES_XSB, &xfull[s]);
           bulk_g2s(Xs + s * STG + h * STB + RES_XSB, csrc + (size_t)(gb % nkc) * CSL, CSL, &xfull[s]);
         }
@@ -863,7 +864,7 @@ EncodeTiled encode_tiled() {
 template <int NC>
 size_t res_smem(const DevModel& m) {
   (void)m;
-  return (size_t)RES_NXS * 2 * (RES_XSB + 2 * 4 * NC * 16) + 4 * NC * (sizeof(double) + sizeof(float)) +
+  return (size_t)RES_NXS * RES_KB * (RES_XSB + 2 * 4 * NC * 16) + 4 * NC * (sizeof(double) + sizeof(float)) +
          NC * sizeof(float);
 }
 
