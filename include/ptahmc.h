@@ -40,8 +40,11 @@ extern "C" {
 #define PTA_ETIMEOUT (-5) /* a bounded device wait gave up */
 
 /* Precision of the TOA-length contractions F a, F^T w, M^T w (Sec. "Single
- * precision").  The per-frequency Cholesky, its log-det, the timing-model solve
- * and the final sums are FP64 in every mode. */
+ * precision").  The log-det, the timing-model solve and the final sums are FP64 in
+ * every mode; the per-frequency Cholesky of the dense bins (with its inverse and
+ * adjoint) is FP64 in PTA_PREC_FP64 and under the CURN transform, and double-word
+ * (a pair of floats, ~48-bit significand, relative error ~1e-14) on the FP32 pipes
+ * otherwise. */
 #define PTA_PREC_FP64 0   /* plain path: stored FP64 basis, SIMT FP64 */
 #define PTA_PREC_FP32 1   /* basis generated on the fly, SIMT FP32 */
 #define PTA_PREC_TF32X3 2 /* tcgen05 tensor cores, 3-term split TF32 */
@@ -122,7 +125,7 @@ typedef struct {
 int pta_create(pta_ctx** out, const pta_model_desc* desc);
 /* Copies the pulsar's arrays.  PTA_EINVAL for inconsistent sizes, after
  * finalize, or beyond 166 pulsars (the per-frequency N_p x N_p Cholesky and its
- * adjoint are held in FP64 shared memory). */
+ * adjoint are held in shared memory, 8 bytes per element). */
 int pta_add_pulsar(pta_ctx* ctx, const pta_pulsar_desc* psr);
 /* Precompute (noise weights, normalised timing model, its FP64 Cholesky, the
  * Hellings-Downs matrix of Eq. HD, tile table) and upload.  Synchronises. */

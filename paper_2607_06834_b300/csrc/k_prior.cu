@@ -1,16 +1,18 @@
-// Prior side of the evaluation, FP64: spectra (Eq. power_law), the per-frequency
+// Prior side of the evaluation: spectra (Eq. power_law), the per-frequency
 // prior covariance Phi_k = rho_k Gamma + diag(kappa_.k) (Eq. prior_cov, Gamma of
 // Eq. HD), its Cholesky factor, inverse and log-det, the standardizing transform
 // a = L z (Eq. standardizing_transform with mu = 0), the adjoint of that transform
 // and the final per-chain sum.
 //
-// FP64 issue is the scarce resource on this part (about 1/58 of the FP32 rate), so
-// the dense-bin kernel keeps every FP64 warp instruction full: the triangular
+// FP64 issue is the scarce resource on this part (about 1/64 of the FP32 rate).  In
+// FP64 mode the dense-bin kernel keeps every FP64 warp instruction full: the triangular
 // updates walk a flat index over the active triangle / rectangle (decoded from a
 // table, no per-element square roots), the factorisation and the inverse advance in
 // one sweep with two barriers per column, and the per-column pivot work is one
 // Newton-refined reciprocal (LDL^T form; the square roots come at the end, all
-// pivots at once).
+// pivots at once).  In the other modes the dense-bin sweep and its adjoint run in
+// double-word arithmetic on the FP32 pipes (k_chol_forward_dw, k_chol_adjoint_dw);
+// spectra, pivots' square roots and every sum stay FP64.
 #include <cmath>
 
 #include "pta_internal.cuh"
@@ -167,6 +169,342 @@ __global__ void __launch_bounds__(512)
     const int i = t >> 8, j = t & 255;
     Lg[idx] = (i == j) ? u[j] : A[idx] * u[j];
     Xg[idx] = (i == j) ? rd[i] : X[idx] * rd[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Double-word arithmetic for the dense-bin sweep outside FP64 mode.  A value is the
+// unevaluated sum h + l of two floats with |l| <= ulp(h) / 2 (about 48 significant
+// bits).  A product takes the exact remainder of h_a h_b from a fused multiply-add
+// (Dekker's product); a sum takes the exact error of h_a + h_b from Knuth's TwoSum and
+// renormalises (the double-word algorithms analysed by Joldes, Muller and Popescu,
+// ACM TOMS 44, 2017).  The _rn intrinsics keep the compiler from contracting a product
+// into the following sum, which would lose the remainder.  On this part the FP32 pipes
+// issue 64 times as many operations per clock as the FP64 pipe, so ~15 FP32 operations
+// per multiply-add still run the sweep several times faster than FP64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 dw_renorm(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ float2 dw_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float q = __fmaf_rn(a.x, b.x, -p);
+  q = __fmaf_rn(a.x, b.y, q);
+  q = __fmaf_rn(a.y, b.x, q);
+  return dw_renorm(p, q);
+}
+// c - a b
+__device__ __forceinline__ float2 dw_fms(float2 c, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float q = __fmaf_rn(a.x, b.x, -p);
+  q = __fmaf_rn(a.x, b.y, q);
+  q = __fmaf_rn(a.y, b.x, q);
+  const float s = __fsub_rn(c.x, p);
+  const float t = __fsub_rn(s, c.x);
+  float e = __fsub_rn(__fsub_rn(c.x, __fsub_rn(s, t)), __fadd_rn(p, t));  // (c.x - p) - s exactly
+  e = __fadd_rn(e, __fsub_rn(c.y, q));
+  return dw_renorm(s, e);
+}
+__device__ __forceinline__ float2 dw_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float t = __fsub_rn(s, a.x);
+  float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, t)), __fsub_rn(b.x, t));
+  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+  return dw_renorm(s, e);
+}
+// 1 / d for d > 0: one Newton step from the correctly rounded float reciprocal
+// (relative error ~2^-47: the step squares the float's 2^-24)
+__device__ __forceinline__ float2 dw_recip(float2 d) {
+  const float r = __frcp_rn(d.x);
+  float e = __fmaf_rn(-d.x, r, 1.0f);  // exact: |1 - d.x r| < 2^-23 has at most 24 significant bits
+  e = __fmaf_rn(-d.y, r, e);
+  return dw_renorm(r, __fmul_rn(r, e));
+}
+__device__ __forceinline__ float2 d2dw(double v) {
+  const float h = __double2float_rn(v);
+  return make_float2(h, __double2float_rn(v - (double)h));
+}
+// Exact float -> double on the integer pipes (the exponent rebias 127 -> 1023 and the
+// 23-bit fraction moved to the top of the 52-bit one; zero and subnormals give 0,
+// infinities and NaNs keep their class), so that the conversions of the output
+// triangles do not queue on the FP64 pipe.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f), e = (u >> 23) & 0xffu;
+  const unsigned ef = (e == 0xffu) ? 0x7ffu : e + 896u;
+  const unsigned hi = (u & 0x80000000u) | (ef << 20) | ((u & 0x7fffffu) >> 3);
+  return (e == 0u) ? 0.0 : __hiloint2double((int)hi, (int)(u << 29));
+}
+__device__ __forceinline__ double dw2d(float2 v) { return f2d_bits(v.x) + f2d_bits(v.y); }
+
+// The dense-bin factorisation of k_chol_forward with the sweep in double-word
+// arithmetic, two columns per step.  Phi_k is scaled by 2^-E (E from its largest
+// diagonal entry, so every entry and pivot lies in (0, 1]) before the sweep, which
+// leaves the unit factor and its inverse unchanged and scales the pivots by 2^-E; the
+// pivots return to double and their true scale before the square roots.
+//
+// Step for columns (j, j+1): every thread factors the 2x2 pivot block itself from the
+// three values the previous step left in pv (the same arithmetic, so the same result
+// in every thread, and no barrier to share it); pass A scales column j, updates column
+// j+1 by it and scales that for the rows below, and eliminates row j+1 of L^-1; pass B
+// applies the rank-2 update to the trailing triangle and the two eliminations to the
+// rows of L^-1 below.  Two barriers per two columns.
+//
+// Outputs: a64 as k_chol_forward; L D^(1/2) and D^(-1/2) L^-1 packed lower in the
+// same slots as k_chol_forward's, as double-word float pairs (read by
+// k_chol_adjoint_dw).
+__global__ void __launch_bounds__(512)
+    k_chol_forward_dw(DevModel m, const float* __restrict__ x, const double* __restrict__ sk,
+                      const double* __restrict__ srho, double* a64, float2* Lpk, float2* Lipk, int32_t* stat) {
+  extern __shared__ float2 smw[];
+  const int np = m.npsr, ntri = np * (np + 1) / 2;
+  float2* A = smw;            // packed lower: L (unit, below the diagonal) and D (diagonal)
+  float2* X = A + ntri;       // packed lower: L^-1 (unit lower)
+  float2* u0 = X + ntri;      // [np] unscaled column j
+  float2* u1 = u0 + np;       // [np] unscaled column j+1 after column j's update
+  float2* ww = u1 + np;       // [2][np] sqrt(d_J) z_J
+  float2* sqw = ww + 2 * np;  // [np] sqrt(d_j)
+  float2* rqw = sqw + np;     // [np] 1 / sqrt(d_j)
+  __shared__ float2 pv[3];    // the next step's pivot block: A_jj, A_j+1,j, A_j+1,j+1
+  __shared__ int s_bad;
+  const int k = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, nt = blockDim.x;
+  const float* xb = x + (size_t)b * m.d;
+  const double sr = srho[(size_t)b * m.na + k];
+  const double rho = sr * sr;
+  const double* skb = sk + (size_t)b * np * m.na + k;
+  // scale 2^-E from the largest diagonal entry (every warp computes it; no barrier)
+  double dmax = 0.0;
+  for (int i = tid & 31; i < np; i += 32) {
+    const double s = skb[(size_t)i * m.na];
+    dmax = fmax(dmax, fma(s, s, rho * m.Gamma[i * np + i]));
+  }
+  for (int o = 16; o; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  int E = 0;
+  if (dmax > 0.0 && isfinite(dmax)) frexp(dmax, &E);
+  const float2 rhow = d2dw(ldexp(rho, -E));
+  if (tid == 0) s_bad = 0;
+  for (int idx = tid; idx < ntri; idx += nt) {
+    const unsigned t = m.trimap[idx];
+    const int i = t >> 8, j = t & 255;
+    float2 v = dw_mul(rhow, m.Gamma_dw[idx]);
+    if (i == j) {
+      const double s = skb[(size_t)i * m.na];
+      v = dw_add(v, d2dw(ldexp(s * s, -E)));
+    }
+    A[idx] = v;
+    X[idx] = make_float2((i == j) ? 1.0f : 0.0f, 0.0f);
+    if (idx < 3) pv[idx] = v;
+  }
+  __syncthreads();
+  for (int j = 0; j < np; j += 2) {
+    float2 d0 = pv[0];
+    int bad = !(d0.x > 0.0f);
+    if (bad) d0 = make_float2(1.0f, 0.0f);
+    const float2 r0 = dw_recip(d0);
+    if (j + 1 == np) {  // odd order: the last column has its pivot only
+      if (tid == 0) {
+        A[tri(j, j)] = d0;
+        if (bad) s_bad = 1;
+      }
+      break;
+    }
+    const float2 a10 = pv[1];  // unscaled A_{j+1,j}
+    const float2 l10 = dw_mul(a10, r0);
+    float2 d1 = dw_fms(pv[2], l10, a10);
+    if (!(d1.x > 0.0f)) {
+      bad = 1;
+      d1 = make_float2(1.0f, 0.0f);
+    }
+    const float2 r1 = dw_recip(d1);
+    const int rj = j * (j + 1) / 2, rj1 = rj + j + 1;  // offsets of rows j and j+1
+    if (tid == 0) {
+      A[rj + j] = d0;
+      A[rj1 + j] = l10;
+      A[rj1 + j + 1] = d1;
+      if (bad) s_bad = 1;
+    }
+    // pass A: columns j, j+1 of rows i >= j+2; row j+1 of L^-1 (columns <= j)
+    const int s2 = np - j - 2;
+    for (int e = tid; e < s2 + j + 1; e += nt) {
+      if (e < s2) {
+        const int i = j + 2 + e, rb = i * (i + 1) / 2;
+        const float2 a0 = A[rb + j], a1 = A[rb + j + 1];
+        const float2 l0 = dw_mul(a0, r0);
+        const float2 w = dw_fms(a1, l0, a10);
+        u0[i] = a0;
+        u1[i] = w;
+        A[rb + j] = l0;
+        A[rb + j + 1] = dw_mul(w, r1);
+      } else {
+        const int c = e - s2;
+        X[rj1 + c] = dw_fms(X[rj1 + c], l10, X[rj + c]);
+      }
+    }
+    __syncthreads();
+    // pass B: rank-2 update of the trailing triangle (rows, columns >= j+2) and the
+    // eliminations of rows >= j+2 of L^-1 in columns <= j+1
+    const int w2 = j + 2, cntA = s2 * (s2 + 1) / 2, cnt = cntA + s2 * w2;
+    const float rw = 1.0f / (float)w2;
+    for (int idx = tid; idx < cnt; idx += nt) {
+      if (idx < cntA) {
+        const unsigned t = m.trimap[idx];
+        const int i = (t >> 8) + j + 2, l = (t & 255) + j + 2, rb = i * (i + 1) / 2;
+        float2 v = dw_fms(A[rb + l], A[rb + j], u0[l]);
+        v = dw_fms(v, A[rb + j + 1], u1[l]);
+        A[rb + l] = v;
+        if (idx < 3) pv[idx] = v;
+      } else {
+        const int e = idx - cntA;
+        int q = (int)(((float)e + 0.5f) * rw);
+        q -= (q * w2 > e);
+        q += ((q + 1) * w2 <= e);
+        const int i = j + 2 + q, c = e - q * w2, rb = i * (i + 1) / 2;
+        float2 v;
+        if (c <= j) {
+          v = dw_fms(X[rb + c], A[rb + j], X[rj + c]);
+          v = dw_fms(v, A[rb + j + 1], X[rj1 + c]);
+        } else {  // c = j+1: X_{j,j+1} = 0 and X_{j+1,j+1} = 1, so X_{i,j+1} = -l_{i,j+1}
+          const float2 l1 = A[rb + j + 1];
+          v = make_float2(-l1.x, -l1.y);
+        }
+        X[rb + c] = v;
+      }
+    }
+    __syncthreads();
+  }
+  if (s_bad && tid == 0) atomicOr(&stat[b], 2);
+  __syncthreads();
+  // pivots at their true scale: sqrt(d_j) and 1/sqrt(d_j) in FP64, kept as double words
+  for (int j = tid; j < np; j += nt) {
+    const double d = ldexp(dw2d(A[tri(j, j)]), E);
+    const double y = rsqrt64(d);
+    sqw[j] = d2dw(d * y);
+    rqw[j] = d2dw(y);
+    const double zs0 = xb[m.z_ach + (2 * k) * np + j], zs1 = xb[m.z_ach + (2 * k + 1) * np + j];
+    ww[j] = d2dw(d * y * zs0);
+    ww[np + j] = d2dw(d * y * zs1);
+  }
+  __syncthreads();
+  float2* Lg = Lpk + ((size_t)b * m.n_chol + k) * ntri;
+  float2* Xg = Lipk + ((size_t)b * m.n_chol + k) * ntri;
+  for (int idx = tid; idx < ntri; idx += nt) {
+    const unsigned t = m.trimap[idx];
+    const int i = t >> 8, j = t & 255;
+    Lg[idx] = (i == j) ? sqw[j] : dw_mul(A[idx], sqw[j]);
+    Xg[idx] = (i == j) ? rqw[i] : dw_mul(X[idx], rqw[i]);
+  }
+  // a_{I,k,c} = sum_{J<=I} L[I][J] (sqrt(d_J) z_{J,k,c}), L unit lower
+  for (int i = tid; i < 2 * np; i += nt) {
+    const int c = i / np, I = i % np, rb = I * (I + 1) / 2;
+    const float2* wc = ww + c * np;
+    float2 acc = wc[I];
+    for (int J = 0; J < I; ++J) {
+      const float2 w = wc[J];
+      acc = dw_fms(acc, A[rb + J], make_float2(-w.x, -w.y));
+    }
+    a64[((size_t)I * gridDim.y + b) * m.PM + 2 * k + c] = dw2d(acc);
+  }
+}
+
+// Adjoint of k_chol_forward_dw's transform (the formulas of k_chol_adjoint below) in
+// double-word arithmetic, from its double-word factors.  The walk over a >= I behind
+// kappa_I d logp / d kappa_I is cut into nseg segments taken by different threads:
+// segment q returns its own sum with prefixes started at zero (loc), its prefix totals
+// P_c = sum u_a z_ca and the sums V_c = sum gt_ca u_a, and the walk is
+// sum_q loc_q + sum_c (P_c of the segments before q) V_cq.
+__device__ __forceinline__ float2 dw_mulf(float2 a, float b) {
+  const float p = __fmul_rn(a.x, b);
+  float q = __fmaf_rn(a.x, b, -p);
+  q = __fmaf_rn(a.y, b, q);
+  return dw_renorm(p, q);
+}
+__device__ __forceinline__ float2 dw_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+__global__ void __launch_bounds__(512)
+    k_chol_adjoint_dw(DevModel m, const float* __restrict__ x, const double* __restrict__ ghat,
+                      const float2* __restrict__ Lpk, const float2* __restrict__ Lipk, const double* __restrict__ sk,
+                      float* grad, double* dlnk, double* dlnr, int B) {
+  extern __shared__ float2 smw[];
+  const int np = m.npsr, ntri = np * (np + 1) / 2, nt = blockDim.x;
+  const int nseg = max(1, min(4, nt / np));
+  float2* Ls = smw;
+  float2* Xs = smw + max(ntri, 5 * nseg * np + np);
+  float2* gs = Xs + ntri;   // [2][np] ghat
+  float2* gt = gs + 2 * np; // [2][np] L^T ghat
+  // once gt no longer needs L, its slot holds the partial walks: (loc, V0, V1) per
+  // segment, the prefix totals P_c, and kappa d logp / d kappa
+  float2* seg = Ls;                                            // [nseg][np][3]
+  double* segp = reinterpret_cast<double*>(Ls + 3 * nseg * np);  // [nseg][np][2]
+  double* red = segp + 2 * nseg * np;                          // [np]
+  const int k = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
+  const float* xb = x + (size_t)b * m.d;
+  const float* zb = xb + m.z_ach + (2 * k) * np;  // [2][np]
+  const float2* Lg = Lpk + ((size_t)b * m.n_chol + k) * ntri;
+  const float2* Xg = Lipk + ((size_t)b * m.n_chol + k) * ntri;
+  for (int idx = tid; idx < ntri; idx += nt) {
+    Ls[idx] = Lg[idx];
+    Xs[idx] = Xg[idx];
+  }
+  for (int i = tid; i < 2 * np; i += nt) {
+    const int c = i / np, I = i % np;
+    gs[i] = d2dw(ghat[((size_t)I * B + b) * m.P + 2 * k + c]);
+  }
+  __syncthreads();
+  for (int i = tid; i < 2 * np; i += nt) {
+    const int c = i / np, J = i % np;
+    const float2* gc = gs + c * np;
+    float2 s = make_float2(0.0f, 0.0f);
+    for (int I = J; I < np; ++I) s = dw_fms(s, Ls[tri(I, J)], dw_neg(gc[I]));
+    gt[i] = s;
+    grad[(size_t)b * m.d + m.z_ach + (2 * k) * np + i] = __fadd_rn(__fsub_rn(s.x, zb[i]), s.y);
+  }
+  __syncthreads();
+  for (int r = tid; r < nseg * np; r += nt) {
+    const int I = r % np, q = r / np, len = np - I;
+    const int a0 = I + len * q / nseg, a1 = I + len * (q + 1) / nseg;
+    float2 p0 = make_float2(0.0f, 0.0f), p1 = p0, v0 = p0, v1 = p0, acc = p0;
+    for (int a = a0; a < a1; ++a) {
+      const float2 u = Xs[tri(a, I)];
+      const float2 g0 = dw_mul(gt[a], u), g1 = dw_mul(gt[np + a], u);
+      const float2 w0 = dw_mulf(u, zb[a]), w1 = dw_mulf(u, zb[np + a]);
+      const float2 h0 = dw_add(p0, make_float2(0.5f * w0.x, 0.5f * w0.y));
+      const float2 h1 = dw_add(p1, make_float2(0.5f * w1.x, 0.5f * w1.y));
+      acc = dw_fms(acc, g0, dw_neg(h0));
+      acc = dw_fms(acc, g1, dw_neg(h1));
+      p0 = dw_add(p0, w0);
+      p1 = dw_add(p1, w1);
+      v0 = dw_add(v0, g0);
+      v1 = dw_add(v1, g1);
+    }
+    float2* sg = seg + 3 * r;
+    sg[0] = acc;
+    sg[1] = v0;
+    sg[2] = v1;
+    segp[2 * r] = dw2d(p0);
+    segp[2 * r + 1] = dw2d(p1);
+  }
+  __syncthreads();
+  for (int I = tid; I < np; I += nt) {
+    double acc = 0.0, p0 = 0.0, p1 = 0.0;
+    for (int q = 0; q < nseg; ++q) {
+      const int r = q * np + I;
+      const float2* sg = seg + 3 * r;
+      acc += dw2d(sg[0]) + p0 * dw2d(sg[1]) + p1 * dw2d(sg[2]);
+      p0 += segp[2 * r];
+      p1 += segp[2 * r + 1];
+    }
+    const double s = sk[((size_t)b * np + I) * m.na + k];
+    const double v = s * s * acc;
+    red[I] = v;
+    dlnk[((size_t)b * np + I) * m.na + k] = v;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    double s = 0.0;
+    for (int i = tid; i < np; i += 32)
+      s += 0.5 * (dw2d(gt[i]) * (double)zb[i] + dw2d(gt[np + i]) * (double)zb[np + i]) - red[i];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (tid == 0) dlnr[(size_t)b * m.na + k] = s;
   }
 }
 
@@ -492,6 +830,19 @@ static size_t chol_smem(const DevModel& m) {
   const size_t np = m.npsr, ntri = np * (np + 1) / 2;
   return (2 * ntri + 4 * np) * sizeof(double);
 }
+// The double-word sweep and adjoint run everywhere but in FP64 mode and under the CURN
+// transform (whose whitening kernel reads the FP64 inverse factors).
+static bool chol_dw(const DevModel& m, int fp64) { return !fp64 && !m.curn; }
+
+static size_t adj_smem_dw(const DevModel& m) {
+  const size_t np = m.npsr, ntri = np * (np + 1) / 2;
+  const size_t nseg = std::max<size_t>(1, std::min<size_t>(4, chol_threads(m) / np));
+  return (std::max(ntri, 5 * nseg * np + np) + ntri + 4 * np) * 8;
+}
+static size_t chol_smem_dw(const DevModel& m) {
+  const size_t np = m.npsr, ntri = np * (np + 1) / 2;
+  return (2 * ntri + 6 * np) * sizeof(float2);
+}
 static size_t adj_smem(const DevModel& m) {
   const size_t np = m.npsr, ntri = np * (np + 1) / 2;
   return (2 * ntri + 7 * np) * sizeof(double);
@@ -505,15 +856,21 @@ int count_prior_adjoint(const DevModel& m) { return m.curn ? 1 : count_prior_for
 
 cudaError_t launch_prior_forward(const DevModel& m, const Scratch& s, int B, const float* x, int fp64,
                                  cudaStream_t st, cudaEvent_t* kev) {
-  (void)fp64;
   const int nspec = m.npsr * (m.na + m.nd) + m.na;
   k_spectra<<<dim3((nspec + 127) / 128, B), 128, 0, st>>>(m, x, s.sk, s.skd, s.srho);
   if (m.n_chol > 0) {
-    const size_t sm = chol_smem(m);
-    cudaError_t e = cudaFuncSetAttribute(k_chol_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const bool dw = chol_dw(m, fp64);
+    const size_t sm = dw ? chol_smem_dw(m) : chol_smem(m);
+    cudaError_t e = dw ? cudaFuncSetAttribute(k_chol_forward_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                       : cudaFuncSetAttribute(k_chol_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     if (kev) cudaEventRecord(kev[0], st);
-    k_chol_forward<<<dim3(m.n_chol, B), chol_threads(m), sm, st>>>(m, x, s.sk, s.srho, s.a64, s.Lpk, s.Lipk, s.stat);
+    if (dw)
+      k_chol_forward_dw<<<dim3(m.n_chol, B), chol_threads(m), sm, st>>>(
+          m, x, s.sk, s.srho, s.a64, reinterpret_cast<float2*>(s.Lpk), reinterpret_cast<float2*>(s.Lipk), s.stat);
+    else
+      k_chol_forward<<<dim3(m.n_chol, B), chol_threads(m), sm, st>>>(m, x, s.sk, s.srho, s.a64, s.Lpk, s.Lipk,
+                                                                      s.stat);
     if (kev) cudaEventRecord(kev[1], st);
   }
   if (m.curn) return cudaGetLastError();  // a comes from the CURN transform (launch_curn_forward)
@@ -523,14 +880,21 @@ cudaError_t launch_prior_forward(const DevModel& m, const Scratch& s, int B, con
   return cudaGetLastError();
 }
 
-cudaError_t launch_prior_adjoint(const DevModel& m, const Scratch& s, int B, const float* x, float* grad,
+cudaError_t launch_prior_adjoint(const DevModel& m, const Scratch& s, int B, const float* x, float* grad, int fp64,
                                  cudaStream_t st) {
   if (m.n_chol > 0) {
-    const size_t sm = adj_smem(m);
-    cudaError_t e = cudaFuncSetAttribute(k_chol_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const bool dw = chol_dw(m, fp64);
+    const size_t sm = dw ? adj_smem_dw(m) : adj_smem(m);
+    cudaError_t e = dw ? cudaFuncSetAttribute(k_chol_adjoint_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                       : cudaFuncSetAttribute(k_chol_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_chol_adjoint<<<dim3(m.n_chol, B), chol_threads(m), sm, st>>>(m, x, s.ghat, s.Lpk, s.Lipk, s.sk, grad, s.dlnk, s.dlnr,
-                                                       B);
+    if (dw)
+      k_chol_adjoint_dw<<<dim3(m.n_chol, B), chol_threads(m), sm, st>>>(
+          m, x, s.ghat, reinterpret_cast<const float2*>(s.Lpk), reinterpret_cast<const float2*>(s.Lipk), s.sk, grad,
+          s.dlnk, s.dlnr, B);
+    else
+      k_chol_adjoint<<<dim3(m.n_chol, B), chol_threads(m), sm, st>>>(m, x, s.ghat, s.Lpk, s.Lipk, s.sk, grad, s.dlnk,
+                                                                      s.dlnr, B);
   }
   if (m.n_gwbonly > 0)
     k_gwbonly_adjoint<<<dim3(m.n_gwbonly, B), 128, 0, st>>>(m, x, s.ghat, s.srho, grad, s.dlnr, B);

@@ -556,6 +556,16 @@ int pta_finalize(pta_ctx* c, void* stream) {
     if (cudaDeviceGetAttribute(&m.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || m.nsm < 1) m.nsm = 1;
   }
   UP(Gam, Gamma);
+  {
+    std::vector<float2> gdw((size_t)npsr * (npsr + 1) / 2);
+    for (int i = 0, q = 0; i < npsr; ++i)
+      for (int j = 0; j <= i; ++j, ++q) {
+        const double g = Gam[(size_t)i * npsr + j];
+        const float h = (float)g;
+        gdw[q] = make_float2(h, (float)(g - (double)h));
+      }
+    UP(gdw, Gamma_dw);
+  }
   UP(LG, LGamma);
   UP(LGi, LGammaInv);
   UP(Grev, Grev);
@@ -805,7 +815,7 @@ int pta_eval_scratch(pta_ctx* c, const pta::Scratch& s, int B, const float* x, d
   if (grad) {
     tm.begin(3);
     if (e == cudaSuccess)
-      e = m.curn ? pta::launch_curn_adjoint(m, s, B, x, grad, st) : pta::launch_prior_adjoint(m, s, B, x, grad, st);
+      e = m.curn ? pta::launch_curn_adjoint(m, s, B, x, grad, st) : pta::launch_prior_adjoint(m, s, B, x, grad, fp64, st);
     if (e == cudaSuccess && m.curn && m.cw) {
       // CW gradient through the mean: weights w~ - N~^-1 F A^-1 gbar at every TOA, the
       // second from a TOA pass with a = a_ref - A^-1 gbar, zero residual and no signal

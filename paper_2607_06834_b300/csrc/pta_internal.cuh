@@ -90,6 +90,7 @@ struct DevModel {
   const double* lnk;            // ln k, k = 0..max(na, nd) (entry 0 unused)
   const unsigned short* trimap; // packed-lower index -> (row << 8) | col, for npsr <= 256
   const double* Gamma;          // [npsr x npsr]
+  const float2* Gamma_dw;       // Gamma packed lower (trimap order) as double-word float pairs
   const double* LGamma;         // chol(Gamma), lower, [npsr x npsr]
   const double* LGammaInv;      // chol(Gamma)^-1, lower, [npsr x npsr]
   // CURN-posterior transform (Eq. PTA_standard_transform_curn), when curn = 1
@@ -114,7 +115,7 @@ struct Scratch {
   float* a32 = nullptr;        // [npsr][cap][PM]  (a, then timing-model offsets c)
   unsigned char* a16 = nullptr; // BF16 hi/lo coefficient chunks in the tensor-core layout
   double* a64 = nullptr;       // [npsr][cap][PM]
-  double* Lpk = nullptr;       // [cap][n_chol][np(np+1)/2]
+  double* Lpk = nullptr;       // [cap][n_chol][np(np+1)/2]; double-word float pairs outside FP64 mode
   double* Lipk = nullptr;      // same, inverse factor
   float* gpart = nullptr;      // [units][cap][Qs]
   double* gpart64 = nullptr;   // [units][cap][Qs] (FP64 path)
@@ -202,7 +203,7 @@ cudaError_t launch_cw_gradient(const DevModel& m, const Scratch& s, int B, cudaS
 cudaError_t launch_tm_prologue(const DevModel& m, const Scratch& s, int B, int fp64, cudaStream_t st);
 cudaError_t launch_reduce(const DevModel& m, const Scratch& s, int B, int fp64, cudaStream_t st);
 cudaError_t launch_prior_adjoint(const DevModel& m, const Scratch& s, int B, const float* x,
-                                 float* grad, cudaStream_t st);
+                                 float* grad, int fp64, cudaStream_t st);
 int count_prior_forward(const DevModel& m);
 size_t curn_w_doubles(const DevModel& m);  // P (P + 1) / 2
 cudaError_t launch_curn_forward(const DevModel& m, const Scratch& s, int B, const float* x, cudaStream_t st);
