@@ -15,6 +15,7 @@
 // spectra, pivots' square roots and every sum stay FP64.
 #include <cmath>
 
+#include "dwarith.cuh"
 #include "pta_internal.cuh"
 
 namespace pta {
@@ -23,9 +24,28 @@ namespace {
 __device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 
 // ---------------------------------------------------------------------------
-// Spectra: sqrt(kappa_Ik) (red noise, k < n_rn), sqrt(kappa^DM_Ik), sqrt(rho_k)
-// (k < n_gwb), FP64, one thread per value.
+// Spectra: sqrt(kappa_Ik) (red noise, k < n_rn; 0 up to na), sqrt(kappa^DM_Ik),
+// sqrt(rho_k) (k < n_gwb), one thread per value: exp(ln_pl / 2) (Eq. power_law) or
+// 10^((theta + 18) / 2) for a free spectrum.  DW (outside FP64 mode): the argument is
+// formed and exponentiated in double-word arithmetic on the FP32 pipes (relative
+// error ~1e-13, from the argument's ~2^-48 |terms|), so a value costs one FP64 add
+// instead of an FP64 exponential; FP64 mode keeps the FP64 exponential.
 // ---------------------------------------------------------------------------
+template <bool DW>
+__device__ __forceinline__ double half_pl(const DevModel& m, float lnA, float ga, int k) {  // exp(ln_pl/2)
+  if (!DW) return exp(0.5 * ln_pl(m.ln_rho0, m.ln_Tfyr, lnA, ga, m.lnk[k]));
+  constexpr float2 kLn10 = {0x1.26bb1cp+1f, -0x1.12aabap-25f};
+  const float2 arg = dw_add(dw_add(dw_mulf(kLn10, lnA), m.hr0), dw_neg(dw_mulf(m.lkT[k], __fmul_rn(0.5f, ga))));
+  return dw_exp_d(arg);
+}
+template <bool DW>
+__device__ __forceinline__ double half_free(float theta) {  // 10^((theta + 18) / 2)
+  if (!DW) return exp(0.5 * kLn10 * ((double)theta + 18.0));
+  constexpr float2 kHalfLn10 = {0x1.26bb1cp+0f, -0x1.12aabap-26f};
+  return dw_exp_d(dw_mul(kHalfLn10, dw_addf(make_float2(theta, 0.0f), 18.0f)));
+}
+
+template <bool DW>
 __global__ void k_spectra(DevModel m, const float* __restrict__ x, double* sk, double* skd, double* srho) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
   const int np = m.npsr, nach = np * m.na, ndm = np * m.nd;
@@ -35,19 +55,17 @@ __global__ void k_spectra(DevModel m, const float* __restrict__ x, double* sk, d
   if (r < nach) {
     const int I = r / m.na, k = r % m.na;
     if (k < m.n_rn)  // free spectrum: kappa = 10^theta s^2 = 10^(theta + 18) ns^2
-      v = m.rn_free ? exp(0.5 * kLn10 * ((double)xb[m.th_rn + m.n_rn * I + k] + 18.0))
-                    : exp(0.5 * ln_pl(m.ln_rho0, m.ln_Tfyr, xb[m.th_rn + 2 * I], xb[m.th_rn + 2 * I + 1],
-                                      m.lnk[k + 1]));
+      v = m.rn_free ? half_free<DW>(xb[m.th_rn + m.n_rn * I + k])
+                    : half_pl<DW>(m, xb[m.th_rn + 2 * I], xb[m.th_rn + 2 * I + 1], k + 1);
     sk[(size_t)b * nach + r] = v;
   } else if (r < nach + ndm) {
     const int q = r - nach, I = q / m.nd, k = q % m.nd;
-    v = exp(0.5 * ln_pl(m.ln_rho0, m.ln_Tfyr, xb[m.th_dm + 2 * I], xb[m.th_dm + 2 * I + 1], m.lnk[k + 1]));
+    v = half_pl<DW>(m, xb[m.th_dm + 2 * I], xb[m.th_dm + 2 * I + 1], k + 1);
     skd[(size_t)b * ndm + q] = v;
   } else {
     const int k = r - nach - ndm;
     if (k < m.n_gwb)
-      v = m.gwb_free ? exp(0.5 * kLn10 * ((double)xb[m.th_gwb + k] + 18.0))
-                     : exp(0.5 * ln_pl(m.ln_rho0, m.ln_Tfyr, xb[m.th_gwb], xb[m.th_gwb + 1], m.lnk[k + 1]));
+      v = m.gwb_free ? half_free<DW>(xb[m.th_gwb + k]) : half_pl<DW>(m, xb[m.th_gwb], xb[m.th_gwb + 1], k + 1);
     srho[(size_t)b * m.na + k] = v;
   }
 }
@@ -172,70 +190,63 @@ __global__ void __launch_bounds__(512)
   }
 }
 
-// ---------------------------------------------------------------------------
-// Double-word arithmetic for the dense-bin sweep outside FP64 mode.  A value is the
-// unevaluated sum h + l of two floats with |l| <= ulp(h) / 2 (about 48 significant
-// bits).  A product takes the exact remainder of h_a h_b from a fused multiply-add
-// (Dekker's product); a sum takes the exact error of h_a + h_b from Knuth's TwoSum and
-// renormalises (the double-word algorithms analysed by Joldes, Muller and Popescu,
-// ACM TOMS 44, 2017).  The _rn intrinsics keep the compiler from contracting a product
-// into the following sum, which would lose the remainder.  On this part the FP32 pipes
-// issue 64 times as many operations per clock as the FP64 pipe, so ~15 FP32 operations
-// per multiply-add still run the sweep several times faster than FP64.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 dw_renorm(float s, float e) {
-  const float h = __fadd_rn(s, e);
-  return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+// Packed lower triangle with every row starting at an even element (row i holds i+1
+// elements, padded to an even count), so that a pair of entries at an even column is
+// one 16-byte access: row i starts at i(i+2)/2 (i even) or (i+1)^2/2 (i odd).
+__host__ __device__ __forceinline__ int prow(int i) { return (i & 1) ? (i + 1) * (i + 1) / 2 : i * (i + 2) / 2; }
+
+// Factor a 2x2 pivot block (a00, a10, a11) of the sweep (or the single pivot a00 when
+// two is false): the LDL^T entries d0, l10, d1 go to A, and r0 = 1/d0, r1 = 1/d1, the
+// unscaled a10 and l10 to pv for the step that uses them.  A pivot that is not positive
+// marks the factorisation bad and continues with 1.
+__device__ __forceinline__ void dw_pivot_pair(float2 a00, float2 a10, float2 a11, bool two, float2* A, int j,
+                                              float2* pv, int* s_bad) {
+  const int rj = prow(j), rj1 = prow(j + 1);
+  int bad = !(a00.x > 0.0f);
+  if (bad) a00 = make_float2(1.0f, 0.0f);
+  const float2 r0 = dw_recip(a00);
+  A[rj + j] = a00;
+  if (two) {
+    const float2 l10 = dw_mul(a10, r0);
+    float2 d1 = dw_fms(a11, l10, a10);
+    if (!(d1.x > 0.0f)) {
+      bad = 1;
+      d1 = make_float2(1.0f, 0.0f);
+    }
+    A[rj1 + j] = l10;
+    A[rj1 + j + 1] = d1;
+    pv[0] = r0;
+    pv[1] = dw_recip(d1);
+    pv[2] = a10;
+    pv[3] = l10;
+  }
+  if (bad) *s_bad = 1;
 }
-__device__ __forceinline__ float2 dw_mul(float2 a, float2 b) {
-  const float p = __fmul_rn(a.x, b.x);
-  float q = __fmaf_rn(a.x, b.x, -p);
-  q = __fmaf_rn(a.x, b.y, q);
-  q = __fmaf_rn(a.y, b.x, q);
-  return dw_renorm(p, q);
+
+// v - (p.xy q.xy + p.zw q.zw): one element's rank-2 update from the row's (l_ij, l_i,j+1)
+// and the column's two unscaled entries (or L^-1's rows j and j+1).  Both products are
+// exact (hi) plus rounded cross terms (lo); the two high parts come off v.x by two
+// TwoSums and everything else is summed in the low word before one renormalisation.
+__device__ __forceinline__ float2 dw_upd2(float2 v, float4 p, float4 q) {
+  const float P0 = __fmul_rn(p.x, q.x), P1 = __fmul_rn(p.z, q.z);
+  float E0 = __fmaf_rn(p.x, q.x, -P0), E1 = __fmaf_rn(p.z, q.z, -P1);
+  E0 = __fmaf_rn(p.x, q.y, E0);
+  E0 = __fmaf_rn(p.y, q.x, E0);
+  E1 = __fmaf_rn(p.z, q.w, E1);
+  E1 = __fmaf_rn(p.w, q.z, E1);
+  const float s1 = __fsub_rn(v.x, P0);  // s1 + e1 = v.x - P0
+  const float t1 = __fsub_rn(s1, v.x);
+  const float e1 = __fsub_rn(__fsub_rn(v.x, __fsub_rn(s1, t1)), __fadd_rn(P0, t1));
+  const float s2 = __fsub_rn(s1, P1);   // s2 + e2 = s1 - P1
+  const float t2 = __fsub_rn(s2, s1);
+  const float e2 = __fsub_rn(__fsub_rn(s1, __fsub_rn(s2, t2)), __fadd_rn(P1, t2));
+  const float lo = __fadd_rn(__fadd_rn(e1, e2), __fsub_rn(v.y, __fadd_rn(E0, E1)));
+  return dw_renorm(s2, lo);
 }
-// c - a b
-__device__ __forceinline__ float2 dw_fms(float2 c, float2 a, float2 b) {
-  const float p = __fmul_rn(a.x, b.x);
-  float q = __fmaf_rn(a.x, b.x, -p);
-  q = __fmaf_rn(a.x, b.y, q);
-  q = __fmaf_rn(a.y, b.x, q);
-  const float s = __fsub_rn(c.x, p);
-  const float t = __fsub_rn(s, c.x);
-  float e = __fsub_rn(__fsub_rn(c.x, __fsub_rn(s, t)), __fadd_rn(p, t));  // (c.x - p) - s exactly
-  e = __fadd_rn(e, __fsub_rn(c.y, q));
-  return dw_renorm(s, e);
+__device__ __forceinline__ void dw_upd2x2(float4& v, float4 p, float4 q0, float4 q1) {
+  const float2 a = dw_upd2(make_float2(v.x, v.y), p, q0), b = dw_upd2(make_float2(v.z, v.w), p, q1);
+  v = make_float4(a.x, a.y, b.x, b.y);
 }
-__device__ __forceinline__ float2 dw_add(float2 a, float2 b) {
-  const float s = __fadd_rn(a.x, b.x);
-  const float t = __fsub_rn(s, a.x);
-  float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, t)), __fsub_rn(b.x, t));
-  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
-  return dw_renorm(s, e);
-}
-// 1 / d for d > 0: one Newton step from the correctly rounded float reciprocal
-// (relative error ~2^-47: the step squares the float's 2^-24)
-__device__ __forceinline__ float2 dw_recip(float2 d) {
-  const float r = __frcp_rn(d.x);
-  float e = __fmaf_rn(-d.x, r, 1.0f);  // exact: |1 - d.x r| < 2^-23 has at most 24 significant bits
-  e = __fmaf_rn(-d.y, r, e);
-  return dw_renorm(r, __fmul_rn(r, e));
-}
-__device__ __forceinline__ float2 d2dw(double v) {
-  const float h = __double2float_rn(v);
-  return make_float2(h, __double2float_rn(v - (double)h));
-}
-// Exact float -> double on the integer pipes (the exponent rebias 127 -> 1023 and the
-// 23-bit fraction moved to the top of the 52-bit one; zero and subnormals give 0,
-// infinities and NaNs keep their class), so that the conversions of the output
-// triangles do not queue on the FP64 pipe.
-__device__ __forceinline__ double f2d_bits(float f) {
-  const unsigned u = __float_as_uint(f), e = (u >> 23) & 0xffu;
-  const unsigned ef = (e == 0xffu) ? 0x7ffu : e + 896u;
-  const unsigned hi = (u & 0x80000000u) | (ef << 20) | ((u & 0x7fffffu) >> 3);
-  return (e == 0u) ? 0.0 : __hiloint2double((int)hi, (int)(u << 29));
-}
-__device__ __forceinline__ double dw2d(float2 v) { return f2d_bits(v.x) + f2d_bits(v.y); }
 
 // The dense-bin factorisation of k_chol_forward with the sweep in double-word
 // arithmetic, two columns per step.  Phi_k is scaled by 2^-E (E from its largest
@@ -243,29 +254,34 @@ __device__ __forceinline__ double dw2d(float2 v) { return f2d_bits(v.x) + f2d_bi
 // leaves the unit factor and its inverse unchanged and scales the pivots by 2^-E; the
 // pivots return to double and their true scale before the square roots.
 //
-// Step for columns (j, j+1): every thread factors the 2x2 pivot block itself from the
-// three values the previous step left in pv (the same arithmetic, so the same result
-// in every thread, and no barrier to share it); pass A scales column j, updates column
-// j+1 by it and scales that for the rows below, and eliminates row j+1 of L^-1; pass B
-// applies the rank-2 update to the trailing triangle and the two eliminations to the
-// rows of L^-1 below.  Two barriers per two columns.
+// Step for columns (j, j+1), whose 2x2 pivot block the previous step factored: pass A
+// scales column j, updates column j+1 by it and scales that, for every row below (and
+// stages each row's pair (l_ij, l_i,j+1) and each column's unscaled pair as 16-byte
+// entries, even and odd indices in separate arrays so that a warp's reads of
+// consecutive pairs hit distinct banks), and eliminates row j+1 of L^-1 (staging rows j
+// and j+1 of L^-1 per column); pass B applies the rank-2 update in 2x2 tiles, one tile
+// per thread and visit, to the trailing triangle and to the rows of L^-1 below, and
+// the thread of the trailing triangle's first tile factors the next pivot block.  A
+// tile row is one 16-byte load and store (rows start at even elements; a diagonal
+// tile's upper entry is the even row's padding).  Two barriers per two columns.
 //
-// Outputs: a64 as k_chol_forward; L D^(1/2) and D^(-1/2) L^-1 packed lower in the
-// same slots as k_chol_forward's, as double-word float pairs (read by
+// Outputs: a64 as k_chol_forward; L D^(1/2) and D^(-1/2) L^-1 packed lower (plain
+// packing) in the same slots as k_chol_forward's, as double-word float pairs (read by
 // k_chol_adjoint_dw).
 __global__ void __launch_bounds__(512)
     k_chol_forward_dw(DevModel m, const float* __restrict__ x, const double* __restrict__ sk,
                       const double* __restrict__ srho, double* a64, float2* Lpk, float2* Lipk, int32_t* stat) {
-  extern __shared__ float2 smw[];
-  const int np = m.npsr, ntri = np * (np + 1) / 2;
-  float2* A = smw;            // packed lower: L (unit, below the diagonal) and D (diagonal)
-  float2* X = A + ntri;       // packed lower: L^-1 (unit lower)
-  float2* u0 = X + ntri;      // [np] unscaled column j
-  float2* u1 = u0 + np;       // [np] unscaled column j+1 after column j's update
-  float2* ww = u1 + np;       // [2][np] sqrt(d_J) z_J
-  float2* sqw = ww + 2 * np;  // [np] sqrt(d_j)
-  float2* rqw = sqw + np;     // [np] 1 / sqrt(d_j)
-  __shared__ float2 pv[3];    // the next step's pivot block: A_jj, A_j+1,j, A_j+1,j+1
+  extern __shared__ float4 smq[];
+  const int np = m.npsr, ntri = np * (np + 1) / 2, nh = np / 2 + 1, nrow = prow(np);
+  float4* plE = smq;     // [nh] (l_ij, l_i,j+1) of rows j+2+e, e even (index e/2)
+  float4* plO = plE + nh;  // e odd
+  float4* uuE = plO + nh;  // [nh] unscaled (u_j, u_j+1) of columns j+2+f, f even
+  float4* uuO = uuE + nh;  // f odd
+  float4* xrE = uuO + nh;  // [nh] (X_jc, X_j+1,c), c even
+  float4* xrO = xrE + nh;  // c odd
+  float2* A = reinterpret_cast<float2*>(xrO + nh);  // padded packed lower: L (unit) and D
+  float2* X = A + nrow;                             // padded packed lower: L^-1 (unit lower)
+  __shared__ float2 pv[4];                          // r0, r1, unscaled a10, l10 of the step
   __shared__ int s_bad;
   const int k = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, nt = blockDim.x;
   const float* xb = x + (size_t)b * m.d;
@@ -281,121 +297,129 @@ __global__ void __launch_bounds__(512)
   for (int o = 16; o; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
   int E = 0;
   if (dmax > 0.0 && isfinite(dmax)) frexp(dmax, &E);
-  const float2 rhow = d2dw(ldexp(rho, -E));
+  const float2 rhow = d2dw_bits(ldexp(rho, -E));
   if (tid == 0) s_bad = 0;
   for (int idx = tid; idx < ntri; idx += nt) {
     const unsigned t = m.trimap[idx];
-    const int i = t >> 8, j = t & 255;
+    const int i = t >> 8, j = t & 255, o = prow(i) + j;
     float2 v = dw_mul(rhow, m.Gamma_dw[idx]);
     if (i == j) {
       const double s = skb[(size_t)i * m.na];
-      v = dw_add(v, d2dw(ldexp(s * s, -E)));
+      v = dw_add(v, d2dw_bits(ldexp(s * s, -E)));
     }
-    A[idx] = v;
-    X[idx] = make_float2((i == j) ? 1.0f : 0.0f, 0.0f);
-    if (idx < 3) pv[idx] = v;
+    A[o] = v;
+    X[o] = make_float2((i == j) ? 1.0f : 0.0f, 0.0f);
+    if (i == j && !(i & 1)) {  // an even row's padding
+      A[o + 1] = make_float2(0.0f, 0.0f);
+      X[o + 1] = make_float2(0.0f, 0.0f);
+    }
   }
   __syncthreads();
-  for (int j = 0; j < np; j += 2) {
-    float2 d0 = pv[0];
-    int bad = !(d0.x > 0.0f);
-    if (bad) d0 = make_float2(1.0f, 0.0f);
-    const float2 r0 = dw_recip(d0);
-    if (j + 1 == np) {  // odd order: the last column has its pivot only
-      if (tid == 0) {
-        A[tri(j, j)] = d0;
-        if (bad) s_bad = 1;
-      }
-      break;
-    }
-    const float2 a10 = pv[1];  // unscaled A_{j+1,j}
-    const float2 l10 = dw_mul(a10, r0);
-    float2 d1 = dw_fms(pv[2], l10, a10);
-    if (!(d1.x > 0.0f)) {
-      bad = 1;
-      d1 = make_float2(1.0f, 0.0f);
-    }
-    const float2 r1 = dw_recip(d1);
-    const int rj = j * (j + 1) / 2, rj1 = rj + j + 1;  // offsets of rows j and j+1
-    if (tid == 0) {
-      A[rj + j] = d0;
-      A[rj1 + j] = l10;
-      A[rj1 + j + 1] = d1;
-      if (bad) s_bad = 1;
-    }
-    // pass A: columns j, j+1 of rows i >= j+2; row j+1 of L^-1 (columns <= j)
-    const int s2 = np - j - 2;
-    for (int e = tid; e < s2 + j + 1; e += nt) {
+  if (tid == 0) dw_pivot_pair(A[0], np > 1 ? A[2] : A[0], np > 1 ? A[3] : A[0], np > 1, A, 0, pv, &s_bad);
+  __syncthreads();
+  for (int j = 0; j + 1 < np; j += 2) {
+    const float2 r0 = pv[0], r1 = pv[1], a10 = pv[2], l10 = pv[3];
+    const int rj = prow(j), rj1 = prow(j + 1), s2 = np - j - 2;
+    // pass A
+    for (int e = tid; e < s2 + j + 2; e += nt) {
       if (e < s2) {
-        const int i = j + 2 + e, rb = i * (i + 1) / 2;
-        const float2 a0 = A[rb + j], a1 = A[rb + j + 1];
+        const int i = j + 2 + e;
+        float4* ap = reinterpret_cast<float4*>(A + prow(i) + j);
+        const float4 a = *ap;
+        const float2 a0 = make_float2(a.x, a.y);
         const float2 l0 = dw_mul(a0, r0);
-        const float2 w = dw_fms(a1, l0, a10);
-        u0[i] = a0;
-        u1[i] = w;
-        A[rb + j] = l0;
-        A[rb + j + 1] = dw_mul(w, r1);
+        const float2 w = dw_fms(make_float2(a.z, a.w), l0, a10);
+        const float2 l1 = dw_mul(w, r1);
+        const float4 pl = make_float4(l0.x, l0.y, l1.x, l1.y);
+        *ap = pl;
+        (e & 1 ? plO : plE)[e >> 1] = pl;
+        (e & 1 ? uuO : uuE)[e >> 1] = make_float4(a0.x, a0.y, w.x, w.y);
       } else {
-        const int c = e - s2;
-        X[rj1 + c] = dw_fms(X[rj1 + c], l10, X[rj + c]);
+        const int c = e - s2;  // 0 .. j+1
+        float2 xj = make_float2(0.0f, 0.0f), x1 = make_float2(1.0f, 0.0f);
+        if (c <= j) {
+          xj = X[rj + c];
+          x1 = dw_fms(X[rj1 + c], l10, xj);
+          X[rj1 + c] = x1;
+        }
+        (c & 1 ? xrO : xrE)[c >> 1] = make_float4(xj.x, xj.y, x1.x, x1.y);
       }
     }
+    if (tid == 0 && (s2 & 1)) plO[s2 >> 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // the odd row's partner
     __syncthreads();
-    // pass B: rank-2 update of the trailing triangle (rows, columns >= j+2) and the
-    // eliminations of rows >= j+2 of L^-1 in columns <= j+1
-    const int w2 = j + 2, cntA = s2 * (s2 + 1) / 2, cnt = cntA + s2 * w2;
-    const float rw = 1.0f / (float)w2;
-    for (int idx = tid; idx < cnt; idx += nt) {
-      if (idx < cntA) {
-        const unsigned t = m.trimap[idx];
-        const int i = (t >> 8) + j + 2, l = (t & 255) + j + 2, rb = i * (i + 1) / 2;
-        float2 v = dw_fms(A[rb + l], A[rb + j], u0[l]);
-        v = dw_fms(v, A[rb + j + 1], u1[l]);
-        A[rb + l] = v;
-        if (idx < 3) pv[idx] = v;
-      } else {
-        const int e = idx - cntA;
-        int q = (int)(((float)e + 0.5f) * rw);
-        q -= (q * w2 > e);
-        q += ((q + 1) * w2 <= e);
-        const int i = j + 2 + q, c = e - q * w2, rb = i * (i + 1) / 2;
-        float2 v;
-        if (c <= j) {
-          v = dw_fms(X[rb + c], A[rb + j], X[rj + c]);
-          v = dw_fms(v, A[rb + j + 1], X[rj1 + c]);
-        } else {  // c = j+1: X_{j,j+1} = 0 and X_{j+1,j+1} = 1, so X_{i,j+1} = -l_{i,j+1}
-          const float2 l1 = A[rb + j + 1];
-          v = make_float2(-l1.x, -l1.y);
+    // pass B: 2x2 tiles; T row pairs (the last one short when s2 is odd), W = (j+2)/2
+    // column pairs of L^-1
+    // (tile rows i0 are even: row i0 starts at i0(i0+2)/2 and row i0+1 at (i0+2)^2/2)
+    const int T = (s2 + 1) >> 1, cntT = T * (T + 1) / 2, W = (j + 2) >> 1, cnt = cntT + T * W;
+    const float rw = __fdividef(1.0f, (float)W);  // the quotient below is corrected by +-1
+    for (int t = tid; t < cnt; t += nt) {
+      if (t < cntT) {
+        const unsigned tm = m.trimap[t];
+        const int I = tm >> 8, L = tm & 255, i0 = j + 2 + 2 * I, c0 = j + 2 + 2 * L;
+        const float4 p0 = plE[I], p1 = plO[I], q0 = uuE[L], q1 = uuO[L];
+        float4* r0p = reinterpret_cast<float4*>(A + i0 * (i0 + 2) / 2 + c0);
+        float4 v0 = *r0p;
+        dw_upd2x2(v0, p0, q0, q1);  // on a diagonal tile the second entry is the padding
+        *r0p = v0;
+        const bool row1 = 2 * I + 1 < s2;
+        float4 v1 = v0;
+        if (row1) {
+          float4* r1p = reinterpret_cast<float4*>(A + (i0 + 2) * (i0 + 2) / 2 + c0);
+          v1 = *r1p;
+          dw_upd2x2(v1, p1, q0, q1);
+          *r1p = v1;
         }
-        X[rb + c] = v;
+        if (t == 0)
+          dw_pivot_pair(make_float2(v0.x, v0.y), make_float2(v1.x, v1.y), make_float2(v1.z, v1.w), row1, A, j + 2,
+                        pv, &s_bad);
+      } else {
+        const int e = t - cntT;
+        int q = (int)(((float)e + 0.5f) * rw);
+        q -= (q * W > e);
+        q += ((q + 1) * W <= e);
+        const int cc = e - q * W, i0 = j + 2 + 2 * q, c0 = 2 * cc;
+        const float4 p0 = plE[q], p1 = plO[q], q0 = xrE[cc], q1 = xrO[cc];
+        float4* r0p = reinterpret_cast<float4*>(X + i0 * (i0 + 2) / 2 + c0);
+        float4 v0 = *r0p;
+        dw_upd2x2(v0, p0, q0, q1);
+        *r0p = v0;
+        if (2 * q + 1 < s2) {
+          float4* r1p = reinterpret_cast<float4*>(X + (i0 + 2) * (i0 + 2) / 2 + c0);
+          float4 v1 = *r1p;
+          dw_upd2x2(v1, p1, q0, q1);
+          *r1p = v1;
+        }
       }
     }
     __syncthreads();
   }
   if (s_bad && tid == 0) atomicOr(&stat[b], 2);
-  __syncthreads();
-  // pivots at their true scale: sqrt(d_j) and 1/sqrt(d_j) in FP64, kept as double words
+  // pivots at their true scale: sqrt(d_j) and 1/sqrt(d_j) in FP64, kept as double
+  // words (the staging area is free now)
+  float2* ww = reinterpret_cast<float2*>(smq);  // [2][np] sqrt(d_J) z_J
+  float2* sqw = ww + 2 * np;                     // [np] sqrt(d_j)
+  float2* rqw = sqw + np;                        // [np] 1 / sqrt(d_j)
   for (int j = tid; j < np; j += nt) {
-    const double d = ldexp(dw2d(A[tri(j, j)]), E);
+    const double d = ldexp(dw2d(A[prow(j) + j]), E);
     const double y = rsqrt64(d);
-    sqw[j] = d2dw(d * y);
-    rqw[j] = d2dw(y);
+    sqw[j] = d2dw_bits(d * y);
+    rqw[j] = d2dw_bits(y);
     const double zs0 = xb[m.z_ach + (2 * k) * np + j], zs1 = xb[m.z_ach + (2 * k + 1) * np + j];
-    ww[j] = d2dw(d * y * zs0);
-    ww[np + j] = d2dw(d * y * zs1);
+    ww[j] = d2dw_bits(d * y * zs0);
+    ww[np + j] = d2dw_bits(d * y * zs1);
   }
   __syncthreads();
   float2* Lg = Lpk + ((size_t)b * m.n_chol + k) * ntri;
   float2* Xg = Lipk + ((size_t)b * m.n_chol + k) * ntri;
   for (int idx = tid; idx < ntri; idx += nt) {
     const unsigned t = m.trimap[idx];
-    const int i = t >> 8, j = t & 255;
-    Lg[idx] = (i == j) ? sqw[j] : dw_mul(A[idx], sqw[j]);
-    Xg[idx] = (i == j) ? rqw[i] : dw_mul(X[idx], rqw[i]);
+    const int i = t >> 8, j = t & 255, o = prow(i) + j;
+    Lg[idx] = (i == j) ? sqw[j] : dw_mul(A[o], sqw[j]);
+    Xg[idx] = (i == j) ? rqw[i] : dw_mul(X[o], rqw[i]);
   }
   // a_{I,k,c} = sum_{J<=I} L[I][J] (sqrt(d_J) z_{J,k,c}), L unit lower
   for (int i = tid; i < 2 * np; i += nt) {
-    const int c = i / np, I = i % np, rb = I * (I + 1) / 2;
+    const int c = i / np, I = i % np, rb = prow(I);
     const float2* wc = ww + c * np;
     float2 acc = wc[I];
     for (int J = 0; J < I; ++J) {
@@ -412,13 +436,6 @@ __global__ void __launch_bounds__(512)
 // segment q returns its own sum with prefixes started at zero (loc), its prefix totals
 // P_c = sum u_a z_ca and the sums V_c = sum gt_ca u_a, and the walk is
 // sum_q loc_q + sum_c (P_c of the segments before q) V_cq.
-__device__ __forceinline__ float2 dw_mulf(float2 a, float b) {
-  const float p = __fmul_rn(a.x, b);
-  float q = __fmaf_rn(a.x, b, -p);
-  q = __fmaf_rn(a.y, b, q);
-  return dw_renorm(p, q);
-}
-__device__ __forceinline__ float2 dw_neg(float2 a) { return make_float2(-a.x, -a.y); }
 
 __global__ void __launch_bounds__(512)
     k_chol_adjoint_dw(DevModel m, const float* __restrict__ x, const double* __restrict__ ghat,
@@ -447,7 +464,7 @@ __global__ void __launch_bounds__(512)
   }
   for (int i = tid; i < 2 * np; i += nt) {
     const int c = i / np, I = i % np;
-    gs[i] = d2dw(ghat[((size_t)I * B + b) * m.P + 2 * k + c]);
+    gs[i] = d2dw_bits(ghat[((size_t)I * B + b) * m.P + 2 * k + c]);
   }
   __syncthreads();
   for (int i = tid; i < 2 * np; i += nt) {
@@ -636,6 +653,10 @@ __device__ __forceinline__ void diag_index(const DevModel& m, int r, int& I, int
   k = dm ? q - nrn_only : m.n_chol + m.n_gwbonly + q;
 }
 
+// DW: double-word products (outside FP64 mode), whose only FP64 operation is the
+// final add of each double output; the float gradient needs none.  A DM bin's two
+// coefficients, z's and gradient entries are adjacent: one paired access each.
+template <bool DW>
 __global__ void k_diag_forward(DevModel m, const float* __restrict__ x, const double* __restrict__ sk,
                                const double* __restrict__ skd, double* a64, int B, int per_chain) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
@@ -645,14 +666,27 @@ __global__ void k_diag_forward(DevModel m, const float* __restrict__ x, const do
   diag_index(m, r, I, k, dm);
   const float* xb = x + (size_t)b * m.d;
   const double s = dm ? skd[((size_t)b * m.npsr + I) * m.nd + k] : sk[((size_t)b * m.npsr + I) * m.na + k];
-  const int zo = dm ? m.z_dm + (I * m.nd + k) * 2 : 0;
-  const double z0 = dm ? xb[zo] : xb[m.z_ach + (2 * k) * m.npsr + I];
-  const double z1 = dm ? xb[zo + 1] : xb[m.z_ach + (2 * k + 1) * m.npsr + I];
+  const int zo = dm ? m.z_dm + (I * m.nd + k) * 2 : m.z_ach + (2 * k) * m.npsr + I;
+  float z0, z1;
+  if (dm && !(reinterpret_cast<uintptr_t>(xb + zo) & 7)) {
+    const float2 zz = *reinterpret_cast<const float2*>(xb + zo);
+    z0 = zz.x;
+    z1 = zz.y;
+  } else {
+    z0 = xb[zo];
+    z1 = xb[dm ? zo + 1 : zo + m.npsr];
+  }
   const size_t o = ((size_t)I * B + b) * m.PM + (dm ? 2 * m.na : 0) + 2 * k;
-  a64[o] = s * z0;
-  a64[o + 1] = s * z1;
+  if (DW) {
+    const float2 sw = d2dw_bits(s);
+    *reinterpret_cast<double2*>(a64 + o) = make_double2(dw2d(dw_mulf(sw, z0)), dw2d(dw_mulf(sw, z1)));
+  } else {
+    a64[o] = s * z0;
+    a64[o + 1] = s * z1;
+  }
 }
 
+template <bool DW>
 __global__ void k_diag_adjoint(DevModel m, const float* __restrict__ x, const double* __restrict__ ghat,
                                const double* __restrict__ sk, const double* __restrict__ skd, float* grad,
                                double* dlnk, double* dlnkd, int B, int per_chain) {
@@ -662,15 +696,42 @@ __global__ void k_diag_adjoint(DevModel m, const float* __restrict__ x, const do
   bool dm;
   diag_index(m, r, I, k, dm);
   const float* xb = x + (size_t)b * m.d;
+  float* gb = grad + (size_t)b * m.d;
   const double s = dm ? skd[((size_t)b * m.npsr + I) * m.nd + k] : sk[((size_t)b * m.npsr + I) * m.na + k];
   const int z0i = dm ? m.z_dm + (I * m.nd + k) * 2 : m.z_ach + (2 * k) * m.npsr + I;
   const int z1i = dm ? z0i + 1 : z0i + m.npsr;
+  const bool pair = dm && !(reinterpret_cast<uintptr_t>(xb + z0i) & 7);  // xb and gb rows share the offset
   const size_t o = ((size_t)I * B + b) * m.P + (dm ? 2 * m.na : 0) + 2 * k;
-  const double g0 = ghat[o], g1 = ghat[o + 1];
-  const double z0 = xb[z0i], z1 = xb[z1i];
-  grad[(size_t)b * m.d + z0i] = (float)(s * g0 - z0);
-  grad[(size_t)b * m.d + z1i] = (float)(s * g1 - z1);
-  const double v = 0.5 * s * (g0 * z0 + g1 * z1);
+  const double2 g = *reinterpret_cast<const double2*>(ghat + o);
+  float z0, z1;
+  if (pair) {
+    const float2 zz = *reinterpret_cast<const float2*>(xb + z0i);
+    z0 = zz.x;
+    z1 = zz.y;
+  } else {
+    z0 = xb[z0i];
+    z1 = xb[z1i];
+  }
+  float gr0, gr1;
+  double v;
+  if (DW) {
+    const float2 sw = d2dw_bits(s), g0 = dw_mul(sw, d2dw_bits(g.x)), g1 = dw_mul(sw, d2dw_bits(g.y));
+    const float2 d0 = dw_addf(g0, -z0), d1 = dw_addf(g1, -z1);
+    gr0 = __fadd_rn(d0.x, d0.y);
+    gr1 = __fadd_rn(d1.x, d1.y);
+    const float2 q = dw_add(dw_mulf(g0, z0), dw_mulf(g1, z1));  // s (g0 z0 + g1 z1)
+    v = 0.5 * dw2d(q);
+  } else {
+    gr0 = (float)(s * g.x - z0);
+    gr1 = (float)(s * g.y - z1);
+    v = 0.5 * s * (g.x * z0 + g.y * z1);
+  }
+  if (pair) {
+    *reinterpret_cast<float2*>(gb + z0i) = make_float2(gr0, gr1);
+  } else {
+    gb[z0i] = gr0;
+    gb[z1i] = gr1;
+  }
   if (dm)
     dlnkd[((size_t)b * m.npsr + I) * m.nd + k] = v;
   else
@@ -682,6 +743,7 @@ __global__ void k_diag_adjoint(DevModel m, const float* __restrict__ x, const do
 // status, and the hyper-parameter gradient by the chain rule through the power law:
 // d/d log10A = 2 ln10 sum_k kappa_k dlogp/dkappa_k, d/d gamma = -sum_k ln(f_k/f_yr) (...).
 // ---------------------------------------------------------------------------
+template <bool DW>
 __global__ void k_final(DevModel m, const float* __restrict__ x, const double* __restrict__ chi2,
                         const double* __restrict__ dlnk, const double* __restrict__ dlnkd,
                         const double* __restrict__ dlnr, const int32_t* __restrict__ stat,
@@ -698,9 +760,25 @@ __global__ void k_final(DevModel m, const float* __restrict__ x, const double* _
   if (m.curn) {  // CURN transform: HD prior terms per bin and log det L_CURN per pulsar
     for (int j = tid; j <= m.na; j += nt) acc += curnQ[(size_t)b * (m.na + 1) + j];
     for (int I = tid; I < np; I += nt) acc += curnLd[(size_t)I * B + b];
-  } else {
+  } else if (!DW) {
     for (int j = tid; j < m.d_z; j += nt) acc = fma((double)xb[j], (double)xb[j], acc);
     acc *= -0.5;
+  } else {  // -|z|^2 / 2: exact squares summed as double words, one FP64 add per thread;
+            // four independent loads per step keep the loop off the load latency
+    float2 zz = make_float2(0.0f, 0.0f);
+    int j = tid;
+    for (; j + 3 * nt < m.d_z; j += 4 * nt) {
+      const float z0 = xb[j], z1 = xb[j + nt], z2 = xb[j + 2 * nt], z3 = xb[j + 3 * nt];
+      const float p0 = __fmul_rn(z0, z0), p1 = __fmul_rn(z1, z1), p2 = __fmul_rn(z2, z2), p3 = __fmul_rn(z3, z3);
+      const float2 s01 = dw_add(make_float2(p0, __fmaf_rn(z0, z0, -p0)), make_float2(p1, __fmaf_rn(z1, z1, -p1)));
+      const float2 s23 = dw_add(make_float2(p2, __fmaf_rn(z2, z2, -p2)), make_float2(p3, __fmaf_rn(z3, z3, -p3)));
+      zz = dw_add(zz, dw_add(s01, s23));
+    }
+    for (; j < m.d_z; j += nt) {
+      const float z = xb[j], p = __fmul_rn(z, z);
+      zz = dw_add(zz, make_float2(p, __fmaf_rn(z, z, -p)));
+    }
+    acc = -0.5 * dw2d(zz);
   }
   const double bt = m.beta ? m.beta[b] : 1.0;  // tempered likelihood: beta chi2
   for (int I = tid; I < np; I += nt) acc -= 0.5 * bt * chi2[(size_t)I * B + b];
@@ -765,32 +843,79 @@ __global__ void k_final(DevModel m, const float* __restrict__ x, const double* _
     for (int j = tid; j < m.d; j += nt) gb[j] = 0.f;
     return;
   }
-  for (int I = tid; I < np; I += nt) {
+  // noise hyper-parameters: one warp per pulsar, lanes over the bins, shuffle sums
+  const int lane = tid & 31, nwarp = nt >> 5;
+  if (DW) {  // sums as double words: the FP64 pipe's latency is what this loop would wait on
+    constexpr float2 kLn10w = {0x1.26bb1cp+1f, -0x1.12aabap-25f};
+    auto wsum = [&](float2 v) {
+      for (int o = 16; o; o >>= 1)
+        v = dw_add(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)));
+      return v;
+    };
+    auto tof = [](float2 v) { return __fadd_rn(v.x, v.y); };
+    for (int I = tid >> 5; I < np; I += nwarp) {
+      float2 s1 = make_float2(0.0f, 0.0f), s2 = s1, d1 = s1, d2 = s1;
+      for (int k = lane; k < m.n_rn; k += 32) {
+        const float2 v = d2dw_bits(dlnk[((size_t)b * np + I) * m.na + k]);  // kappa d logp / d kappa
+        if (m.rn_free) gb[m.th_rn + m.n_rn * I + k] = tof(dw_mul(kLn10w, v));  // d kappa / d theta = ln10 kappa
+        s1 = dw_add(s1, v);
+        s2 = dw_fms(s2, m.lkT[k + 1], v);
+      }
+      for (int k = lane; k < m.nd; k += 32) {
+        const float2 v = d2dw_bits(dlnkd[((size_t)b * np + I) * m.nd + k]);
+        d1 = dw_add(d1, v);
+        d2 = dw_fms(d2, m.lkT[k + 1], v);
+      }
+      s1 = wsum(s1);
+      s2 = wsum(s2);
+      d1 = wsum(d1);
+      d2 = wsum(d2);
+      if (lane == 0) {
+        if (!m.rn_free) {  // power-law chain rule
+          gb[m.th_rn + 2 * I] = 2.0f * tof(dw_mul(kLn10w, s1));
+          gb[m.th_rn + 2 * I + 1] = tof(s2);
+        }
+        if (m.nd) {
+          gb[m.th_dm + 2 * I] = 2.0f * tof(dw_mul(kLn10w, d1));
+          gb[m.th_dm + 2 * I + 1] = tof(d2);
+        }
+      }
+    }
+  }
+  for (int I = tid >> 5; !DW && I < np; I += nwarp) {
     double s1 = 0.0, s2 = 0.0;
-    for (int k = 0; k < m.n_rn; ++k) {
+    for (int k = lane; k < m.n_rn; k += 32) {
       const double v = dlnk[((size_t)b * np + I) * m.na + k];  // kappa d logp / d kappa
       if (m.rn_free) gb[m.th_rn + m.n_rn * I + k] = (float)(kLn10 * v);  // d kappa / d theta = ln10 kappa
       s1 += v;
       s2 -= (m.lnk[k + 1] - m.ln_Tfyr) * v;
     }
-    if (!m.rn_free) {  // power-law chain rule
-      gb[m.th_rn + 2 * I] = (float)(2.0 * kLn10 * s1);
-      gb[m.th_rn + 2 * I + 1] = (float)s2;
+    double d1 = 0.0, d2 = 0.0;
+    for (int k = lane; k < m.nd; k += 32) {
+      const double v = dlnkd[((size_t)b * np + I) * m.nd + k];
+      d1 += v;
+      d2 -= (m.lnk[k + 1] - m.ln_Tfyr) * v;
     }
-    if (m.nd) {
-      double d1 = 0.0, d2 = 0.0;
-      for (int k = 0; k < m.nd; ++k) {
-        const double v = dlnkd[((size_t)b * np + I) * m.nd + k];
-        d1 += v;
-        d2 -= (m.lnk[k + 1] - m.ln_Tfyr) * v;
+    for (int o = 16; o; o >>= 1) {
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+      d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    }
+    if (lane == 0) {
+      if (!m.rn_free) {  // power-law chain rule
+        gb[m.th_rn + 2 * I] = (float)(2.0 * kLn10 * s1);
+        gb[m.th_rn + 2 * I + 1] = (float)s2;
       }
-      gb[m.th_dm + 2 * I] = (float)(2.0 * kLn10 * d1);
-      gb[m.th_dm + 2 * I + 1] = (float)d2;
+      if (m.nd) {
+        gb[m.th_dm + 2 * I] = (float)(2.0 * kLn10 * d1);
+        gb[m.th_dm + 2 * I + 1] = (float)d2;
+      }
     }
   }
-  if (tid == 0) {
+  if (tid < 32) {  // GWB hyper-parameters: lanes over the bins
     double s1 = 0.0, s2 = 0.0;
-    for (int k = 0; k < m.n_gwb; ++k) {
+    for (int k = tid; k < m.n_gwb; k += 32) {
       double v = dlnr[(size_t)b * m.na + k];  // rho d logp / d rho
       if (m.curn)  // the transform's part, per pulsar, summed in a fixed order
         for (int I = 0; I < np; ++I) v += dlnrc[((size_t)b * np + I) * m.na + k];
@@ -798,7 +923,11 @@ __global__ void k_final(DevModel m, const float* __restrict__ x, const double* _
       s1 += v;
       s2 -= (m.lnk[k + 1] - m.ln_Tfyr) * v;
     }
-    if (!m.gwb_free) {
+    for (int o = 16; o; o >>= 1) {
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (!m.gwb_free && tid == 0) {
       gb[m.th_gwb] = (float)(2.0 * kLn10 * s1);
       gb[m.th_gwb + 1] = (float)s2;
     }
@@ -825,6 +954,7 @@ __global__ void k_final(DevModel m, const float* __restrict__ x, const double* _
 // at 67 pulsars (8 warps each), but only one at 150 (181 KB), where few warps would leave
 // the FP64 latency exposed: 16 warps per CTA there.
 static int chol_threads(const DevModel& m) { return m.npsr >= 96 ? 512 : 256; }
+static int chol_threads_dw(const DevModel& m) { return m.npsr >= 96 ? 512 : 256; }
 
 static size_t chol_smem(const DevModel& m) {
   const size_t np = m.npsr, ntri = np * (np + 1) / 2;
@@ -840,8 +970,8 @@ static size_t adj_smem_dw(const DevModel& m) {
   return (std::max(ntri, 5 * nseg * np + np) + ntri + 4 * np) * 8;
 }
 static size_t chol_smem_dw(const DevModel& m) {
-  const size_t np = m.npsr, ntri = np * (np + 1) / 2;
-  return (2 * ntri + 6 * np) * sizeof(float2);
+  const size_t np = m.npsr, nh = np / 2 + 1;
+  return 6 * nh * sizeof(float4) + 2 * (size_t)prow((int)np) * sizeof(float2);
 }
 static size_t adj_smem(const DevModel& m) {
   const size_t np = m.npsr, ntri = np * (np + 1) / 2;
@@ -857,7 +987,10 @@ int count_prior_adjoint(const DevModel& m) { return m.curn ? 1 : count_prior_for
 cudaError_t launch_prior_forward(const DevModel& m, const Scratch& s, int B, const float* x, int fp64,
                                  cudaStream_t st, cudaEvent_t* kev) {
   const int nspec = m.npsr * (m.na + m.nd) + m.na;
-  k_spectra<<<dim3((nspec + 127) / 128, B), 128, 0, st>>>(m, x, s.sk, s.skd, s.srho);
+  if (fp64)
+    k_spectra<false><<<dim3((nspec + 127) / 128, B), 128, 0, st>>>(m, x, s.sk, s.skd, s.srho);
+  else
+    k_spectra<true><<<dim3((nspec + 127) / 128, B), 128, 0, st>>>(m, x, s.sk, s.skd, s.srho);
   if (m.n_chol > 0) {
     const bool dw = chol_dw(m, fp64);
     const size_t sm = dw ? chol_smem_dw(m) : chol_smem(m);
@@ -866,7 +999,7 @@ cudaError_t launch_prior_forward(const DevModel& m, const Scratch& s, int B, con
     if (e != cudaSuccess) return e;
     if (kev) cudaEventRecord(kev[0], st);
     if (dw)
-      k_chol_forward_dw<<<dim3(m.n_chol, B), chol_threads(m), sm, st>>>(
+      k_chol_forward_dw<<<dim3(m.n_chol, B), chol_threads_dw(m), sm, st>>>(
           m, x, s.sk, s.srho, s.a64, reinterpret_cast<float2*>(s.Lpk), reinterpret_cast<float2*>(s.Lipk), s.stat);
     else
       k_chol_forward<<<dim3(m.n_chol, B), chol_threads(m), sm, st>>>(m, x, s.sk, s.srho, s.a64, s.Lpk, s.Lipk,
@@ -876,7 +1009,12 @@ cudaError_t launch_prior_forward(const DevModel& m, const Scratch& s, int B, con
   if (m.curn) return cudaGetLastError();  // a comes from the CURN transform (launch_curn_forward)
   if (m.n_gwbonly > 0) k_gwbonly_forward<<<dim3(m.n_gwbonly, B), 128, 0, st>>>(m, x, s.srho, s.a64);
   const int per = m.npsr * ((m.na - m.n_chol - m.n_gwbonly) + m.nd);
-  if (per > 0) k_diag_forward<<<dim3((per + 127) / 128, B), 128, 0, st>>>(m, x, s.sk, s.skd, s.a64, B, per);
+  if (per > 0) {
+    if (fp64)
+      k_diag_forward<false><<<dim3((per + 127) / 128, B), 128, 0, st>>>(m, x, s.sk, s.skd, s.a64, B, per);
+    else
+      k_diag_forward<true><<<dim3((per + 127) / 128, B), 128, 0, st>>>(m, x, s.sk, s.skd, s.a64, B, per);
+  }
   return cudaGetLastError();
 }
 
@@ -899,15 +1037,20 @@ cudaError_t launch_prior_adjoint(const DevModel& m, const Scratch& s, int B, con
   if (m.n_gwbonly > 0)
     k_gwbonly_adjoint<<<dim3(m.n_gwbonly, B), 128, 0, st>>>(m, x, s.ghat, s.srho, grad, s.dlnr, B);
   const int per = m.npsr * ((m.na - m.n_chol - m.n_gwbonly) + m.nd);
-  if (per > 0)
-    k_diag_adjoint<<<dim3((per + 127) / 128, B), 128, 0, st>>>(m, x, s.ghat, s.sk, s.skd, grad, s.dlnk, s.dlnkd,
-                                                               B, per);
+  if (per > 0) {
+    if (fp64)
+      k_diag_adjoint<false><<<dim3((per + 127) / 128, B), 128, 0, st>>>(m, x, s.ghat, s.sk, s.skd, grad, s.dlnk,
+                                                                      s.dlnkd, B, per);
+    else
+      k_diag_adjoint<true><<<dim3((per + 127) / 128, B), 128, 0, st>>>(m, x, s.ghat, s.sk, s.skd, grad, s.dlnk,
+                                                                     s.dlnkd, B, per);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_final(const DevModel& m, const Scratch& s, int B, const float* x, double* logp, float* grad,
-                         int32_t* status, cudaStream_t st) {
-  k_final<<<B, 256, 0, st>>>(m, x, s.chi2, s.dlnk, s.dlnkd, s.dlnr, s.stat, s.cwg, s.curnQ, s.curnLd, s.dlnrc, logp,
+                         int32_t* status, int fp64, cudaStream_t st) {
+  (fp64 ? k_final<false> : k_final<true>)<<<B, 512, 0, st>>>(m, x, s.chi2, s.dlnk, s.dlnkd, s.dlnr, s.stat, s.cwg, s.curnQ, s.curnLd, s.dlnrc, logp,
                              grad, status, B);
   return cudaGetLastError();
 }

@@ -18,6 +18,7 @@
 // FP64 variant (plain path): stored FP64 basis, one CTA per (unit, chain).
 #include <algorithm>
 
+#include "dwarith.cuh"
 #include "pta_internal.cuh"
 
 namespace pta {
@@ -507,23 +508,29 @@ __global__ void __launch_bounds__(128)
   if (tid == 0) c2part[(size_t)u * B + b] = c2;
 }
 
-// FP64 reduction over a pulsar's units (fixed order): ghat = F^T N~^-1 r, chi2.
-__global__ void __launch_bounds__(128)
+// Reduction over a pulsar's units (fixed order): ghat = F^T N~^-1 r, chi2.  One thread
+// per (chain, coefficient) of a pulsar, consecutive threads on consecutive coefficients.
+// FP32 partials are summed as double words (exact sums, TwoSum) and reach double with
+// one FP64 add; FP64 partials (FP64 mode) are summed in FP64.
+__global__ void __launch_bounds__(256)
     k_reduce(DevModel m, const float* __restrict__ gpart, const double* __restrict__ gpart64,
              const double* __restrict__ c2part, double* __restrict__ ghat, double* __restrict__ chi2, int B,
              int fp64) {
-  const int I = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
-  const int P = m.P, u0 = m.unit0[I], nu = m.nunit[I];
-  const double bt = m.beta ? m.beta[b] : 1.0;  // tempered likelihood: d logp / d a scales with beta
-  for (int q = tid; q < P; q += 128) {
-    double s = 0.0;
-    for (int j = 0; j < nu; ++j) {
-      const size_t o = ((size_t)(u0 + j) * B + b) * m.Qs + q;
-      s += fp64 ? gpart64[o] : (double)gpart[o];
-    }
-    ghat[((size_t)I * B + b) * P + q] = bt * s;
+  const int I = blockIdx.y, P = m.P, u0 = m.unit0[I], nu = m.nunit[I];
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= B * P) return;
+  const int b = r / P, q = r - b * P;
+  double s = 0.0;
+  if (fp64) {
+    for (int j = 0; j < nu; ++j) s += gpart64[((size_t)(u0 + j) * B + b) * m.Qs + q];
+  } else {
+    float2 acc = make_float2(0.0f, 0.0f);
+    for (int j = 0; j < nu; ++j) acc = dw_addf(acc, gpart[((size_t)(u0 + j) * B + b) * m.Qs + q]);
+    s = dw2d(acc);
   }
-  if (tid == 0) {
+  // tempered likelihood: d logp / d a scales with beta
+  ghat[((size_t)I * B + b) * P + q] = m.beta ? m.beta[b] * s : s;
+  if (q == 0) {
     double c2 = 0.0;
     for (int j = 0; j < nu; ++j) c2 += c2part[(size_t)(u0 + j) * B + b];
     chi2[(size_t)I * B + b] = c2;
@@ -651,7 +658,8 @@ cudaError_t launch_toa_fp64(const DevModel& m, const Scratch& s, int B, cudaStre
 }
 
 cudaError_t launch_reduce(const DevModel& m, const Scratch& s, int B, int fp64, cudaStream_t st) {
-  k_reduce<<<dim3(m.npsr, B), 128, 0, st>>>(m, s.gpart, s.gpart64, s.c2part, s.ghat, s.chi2, B, fp64);
+  k_reduce<<<dim3((B * m.P + 255) / 256, m.npsr), 256, 0, st>>>(m, s.gpart, s.gpart64, s.c2part, s.ghat, s.chi2, B,
+                                                                  fp64);
   return cudaGetLastError();
 }
 

@@ -54,6 +54,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
+#include "dwarith.cuh"
 #include "pta_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -332,7 +333,8 @@ __global__ void __launch_bounds__(128)
 // the FP64 c_s that k_tm_prologue wrote after them.  Stored basis column q carries
 // 2^(14 - c_q), so coefficient q carries 2^c_q, and each chain row is normalised to
 // 2^14 by its own exponent E_n (y = L 2^(E_n - 28)).  The FP64 value is carried as an
-// unevaluated float pair and cut with FP32 operations (B300's FP64 rate is 1/64 of FP32).
+// unevaluated float pair, split off its encoding with integer operations, and cut with
+// FP32 operations (B300's FP64 rate is 1/64 of FP32).
 // ---------------------------------------------------------------------------
 
 // hi + lo (|hi| <= 2^14, |lo| <= ulp(hi) / 2) = v0 + v1 + v2 + v3: v0, v1 on the 2^7 and
@@ -362,12 +364,13 @@ __global__ void __launch_bounds__(256)
   for (int q = tid; q < KX; q += 256) ce[q] = m.x16_cexp[(size_t)I * KXM + q];
   __syncthreads();
   auto coef = [&](int n, int q) -> double { return q < P ? rows[(size_t)n * PM + q] - ar[q] : rows[(size_t)n * PM + q]; };
-  // per-chain exponent of max_q |C_nq 2^c_q| (one warp per chain).  The FP32 rounding of
-  // |C| can only raise the maximum to the next power of two, which keeps |v| < 2^14.
+  // per-chain exponent of max_q |C_nq 2^c_q| (one warp per chain).  |C| is truncated to a
+  // float, and frexpf's exponent of a truncated value still bounds the exact one
+  // strictly, which keeps |v| < 2^14.
   for (int n = warp; n < NC; n += 8) {
     float mx = 0.f;
     if (n < nvalid)
-      for (int q = lane; q < ncol; q += 32) mx = fmaxf(mx, fabsf((float)coef(n, q)) * pow2f(ce[q]));
+      for (int q = lane; q < ncol; q += 32) mx = fmaxf(mx, fabsf(d2f_trunc(coef(n, q))) * pow2f(ce[q]));
     for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) {
       s_e[n] = exp_up(mx);
@@ -385,11 +388,10 @@ __global__ void __launch_bounds__(256)
       const int q = 8 * g + i;
       float hi = 0.f, lo = 0.f;
       if (n < nvalid && q < ncol) {
-        const double d = coef(n, q);
+        const float2 d = d2dw_bits(coef(n, q));      // integer split, off the FP64 pipe
         const float sc = pow2f(ce[q] + 14 - s_e[n]);  // exact: a power of two
-        hi = (float)d;
-        lo = (float)(d - (double)hi) * sc;
-        hi *= sc;
+        hi = d.x * sc;
+        lo = d.y * sc;
       }
       split4_ff(hi, lo, c0[i], c1[i], c2[i], c3[i]);
     }

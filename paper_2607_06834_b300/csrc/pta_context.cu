@@ -578,6 +578,18 @@ int pta_finalize(pta_ctx* c, void* stream) {
     for (int i = 0, q = 0; i < npsr; ++i)
       for (int j = 0; j <= i; ++j) tm[q++] = (unsigned short)((i << 8) | j);
     UP(lnk, lnk);
+    std::vector<float2> lkT(kmax + 1);
+    for (int k = 0; k <= kmax; ++k) {
+      const double v = (k ? std::log((double)k) : 0.0) - m.ln_Tfyr;
+      const float h = (float)v;
+      lkT[k] = make_float2(h, (float)(v - (double)h));
+    }
+    UP(lkT, lkT);
+    {
+      const double v = 0.5 * m.ln_rho0;
+      const float h = (float)v;
+      m.hr0 = make_float2(h, (float)(v - (double)h));
+    }
     UP(tm, trimap);
   }
   UP(nuw64, chrom64);
@@ -836,7 +848,7 @@ int pta_eval_scratch(pta_ctx* c, const pta::Scratch& s, int B, const float* x, d
     tm.end(pta::count_prior_adjoint(m) + (m.cw ? 2 : 0) + (m.curn && m.cw ? 4 : 0));
   }
   tm.begin(4);
-  if (e == cudaSuccess) e = pta::launch_final(m, s, B, x, logp, grad, status, st);
+  if (e == cudaSuccess) e = pta::launch_final(m, s, B, x, logp, grad, status, fp64, st);
   tm.end(1);
   if (e != cudaSuccess) return fail(c, PTA_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
   return PTA_OK;

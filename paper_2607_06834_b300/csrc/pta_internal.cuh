@@ -10,6 +10,7 @@
 
 namespace pta {
 
+
 constexpr double kYearS = 365.25 * 86400.0;
 constexpr double kFyr = 1.0 / kYearS;
 constexpr double kLn10 = 2.302585092994045684;
@@ -88,6 +89,8 @@ struct DevModel {
   int nsm;                      // streaming multiprocessors of the device
   // global
   const double* lnk;            // ln k, k = 0..max(na, nd) (entry 0 unused)
+  const float2* lkT;            // ln k - ln(T f_yr) as float pairs, k = 0..max(na, nd)
+  float2 hr0;                   // ln_rho0 / 2 as a float pair
   const unsigned short* trimap; // packed-lower index -> (row << 8) | col, for npsr <= 256
   const double* Gamma;          // [npsr x npsr]
   const float2* Gamma_dw;       // Gamma packed lower (trimap order) as double-word float pairs
@@ -214,7 +217,7 @@ cudaError_t launch_curn_set_a(const DevModel& m, const Scratch& s, int B, const 
 cudaError_t launch_sub(float* out, const float* w, size_t n, cudaStream_t st);
 int count_prior_adjoint(const DevModel& m);
 cudaError_t launch_final(const DevModel& m, const Scratch& s, int B, const float* x,
-                         double* logp, float* grad, int32_t* status, cudaStream_t st);
+                         double* logp, float* grad, int32_t* status, int fp64, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Device helpers
