@@ -185,6 +185,17 @@ int pta_set_beta(pta_ctx* ctx, int n, const double* beta, void* stream);
 #define PTA_TRANSFORM_PRIOR 0
 #define PTA_TRANSFORM_CURN 1
 int pta_set_transform(pta_ctx* ctx, int transform);
+/* Arithmetic of the per-frequency N_p x N_p Cholesky of the dense bins (Eq. prior_cov:
+ * Phi_k = rho_k Gamma + diag(kappa_.k)), its inverse and the adjoint of a = L z.
+ * PTA_CHOL_DW (the default): double-word arithmetic on the FP32 pipes (pairs of floats,
+ * ~48-bit significand; factor, inverse and transform agree with FP64 to ~1e-14
+ * relative), several times faster on B300, whose FP64 rate is 1/64 of its FP32 rate.
+ * PTA_CHOL_FP64: the FP64 sweep.  PTA_PREC_FP64 and the CURN transform always use the
+ * FP64 sweep.  The log-det, the pivots' square roots and every sum stay FP64 either
+ * way.  PTA_EINVAL for an unknown value; recaptures HMC graphs. */
+#define PTA_CHOL_DW 0
+#define PTA_CHOL_FP64 1
+int pta_set_cholesky(pta_ctx* ctx, int mode);
 /* Test hook for the bounded device waits (no counterpart in the paper).  code 1:
  * in PTA_PREC_BF16X3 evaluations the tensor-core kernel withholds the completion
  * signal of its first tile's F a product, so its epilogue's bounded mbarrier wait

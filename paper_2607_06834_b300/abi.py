@@ -13,11 +13,13 @@ LIB_PATH = os.path.join(HERE, "libptahmc.so")
 PTA_OK, PTA_EINVAL, PTA_ESTATE, PTA_ECUDA, PTA_ENOMEM, PTA_ETIMEOUT = 0, -1, -2, -3, -4, -5
 PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2, "tf32": 3, "bf16x3": 4, "gram": 5, "f16split": 6}
 TRANSFORM = {"prior": 0, "curn": 1}
+CHOLESKY = {"dw": 0, "fp64": 1}
 
 EXPORTED = ["pta_create", "pta_add_pulsar", "pta_finalize", "pta_layout", "pta_set_precision",
             "pta_set_hyperprior", "pta_logp_and_grad", "pta_hmc_trajectory", "pta_logp_constant",
             "pta_profile_enable", "pta_profile_read", "pta_logp_and_grad_noalloc", "pta_autotune",
             "pta_set_toa_config", "pta_toa_config_info", "pta_debug_inject", "pta_set_beta", "pta_set_transform",
+            "pta_set_cholesky",
             "pta_param_bounds", "pta_last_error", "pta_destroy"]
 NSTAGES = 8
 STAGES = ["prior_forward", "toa", "epilogue", "adjoint", "final"]
@@ -71,6 +73,7 @@ def _load():
     lib.pta_debug_inject.argtypes = [vp, C.c_int]
     lib.pta_set_beta.argtypes = [vp, C.c_int, vp, vp]
     lib.pta_set_transform.argtypes = [vp, C.c_int]
+    lib.pta_set_cholesky.argtypes = [vp, C.c_int]
     lib.pta_param_bounds.argtypes = [vp, vp, vp]
     lib.pta_toa_config_info.argtypes = [C.c_int] + [C.POINTER(C.c_int)] * 4
     lib.pta_last_error.argtypes = [vp]

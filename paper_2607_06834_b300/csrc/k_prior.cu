@@ -960,9 +960,10 @@ static size_t chol_smem(const DevModel& m) {
   const size_t np = m.npsr, ntri = np * (np + 1) / 2;
   return (2 * ntri + 4 * np) * sizeof(double);
 }
-// The double-word sweep and adjoint run everywhere but in FP64 mode and under the CURN
-// transform (whose whitening kernel reads the FP64 inverse factors).
-static bool chol_dw(const DevModel& m, int fp64) { return !fp64 && !m.curn; }
+// The double-word sweep and adjoint run everywhere but in FP64 mode, under the CURN
+// transform (whose whitening kernel reads the FP64 inverse factors) and when
+// pta_set_cholesky asked for the FP64 sweep.
+static bool chol_dw(const DevModel& m, int fp64) { return !fp64 && !m.curn && !m.chol64; }
 
 static size_t adj_smem_dw(const DevModel& m) {
   const size_t np = m.npsr, ntri = np * (np + 1) / 2;

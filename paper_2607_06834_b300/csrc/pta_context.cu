@@ -1047,6 +1047,14 @@ int pta_set_transform(pta_ctx* c, int transform) {
   return PTA_OK;
 }
 
+int pta_set_cholesky(pta_ctx* c, int mode) {
+  if (!c) return PTA_EINVAL;
+  if (mode != PTA_CHOL_DW && mode != PTA_CHOL_FP64) return fail(c, PTA_EINVAL, "set_cholesky: unknown mode");
+  if (mode != c->dm.chol64) drop_graphs(c);
+  c->dm.chol64 = mode == PTA_CHOL_FP64 ? 1 : 0;
+  return PTA_OK;
+}
+
 int pta_debug_inject(pta_ctx* c, int code) {
   if (!c) return PTA_EINVAL;
   if (code < 0 || code > 1) return fail(c, PTA_EINVAL, "debug_inject: unknown code");

@@ -90,6 +90,7 @@ struct DevModel {
   // global
   const double* lnk;            // ln k, k = 0..max(na, nd) (entry 0 unused)
   const float2* lkT;            // ln k - ln(T f_yr) as float pairs, k = 0..max(na, nd)
+  int chol64;                   // 1: FP64 dense-bin Cholesky even outside FP64 mode (pta_set_cholesky)
   float2 hr0;                   // ln_rho0 / 2 as a float pair
   const unsigned short* trimap; // packed-lower index -> (row << 8) | col, for npsr <= 256
   const double* Gamma;          // [npsr x npsr]

@@ -114,6 +114,13 @@ class Engine:
         self._check(abi.lib.pta_set_transform(self._h, abi.TRANSFORM[transform]), "pta_set_transform")
         self.transform = transform
 
+    def set_cholesky(self, mode: str):
+        """Arithmetic of the dense-bin per-frequency Cholesky, its inverse and adjoint:
+        "dw" (double-word float pairs on the FP32 pipes, the default) or "fp64".  FP64
+        precision mode and the CURN transform always use FP64."""
+        self._check(abi.lib.pta_set_cholesky(self._h, abi.CHOLESKY[mode]), "pta_set_cholesky")
+        self.cholesky = mode
+
     def param_bounds(self):
         """(lo, hi) float64 arrays of the prior support of each coordinate (+-inf where
         unbounded); the HMC trajectory moves the bounded ones in logit space."""

@@ -567,3 +567,39 @@ def test_cw_tempered_free_spectra_combined(prec):
         assert np.all(err <= BF16_REPORTED_LOGP + REL_RANDOM["bf16x3"] * np.abs(lo))
         assert rel.max() < BF16_REPORTED_GRAD
     eng.set_beta(None)
+
+
+# ------------------------------------------------------------------ dense-bin Cholesky arithmetic
+@pytest.mark.parametrize("prec", ["fp32", "gram"])
+def test_cholesky_fp64_switch(prec):
+    """pta_set_cholesky: the double-word sweep (default outside FP64 mode) and the FP64
+    sweep give the same posterior to well below the tolerances (the factor agrees with
+    FP64 to ~1e-14 relative), both at the oracle's FP64 level in the Gram form; and the
+    switch applies to an existing context."""
+    kw = dict(npsr=6, ntoa=[300, 500, 800, 1200, 400, 700], m=[3, 5, 8, 4, 6, 7], n_gwb=6, n_rn=8, n_dm=5,
+              seed=33, nbackend=2)
+    arr = synth.small_array(**kw)
+    orc = O.Oracle(arr)
+    X = synth.make_points(arr, 40, seed=9)
+    X[:8] = np.array([O.curn_point(orc, x.astype(np.float64), 1.0, seed=i) for i, x in enumerate(X[:8])])
+    lo, go = _oracle(orc, X[:12])
+    eng = _engine(arr, prec)
+    lp_dw, g_dw, st = _eval(eng, X)
+    assert np.all(st == 0)
+    eng.set_cholesky("fp64")
+    lp_64, g_64, st = _eval(eng, X)
+    assert np.all(st == 0)
+    eng.set_cholesky("dw")
+    lp_dw2, g_dw2, _ = _eval(eng, X)
+    assert np.array_equal(lp_dw, lp_dw2) and np.array_equal(g_dw, g_dw2)
+    d = np.abs(lp_dw - lp_64) / np.maximum(1.0, np.abs(lp_64))
+    dg = _grad_rel(g_dw, g_64)
+    print(f"{prec}: dw vs FP64 Cholesky: max rel dlogp {d.max():.2e}, max grad rel {dg.max():.2e}")
+    assert d.max() < 1e-10 and dg.max() < 1e-6
+    for lp, g in ((lp_dw, g_dw), (lp_64, g_64)):
+        if prec == "gram":
+            assert np.max(np.abs(lp[:12] - lo) / np.maximum(1.0, np.abs(lo))) < FP64_REL
+            assert np.max(_grad_rel(g[:12], go)) < 1e-6
+        else:
+            assert np.max(np.abs(lp[:8] - lo[:8])) < LOGP_ABS
+            assert np.max(_grad_rel(g[:12], go)) < GRAD_REL
