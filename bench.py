@@ -942,7 +942,7 @@ def main():
     ap.add_argument("--transform", default="prior", choices=["prior", "curn"])
     ap.add_argument("--hmc-warmup", type=int, default=400)
     ap.add_argument("--hmc-samples", type=int, default=200)
-    ap.add_argument("--hmc-samples-curn", type=int, default=800,
+    ap.add_argument("--hmc-samples-curn", type=int, default=2000,
                     help="sampling trajectories of the CURN leg on the paper's model")
     ap.add_argument("--hmc-warmup-curn", type=int, default=1000,
                     help="warm-up trajectories of the CURN leg on the paper's model")
