@@ -93,6 +93,11 @@ __device__ __forceinline__ void st16(uint32_t taddr, const uint32_t (&r)[16]) {
       "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
       : "memory");
 }
+__device__ __forceinline__ void st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
 // 32 lanes x 16 columns of 32-bit values, completion awaited by wait_ld
 __device__ __forceinline__ void ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
@@ -652,7 +657,8 @@ constexpr int FW_XST = 3 * FW_XARR;                     // one stage: pieces X0,
 constexpr int FW_WSB = 128 * KWB * 4;                   // w~ stage: two halves of 128 chains x 32 TOAs (128-byte swizzled rows)
 constexpr int FW_WHB = 128 * 32 * 4;                    // one half
 constexpr int FW_SMEM = NSM * FW_XST + NSM * FW_WSB;
-constexpr int FW_THREADS = 192;                         // warp 0 MMA, warps 1-4 w~ and epilogue, warp 5 copies
+constexpr int FW_THREADS = 320;                         // warp 0 MMA, warps 1-8 w~ and epilogue, warp 9 copies
+static_assert(KWB == 32, "the w~ producers take 16 TOAs of a stage each");
 static_assert((NSM * FW_XST) % 1024 == 0, "swizzled w~ stages start on 1024-byte boundaries");
 static_assert(FW_SMEM + 2048 <= 227 * 1024, "shared memory");
 
@@ -700,12 +706,12 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
   if (tid == 0) {
     for (int s = 0; s < NSM; ++s) {
       tc::mbar_init(&wland[s], 1);
-      tc::mbar_init(&wread[s], 4);
+      tc::mbar_init(&wread[s], 8);
       tc::mbar_init(&xfull[s], 1);
       tc::mbar_init(&xfree[s], 1);
     }
     for (int s = 0; s < NSB; ++s) {
-      tc::mbar_init(&wfull[s], 4);
+      tc::mbar_init(&wfull[s], 8);
       tc::mbar_init(&wfree[s], 1);
     }
     tc::mbar_init(&dfull, 1);
@@ -759,9 +765,11 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
       if (!tc::mbar_wait(&drain, 0, kDrainLimit)) s_bad = 1;
     }
     __syncwarp();
-  } else if (warp < 5) {
-    // ------------------------------------------------ w~ into tensor memory (lane = chain), epilogue
-    const int qwp = warp & 3, n = 32 * qwp + lane;
+  } else if (warp < 9) {
+    // ------------------------------------------------ w~ into tensor memory (lane = chain), epilogue.
+    // Two warps per 32-lane group of tensor memory (warp % 4 picks the group): warp hf = 0
+    // cuts TOAs 0-15 of a stage, hf = 1 TOAs 16-31, into columns 8 hf .. 8 hf + 7 of each piece.
+    const int qwp = warp & 3, hf = (warp - 1) >> 2, n = 32 * qwp + lane;
     const uint32_t lanef = (uint32_t)(32 * qwp) << 16;
     const bool valid = n < nvalid;
     const int ew = valid ? exp_up(wmx[(size_t)u * B + b0 + n]) : 0;
@@ -770,43 +778,42 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
     for (int g = 0; g < nst; ++g) {
       const int s = g % NSB, sx = g % NSM;
       if (!(ok = __all_sync(0xffffffffu, wait(&wland[sx], (g / NSM) & 1)))) break;
-      // row n of each swizzled half: 16-byte chunk j at chunk j ^ (n % 8)
+      // row n of the swizzled stage: 16-byte chunk j at chunk j ^ (n % 8)
       const unsigned char* row = wsm + sx * FW_WSB + n * 128;
-      uint32_t p0[KWB / 2], ph[KWB / 2], pl[KWB / 2];
+      uint32_t p0[8], ph[8], pl[8];
 #pragma unroll
-      for (int j = 0; j < KWB / 4; ++j) {
-        const float4 v = *reinterpret_cast<const float4*>(row + (j / 8) * FW_WHB + 16 * ((j % 8) ^ (n & 7)));
+      for (int jj = 0; jj < 4; ++jj) {
+        const int j = 4 * hf + jj;
+        const float4 v = *reinterpret_cast<const float4*>(row + 16 * (j ^ (n & 7)));
         const float vv[4] = {v.x, v.y, v.z, v.w};
         float a0[4], ah[4], al[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) split_w(vv[e] * wsc, a0[e], ah[e], al[e]);
-        p0[2 * j] = h2(a0[0], a0[1]);
-        p0[2 * j + 1] = h2(a0[2], a0[3]);
-        ph[2 * j] = h2(ah[0], ah[1]);
-        ph[2 * j + 1] = h2(ah[2], ah[3]);
-        pl[2 * j] = h2(al[0], al[1]);
-        pl[2 * j + 1] = h2(al[2], al[3]);
+        p0[2 * jj] = h2(a0[0], a0[1]);
+        p0[2 * jj + 1] = h2(a0[2], a0[3]);
+        ph[2 * jj] = h2(ah[0], ah[1]);
+        ph[2 * jj + 1] = h2(ah[2], ah[3]);
+        pl[2 * jj] = h2(al[0], al[1]);
+        pl[2 * jj + 1] = h2(al[2], al[3]);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&wread[sx]);  // the staged rows may be refilled
       if (g >= NSB && !(ok = __all_sync(0xffffffffu, wait(&wfree[s], ((g / NSB) - 1) & 1)))) break;
-      const uint32_t col = tmem + lanef + FW_WB + s * FW_WST;
-#pragma unroll
-      for (int h = 0; h < KWB / 32; ++h) {
-        st16(col + 16 * h, *reinterpret_cast<uint32_t(*)[16]>(p0 + 16 * h));
-        st16(col + KWB / 2 + 16 * h, *reinterpret_cast<uint32_t(*)[16]>(ph + 16 * h));
-        st16(col + KWB + 16 * h, *reinterpret_cast<uint32_t(*)[16]>(pl + 16 * h));
-      }
+      const uint32_t col = tmem + lanef + FW_WB + s * FW_WST + 8 * hf;
+      st8(col, p0);
+      st8(col + KWB / 2, ph);
+      st8(col + KWB, pl);
       wait_st();
       tc::fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&wfull[s]);
     }
-    // ghat rows of this unit and column chunk: undo 2^(12 - ew) and 2^(14 - c_q)
+    // ghat rows of this unit and column chunk: undo 2^(12 - ew) and 2^(14 - c_q); the two
+    // warps of a lane group take alternate 16-column blocks
     const int* ce = m.x16_cexp + (size_t)I * m.x16_kxm + q0;
     if (ok && __all_sync(0xffffffffu, wait(&dfull, 0))) {
       tc::fence_after();
-      for (int c0 = 0; c0 < NQ; c0 += 16) {
+      for (int c0 = 16 * hf; c0 < NQ; c0 += 32) {
         uint32_t l0[16], lr[16];
         ld16(tmem + lanef + FW_D0 + c0, l0);
         ld16(tmem + lanef + FW_DR + c0, lr);
