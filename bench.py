@@ -47,6 +47,9 @@ FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12     # SMs x 2 FP64 FMA/clk x 2 f
 # the FP32 pipes: one multiply-add of the algorithm issues 14 FP32 operations (an exact
 # product with three fused multiply-adds, TwoSum and a renormalisation), so its peak in
 # flop of the algorithm is the FP32 operation rate x 2 / 14.
+# the HMC legs sample with the headline evaluation path
+HMC_PRECISION = "f16split"
+HMC_PATH = "exact-split tensor-core path"
 DW_OPS_PER_FMA = 14
 DW_PEAK_TFLOPS = 148 * 128 * 2.032e9 * 2 / DW_OPS_PER_FMA / 1e12
 
@@ -481,7 +484,7 @@ def hmc_ess(args, dev):
     name = "ng15_cw"
     arr = synth.make_array(name)
     B, L = synth.WORKLOADS[name]["chains"], 20
-    eng = Engine(arr, precision="fp32")
+    eng = Engine(arr, precision=HMC_PRECISION)
     lay = eng.layout
     x0 = torch.tensor(synth.make_points(arr, B, seed=6834 + 3), device=dev)
     th0 = lay["d_z"]
@@ -504,7 +507,7 @@ def hmc_ess(args, dev):
     t = res.sampling_s
     eng.close()
     return {"workload": "NANOGrav-15-yr-like array + circular SMBHB (Earth and pulsar terms), "
-                        f"{B} chains, {L} leapfrog steps per trajectory, FP32 path",
+                        f"{B} chains, {L} leapfrog steps per trajectory, {HMC_PATH}",
             "warmup_trajectories": args.hmc_warmup, "sampling_trajectories": args.hmc_samples,
             "gwb": ess_rate(e_gwb, np.nanmax(rh[g0:g0 + 2]), t),
             "theta_median": ess_rate(e_med, np.nanmax(rh), t),
@@ -536,13 +539,13 @@ def hmc_ess_transforms(args, dev):
     arr = synth.make_array(name)
     B, L = synth.WORKLOADS[name]["chains"], 20
     out = {"workload": "paper's NANOGrav-15-yr model (RN 30 / HD-GWB 14 bins, no DM) on the 67-pulsar "
-                       f"array, {B} chains, {L} leapfrog steps per trajectory, FP32 path",
+                       f"array, {B} chains, {L} leapfrog steps per trajectory, {HMC_PATH}",
            "warmup_trajectories": {"curn": args.hmc_warmup_curn, "prior": args.hmc_warmup},
            "sampling_trajectories": {"curn": args.hmc_samples_curn, "prior": args.hmc_samples}}
     for tr in ("curn", "prior"):
         ns = args.hmc_samples_curn if tr == "curn" else args.hmc_samples
         nw = args.hmc_warmup_curn if tr == "curn" else args.hmc_warmup
-        eng = Engine(arr, precision="fp32")
+        eng = Engine(arr, precision=HMC_PRECISION)
         eng.set_transform(tr)
         lay = eng.layout
         th0 = lay["d_z"]
@@ -569,7 +572,7 @@ def hmc_ess_transforms(args, dev):
     # the same model with a circular binary, CURN transform with the signal-dependent mean
     # (Eq. decenter_det_PTA)
     arr = synth.make_array("ng15_nodm_cw")
-    eng = Engine(arr, precision="fp32")
+    eng = Engine(arr, precision=HMC_PRECISION)
     eng.set_transform("curn")
     lay = eng.layout
     th0 = lay["d_z"]

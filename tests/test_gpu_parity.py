@@ -388,9 +388,10 @@ def test_autograd_function(tiny):
 
 
 # ------------------------------------------------------------------ HMC
-def test_hmc_trajectory_matches_oracle(tiny):
+@pytest.mark.parametrize("prec", ["fp32", "f16split"])
+def test_hmc_trajectory_matches_oracle(tiny, prec):
     arr, orc = tiny
-    eng = _engine(arr, "fp32")
+    eng = _engine(arr, prec)
     B, L, step = 6, 8, 0.02
     X = synth.make_points(arr, B, seed=9).astype(np.float64)
     X = np.array([O.curn_point(orc, x, 0.5, seed=i) for i, x in enumerate(X)], dtype=np.float32)
