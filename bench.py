@@ -227,8 +227,9 @@ def curn_variant(dev, steps):
     prior-whitened one on the same batch: the paper's NANOGrav-15-yr model (RN 30 /
     HD-GWB 14 bins, no DM: P = 60, the factor in shared memory) with 64 and 256 chains,
     and the 100-DM-bin workload (P = 260, the factor in the global inverse buffer) with
-    256 chains.  CUDA events per step with L2 flushed; the FP64 factorisation stage is
-    the CURN forward stage minus the prior-whitened one."""
+    256 chains, on the headline path.  CUDA events per step with L2 flushed; the
+    factorisation stage is the CURN forward stage minus the prior-whitened one: double-word
+    (k_curn_forward_dw) where the two triangles fit in shared memory, FP64 otherwise."""
     import ctypes as C
     import torch
     from paper_2607_06834_b300 import abi, synth
@@ -238,7 +239,7 @@ def curn_variant(dev, steps):
     out = []
     for name, B in (("ng15_nodm", 64), ("ng15_nodm", 256), ("ng15_b256", 256)):
         arr = synth.make_array(name)
-        eng = Engine(arr, precision="fp32")
+        eng = Engine(arr, precision=HMC_PRECISION)
         x = torch.tensor(synth.make_points(arr, B, seed=6834 + 7), device=dev)
         rec = {"workload": name, "chains": B, "P": 2 * max(arr.n_gwb, arr.n_rn) + 2 * arr.n_dm}
         for tr in ("prior", "curn"):
@@ -266,12 +267,22 @@ def curn_variant(dev, steps):
                        "stage_ms": dict(zip(abi.STAGES, [round(v / n, 4) for v in sm]))}
         fac_ms = rec["curn"]["stage_ms"]["prior_forward"] - rec["prior"]["stage_ms"]["prior_forward"]
         ach = curn_flops_per_launch(arr, B) / (fac_ms * 1e-3) / 1e12
-        rec["roofline"] = {"kernel": "k_curn_forward + k_curn_whiten (FP64 LDL^T sweep with inverse)",
-                           "bound": "alu", "unit": "TFLOP/s", "achieved": ach, "peak": peak,
-                           "peak_source": "derived: 148 SM x 2 FP64 FMA/clk x 2 flop x 2.032 GHz",
-                           "frac": ach / peak, "stage_ms": fac_ms,
-                           "factor_in": "shared memory" if (rec["P"] * (rec["P"] + 1) // 2 + 8 * rec["P"]) * 8
-                           <= 200 * 1024 else "global inverse buffer"}
+        P = rec["P"]
+        dw = 6 * (P // 2 + 1) * 16 + 2 * (P * (P + 2) // 2 if P % 2 == 0 else (P + 1) ** 2 // 2) * 8 <= 227 * 1024
+        if dw:
+            rec["roofline"] = {"kernel": "k_curn_forward_dw + k_curn_whiten (double-word LDL^T sweep with inverse)",
+                               "bound": "alu", "unit": "TFLOP/s", "achieved": ach, "peak": DW_PEAK_TFLOPS,
+                               "peak_source": f"derived: 148 SM x 128 FP32 lanes x 2.032 GHz x 2 flop / "
+                                              f"{DW_OPS_PER_FMA} FP32 operations per double-word multiply-add",
+                               "frac": ach / DW_PEAK_TFLOPS, "fp64_peak_frac": ach / peak, "stage_ms": fac_ms,
+                               "factor_in": "shared memory"}
+        else:
+            rec["roofline"] = {"kernel": "k_curn_forward + k_curn_whiten (FP64 LDL^T sweep with inverse)",
+                               "bound": "alu", "unit": "TFLOP/s", "achieved": ach, "peak": peak,
+                               "peak_source": "derived: 148 SM x 2 FP64 FMA/clk x 2 flop x 2.032 GHz",
+                               "frac": ach / peak, "stage_ms": fac_ms,
+                               "factor_in": "shared memory" if (P * (P + 1) // 2 + 8 * P) * 8 <= 200 * 1024
+                               else "global inverse buffer"}
         eng.close()
         out.append(rec)
     return out

@@ -72,6 +72,17 @@ __device__ __forceinline__ float2 dw_recip(float2 d) {
   return dw_renorm(r, __fmul_rn(r, e));
 }
 
+// sqrt(d) for d > 0: the float reciprocal square root refined once in FP32, then one
+// Newton correction s0 + (d - s0^2) / (2 s0) with d - s0^2 formed in double words
+// (relative error ~2^-45)
+__device__ __forceinline__ float2 dw_sqrt(float2 d) {
+  float y = rsqrtf(d.x);
+  y = __fmul_rn(y, __fmaf_rn(__fmul_rn(-0.5f * d.x, y), y, 1.5f));
+  const float s0 = __fmul_rn(d.x, y);
+  const float2 e = dw_fms(d, make_float2(s0, 0.0f), make_float2(s0, 0.0f));
+  return dw_addf(make_float2(s0, 0.0f), __fmul_rn(__fmul_rn(e.x, y), 0.5f));
+}
+
 // Exact float -> double: the exponent rebias 127 -> 1023 and the 23-bit fraction moved
 // to the top of the 52-bit one; zero and subnormals give 0, infinities and NaNs keep
 // their class.

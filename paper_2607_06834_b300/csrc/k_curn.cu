@@ -30,6 +30,8 @@
 // columns of W give every p in O(P^2).
 #include <cmath>
 
+#include "dw_ldl.cuh"
+#include "dwarith.cuh"
 #include "pta_internal.cuh"
 
 namespace pta {
@@ -222,6 +224,127 @@ __global__ void __launch_bounds__(kCT)
 }
 
 // ---------------------------------------------------------------------------
+// The forward of k_curn_forward with the factorisation in double-word arithmetic on the
+// FP32 pipes (dw_ldl_sweep on A' scaled by 2^-E, E even, from its largest diagonal
+// entry), the inverse's scaling, both triangular products and the transform in double
+// words; outputs as k_curn_forward (Y' as FP64 in the W slot for the gradient and the
+// whitening, log det L_CURN in FP64).  Used outside FP64 mode when the two triangles fit
+// in shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kCTdw = 128;
+
+__global__ void __launch_bounds__(kCTdw)
+    k_curn_forward_dw(DevModel m, const float* __restrict__ x, const double* __restrict__ sk,
+                      const double* __restrict__ skd, const double* __restrict__ srho, double* a64, double* Wg,
+                      double* ahat, double* ld, int32_t* stat, const double* __restrict__ g0, int B) {
+  extern __shared__ float4 smq[];
+  __shared__ float2 pv[4];
+  __shared__ int s_bad;
+  __shared__ double red[kCTdw / 32];
+  const int I = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, nt = blockDim.x, P = m.P;
+  const int ntri = P * (P + 1) / 2, nh = P / 2 + 1;
+  float2* A = reinterpret_cast<float2*>(smq + 6 * nh);  // after the sweep's staging
+  float2* X = A + prow(P);
+  const size_t o = (size_t)I * B + b;
+  const double bt = m.beta ? m.beta[b] : 1.0;
+  const double gsc = g0 ? 1.0 : bt;  // factor of Y'^T Y' g in the mean
+  const float2 btw = d2dw_bits(bt), gscw = d2dw_bits(gsc);
+  const float* xb = x + (size_t)b * m.d;
+  const float2* G = m.Grev_dw + (size_t)I * ntri;
+  float2* rdw = reinterpret_cast<float2*>(smq);  // [P] 1 / phi_C of reversed coefficient i (staging, free until the sweep)
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (int i = tid; i < P; i += nt) {
+    const double ph = phic(m, sk, skd, srho, b, I, P - 1 - i);
+    float2 r = make_float2(1.0f, 0.0f);
+    if (ph > 0.0 && ph < INFINITY)
+      r = dw_recip(d2dw_bits(ph));
+    else
+      s_bad = 1;
+    rdw[i] = r;
+  }
+  __syncthreads();
+  // scale 2^-E, E even, from the largest diagonal entry (every warp computes it)
+  float dmax = 0.0f;
+  for (int i = tid & 31; i < P; i += 32) dmax = fmaxf(dmax, dw_add(dw_mul(btw, G[i * (i + 3) / 2]), rdw[i]).x);
+  for (int off = 16; off; off >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
+  int E = 0;
+  if (dmax > 0.0f && dmax < INFINITY) frexpf(dmax, &E);
+  E += E & 1;
+  const float sc = __int_as_float((127 - E) << 23);  // 2^-E (E within the float exponent range here)
+  for (int e = tid; e < ntri; e += nt) {
+    int i, j;
+    tri_decode_f(e, i, j);
+    float2 v = dw_mul(btw, G[e]);
+    if (i == j) v = dw_add(v, rdw[i]);
+    const int q = prow(i) + j;
+    A[q] = make_float2(v.x * sc, v.y * sc);
+    X[q] = make_float2(i == j ? 1.0f : 0.0f, 0.0f);
+    if (i == j && !(i & 1)) {
+      A[q + 1] = make_float2(0.0f, 0.0f);
+      X[q + 1] = make_float2(0.0f, 0.0f);
+    }
+  }
+  __syncthreads();
+  dw_ldl_sweep(P, A, X, smq, pv, &s_bad, nullptr);
+  // 1 / sqrt(d_i) at the true scale, g and z in reversed order (the staging area is free)
+  float2* rqw = reinterpret_cast<float2*>(smq);  // [P]
+  float2* gpw = rqw + P;                          // [P] g'
+  float2* zpw = gpw + P;                          // [P] z'
+  float2* upw = zpw + P;                          // [P] Y' g'
+  float2* tpw = upw + P;                          // [P] gsc Y' g' + z'
+  const float usc = __int_as_float((127 - E / 2) << 23);  // 2^(-E/2)
+  for (int i = tid; i < P; i += nt) {
+    const int p = P - 1 - i;
+    const float2 r = dw_recip(dw_sqrt(A[prow(i) + i]));
+    rqw[i] = make_float2(r.x * usc, r.y * usc);
+    gpw[i] = d2dw_bits(g0 ? fma(bt, m.ga[(size_t)I * P + p], g0[o * P + p]) : m.gt[(size_t)I * P + p]);
+    zpw[i] = make_float2(xb[zidx(m, I, p)], 0.0f);
+  }
+  __syncthreads();
+  // Y' = D^-1/2 L'^-1, in place of L'^-1
+  for (int e = tid; e < ntri; e += nt) {
+    int i, j;
+    tri_decode_f(e, i, j);
+    const int q = prow(i) + j;
+    X[q] = (i == j) ? rqw[i] : dw_mul(X[q], rqw[i]);
+  }
+  __syncthreads();
+  for (int i = tid; i < P; i += nt) {
+    const float2* row = X + prow(i);
+    float2 acc = make_float2(0.0f, 0.0f);
+    for (int c = 0; c <= i; ++c) acc = dw_fms(acc, row[c], dw_neg(gpw[c]));
+    upw[i] = acc;
+    tpw[i] = dw_add(dw_mul(gscw, acc), zpw[i]);
+  }
+  __syncthreads();
+  for (int c = tid; c < P; c += nt) {
+    float2 sa = make_float2(0.0f, 0.0f), sh = sa;
+    for (int i = c; i < P; ++i) {
+      const float2 y = X[prow(i) + c];
+      sa = dw_fms(sa, y, dw_neg(tpw[i]));
+      sh = dw_fms(sh, y, dw_neg(upw[i]));
+    }
+    const int p = P - 1 - c;
+    a64[o * m.PM + p] = dw2d(sa);
+    ahat[o * P + p] = dw2d(dw_mul(gscw, sh));
+  }
+  double acc = 0.0;  // log det L_CURN = sum_i log Y'_ii
+  for (int i = tid; i < P; i += nt) acc += log(dw2d(rqw[i]));
+  acc = block_sum(acc, red);
+  if (tid == 0) {
+    ld[o] = acc;
+    if (s_bad) atomicOr(&stat[b], 2);
+  }
+  double* Wslot = Wg + o * ntri;
+  for (int e = tid; e < ntri; e += nt) {
+    int i, j;
+    tri_decode_f(e, i, j);
+    Wslot[e] = dw2d(X[prow(i) + j]);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // HD prior at the transformed coefficients, per (achromatic bin or DM block, chain):
 // v = Phi_k^-1 a (stored for the gradient), the term -1/2 a^T Phi_k^-1 a - log det Phi_k
 // over both columns, and its derivatives at fixed a:
@@ -230,6 +353,7 @@ __global__ void __launch_bounds__(kCT)
 // Dense bins use L_k^-1 from the prior stage, GWB-only bins chol(Gamma)^-1 / sqrt(rho),
 // diagonal bins 1 / kappa.  Grid (na + 1, B).
 // ---------------------------------------------------------------------------
+template <bool DWL>  // dense-bin inverse factors as double-word float pairs (k_chol_forward_dw)
 __global__ void __launch_bounds__(kCT)
     k_curn_whiten(DevModel m, const double* __restrict__ a64, const double* __restrict__ Lipk,
                   const double* __restrict__ sk, const double* __restrict__ skd, const double* __restrict__ srho,
@@ -283,7 +407,7 @@ __global__ void __launch_bounds__(kCT)
   const double sr = srho[(size_t)b * m.na + k];
   if (dense) {
     const double* Xg = Lipk + ((size_t)b * m.n_chol + k) * ntri;
-    for (int e = tid; e < ntri; e += kCT) X[e] = Xg[e];
+    for (int e = tid; e < ntri; e += kCT) X[e] = DWL ? dw2d(reinterpret_cast<const float2*>(Xg)[e]) : Xg[e];
   } else {
     const double isr = 1.0 / sr;
     for (int e = tid; e < ntri; e += kCT) {
@@ -430,18 +554,30 @@ constexpr size_t kCurnSmemMax = 200 * 1024;
 
 size_t curn_w_doubles(const DevModel& m) { return (size_t)m.P * (m.P + 1) / 2; }
 
-cudaError_t launch_curn_forward(const DevModel& m, const Scratch& s, int B, const float* x, cudaStream_t st) {
-  const bool tri = fwd_smem(m, true) <= kCurnSmemMax;
-  const size_t sm = fwd_smem(m, tri);
-  cudaError_t e = cudaFuncSetAttribute(k_curn_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  k_curn_forward<<<dim3(m.npsr, B), kCT, sm, st>>>(m, x, s.sk, s.skd, s.srho, s.a64, s.curnW, s.curnAhat, s.curnLd,
-                                                    s.stat, m.cw ? s.curnG0 : nullptr, B, tri ? 1 : 0);
+cudaError_t launch_curn_forward(const DevModel& m, const Scratch& s, int B, const float* x, int fp64,
+                                cudaStream_t st) {
+  const size_t smdw = 6 * (size_t)(m.P / 2 + 1) * sizeof(float4) + 2 * (size_t)prow(m.P) * sizeof(float2);
+  cudaError_t e;
+  if (!fp64 && !m.chol64 && smdw <= 227 * 1024) {
+    e = cudaFuncSetAttribute(k_curn_forward_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smdw);
+    if (e != cudaSuccess) return e;
+    k_curn_forward_dw<<<dim3(m.npsr, B), kCTdw, smdw, st>>>(m, x, s.sk, s.skd, s.srho, s.a64, s.curnW, s.curnAhat,
+                                                            s.curnLd, s.stat, m.cw ? s.curnG0 : nullptr, B);
+  } else {
+    const bool tri = fwd_smem(m, true) <= kCurnSmemMax;
+    const size_t sm = fwd_smem(m, tri);
+    e = cudaFuncSetAttribute(k_curn_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_curn_forward<<<dim3(m.npsr, B), kCT, sm, st>>>(m, x, s.sk, s.skd, s.srho, s.a64, s.curnW, s.curnAhat,
+                                                      s.curnLd, s.stat, m.cw ? s.curnG0 : nullptr, B, tri ? 1 : 0);
+  }
   const size_t ws = ((size_t)m.npsr * (m.npsr + 1) / 2 + 4 * m.npsr) * sizeof(double);
-  e = cudaFuncSetAttribute(k_curn_whiten, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws);
+  const bool dwl = chol_uses_dw(m, fp64);
+  e = dwl ? cudaFuncSetAttribute(k_curn_whiten<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws)
+          : cudaFuncSetAttribute(k_curn_whiten<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws);
   if (e != cudaSuccess) return e;
-  k_curn_whiten<<<dim3(m.na + 1, B), kCT, ws, st>>>(m, s.a64, s.Lipk, s.sk, s.skd, s.srho, s.curnV, s.curnQ, s.dlnk,
-                                                    s.dlnkd, s.dlnr, B);
+  (dwl ? k_curn_whiten<true> : k_curn_whiten<false>)<<<dim3(m.na + 1, B), kCT, ws, st>>>(
+      m, s.a64, s.Lipk, s.sk, s.skd, s.srho, s.curnV, s.curnQ, s.dlnk, s.dlnkd, s.dlnr, B);
   return cudaGetLastError();
 }
 

@@ -569,6 +569,14 @@ int pta_finalize(pta_ctx* c, void* stream) {
   UP(LG, LGamma);
   UP(LGi, LGammaInv);
   UP(Grev, Grev);
+  {
+    std::vector<float2> gdw(Grev.size());
+    for (size_t q = 0; q < Grev.size(); ++q) {
+      const float h = (float)Grev[q];
+      gdw[q] = make_float2(h, (float)(Grev[q] - (double)h));
+    }
+    UP(gdw, Grev_dw);
+  }
   UP(gtv, gt);
   UP(gav, ga);
   {
@@ -799,7 +807,7 @@ int pta_eval_scratch(pta_ctx* c, const pta::Scratch& s, int B, const float* x, d
     if (e == cudaSuccess) e = pta::launch_toa_fp32_cfg(m, s0, B, c->toa_cfg, st);
     if (e == cudaSuccess) e = pta::launch_reduce(m, s0, B, 0, st);
   }
-  if (e == cudaSuccess && m.curn) e = pta::launch_curn_forward(m, s, B, x, st);
+  if (e == cudaSuccess && m.curn) e = pta::launch_curn_forward(m, s, B, x, fp64, st);
   // the exact-split path reads a - a_ref itself; its prologue only adds the signal's c_s
   const bool f16 = c->precision == PTA_PREC_F16SPLIT;
   if (e == cudaSuccess && !gram && (!f16 || m.cw))

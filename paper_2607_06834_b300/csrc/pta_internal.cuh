@@ -101,6 +101,7 @@ struct DevModel {
   int curn;
   const double* Grev;           // per pulsar G~ = F^T N~^-1 F, packed lower in reversed order
                                 // (element (i', l') = G~[P-1-i'][P-1-l']), P (P + 1) / 2 each
+  const float2* Grev_dw;        // the same as double-word float pairs
   const double* gt;             // [npsr][P] F^T N~^-1 dt (FP64)
   const double* ga;             // [npsr][P] G~ a_ref (mean with the deterministic signal)
   // exact-split fp16 tensor-core path (PTA_PREC_F16SPLIT)
@@ -210,7 +211,10 @@ cudaError_t launch_prior_adjoint(const DevModel& m, const Scratch& s, int B, con
                                  float* grad, int fp64, cudaStream_t st);
 int count_prior_forward(const DevModel& m);
 size_t curn_w_doubles(const DevModel& m);  // P (P + 1) / 2
-cudaError_t launch_curn_forward(const DevModel& m, const Scratch& s, int B, const float* x, cudaStream_t st);
+cudaError_t launch_curn_forward(const DevModel& m, const Scratch& s, int B, const float* x, int fp64,
+                                cudaStream_t st);
+// the dense-bin Cholesky of this evaluation runs in double words (factors as float pairs)
+bool chol_uses_dw(const DevModel& m, int fp64);
 cudaError_t launch_curn_adjoint(const DevModel& m, const Scratch& s, int B, const float* x, float* grad,
                                 cudaStream_t st);
 // a64 = a_ref - v (v == nullptr: a_ref) for every chain; out -= w elementwise
