@@ -28,6 +28,7 @@
 // s = W gbar (from dahat = -A^-1 dA ahat, dW^T = -W^T Psi(W dA W^T)^T with Psi the
 // upper triangle and half the diagonal, and d log det L_CURN = -1/2 tr(A^-1 dA)): the
 // columns of W give every p in O(P^2).
+#include <algorithm>
 #include <cmath>
 
 #include "dw_ldl.cuh"
@@ -227,9 +228,9 @@ __global__ void __launch_bounds__(kCT)
 // The forward of k_curn_forward with the factorisation in double-word arithmetic on the
 // FP32 pipes (dw_ldl_sweep on A' scaled by 2^-E, E even, from its largest diagonal
 // entry), the inverse's scaling, both triangular products and the transform in double
-// words; outputs as k_curn_forward (Y' as FP64 in the W slot for the gradient and the
-// whitening, log det L_CURN in FP64).  Used outside FP64 mode when the two triangles fit
-// in shared memory.
+// words; outputs as k_curn_forward except Y', which the W slot holds as float pairs for
+// k_curn_adjoint_dw (log det L_CURN in FP64).  Used outside FP64 mode when the two
+// triangles fit in shared memory.
 // ---------------------------------------------------------------------------
 constexpr int kCTdw = 128;
 
@@ -336,11 +337,11 @@ __global__ void __launch_bounds__(kCTdw)
     ld[o] = acc;
     if (s_bad) atomicOr(&stat[b], 2);
   }
-  double* Wslot = Wg + o * ntri;
+  float2* Wslot = reinterpret_cast<float2*>(Wg) + o * ntri;  // Y' as float pairs, for k_curn_adjoint_dw
   for (int e = tid; e < ntri; e += nt) {
     int i, j;
     tri_decode_f(e, i, j);
-    Wslot[e] = dw2d(X[prow(i) + j]);
+    Wslot[e] = X[prow(i) + j];
   }
 }
 
@@ -523,6 +524,90 @@ __global__ void __launch_bounds__(kCT)
     dlnkd[((size_t)b * np + I) * m.nd + k] += pd[2 * m.na + 2 * k] + pd[2 * m.na + 2 * k + 1];
 }
 
+// The gradient of k_curn_adjoint from the double-word Y' of k_curn_forward_dw, in
+// double words.  The column walk of each p (from the last row up) is cut into nseg
+// segments taken by different threads: segment q returns its sums h_q = sum y s', Dg_q,
+// R_q = sum y z' and T_q (the walk's cross term with R started at zero), and the walk is
+// T = sum_q (T_q + h_q R_above), R_above the R of the segments above q.
+__global__ void __launch_bounds__(kCTdw)
+    k_curn_adjoint_dw(DevModel m, const float* __restrict__ x, const double* __restrict__ ghat,
+                      const float2* __restrict__ Wg, const double* __restrict__ vbuf, const double* __restrict__ ahat,
+                      const double* __restrict__ sk, const double* __restrict__ skd, const double* __restrict__ srho,
+                      float* grad, double* dlnk, double* dlnkd, double* dlnrc, double* v2, int B) {
+  extern __shared__ float2 smw[];
+  const int I = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, nt = blockDim.x, P = m.P, np = m.npsr;
+  const int ntri = P * (P + 1) / 2, nseg = max(1, min(4, nt / P));
+  const size_t o = (size_t)I * B + b;
+  float2* Y = smw;          // [ntri] Y', plain packing
+  float2* gb = Y + ntri;    // [P] gbar', reversed
+  float2* zp = gb + P;      // [P] z'
+  float2* sp = zp + P;      // [P] s' = Y' gbar'
+  float2* seg = sp + P;     // [nseg][P][4] (h, T, R, Dg) per segment and column
+  double* pd = reinterpret_cast<double*>(seg + 4 * nseg * P);  // [P] phi_C d logp / d phi_C
+  const float2* Yg = Wg + o * ntri;
+  for (int e = tid; e < ntri; e += nt) Y[e] = Yg[e];
+  const float* xb = x + (size_t)b * m.d;
+  for (int i = tid; i < P; i += nt) {
+    const int p = P - 1 - i;
+    gb[i] = d2dw_bits(ghat[o * P + p] - vbuf[o * P + p]);
+    zp[i] = make_float2(xb[zidx(m, I, p)], 0.0f);
+  }
+  __syncthreads();
+  float* gout = grad + (size_t)b * m.d;
+  for (int i = tid; i < P; i += nt) {
+    const float2* row = Y + trl(i, 0);
+    float2 s = make_float2(0.0f, 0.0f);
+    for (int c = 0; c <= i; ++c) s = dw_fms(s, row[c], dw_neg(gb[c]));
+    sp[i] = s;
+    gout[zidx(m, I, P - 1 - i)] = __fadd_rn(s.x, s.y);  // d logp / d z = W gbar
+  }
+  __syncthreads();
+  for (int r = tid; r < nseg * P; r += nt) {
+    const int c = r % P, q = r / P, len = P - c;
+    const int hi = P - len * q / nseg, lo = P - len * (q + 1) / nseg;  // rows [lo, hi), walked downward
+    float2 h = make_float2(0.0f, 0.0f), R = h, T = h, Dg = h;
+    for (int i = hi - 1; i >= lo; --i) {
+      const float2 y = Y[trl(i, c)];
+      const float2 ys = dw_mul(y, sp[i]);
+      h = dw_add(h, ys);
+      T = dw_fms(T, ys, dw_neg(R));
+      R = dw_fms(R, y, dw_neg(zp[i]));
+      Dg = dw_fms(Dg, dw_mul(y, y), dw_neg(dw_fms(make_float2(1.0f, 0.0f), zp[i], dw_neg(sp[i]))));
+    }
+    float2* sg = seg + 4 * r;
+    sg[0] = h;
+    sg[1] = T;
+    sg[2] = R;
+    sg[3] = Dg;
+  }
+  __syncthreads();
+  for (int c = tid; c < P; c += nt) {
+    float2 h = make_float2(0.0f, 0.0f), T = h, R = h, Dg = h;
+    for (int q = 0; q < nseg; ++q) {  // top segment first
+      const float2* sg = seg + 4 * (q * P + c);
+      T = dw_add(T, dw_fms(sg[1], sg[0], dw_neg(R)));
+      h = dw_add(h, sg[0]);
+      R = dw_add(R, sg[2]);
+      Dg = dw_add(Dg, sg[3]);
+    }
+    const int p = P - 1 - c;
+    const double hd = dw2d(h);
+    const double ab = -hd * ahat[o * P + p] - dw2d(T) - 0.5 * dw2d(Dg);  // d logp / d d_p
+    if (v2) v2[o * P + p] = hd;  // A^-1 gbar, for the CW gradient through the mean
+    pd[p] = -ab / phic(m, sk, skd, srho, b, I, p);  // phi d/dphi = -d_p d/dd_p
+  }
+  __syncthreads();
+  for (int k = tid; k < m.na; k += nt) {
+    const double S = pd[2 * k] + pd[2 * k + 1];
+    const double r = srho[(size_t)b * m.na + k], q = sk[((size_t)b * np + I) * m.na + k];
+    const double rho = r * r, kap = q * q, iphi = 1.0 / (rho + kap);
+    dlnrc[((size_t)b * np + I) * m.na + k] = S * rho * iphi;
+    dlnk[((size_t)b * np + I) * m.na + k] += S * kap * iphi;
+  }
+  for (int k = tid; k < m.nd; k += nt)
+    dlnkd[((size_t)b * np + I) * m.nd + k] += pd[2 * m.na + 2 * k] + pd[2 * m.na + 2 * k + 1];
+}
+
 // Auxiliary passes of the deterministic-signal transform: a = a_ref - v per (pulsar,
 // chain), and the difference of two per-TOA weight arrays.
 __global__ void k_set_a(DevModel m, double* a64, const double* __restrict__ v, int B) {
@@ -554,11 +639,17 @@ constexpr size_t kCurnSmemMax = 200 * 1024;
 
 size_t curn_w_doubles(const DevModel& m) { return (size_t)m.P * (m.P + 1) / 2; }
 
+// shared memory of k_curn_forward_dw, and whether the double-word CURN kernels run
+static size_t curn_fwd_smem_dw(const DevModel& m) {
+  return 6 * (size_t)(m.P / 2 + 1) * sizeof(float4) + 2 * (size_t)prow(m.P) * sizeof(float2);
+}
+static bool curn_dw(const DevModel& m, int fp64) { return !fp64 && !m.chol64 && curn_fwd_smem_dw(m) <= 227 * 1024; }
+
 cudaError_t launch_curn_forward(const DevModel& m, const Scratch& s, int B, const float* x, int fp64,
                                 cudaStream_t st) {
-  const size_t smdw = 6 * (size_t)(m.P / 2 + 1) * sizeof(float4) + 2 * (size_t)prow(m.P) * sizeof(float2);
+  const size_t smdw = curn_fwd_smem_dw(m);
   cudaError_t e;
-  if (!fp64 && !m.chol64 && smdw <= 227 * 1024) {
+  if (curn_dw(m, fp64)) {
     e = cudaFuncSetAttribute(k_curn_forward_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smdw);
     if (e != cudaSuccess) return e;
     k_curn_forward_dw<<<dim3(m.npsr, B), kCTdw, smdw, st>>>(m, x, s.sk, s.skd, s.srho, s.a64, s.curnW, s.curnAhat,
@@ -581,8 +672,18 @@ cudaError_t launch_curn_forward(const DevModel& m, const Scratch& s, int B, cons
   return cudaGetLastError();
 }
 
-cudaError_t launch_curn_adjoint(const DevModel& m, const Scratch& s, int B, const float* x, float* grad,
+cudaError_t launch_curn_adjoint(const DevModel& m, const Scratch& s, int B, const float* x, float* grad, int fp64,
                                 cudaStream_t st) {
+  if (curn_dw(m, fp64)) {
+    const size_t P = m.P, nseg = std::max<size_t>(1, std::min<size_t>(4, kCTdw / P));
+    const size_t sm = (P * (P + 1) / 2 + 3 * P + 4 * nseg * P) * sizeof(float2) + P * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_curn_adjoint_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_curn_adjoint_dw<<<dim3(m.npsr, B), kCTdw, sm, st>>>(
+        m, x, s.ghat, reinterpret_cast<const float2*>(s.curnW), s.curnV, s.curnAhat, s.sk, s.skd, s.srho, grad,
+        s.dlnk, s.dlnkd, s.dlnrc, m.cw ? s.curnV2 : nullptr, B);
+    return cudaGetLastError();
+  }
   const bool tri = adj_smem(m, true) <= kCurnSmemMax;
   const size_t sm = adj_smem(m, tri);
   cudaError_t e = cudaFuncSetAttribute(k_curn_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

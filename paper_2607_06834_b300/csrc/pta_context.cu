@@ -835,7 +835,7 @@ int pta_eval_scratch(pta_ctx* c, const pta::Scratch& s, int B, const float* x, d
   if (grad) {
     tm.begin(3);
     if (e == cudaSuccess)
-      e = m.curn ? pta::launch_curn_adjoint(m, s, B, x, grad, st) : pta::launch_prior_adjoint(m, s, B, x, grad, fp64, st);
+      e = m.curn ? pta::launch_curn_adjoint(m, s, B, x, grad, fp64, st) : pta::launch_prior_adjoint(m, s, B, x, grad, fp64, st);
     if (e == cudaSuccess && m.curn && m.cw) {
       // CW gradient through the mean: weights w~ - N~^-1 F A^-1 gbar at every TOA, the
       // second from a TOA pass with a = a_ref - A^-1 gbar, zero residual and no signal

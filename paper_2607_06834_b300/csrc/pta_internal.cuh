@@ -215,7 +215,7 @@ cudaError_t launch_curn_forward(const DevModel& m, const Scratch& s, int B, cons
                                 cudaStream_t st);
 // the dense-bin Cholesky of this evaluation runs in double words (factors as float pairs)
 bool chol_uses_dw(const DevModel& m, int fp64);
-cudaError_t launch_curn_adjoint(const DevModel& m, const Scratch& s, int B, const float* x, float* grad,
+cudaError_t launch_curn_adjoint(const DevModel& m, const Scratch& s, int B, const float* x, float* grad, int fp64,
                                 cudaStream_t st);
 // a64 = a_ref - v (v == nullptr: a_ref) for every chain; out -= w elementwise
 cudaError_t launch_curn_set_a(const DevModel& m, const Scratch& s, int B, const double* v, cudaStream_t st);
