@@ -226,8 +226,8 @@ __global__ void __launch_bounds__(kCT)
 
 // ---------------------------------------------------------------------------
 // The forward of k_curn_forward with the factorisation in double-word arithmetic on the
-// FP32 pipes (dw_ldl_sweep on A' scaled by 2^-E, E even, from its largest diagonal
-// entry), the inverse's scaling, both triangular products and the transform in double
+// FP32 pipes (dw_ldl_sweep1, one triangle, on A' scaled by 2^-E, E even, from its largest
+// diagonal entry), the inverse's scaling, both triangular products and the transform in double
 // words; outputs as k_curn_forward except Y', which the W slot holds as float pairs for
 // k_curn_adjoint_dw (log det L_CURN in FP64).  Used outside FP64 mode when the two
 // triangles fit in shared memory.
@@ -239,13 +239,13 @@ __global__ void __launch_bounds__(kCTdw)
                       const double* __restrict__ skd, const double* __restrict__ srho, double* a64, double* Wg,
                       double* ahat, double* ld, int32_t* stat, const double* __restrict__ g0, int B) {
   extern __shared__ float4 smq[];
-  __shared__ float2 pv[4];
+  __shared__ float2 pv[6];
   __shared__ int s_bad;
   __shared__ double red[kCTdw / 32];
   const int I = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, nt = blockDim.x, P = m.P;
   const int ntri = P * (P + 1) / 2, nh = P / 2 + 1;
-  float2* A = reinterpret_cast<float2*>(smq + 6 * nh);  // after the sweep's staging
-  float2* X = A + prow(P);
+  float2* A = reinterpret_cast<float2*>(smq + 6 * nh);  // after the sweep's staging: one padded packed triangle
+  float2* X = A;                                        // L'^-1 replaces L' in it
   const size_t o = (size_t)I * B + b;
   const double bt = m.beta ? m.beta[b] : 1.0;
   const double gsc = g0 ? 1.0 : bt;  // factor of Y'^T Y' g in the mean
@@ -280,14 +280,10 @@ __global__ void __launch_bounds__(kCTdw)
     if (i == j) v = dw_add(v, rdw[i]);
     const int q = prow(i) + j;
     A[q] = make_float2(v.x * sc, v.y * sc);
-    X[q] = make_float2(i == j ? 1.0f : 0.0f, 0.0f);
-    if (i == j && !(i & 1)) {
-      A[q + 1] = make_float2(0.0f, 0.0f);
-      X[q + 1] = make_float2(0.0f, 0.0f);
-    }
+    if (i == j && !(i & 1)) A[q + 1] = make_float2(0.0f, 0.0f);
   }
   __syncthreads();
-  dw_ldl_sweep(P, A, X, smq, pv, &s_bad, nullptr);
+  dw_ldl_sweep1(P, A, smq, pv, &s_bad, nullptr, nullptr, 1.0f);
   // 1 / sqrt(d_i) at the true scale, g and z in reversed order (the staging area is free)
   float2* rqw = reinterpret_cast<float2*>(smq);  // [P]
   float2* gpw = rqw + P;                          // [P] g'
@@ -641,7 +637,7 @@ size_t curn_w_doubles(const DevModel& m) { return (size_t)m.P * (m.P + 1) / 2; }
 
 // shared memory of k_curn_forward_dw, and whether the double-word CURN kernels run
 static size_t curn_fwd_smem_dw(const DevModel& m) {
-  return 6 * (size_t)(m.P / 2 + 1) * sizeof(float4) + 2 * (size_t)prow(m.P) * sizeof(float2);
+  return 6 * (size_t)(m.P / 2 + 1) * sizeof(float4) + (size_t)prow(m.P) * sizeof(float2);
 }
 static bool curn_dw(const DevModel& m, int fp64) { return !fp64 && !m.chol64 && curn_fwd_smem_dw(m) <= 227 * 1024; }
 

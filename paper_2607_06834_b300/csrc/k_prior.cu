@@ -199,21 +199,20 @@ __global__ void __launch_bounds__(512)
 // roots.  Outputs: a64 as k_chol_forward; L D^(1/2) and D^(-1/2) L^-1 packed lower (plain
 // packing) in the same slots as k_chol_forward's, as double-word float pairs (read by
 // k_chol_adjoint_dw and, under the CURN transform, by k_curn_whiten).
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, 4)  // 32 registers: 8 CTAs of 256 threads per SM at 67 pulsars
     k_chol_forward_dw(DevModel m, const float* __restrict__ x, const double* __restrict__ sk,
                       const double* __restrict__ srho, double* a64, float2* Lpk, float2* Lipk, int32_t* stat) {
   extern __shared__ float4 smq[];
-  const int np = m.npsr, ntri = np * (np + 1) / 2, nh = np / 2 + 1, nrow = prow(np);
-  float2* A = reinterpret_cast<float2*>(smq + 6 * nh);  // after the sweep's staging: padded packed lower L, D
-  float2* X = A + nrow;                             // padded packed lower: L^-1 (unit lower)
-  __shared__ float2 pv[4];                          // r0, r1, unscaled a10, l10 of the step
+  const int np = m.npsr, ntri = np * (np + 1) / 2, nh = np / 2 + 1;
+  float2* T = reinterpret_cast<float2*>(smq + 6 * nh);  // after the sweep's staging: one padded packed triangle
+  __shared__ float2 pv[6];                              // the step's pivot block (dw_pivot_pair1)
   __shared__ int s_bad;
   const int k = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, nt = blockDim.x;
   const float* xb = x + (size_t)b * m.d;
   const double sr = srho[(size_t)b * m.na + k];
   const double rho = sr * sr;
   const double* skb = sk + (size_t)b * np * m.na + k;
-  // scale 2^-E from the largest diagonal entry (every warp computes it; no barrier)
+  // scale 2^-E, E even, from the largest diagonal entry (every warp computes it; no barrier)
   double dmax = 0.0;
   for (int i = tid & 31; i < np; i += 32) {
     const double s = skb[(size_t)i * m.na];
@@ -222,6 +221,7 @@ __global__ void __launch_bounds__(512)
   for (int o = 16; o; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
   int E = 0;
   if (dmax > 0.0 && isfinite(dmax)) frexp(dmax, &E);
+  E += E & 1;
   const float2 rhow = d2dw_bits(ldexp(rho, -E));
   if (tid == 0) s_bad = 0;
   for (int idx = tid; idx < ntri; idx += nt) {
@@ -231,49 +231,38 @@ __global__ void __launch_bounds__(512)
     if (i == j) {
       const double s = skb[(size_t)i * m.na];
       v = dw_add(v, d2dw_bits(ldexp(s * s, -E)));
+      if (!(i & 1)) T[o + 1] = make_float2(0.0f, 0.0f);  // an even row's padding
     }
-    A[o] = v;
-    X[o] = make_float2((i == j) ? 1.0f : 0.0f, 0.0f);
-    if (i == j && !(i & 1)) {  // an even row's padding
-      A[o + 1] = make_float2(0.0f, 0.0f);
-      X[o + 1] = make_float2(0.0f, 0.0f);
-    }
-  }
-  __syncthreads();
-  dw_ldl_sweep(np, A, X, smq, pv, &s_bad, m.trimap);
-  if (s_bad && tid == 0) atomicOr(&stat[b], 2);
-  // pivots at their true scale: sqrt(d_j) and 1/sqrt(d_j) in FP64, kept as double
-  // words (the staging area is free now)
-  float2* ww = reinterpret_cast<float2*>(smq);  // [2][np] sqrt(d_J) z_J
-  float2* sqw = ww + 2 * np;                     // [np] sqrt(d_j)
-  float2* rqw = sqw + np;                        // [np] 1 / sqrt(d_j)
-  for (int j = tid; j < np; j += nt) {
-    const double d = ldexp(dw2d(A[prow(j) + j]), E);
-    const double y = rsqrt64(d);
-    sqw[j] = d2dw_bits(d * y);
-    rqw[j] = d2dw_bits(y);
-    const double zs0 = xb[m.z_ach + (2 * k) * np + j], zs1 = xb[m.z_ach + (2 * k + 1) * np + j];
-    ww[j] = d2dw_bits(d * y * zs0);
-    ww[np + j] = d2dw_bits(d * y * zs1);
+    T[o] = v;
   }
   __syncthreads();
   float2* Lg = Lpk + ((size_t)b * m.n_chol + k) * ntri;
   float2* Xg = Lipk + ((size_t)b * m.n_chol + k) * ntri;
+  const float usc = __int_as_float((127 + E / 2) << 23);  // 2^(E/2): sqrt of the true pivots
+  dw_ldl_sweep1(np, T, smq, pv, &s_bad, m.trimap, Lg, usc);
+  if (s_bad && tid == 0) atomicOr(&stat[b], 2);
+  // 1/sqrt(d_j) at true scale and z (the staging area is free now)
+  float2* rqw = reinterpret_cast<float2*>(smq);  // [np]
+  float* zs = reinterpret_cast<float*>(rqw + np);  // [2][np]
+  for (int j = tid; j < np; j += nt) {
+    const float2 sq = dw_sqrt(T[prow(j) + j]);
+    rqw[j] = dw_recip(make_float2(sq.x * usc, sq.y * usc));
+  }
+  for (int i = tid; i < 2 * np; i += nt) zs[i] = xb[m.z_ach + (2 * k) * np + i];
+  __syncthreads();
+  // D^(-1/2) L^-1 for the adjoint (L D^(1/2) went out during the sweep)
   for (int idx = tid; idx < ntri; idx += nt) {
     const unsigned t = m.trimap[idx];
-    const int i = t >> 8, j = t & 255, o = prow(i) + j;
-    Lg[idx] = (i == j) ? sqw[j] : dw_mul(A[o], sqw[j]);
-    Xg[idx] = (i == j) ? rqw[i] : dw_mul(X[o], rqw[i]);
+    const int i = t >> 8, j = t & 255;
+    Xg[idx] = (i == j) ? rqw[i] : dw_mul(T[prow(i) + j], rqw[i]);
   }
-  // a_{I,k,c} = sum_{J<=I} L[I][J] (sqrt(d_J) z_{J,k,c}), L unit lower
+  // a_{I,k,c} = sum_{J<=I} (L D^(1/2))[I][J] z_{J,k,c}, from the rows this block wrote
   for (int i = tid; i < 2 * np; i += nt) {
-    const int c = i / np, I = i % np, rb = prow(I);
-    const float2* wc = ww + c * np;
-    float2 acc = wc[I];
-    for (int J = 0; J < I; ++J) {
-      const float2 w = wc[J];
-      acc = dw_fms(acc, A[rb + J], make_float2(-w.x, -w.y));
-    }
+    const int c = i / np, I = i % np;
+    const float2* row = Lg + I * (I + 1) / 2;
+    const float* zc = zs + c * np;
+    float2 acc = make_float2(0.0f, 0.0f);
+    for (int J = 0; J <= I; ++J) acc = dw_fms(acc, row[J], make_float2(-zc[J], 0.0f));
     a64[((size_t)I * gridDim.y + b) * m.PM + 2 * k + c] = dw2d(acc);
   }
 }
@@ -819,7 +808,7 @@ static size_t adj_smem_dw(const DevModel& m) {
 }
 static size_t chol_smem_dw(const DevModel& m) {
   const size_t np = m.npsr, nh = np / 2 + 1;
-  return 6 * nh * sizeof(float4) + 2 * (size_t)prow((int)np) * sizeof(float2);
+  return 6 * nh * sizeof(float4) + (size_t)prow((int)np) * sizeof(float2);
 }
 static size_t adj_smem(const DevModel& m) {
   const size_t np = m.npsr, ntri = np * (np + 1) / 2;
