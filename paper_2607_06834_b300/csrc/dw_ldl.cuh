@@ -1,8 +1,8 @@
 // The double-word LDL^T sweep shared by the dense-bin factorisation (k_chol_forward_dw)
 // and the CURN-transform factorisation (k_curn_forward_dw): a symmetric positive
-// definite matrix A (scaled so its entries lie in (0, 1]) is overwritten by its unit lower
-// factor L (below the diagonal) and D (the diagonal) of A = L D L^T, and X (the identity on
-// entry) by L^-1, with every operation in double-word arithmetic on the FP32 pipes.
+// definite matrix A (scaled so its entries lie in (0, 1]) is overwritten by the pivots D of
+// A = L D L^T (L unit lower) on its diagonal and by L^-1 below it, with every operation in
+// double-word arithmetic on the FP32 pipes.
 //
 // Step for columns (j, j+1), whose 2x2 pivot block the previous step factored: pass A
 // scales column j, updates column j+1 by it and scales that, for every row below (and
@@ -23,34 +23,6 @@ namespace pta {
 // elements, padded to an even count), so that a pair of entries at an even column is
 // one 16-byte access: row i starts at i(i+2)/2 (i even) or (i+1)^2/2 (i odd).
 __host__ __device__ __forceinline__ int prow(int i) { return (i & 1) ? (i + 1) * (i + 1) / 2 : i * (i + 2) / 2; }
-
-// Factor a 2x2 pivot block (a00, a10, a11) of the sweep (or the single pivot a00 when
-// two is false): the LDL^T entries d0, l10, d1 go to A, and r0 = 1/d0, r1 = 1/d1, the
-// unscaled a10 and l10 to pv for the step that uses them.  A pivot that is not positive
-// marks the factorisation bad and continues with 1.
-__device__ __forceinline__ void dw_pivot_pair(float2 a00, float2 a10, float2 a11, bool two, float2* A, int j,
-                                              float2* pv, int* s_bad) {
-  const int rj = prow(j), rj1 = prow(j + 1);
-  int bad = !(a00.x > 0.0f);
-  if (bad) a00 = make_float2(1.0f, 0.0f);
-  const float2 r0 = dw_recip(a00);
-  A[rj + j] = a00;
-  if (two) {
-    const float2 l10 = dw_mul(a10, r0);
-    float2 d1 = dw_fms(a11, l10, a10);
-    if (!(d1.x > 0.0f)) {
-      bad = 1;
-      d1 = make_float2(1.0f, 0.0f);
-    }
-    A[rj1 + j] = l10;
-    A[rj1 + j + 1] = d1;
-    pv[0] = r0;
-    pv[1] = dw_recip(d1);
-    pv[2] = a10;
-    pv[3] = l10;
-  }
-  if (bad) *s_bad = 1;
-}
 
 // v - (p.xy q.xy + p.zw q.zw): one element's rank-2 update from the row's (l_ij, l_i,j+1)
 // and the column's two unscaled entries (or L^-1's rows j and j+1).  Both products are
@@ -86,115 +58,13 @@ __device__ __forceinline__ void tri_decode_f(int e, int& i, int& j) {
   j = e - r * (r + 1) / 2;
 }
 
-// The sweep on an order-np matrix.  A and X: padded packed lower triangles (rows at
-// prow(i)) in shared memory, 16-byte aligned, X the identity (and every even row's
-// padding zero) on entry; stage: 6 (np/2 + 1) float4 of shared memory; pv: 4 float2 of
-// shared memory; s_bad: shared flag set when a pivot is not positive (the sweep goes on
-// with 1).  trimap: packed-lower index -> (row << 8) | column for the ((np-1)/2 + 1)
-// ((np-1)/2 + 2) / 2 tiles of the largest trailing triangle, or nullptr to decode by a
-// square root.  Called by every thread of the block after a barrier that follows the
-// fill of A and X; returns after a barrier.
-__device__ __forceinline__ void dw_ldl_sweep(int np, float2* A, float2* X, float4* stage, float2* pv, int* s_bad,
-                                          const unsigned short* trimap) {
-  const int tid = threadIdx.x, nt = blockDim.x, nh = np / 2 + 1;
-  float4* plE = stage;     // [nh] (l_ij, l_i,j+1) of rows j+2+e, e even (index e/2)
-  float4* plO = plE + nh;  // e odd
-  float4* uuE = plO + nh;  // [nh] unscaled (u_j, u_j+1) of columns j+2+f, f even
-  float4* uuO = uuE + nh;  // f odd
-  float4* xrE = uuO + nh;  // [nh] (X_jc, X_j+1,c), c even
-  float4* xrO = xrE + nh;  // c odd
-  if (tid == 0) dw_pivot_pair(A[0], np > 1 ? A[2] : A[0], np > 1 ? A[3] : A[0], np > 1, A, 0, pv, s_bad);
-  __syncthreads();
-  for (int j = 0; j + 1 < np; j += 2) {
-    const float2 r0 = pv[0], r1 = pv[1], a10 = pv[2], l10 = pv[3];
-    const int rj = prow(j), rj1 = prow(j + 1), s2 = np - j - 2;
-    // pass A
-    for (int e = tid; e < s2 + j + 2; e += nt) {
-      if (e < s2) {
-        const int i = j + 2 + e;
-        float4* ap = reinterpret_cast<float4*>(A + prow(i) + j);
-        const float4 a = *ap;
-        const float2 a0 = make_float2(a.x, a.y);
-        const float2 l0 = dw_mul(a0, r0);
-        const float2 w = dw_fms(make_float2(a.z, a.w), l0, a10);
-        const float2 l1 = dw_mul(w, r1);
-        const float4 pl = make_float4(l0.x, l0.y, l1.x, l1.y);
-        *ap = pl;
-        (e & 1 ? plO : plE)[e >> 1] = pl;
-        (e & 1 ? uuO : uuE)[e >> 1] = make_float4(a0.x, a0.y, w.x, w.y);
-      } else {
-        const int c = e - s2;  // 0 .. j+1
-        float2 xj = make_float2(0.0f, 0.0f), x1 = make_float2(1.0f, 0.0f);
-        if (c <= j) {
-          xj = X[rj + c];
-          x1 = dw_fms(X[rj1 + c], l10, xj);
-          X[rj1 + c] = x1;
-        }
-        (c & 1 ? xrO : xrE)[c >> 1] = make_float4(xj.x, xj.y, x1.x, x1.y);
-      }
-    }
-    if (tid == 0 && (s2 & 1)) plO[s2 >> 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // the odd row's partner
-    __syncthreads();
-    // pass B: 2x2 tiles; T row pairs (the last one short when s2 is odd), W = (j+2)/2
-    // column pairs of L^-1
-    // (tile rows i0 are even: row i0 starts at i0(i0+2)/2 and row i0+1 at (i0+2)^2/2)
-    const int T = (s2 + 1) >> 1, cntT = T * (T + 1) / 2, W = (j + 2) >> 1, cnt = cntT + T * W;
-    const float rw = __fdividef(1.0f, (float)W);  // the quotient below is corrected by +-1
-    for (int t = tid; t < cnt; t += nt) {
-      if (t < cntT) {
-        int I, L;
-        if (trimap) {
-          const unsigned tm = trimap[t];
-          I = tm >> 8;
-          L = tm & 255;
-        } else {
-          tri_decode_f(t, I, L);
-        }
-        const int i0 = j + 2 + 2 * I, c0 = j + 2 + 2 * L;
-        const float4 p0 = plE[I], p1 = plO[I], q0 = uuE[L], q1 = uuO[L];
-        float4* r0p = reinterpret_cast<float4*>(A + i0 * (i0 + 2) / 2 + c0);
-        float4 v0 = *r0p;
-        dw_upd2x2(v0, p0, q0, q1);  // on a diagonal tile the second entry is the padding
-        *r0p = v0;
-        const bool row1 = 2 * I + 1 < s2;
-        float4 v1 = v0;
-        if (row1) {
-          float4* r1p = reinterpret_cast<float4*>(A + (i0 + 2) * (i0 + 2) / 2 + c0);
-          v1 = *r1p;
-          dw_upd2x2(v1, p1, q0, q1);
-          *r1p = v1;
-        }
-        if (t == 0)
-          dw_pivot_pair(make_float2(v0.x, v0.y), make_float2(v1.x, v1.y), make_float2(v1.z, v1.w), row1, A, j + 2,
-                        pv, s_bad);
-      } else {
-        const int e = t - cntT;
-        int q = (int)(((float)e + 0.5f) * rw);
-        q -= (q * W > e);
-        q += ((q + 1) * W <= e);
-        const int cc = e - q * W, i0 = j + 2 + 2 * q, c0 = 2 * cc;
-        const float4 p0 = plE[q], p1 = plO[q], q0 = xrE[cc], q1 = xrO[cc];
-        float4* r0p = reinterpret_cast<float4*>(X + i0 * (i0 + 2) / 2 + c0);
-        float4 v0 = *r0p;
-        dw_upd2x2(v0, p0, q0, q1);
-        *r0p = v0;
-        if (2 * q + 1 < s2) {
-          float4* r1p = reinterpret_cast<float4*>(X + (i0 + 2) * (i0 + 2) / 2 + c0);
-          float4 v1 = *r1p;
-          dw_upd2x2(v1, p1, q0, q1);
-          *r1p = v1;
-        }
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// Pivot block of the single-triangle sweep: as dw_pivot_pair, but the triangle keeps only
-// the pivots (its (j+1, j) entry becomes L^-1's in the next pass A), pv also carries the
-// pivots' square roots at true scale (sqrt(d) usc), and with Lg the step's entries of
-// L D^(1/2) on and next to the diagonal are emitted.
-__device__ __forceinline__ void dw_pivot_pair1(float2 a00, float2 a10, float2 a11, bool two, float2* T, int j,
+// Factor a 2x2 pivot block (a00, a10, a11) of the sweep (or the single pivot a00 when two
+// is false): the pivots d0, d1 go to the triangle's diagonal (its (j+1, j) entry becomes
+// L^-1's in the next pass A), and r0 = 1/d0, r1 = 1/d1, the unscaled a10, l10 and the
+// pivots' square roots at true scale (sqrt(d) usc) to pv for the step that uses them;
+// with Lg the step's entries of L D^(1/2) on and next to the diagonal are emitted.  A
+// pivot that is not positive marks the factorisation bad and continues with 1.
+__device__ __forceinline__ void dw_pivot_pair(float2 a00, float2 a10, float2 a11, bool two, float2* T, int j,
                                                float2* pv, int* s_bad, float2* Lg, float usc) {
   int bad = !(a00.x > 0.0f);
   if (bad) a00 = make_float2(1.0f, 0.0f);
@@ -228,7 +98,7 @@ __device__ __forceinline__ void dw_pivot_pair1(float2 a00, float2 a10, float2 a1
   if (bad) *s_bad = 1;
 }
 
-// The single-triangle form of the sweep: T holds A on entry (padded packed lower, rows at
+// The sweep on an order-np matrix: T holds A on entry (padded packed lower, rows at
 // prow(i), every even row's padding zero) and on exit D on the diagonal and L^-1 (unit
 // lower, its diagonal implied) below it.  Column j of L is consumed by its step: pass A
 // stages the pair (l_ij, l_i,j+1) and leaves zeros in its place, which pass B's
@@ -236,9 +106,12 @@ __device__ __forceinline__ void dw_pivot_pair1(float2 a00, float2 a10, float2 a1
 // l_i,j+1 X_j+1,c for c <= j+1, with X_jj = X_j+1,j+1 = 1 and X_j,j+1 = 0).  With Lg the
 // entries of L D^(1/2) (double words, plain packing, true scale: sqrt(d) usc, usc =
 // 2^(E/2) for A scaled by 2^-E) are written to global memory as the steps produce them.
-// Half the shared memory of dw_ldl_sweep, the same arithmetic.  stage: 6 (np/2 + 1) float4;
-// pv: 6 float2 of shared memory; s_bad, trimap and the barriers as for dw_ldl_sweep.
-__device__ __forceinline__ void dw_ldl_sweep1(int np, float2* T, float4* stage, float2* pv, int* s_bad,
+// stage: 6 (np/2 + 1) float4 of shared memory; pv: 6 float2 of shared memory; s_bad: shared
+// flag set when a pivot is not positive (the sweep goes on with 1).  trimap:
+// packed-lower index -> (row << 8) | column for the ((np-1)/2 + 1) ((np-1)/2 + 2) / 2 tiles
+// of the largest trailing triangle, or nullptr to decode by a square root.  Called by every
+// thread of the block after a barrier that follows the fill of T; returns after a barrier.
+__device__ __forceinline__ void dw_ldl_sweep(int np, float2* T, float4* stage, float2* pv, int* s_bad,
                                            const unsigned short* trimap, float2* Lg, float usc) {
   const int tid = threadIdx.x, nt = blockDim.x, nh = np / 2 + 1;
   float4* plE = stage;     // [nh] (l_ij, l_i,j+1) of rows j+2+e, e even (index e/2)
@@ -247,7 +120,7 @@ __device__ __forceinline__ void dw_ldl_sweep1(int np, float2* T, float4* stage, 
   float4* uuO = uuE + nh;  // f odd
   float4* xrE = uuO + nh;  // [nh] (X_jc, X_j+1,c), c even
   float4* xrO = xrE + nh;  // c odd
-  if (tid == 0) dw_pivot_pair1(T[0], np > 1 ? T[2] : T[0], np > 1 ? T[3] : T[0], np > 1, T, 0, pv, s_bad, Lg, usc);
+  if (tid == 0) dw_pivot_pair(T[0], np > 1 ? T[2] : T[0], np > 1 ? T[3] : T[0], np > 1, T, 0, pv, s_bad, Lg, usc);
   __syncthreads();
   for (int j = 0; j + 1 < np; j += 2) {
     const float2 r0 = pv[0], r1 = pv[1], a10 = pv[2], l10 = pv[3], sq0 = pv[4], sq1 = pv[5];
@@ -318,7 +191,7 @@ __device__ __forceinline__ void dw_ldl_sweep1(int np, float2* T, float4* stage, 
           *r1p = v1;
         }
         if (t == 0)
-          dw_pivot_pair1(make_float2(v0.x, v0.y), make_float2(v1.x, v1.y), make_float2(v1.z, v1.w), row1, T, j + 2,
+          dw_pivot_pair(make_float2(v0.x, v0.y), make_float2(v1.x, v1.y), make_float2(v1.z, v1.w), row1, T, j + 2,
                          pv, s_bad, Lg, usc);
       } else {
         const int e = t - cntT;

@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(kCT)
 
 // ---------------------------------------------------------------------------
 // The forward of k_curn_forward with the factorisation in double-word arithmetic on the
-// FP32 pipes (dw_ldl_sweep1, one triangle, on A' scaled by 2^-E, E even, from its largest
+// FP32 pipes (dw_ldl_sweep, one triangle, on A' scaled by 2^-E, E even, from its largest
 // diagonal entry), the inverse's scaling, both triangular products and the transform in double
 // words; outputs as k_curn_forward except Y', which the W slot holds as float pairs for
 // k_curn_adjoint_dw (log det L_CURN in FP64).  Used outside FP64 mode when the two
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(kCTdw)
     if (i == j && !(i & 1)) A[q + 1] = make_float2(0.0f, 0.0f);
   }
   __syncthreads();
-  dw_ldl_sweep1(P, A, smq, pv, &s_bad, nullptr, nullptr, 1.0f);
+  dw_ldl_sweep(P, A, smq, pv, &s_bad, nullptr, nullptr, 1.0f);
   // 1 / sqrt(d_i) at the true scale, g and z in reversed order (the staging area is free)
   float2* rqw = reinterpret_cast<float2*>(smq);  // [P]
   float2* gpw = rqw + P;                          // [P] g'

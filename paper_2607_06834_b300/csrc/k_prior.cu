@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(512, 4)  // 32 registers: 8 CTAs of 256 thread
   extern __shared__ float4 smq[];
   const int np = m.npsr, ntri = np * (np + 1) / 2, nh = np / 2 + 1;
   float2* T = reinterpret_cast<float2*>(smq + 6 * nh);  // after the sweep's staging: one padded packed triangle
-  __shared__ float2 pv[6];                              // the step's pivot block (dw_pivot_pair1)
+  __shared__ float2 pv[6];                              // the step's pivot block (dw_pivot_pair)
   __shared__ int s_bad;
   const int k = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, nt = blockDim.x;
   const float* xb = x + (size_t)b * m.d;
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(512, 4)  // 32 registers: 8 CTAs of 256 thread
   float2* Lg = Lpk + ((size_t)b * m.n_chol + k) * ntri;
   float2* Xg = Lipk + ((size_t)b * m.n_chol + k) * ntri;
   const float usc = __int_as_float((127 + E / 2) << 23);  // 2^(E/2): sqrt of the true pivots
-  dw_ldl_sweep1(np, T, smq, pv, &s_bad, m.trimap, Lg, usc);
+  dw_ldl_sweep(np, T, smq, pv, &s_bad, m.trimap, Lg, usc);
   if (s_bad && tid == 0) atomicOr(&stat[b], 2);
   // 1/sqrt(d_j) at true scale and z (the staging area is free now)
   float2* rqw = reinterpret_cast<float2*>(smq);  // [np]
