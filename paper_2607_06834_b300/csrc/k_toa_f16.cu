@@ -328,6 +328,8 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+constexpr int PACK_THREADS = 512;  // 16 warps per (pulsar, chain block): the loads' latency needs the warps
+
 // ---------------------------------------------------------------------------
 // Pack: per (pulsar, block of NC chains) the chain exponents and the four fp16 pieces
 // of the scaled coefficients as one K-major B operand of 4 NC rows, the pieces stacked
@@ -356,7 +358,7 @@ __device__ __forceinline__ void split4_ff(float hi, float lo, float& v0, float& 
 }
 
 template <int NC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(PACK_THREADS)
     k_f16_pack(DevModel m, const double* __restrict__ a64, unsigned char* __restrict__ c16, int* __restrict__ yexp,
                int B, int nCB) {
   extern __shared__ int ce[];  // [KX] column exponents c_q
@@ -366,13 +368,13 @@ __global__ void __launch_bounds__(256)
   const int ncol = P + (m.cw ? m.m[I] : 0);  // columns with coefficients; the rest of the block is 0
   const double* rows = a64 + ((size_t)I * B + b0) * PM;
   const double* ar = m.aref + (size_t)I * P;
-  for (int q = tid; q < KX; q += 256) ce[q] = m.x16_cexp[(size_t)I * KXM + q];
+  for (int q = tid; q < KX; q += PACK_THREADS) ce[q] = m.x16_cexp[(size_t)I * KXM + q];
   __syncthreads();
   auto coef = [&](int n, int q) -> double { return q < P ? rows[(size_t)n * PM + q] - ar[q] : rows[(size_t)n * PM + q]; };
   // per-chain exponent of max_q |C_nq 2^c_q| (one warp per chain).  |C| is truncated to a
   // float, and frexpf's exponent of a truncated value still bounds the exact one
   // strictly, which keeps |v| < 2^14.
-  for (int n = warp; n < NC; n += 8) {
+  for (int n = warp; n < NC; n += PACK_THREADS / 32) {
     float mx = 0.f;
     if (n < nvalid)
       for (int q = lane; q < ncol; q += 32) mx = fmaxf(mx, fabsf(d2f_trunc(coef(n, q))) * pow2f(ce[q]));
@@ -385,7 +387,7 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   unsigned char* out = c16 + ((size_t)I * nCB + cb) * 4 * (size_t)KXM * NC * 2;
   constexpr int PS = NC * 16;  // bytes between the pieces' row blocks within one K group
-  for (int e = tid; e < NC * (KX / 8); e += 256) {
+  for (int e = tid; e < NC * (KX / 8); e += PACK_THREADS) {
     const int n = e % NC, g = e / NC;  // consecutive threads: consecutive chains
     float c0[8], c1[8], c2[8], c3[8];
 #pragma unroll
@@ -883,7 +885,7 @@ int res_nc(const DevModel& m) { return res_smem<64>(m) <= 227 * 1024 ? 64 : 32; 
 template <int NC>
 cudaError_t launch_f16_nc(const DevModel& m, const Scratch& s, int B, cudaStream_t st, cudaEvent_t* kev) {
   const int nCB = (B + NC - 1) / NC;
-  k_f16_pack<NC><<<dim3(m.npsr, nCB), 256, sizeof(int) * m.x16_kxm, st>>>(m, s.a64, s.c16, s.yexp, B, nCB);
+  k_f16_pack<NC><<<dim3(m.npsr, nCB), PACK_THREADS, sizeof(int) * m.x16_kxm, st>>>(m, s.a64, s.c16, s.yexp, B, nCB);
   const size_t sm = res_smem<NC>(m);
   if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(k_f16_res<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
