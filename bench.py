@@ -58,17 +58,21 @@ DW_PEAK_TFLOPS = 148 * 128 * 2.032e9 * 2 / DW_OPS_PER_FMA / 1e12
 # kernel from one ncu capture, valid only while the kernel's sources are the ones
 # profiled (sha256 of each file); see profiles/.
 CAPTURED_TRAFFIC = {
-    "k_chol_forward": {"bytes": (5.985536 + 75.970048) * 1e6, "profile": "profiles/k_chol_forward_ng15_b256.md",
-                       "sources": {"k_prior.cu": "dc6cf94d697670755938f93f71f99e51007b84f40523c4983cc20aef77a523ef",
-                                   "pta_internal.cuh":
-                                       "480dbc16e238cb2d8579922f556768df0c7da414ff712d4178b8619814498440"}},
-    "k_f16_res": {"bytes": (743.007488 + 290.465792) * 1e6, "profile": "profiles/k_f16_res_ng15_b256.md",
-                  "sources": {"k_toa_f16.cu": "cac1501f91c7b671dfa2498db5aa29c72c41168bdb3f4fdd277770b91af448da",
-                              "pta_internal.cuh": "480dbc16e238cb2d8579922f556768df0c7da414ff712d4178b8619814498440",
+    "k_chol_forward_dw": {"bytes": (7.379968 + 79.005184) * 1e6, "profile": "profiles/k_chol_forward_dw_ng15_b256.md",
+                          "sources": {"k_prior.cu": "368cfd5966d71bd1828e3579dd6a9e7669dfd31b98c66f26c5ea4b80f08c7727",
+                                      "dw_ldl.cuh": "155831b5eef5337ca1824aaf19e7d3675c28ed743237428e1118db0b9da9d752",
+                                      "dwarith.cuh": "4be7088a6f8969d71310f97b2e84b104c9c30123487c4c14cc9f21107ec192ea",
+                                      "pta_internal.cuh":
+                                          "8337b7312037cce44ff7ff89544a4f04a46a83b602f19d37180c0e446bd3507c"}},
+    "k_f16_res": {"bytes": (742.985216 + 288.452096) * 1e6, "profile": "profiles/k_f16_res_ng15_b256.md",
+                  "sources": {"k_toa_f16.cu": "008e254fef26fd727a0cea74fdfd2114bc9073072fcbd7727849f4bdb7b11bd3",
+                              "dwarith.cuh": "4be7088a6f8969d71310f97b2e84b104c9c30123487c4c14cc9f21107ec192ea",
+                              "pta_internal.cuh": "8337b7312037cce44ff7ff89544a4f04a46a83b602f19d37180c0e446bd3507c",
                               "tc_ptx.cuh": "3c9784327356c5b1fdfbf233ac793b19bb50883f641ee44cceddaaed2465521c"}},
-    "k_f16_ftw": {"bytes": (835.959552 + 42.731520) * 1e6, "profile": "profiles/k_f16_ftw_ng15_b256.md",
-                  "sources": {"k_toa_f16.cu": "cac1501f91c7b671dfa2498db5aa29c72c41168bdb3f4fdd277770b91af448da",
-                              "pta_internal.cuh": "480dbc16e238cb2d8579922f556768df0c7da414ff712d4178b8619814498440",
+    "k_f16_ftw": {"bytes": (835.949824 + 41.853184) * 1e6, "profile": "profiles/k_f16_ftw_ng15_b256.md",
+                  "sources": {"k_toa_f16.cu": "008e254fef26fd727a0cea74fdfd2114bc9073072fcbd7727849f4bdb7b11bd3",
+                              "dwarith.cuh": "4be7088a6f8969d71310f97b2e84b104c9c30123487c4c14cc9f21107ec192ea",
+                              "pta_internal.cuh": "8337b7312037cce44ff7ff89544a4f04a46a83b602f19d37180c0e446bd3507c",
                               "tc_ptx.cuh": "3c9784327356c5b1fdfbf233ac793b19bb50883f641ee44cceddaaed2465521c"}},
 }
 
