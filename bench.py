@@ -343,6 +343,9 @@ def scale150_leg(dev, steps: int, peaks):
 
     n = max(3, min(steps, 5))
     rec["f16split"] = timed("f16split", n)
+    eng.set_cholesky("fp64")  # the same path with the FP64 dense-bin Cholesky (150 x 150)
+    rec["f16split_chol_fp64"] = timed("f16split", n)
+    eng.set_cholesky("dw")
     rec["fp32"] = timed("fp32", n)
     rec["fp64_plain_path"] = timed("fp64", 1)
     rec["f16split_vs_fp64_plain_path"] = rec["f16split"]["value"] / rec["fp64_plain_path"]["value"]
