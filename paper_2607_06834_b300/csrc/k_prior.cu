@@ -46,8 +46,26 @@ __device__ __forceinline__ double half_free(float theta) {  // 10^((theta + 18) 
   return dw_exp_d(dw_mul(kHalfLn10, dw_addf(make_float2(theta, 0.0f), 18.0f)));
 }
 
+// a = sqrt(kappa) z for a diagonal bin's two coefficients (Eq. standardizing_transform
+// with a diagonal Phi_k): an FP64 product, or in double words with one FP64 add each
 template <bool DW>
-__global__ void k_spectra(DevModel m, const float* __restrict__ x, double* sk, double* skd, double* srho) {
+__device__ __forceinline__ void diag_a(double s, float z0, float z1, double* a) {
+  if (DW) {
+    const float2 sw = d2dw_bits(s);
+    *reinterpret_cast<double2*>(a) = make_double2(dw2d(dw_mulf(sw, z0)), dw2d(dw_mulf(sw, z1)));
+  } else {
+    a[0] = s * z0;
+    a[1] = s * z1;
+  }
+}
+
+// With the transform applied here to the diagonal bins (red-noise-only achromatic bins and
+// every DM bin), the value is used where it is made; the dense and GWB-only bins take
+// theirs in k_chol_forward(_dw) and k_gwbonly_forward.  a64 is nullptr under the CURN
+// transform (a comes from k_curn_forward).
+template <bool DW>
+__global__ void k_spectra(DevModel m, const float* __restrict__ x, double* sk, double* skd, double* srho,
+                          double* a64, int B) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
   const int np = m.npsr, nach = np * m.na, ndm = np * m.nd;
   if (r >= nach + ndm + m.na) return;
@@ -59,10 +77,17 @@ __global__ void k_spectra(DevModel m, const float* __restrict__ x, double* sk, d
       v = m.rn_free ? half_free<DW>(xb[m.th_rn + m.n_rn * I + k])
                     : half_pl<DW>(m, xb[m.th_rn + 2 * I], xb[m.th_rn + 2 * I + 1], k + 1);
     sk[(size_t)b * nach + r] = v;
+    if (a64 && k >= m.n_chol + m.n_gwbonly && k < m.n_rn)
+      diag_a<DW>(v, xb[m.z_ach + (2 * k) * np + I], xb[m.z_ach + (2 * k + 1) * np + I],
+                 a64 + ((size_t)I * B + b) * m.PM + 2 * k);
   } else if (r < nach + ndm) {
     const int q = r - nach, I = q / m.nd, k = q % m.nd;
     v = half_pl<DW>(m, xb[m.th_dm + 2 * I], xb[m.th_dm + 2 * I + 1], k + 1);
     skd[(size_t)b * ndm + q] = v;
+    if (a64) {
+      const int zo = m.z_dm + (I * m.nd + k) * 2;
+      diag_a<DW>(v, xb[zo], xb[zo + 1], a64 + ((size_t)I * B + b) * m.PM + 2 * m.na + 2 * k);
+    }
   } else {
     const int k = r - nach - ndm;
     if (k < m.n_gwb)
@@ -490,39 +515,10 @@ __device__ __forceinline__ void diag_index(const DevModel& m, int r, int& I, int
   k = dm ? q - nrn_only : m.n_chol + m.n_gwbonly + q;
 }
 
-// DW: double-word products (outside FP64 mode), whose only FP64 operation is the
-// final add of each double output; the float gradient needs none.  A DM bin's two
-// coefficients, z's and gradient entries are adjacent: one paired access each.
-template <bool DW>
-__global__ void k_diag_forward(DevModel m, const float* __restrict__ x, const double* __restrict__ sk,
-                               const double* __restrict__ skd, double* a64, int B, int per_chain) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
-  if (r >= per_chain) return;
-  int I, k;
-  bool dm;
-  diag_index(m, r, I, k, dm);
-  const float* xb = x + (size_t)b * m.d;
-  const double s = dm ? skd[((size_t)b * m.npsr + I) * m.nd + k] : sk[((size_t)b * m.npsr + I) * m.na + k];
-  const int zo = dm ? m.z_dm + (I * m.nd + k) * 2 : m.z_ach + (2 * k) * m.npsr + I;
-  float z0, z1;
-  if (dm && !(reinterpret_cast<uintptr_t>(xb + zo) & 7)) {
-    const float2 zz = *reinterpret_cast<const float2*>(xb + zo);
-    z0 = zz.x;
-    z1 = zz.y;
-  } else {
-    z0 = xb[zo];
-    z1 = xb[dm ? zo + 1 : zo + m.npsr];
-  }
-  const size_t o = ((size_t)I * B + b) * m.PM + (dm ? 2 * m.na : 0) + 2 * k;
-  if (DW) {
-    const float2 sw = d2dw_bits(s);
-    *reinterpret_cast<double2*>(a64 + o) = make_double2(dw2d(dw_mulf(sw, z0)), dw2d(dw_mulf(sw, z1)));
-  } else {
-    a64[o] = s * z0;
-    a64[o + 1] = s * z1;
-  }
-}
-
+// Adjoint of the diagonal bins' transform (their forward is in k_spectra).  DW:
+// double-word products (outside FP64 mode), whose only FP64 operation is the final add
+// of each double output; the float gradient needs none.  A DM bin's two coefficients,
+// z's and gradient entries are adjacent: one paired access each.
 template <bool DW>
 __global__ void k_diag_adjoint(DevModel m, const float* __restrict__ x, const double* __restrict__ ghat,
                                const double* __restrict__ sk, const double* __restrict__ skd, float* grad,
@@ -819,17 +815,21 @@ bool chol_uses_dw(const DevModel& m, int fp64) { return chol_dw(m, fp64); }
 
 int count_prior_forward(const DevModel& m) {
   if (m.curn) return 1 + (m.n_chol > 0) + 2;  // spectra, Phi_k factors, CURN transform, HD prior
-  return 1 + (m.n_chol > 0) + (m.n_gwbonly > 0) + (m.npsr * ((m.na - m.n_chol - m.n_gwbonly) + m.nd) > 0);
+  return 1 + (m.n_chol > 0) + (m.n_gwbonly > 0);  // the diagonal bins' a comes with the spectra
 }
-int count_prior_adjoint(const DevModel& m) { return m.curn ? 1 : count_prior_forward(m) - 1; }
+int count_prior_adjoint(const DevModel& m) {
+  if (m.curn) return 1;
+  return (m.n_chol > 0) + (m.n_gwbonly > 0) + (m.npsr * ((m.na - m.n_chol - m.n_gwbonly) + m.nd) > 0);
+}
 
 cudaError_t launch_prior_forward(const DevModel& m, const Scratch& s, int B, const float* x, int fp64,
                                  cudaStream_t st, cudaEvent_t* kev) {
   const int nspec = m.npsr * (m.na + m.nd) + m.na;
+  double* ad = m.curn ? nullptr : s.a64;  // the diagonal bins' a, written with their spectra
   if (fp64)
-    k_spectra<false><<<dim3((nspec + 127) / 128, B), 128, 0, st>>>(m, x, s.sk, s.skd, s.srho);
+    k_spectra<false><<<dim3((nspec + 127) / 128, B), 128, 0, st>>>(m, x, s.sk, s.skd, s.srho, ad, B);
   else
-    k_spectra<true><<<dim3((nspec + 127) / 128, B), 128, 0, st>>>(m, x, s.sk, s.skd, s.srho);
+    k_spectra<true><<<dim3((nspec + 127) / 128, B), 128, 0, st>>>(m, x, s.sk, s.skd, s.srho, ad, B);
   if (m.n_chol > 0) {
     const bool dw = chol_dw(m, fp64);
     const size_t sm = dw ? chol_smem_dw(m) : chol_smem(m);
@@ -847,13 +847,6 @@ cudaError_t launch_prior_forward(const DevModel& m, const Scratch& s, int B, con
   }
   if (m.curn) return cudaGetLastError();  // a comes from the CURN transform (launch_curn_forward)
   if (m.n_gwbonly > 0) k_gwbonly_forward<<<dim3(m.n_gwbonly, B), 128, 0, st>>>(m, x, s.srho, s.a64);
-  const int per = m.npsr * ((m.na - m.n_chol - m.n_gwbonly) + m.nd);
-  if (per > 0) {
-    if (fp64)
-      k_diag_forward<false><<<dim3((per + 127) / 128, B), 128, 0, st>>>(m, x, s.sk, s.skd, s.a64, B, per);
-    else
-      k_diag_forward<true><<<dim3((per + 127) / 128, B), 128, 0, st>>>(m, x, s.sk, s.skd, s.a64, B, per);
-  }
   return cudaGetLastError();
 }
 
