@@ -604,3 +604,34 @@ def test_cholesky_fp64_switch(prec):
         else:
             assert np.max(np.abs(lp[:8] - lo[:8])) < LOGP_ABS
             assert np.max(_grad_rel(g[:12], go)) < GRAD_REL
+
+
+@pytest.mark.parametrize("prec", ["gram", "fp64"])
+def test_prior_box_corners(prec):
+    """Hyper-parameters at the corners of the prior box (log10 A at -19.9 and -10.1, gamma at
+    0.1 and 6.9, for the GWB and every pulsar's red noise and DM), where the spectra span
+    ~30 decades and Phi_k is as ill-conditioned as the prior allows: the Gram form (double-word
+    spectra, Cholesky and adjoint) and FP64 mode against the oracle at FP64 tolerances."""
+    kw = dict(npsr=5, ntoa=[300, 500, 800, 400, 650], m=[3, 5, 8, 4, 6], n_gwb=6, n_rn=8, n_dm=5, seed=37,
+              nbackend=2)
+    arr = synth.small_array(**kw)
+    orc = O.Oracle(arr)
+    eng = _engine(arr, prec)
+    lay = eng.layout
+    rng = np.random.default_rng(38)
+    X = synth.make_points(arr, 16, seed=10)
+    for i in range(16):
+        pairs = [lay["th_gwb"]] + [lay["th_rn"] + 2 * I for I in range(arr.npsr)] + \
+                [lay["th_dm"] + 2 * I for I in range(arr.npsr)]
+        for t in pairs:
+            X[i, t] = rng.choice([-19.9, -10.1])
+            X[i, t + 1] = rng.choice([0.1, 6.9])
+    lo, go = _oracle(orc, X)
+    lp, g, st = _eval(eng, X)
+    assert np.all(st == 0)
+    rel = np.abs(lp - lo) / np.maximum(1.0, np.abs(lo))
+    grel = _grad_rel(g, go)
+    print(f"{prec} prior-box corners: max rel dlogp {rel.max():.2e}, max grad rel {grel.max():.2e}, "
+          f"|logp| {np.abs(lo).min():.1e} .. {np.abs(lo).max():.1e}")
+    assert rel.max() < FP64_REL
+    assert grel.max() < 1e-6
