@@ -132,12 +132,13 @@ static __constant__ float2 kExp2Sixteenth[16] = {
     {0x1.ae89fap+0f, -0x1.a94b14p-26f},    {0x1.c199bep+0f, -0x1.3d56b2p-27f}, {0x1.d5818ep+0f, -0x1.822dbcp-27f},
     {0x1.ea4afap+0f, 0x1.52486cp-27f}};
 
-// exp(a) for a double word a, |a| < 700, as a double word and a power of two:
+// exp(a) for a double word a, |a| < 170, as a double word and a power of two:
 // exp(a) = 2^m (h + l).  Cody-Waite reduction a = n ln2/16 + r with ln2/16 split into
 // C1 + C2 + C3 (12, 12 and 24 significant bits, so n C1 and n C2 are exact for |n| <
-// 2^12 and a.h - n C1 is exact by Sterbenz's lemma), |r| <= ~ln2/32; exp(r) - 1 by its
-// Taylor series to r^6 (truncation < 2^-50), the three highest terms in FP32; then the
-// table entry 2^(j/16), j = n mod 16, m = floor(n / 16).  Relative error < 2^-45.
+// 2^12, that is |a| < 177, and a.h - n C1 is exact by Sterbenz's lemma), |r| <= ~ln2/32;
+// exp(r) - 1 by its Taylor series to r^6 (truncation < 2^-50), the three highest terms in
+// FP32; then the table entry 2^(j/16), j = n mod 16, m = floor(n / 16).  Relative error
+// < 2^-45.
 // The constants are the float pairs nearest ln2/16, 16/ln2, 2^(j/16), 1/6, 1/24,
 // 1/120 and 1/720.
 __device__ __forceinline__ float2 dw_exp(float2 a, int& m) {
@@ -157,8 +158,10 @@ __device__ __forceinline__ float2 dw_exp(float2 a, int& m) {
   const float2 T = kExp2Sixteenth[j];
   return dw_add(T, dw_mul(T, em1));
 }
-// exp of a double word, as a double
+// exp of a double word, as a double (the FP64 exponential outside |a| < 170, where the
+// reduction above stops being exact; NaN propagates)
 __device__ __forceinline__ double dw_exp_d(float2 a) {
+  if (!(fabsf(a.x) < 170.0f)) return exp(f2d_bits(a.x) + f2d_bits(a.y));
   int m;
   const float2 v = dw_exp(a, m);
   return ldexp_bits(dw2d(v), m);
