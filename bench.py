@@ -226,14 +226,32 @@ def curn_flops_per_launch(arr, B):
     return float(B * arr.npsr * (2.0 * P ** 3 / 3.0 + 3.0 * P ** 2))
 
 
+def curn_factor_mode(P):
+    """Which CURN forward kernel the library runs outside FP64 mode (the rule of
+    launch_curn_forward): 1 = k_curn_forward_dw, the triangle in one CTA's shared memory;
+    C > 1 = k_curn_forward_dwc over a cluster of C CTAs (row pairs interleaved); 0 = FP64."""
+    lim = 226 * 1024
+    stage = 6 * (P // 2 + 1) * 16
+    prow = P * (P + 2) // 2 if P % 2 == 0 else (P + 1) ** 2 // 2
+    if stage + prow * 8 <= lim:
+        return 1
+    npairs = (P + 1) // 2
+    for C in (2, 4, 8):
+        part = max(4 * M * (k + 1) + 2 * C * M * (M - 1)
+                   for k in range(C) for M in [(npairs - k + C - 1) // C if npairs > k else 0])
+        if stage + 2 * P * 8 + part * 8 <= lim:
+            return C
+    return 0
+
+
 def curn_variant(dev, steps):
     """The CURN-posterior transform (Eq. PTA_standard_transform_curn) against the default
     prior-whitened one on the same batch: the paper's NANOGrav-15-yr model (RN 30 /
-    HD-GWB 14 bins, no DM: P = 60, the factor in shared memory) with 64 and 256 chains,
-    and the 100-DM-bin workload (P = 260, the factor in the global inverse buffer) with
-    256 chains, on the headline path.  CUDA events per step with L2 flushed; the
-    factorisation stage is the CURN forward stage minus the prior-whitened one: double-word
-    (k_curn_forward_dw) where the two triangles fit in shared memory, FP64 otherwise."""
+    HD-GWB 14 bins, no DM: P = 60, the factor in one CTA's shared memory) with 64 and 256
+    chains, and the 100-DM-bin workload (P = 260, the factor over a cluster of two CTAs)
+    with 256 chains, on the headline path.  CUDA events per step with L2 flushed; the
+    factorisation stage is the CURN forward stage minus the prior-whitened one, in double
+    words (curn_factor_mode)."""
     import ctypes as C
     import torch
     from paper_2607_06834_b300 import abi, synth
@@ -272,14 +290,16 @@ def curn_variant(dev, steps):
         fac_ms = rec["curn"]["stage_ms"]["prior_forward"] - rec["prior"]["stage_ms"]["prior_forward"]
         ach = curn_flops_per_launch(arr, B) / (fac_ms * 1e-3) / 1e12
         P = rec["P"]
-        dw = 6 * (P // 2 + 1) * 16 + 2 * (P * (P + 2) // 2 if P % 2 == 0 else (P + 1) ** 2 // 2) * 8 <= 227 * 1024
-        if dw:
-            rec["roofline"] = {"kernel": "k_curn_forward_dw + k_curn_whiten (double-word LDL^T sweep with inverse)",
+        mode = curn_factor_mode(P)
+        if mode:
+            kern = "k_curn_forward_dw" if mode == 1 else f"k_curn_forward_dwc<{mode}>"
+            rec["roofline"] = {"kernel": f"{kern} + k_curn_whiten (double-word LDL^T sweep with inverse)",
                                "bound": "alu", "unit": "TFLOP/s", "achieved": ach, "peak": DW_PEAK_TFLOPS,
                                "peak_source": f"derived: 148 SM x 128 FP32 lanes x 2.032 GHz x 2 flop / "
                                               f"{DW_OPS_PER_FMA} FP32 operations per double-word multiply-add",
                                "frac": ach / DW_PEAK_TFLOPS, "fp64_peak_frac": ach / peak, "stage_ms": fac_ms,
-                               "factor_in": "shared memory"}
+                               "factor_in": "shared memory" if mode == 1 else
+                               f"distributed shared memory of a {mode}-CTA cluster"}
         else:
             rec["roofline"] = {"kernel": "k_curn_forward + k_curn_whiten (FP64 LDL^T sweep with inverse)",
                                "bound": "alu", "unit": "TFLOP/s", "achieved": ach, "peak": peak,
@@ -780,9 +800,18 @@ def run_ours(args):
                 "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 flop x 2.032 GHz"}
     elif args.transform == "curn":
         flops = curn_flops_per_launch(arr, B) + chol_flops_per_launch(arr, B)
-        roof = {"kernel": "prior stage with k_curn_forward (FP64 LDL^T sweep with inverse)", "bound": "alu",
-                "unit": "TFLOP/s", "achieved": flops / (stage_ms[dom] * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
-                "peak_source": "derived: 148 SM x 2 FP64 FMA/clk x 2 flop x 2.032 GHz"}
+        P = 2 * max(arr.n_gwb, arr.n_rn) + 2 * arr.n_dm
+        mode = 0 if args.precision == "fp64" else curn_factor_mode(P)
+        if mode:
+            kern = "k_curn_forward_dw" if mode == 1 else f"k_curn_forward_dwc<{mode}>"
+            roof = {"kernel": f"prior stage with {kern} (double-word LDL^T sweep with inverse)", "bound": "alu",
+                    "unit": "TFLOP/s", "achieved": flops / (stage_ms[dom] * 1e-3) / 1e12, "peak": DW_PEAK_TFLOPS,
+                    "peak_source": f"derived: 148 SM x 128 FP32 lanes x 2.032 GHz x 2 flop / "
+                                   f"{DW_OPS_PER_FMA} FP32 operations per double-word multiply-add"}
+        else:
+            roof = {"kernel": "prior stage with k_curn_forward (FP64 LDL^T sweep with inverse)", "bound": "alu",
+                    "unit": "TFLOP/s", "achieved": flops / (stage_ms[dom] * 1e-3) / 1e12,
+                    "peak": FP64_PEAK_TFLOPS, "peak_source": "derived: 148 SM x 2 FP64 FMA/clk x 2 flop x 2.032 GHz"}
     else:
         roof = chol_roofline(arr, B, kernel_ms["chol_forward"], args.precision == "fp64")
     roof["frac"] = roof["achieved"] / roof["peak"]

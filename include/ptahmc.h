@@ -42,9 +42,9 @@ extern "C" {
 /* Precision of the TOA-length contractions F a, F^T w, M^T w (Sec. "Single
  * precision").  The log-det, the timing-model solve and the final sums are FP64 in
  * every mode; the per-frequency Cholesky of the dense bins (with its inverse and
- * adjoint) is FP64 in PTA_PREC_FP64 and under the CURN transform, and double-word
- * (a pair of floats, ~48-bit significand, relative error ~1e-14) on the FP32 pipes
- * otherwise. */
+ * adjoint) and the CURN transform's factorisation are FP64 in PTA_PREC_FP64, and
+ * double-word (a pair of floats, ~48-bit significand, relative error ~1e-14) on the FP32
+ * pipes otherwise (pta_set_cholesky restores FP64). */
 #define PTA_PREC_FP64 0   /* plain path: stored FP64 basis, SIMT FP64 */
 #define PTA_PREC_FP32 1   /* basis generated on the fly, SIMT FP32 */
 #define PTA_PREC_TF32X3 2 /* tcgen05 tensor cores, 3-term split TF32 */
@@ -173,10 +173,11 @@ int pta_set_beta(pta_ctx* ctx, int n, const double* beta, void* stream);
  *     Hellings-Downs-correlated phi (Eq. standardized_stochastic_posterior, the
  *     (2 pi)^(-D_z/2) and the data constant dropped as in the default transform).  z
  *     keeps the layout of pta_layout: the entry of coefficient (I, p) sits where the
- *     prior-whitened transform keeps it.  Each evaluation factorises one P x P FP64
- *     matrix per (pulsar, chain), about P^3/3 FP64 multiply-adds, and keeps
- *     B N_p P (P + 1) / 2 doubles of inverse factors between the value and the gradient
- *     (PTA_ENOMEM from the evaluation if they do not fit).
+ *     prior-whitened transform keeps it.  Each evaluation factorises one P x P matrix
+ *     per (pulsar, chain), about P^3/3 multiply-adds (double-word outside PTA_PREC_FP64 and
+ *     PTA_CHOL_FP64, in one CTA or, for P >= 236, over a cluster of 2 to 8 CTAs; FP64 for
+ *     P >= 612), and keeps B N_p P (P + 1) / 2 doubles of inverse factors between the value
+ *     and the gradient (PTA_ENOMEM from the evaluation if they do not fit).
  * With the continuous-wave signal h(theta) the mean is abar_I = beta Sigma_I F_I^T N~_I^-1
  * (dt_I - h_I) (Eq. decenter_det_PTA) and the CW gradient includes its dependence on theta;
  * this costs one extra TOA pass per evaluation and one more when the gradient is asked for.
@@ -190,9 +191,9 @@ int pta_set_transform(pta_ctx* ctx, int transform);
  * PTA_CHOL_DW (the default): double-word arithmetic on the FP32 pipes (pairs of floats,
  * ~48-bit significand; factor, inverse and transform agree with FP64 to ~1e-14
  * relative), several times faster on B300, whose FP64 rate is 1/64 of its FP32 rate.
- * PTA_CHOL_FP64: the FP64 sweep.  PTA_PREC_FP64 and the CURN transform always use the
- * FP64 sweep.  The log-det, the pivots' square roots and every sum stay FP64 either
- * way.  PTA_EINVAL for an unknown value; recaptures HMC graphs. */
+ * PTA_CHOL_FP64: the FP64 sweep, and the FP64 factorisation of the CURN transform.
+ * PTA_PREC_FP64 always uses the FP64 sweeps.  The log-det and the final sums stay FP64
+ * either way.  PTA_EINVAL for an unknown value; recaptures HMC graphs. */
 #define PTA_CHOL_DW 0
 #define PTA_CHOL_FP64 1
 int pta_set_cholesky(pta_ctx* ctx, int mode);

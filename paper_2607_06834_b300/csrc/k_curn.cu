@@ -32,6 +32,7 @@
 #include <cmath>
 
 #include "dw_ldl.cuh"
+#include "dw_ldl_cluster.cuh"
 #include "dwarith.cuh"
 #include "pta_internal.cuh"
 
@@ -342,6 +343,157 @@ __global__ void __launch_bounds__(kCTdw)
 }
 
 // ---------------------------------------------------------------------------
+// k_curn_forward_dw for P whose triangle exceeds one CTA's shared memory: a cluster of C
+// CTAs per (pulsar, chain) holds A' by interleaved row pairs (dwc_ldl_sweep); every row
+// operation after the sweep runs where the row is, the column sums of the transform are
+// formed per CTA over its rows and added across the cluster in rank order, and each CTA
+// writes its rows of Y' to the W slot.  Grid (npsr C, B), cluster (C, 1, 1), NT threads
+// (at most 64 registers: one 1024-thread CTA, or two 512-thread CTAs, per SM).
+// ---------------------------------------------------------------------------
+template <int C, int NT>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NT, 1024 / NT)
+    k_curn_forward_dwc(DevModel m, const float* __restrict__ x, const double* __restrict__ sk,
+                       const double* __restrict__ skd, const double* __restrict__ srho, double* a64, double* Wg,
+                       double* ahat, double* ld, int32_t* stat, const double* __restrict__ g0, int B) {
+  extern __shared__ float4 smq[];
+  __shared__ __align__(16) float2 pv[4];
+  __shared__ int s_bad;
+  __shared__ double red[NT / 32];
+  __shared__ double s_ld;
+  const int k = cl_rank(), I = blockIdx.x / C, b = blockIdx.y, tid = threadIdx.x, nt = blockDim.x, P = m.P;
+  const int nh = P / 2 + 1, lane = tid & 31, wp = tid >> 5, nw = nt >> 5;
+  const int nrow = 2 * cpairs<C>(P, k);  // this CTA's rows 2 (k + C m) + h, m < nrow / 2, h = 0, 1
+  float2* part = reinterpret_cast<float2*>(smq + 6 * nh);  // [2P] column sums over this CTA's rows
+  float2* T = part + 2 * P;                                 // this CTA's row pairs of A', then of L'^-1
+  const size_t o = (size_t)I * B + b;
+  const double bt = m.beta ? m.beta[b] : 1.0;
+  const double gsc = g0 ? 1.0 : bt;
+  const float2 btw = d2dw_bits(bt), gscw = d2dw_bits(gsc);
+  const float* xb = x + (size_t)b * m.d;
+  const float2* G = m.Grev_dw + (size_t)I * (P * (P + 1) / 2);
+  float2* rdw = reinterpret_cast<float2*>(smq);  // [P] 1 / phi_C of reversed coefficient i
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (int i = tid; i < P; i += nt) {
+    const double ph = phic(m, sk, skd, srho, b, I, P - 1 - i);
+    float2 r = make_float2(1.0f, 0.0f);
+    if (ph > 0.0 && ph < INFINITY)
+      r = dw_recip(d2dw_bits(ph));
+    else
+      s_bad = 1;
+    rdw[i] = r;
+  }
+  __syncthreads();
+  float dmax = 0.0f;  // the same 2^-E in every CTA of the cluster
+  for (int i = lane; i < P; i += 32) dmax = fmaxf(dmax, dw_add(dw_mul(btw, G[i * (i + 3) / 2]), rdw[i]).x);
+  for (int off = 16; off; off >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
+  int E = 0;
+  if (dmax > 0.0f && dmax < INFINITY) frexpf(dmax, &E);
+  E += E & 1;
+  const float sc = __int_as_float((127 - E) << 23);
+  for (int rr = wp; rr < nrow; rr += nw) {  // a warp per row
+    const int i = 2 * (k + C * (rr >> 1)) + (rr & 1);
+    if (i >= P) continue;
+    float2* row = T + crow<C>(i);
+    const float2* Gi = G + i * (i + 1) / 2;
+    for (int c = lane; c <= i; c += 32) {
+      float2 v = dw_mul(btw, Gi[c]);
+      if (c == i) v = dw_add(v, rdw[i]);
+      row[c] = make_float2(v.x * sc, v.y * sc);
+    }
+    if (!(i & 1) && lane == 0) row[i + 1] = make_float2(0.0f, 0.0f);
+  }
+  dwc_ldl_sweep<C>(P, T, smq, pv, &s_bad);
+  float2* rqw = reinterpret_cast<float2*>(smq);  // [P] (this CTA's rows)
+  float2* gpw = rqw + P;
+  float2* zpw = gpw + P;
+  float2* upw = zpw + P;  // (this CTA's rows)
+  float2* tpw = upw + P;  // (this CTA's rows)
+  const float usc = __int_as_float((127 - E / 2) << 23);
+  for (int i = tid; i < P; i += nt) {
+    const int p = P - 1 - i;
+    if ((i >> 1) % C == k) {
+      const float2 r = dw_recip(dw_sqrt(T[crow<C>(i) + i]));
+      rqw[i] = make_float2(r.x * usc, r.y * usc);
+    }
+    gpw[i] = d2dw_bits(g0 ? fma(bt, m.ga[(size_t)I * P + p], g0[o * P + p]) : m.gt[(size_t)I * P + p]);
+    zpw[i] = make_float2(xb[zidx(m, I, p)], 0.0f);
+  }
+  __syncthreads();
+  for (int rr = wp; rr < nrow; rr += nw) {  // Y' = D^-1/2 L'^-1
+    const int i = 2 * (k + C * (rr >> 1)) + (rr & 1);
+    if (i >= P) continue;
+    float2* row = T + crow<C>(i);
+    const float2 ri = rqw[i];
+    for (int c = lane; c <= i; c += 32) row[c] = (c == i) ? ri : dw_mul(row[c], ri);
+  }
+  __syncthreads();
+  for (int rr = tid; rr < nrow; rr += nt) {
+    const int i = 2 * (k + C * (rr >> 1)) + (rr & 1);
+    if (i >= P) continue;
+    const float2* row = T + crow<C>(i);
+    float2 acc = make_float2(0.0f, 0.0f);
+    for (int c = 0; c <= i; ++c) acc = dw_fms(acc, row[c], dw_neg(gpw[c]));
+    upw[i] = acc;
+    tpw[i] = dw_add(dw_mul(gscw, acc), zpw[i]);
+  }
+  __syncthreads();
+  for (int c = tid; c < P; c += nt) {  // this CTA's rows i >= c, in increasing order
+    float2 sa = make_float2(0.0f, 0.0f), sh = sa;
+    int r = c >> 1;
+    int d = (k - r) % C;
+    if (d < 0) d += C;
+    for (r += d; 2 * r < P; r += C) {
+      const int b0 = crow<C>(2 * r);
+      if (2 * r >= c) {
+        const float2 y = T[b0 + c];
+        sa = dw_fms(sa, y, dw_neg(tpw[2 * r]));
+        sh = dw_fms(sh, y, dw_neg(upw[2 * r]));
+      }
+      if (2 * r + 1 < P) {
+        const float2 y = T[b0 + 2 * (r + 1) + c];
+        sa = dw_fms(sa, y, dw_neg(tpw[2 * r + 1]));
+        sh = dw_fms(sh, y, dw_neg(upw[2 * r + 1]));
+      }
+    }
+    part[c] = sa;
+    part[P + c] = sh;
+  }
+  double acc = 0.0;
+  for (int i = tid; i < P; i += nt)
+    if ((i >> 1) % C == k) acc += log(dw2d(rqw[i]));
+  acc = block_sum(acc, red);
+  if (tid == 0) {
+    s_ld = acc;
+    if (s_bad) atomicOr(&stat[b], 2);
+  }
+  float2* Wslot = reinterpret_cast<float2*>(Wg) + o * (P * (P + 1) / 2);
+  for (int rr = wp; rr < nrow; rr += nw) {
+    const int i = 2 * (k + C * (rr >> 1)) + (rr & 1);
+    if (i >= P) continue;
+    const float2* row = T + crow<C>(i);
+    for (int c = lane; c <= i; c += 32) Wslot[i * (i + 1) / 2 + c] = row[c];
+  }
+  cl_sync();  // every CTA's column sums and log det part are in place
+  for (int c = k + C * tid; c < P; c += C * nt) {
+    float2 sa = make_float2(0.0f, 0.0f), sh = sa;
+    for (int q = 0; q < C; ++q) {
+      sa = dw_add(sa, cl_ld2(cl_map(part + c, q)));
+      sh = dw_add(sh, cl_ld2(cl_map(part + P + c, q)));
+    }
+    const int p = P - 1 - c;
+    a64[o * m.PM + p] = dw2d(sa);
+    ahat[o * P + p] = dw2d(dw_mul(gscw, sh));
+  }
+  if (k == 0 && tid == 0) {
+    double s = 0.0;
+    for (int q = 0; q < C; ++q) s += cl_ldd(cl_map(&s_ld, q));
+    ld[o] = s;
+  }
+  cl_sync();  // no CTA leaves while another reads its shared memory
+}
+
+// ---------------------------------------------------------------------------
 // HD prior at the transformed coefficients, per (achromatic bin or DM block, chain):
 // v = Phi_k^-1 a (stored for the gradient), the term -1/2 a^T Phi_k^-1 a - log det Phi_k
 // over both columns, and its derivatives at fixed a:
@@ -529,19 +681,21 @@ __global__ void __launch_bounds__(kCTdw)
     k_curn_adjoint_dw(DevModel m, const float* __restrict__ x, const double* __restrict__ ghat,
                       const float2* __restrict__ Wg, const double* __restrict__ vbuf, const double* __restrict__ ahat,
                       const double* __restrict__ sk, const double* __restrict__ skd, const double* __restrict__ srho,
-                      float* grad, double* dlnk, double* dlnkd, double* dlnrc, double* v2, int B) {
+                      float* grad, double* dlnk, double* dlnkd, double* dlnrc, double* v2, int B, int ysm) {
   extern __shared__ float2 smw[];
   const int I = blockIdx.x, b = blockIdx.y, tid = threadIdx.x, nt = blockDim.x, P = m.P, np = m.npsr;
   const int ntri = P * (P + 1) / 2, nseg = max(1, min(4, nt / P));
   const size_t o = (size_t)I * B + b;
-  float2* Y = smw;          // [ntri] Y', plain packing
-  float2* gb = Y + ntri;    // [P] gbar', reversed
-  float2* zp = gb + P;      // [P] z'
-  float2* sp = zp + P;      // [P] s' = Y' gbar'
-  float2* seg = sp + P;     // [nseg][P][4] (h, T, R, Dg) per segment and column
+  float2* Ys = smw;                    // [ntri] Y', plain packing (ysm), else read from the W slot
+  float2* gb = Ys + (ysm ? ntri : 0);  // [P] gbar', reversed
+  float2* zp = gb + P;                 // [P] z'
+  float2* sp = zp + P;                 // [P] s' = Y' gbar'
+  float2* seg = sp + P;                // [nseg][P][4] (h, T, R, Dg) per segment and column
   double* pd = reinterpret_cast<double*>(seg + 4 * nseg * P);  // [P] phi_C d logp / d phi_C
   const float2* Yg = Wg + o * ntri;
-  for (int e = tid; e < ntri; e += nt) Y[e] = Yg[e];
+  if (ysm)
+    for (int e = tid; e < ntri; e += nt) Ys[e] = Yg[e];
+  const float2* Y = ysm ? Ys : Yg;
   const float* xb = x + (size_t)b * m.d;
   for (int i = tid; i < P; i += nt) {
     const int p = P - 1 - i;
@@ -635,21 +789,56 @@ constexpr size_t kCurnSmemMax = 200 * 1024;
 
 size_t curn_w_doubles(const DevModel& m) { return (size_t)m.P * (m.P + 1) / 2; }
 
-// shared memory of k_curn_forward_dw, and whether the double-word CURN kernels run
+// shared memory of k_curn_forward_dw and of k_curn_forward_dwc<C> (its largest part of the
+// triangle); which CURN forward runs: 0 the FP64 kernel (FP64 mode, PTA_CHOL_FP64, or no
+// cluster of at most 8 CTAs holds the triangle), 1 the double-word kernel with the triangle
+// in one CTA, C > 1 the double-word kernel over a cluster of C CTAs
 static size_t curn_fwd_smem_dw(const DevModel& m) {
   return 6 * (size_t)(m.P / 2 + 1) * sizeof(float4) + (size_t)prow(m.P) * sizeof(float2);
 }
-static bool curn_dw(const DevModel& m, int fp64) { return !fp64 && !m.chol64 && curn_fwd_smem_dw(m) <= 227 * 1024; }
+template <int C>
+static size_t curn_fwd_smem_dwc(const DevModel& m) {
+  int mx = 0;
+  for (int k = 0; k < C; ++k) mx = std::max(mx, cpart<C>(m.P, k));
+  return 6 * (size_t)(m.P / 2 + 1) * sizeof(float4) + 2 * (size_t)m.P * sizeof(float2) + (size_t)mx * sizeof(float2);
+}
+constexpr size_t kDwSmemMax = 226 * 1024;  // of the 227 KB a CTA may opt into, 1 KB for static shared memory
+static int curn_dw_mode(const DevModel& m, int fp64) {
+  if (fp64 || m.chol64) return 0;
+  if (curn_fwd_smem_dw(m) <= kDwSmemMax) return 1;
+  if (curn_fwd_smem_dwc<2>(m) <= kDwSmemMax) return 2;
+  if (curn_fwd_smem_dwc<4>(m) <= kDwSmemMax) return 4;
+  if (curn_fwd_smem_dwc<8>(m) <= kDwSmemMax) return 8;
+  return 0;
+}
+
+template <int C>
+static cudaError_t launch_fwd_dwc(const DevModel& m, const Scratch& s, int B, const float* x, cudaStream_t st) {
+  constexpr int NT = C == 2 ? 1024 : 512;
+  const size_t sm = curn_fwd_smem_dwc<C>(m);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_curn_forward_dwc<C, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_curn_forward_dwc<C, NT><<<dim3(m.npsr * C, B), NT, sm, st>>>(m, x, s.sk, s.skd, s.srho, s.a64, s.curnW,
+                                                               s.curnAhat, s.curnLd, s.stat,
+                                                               m.cw ? s.curnG0 : nullptr, B);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_curn_forward(const DevModel& m, const Scratch& s, int B, const float* x, int fp64,
                                 cudaStream_t st) {
-  const size_t smdw = curn_fwd_smem_dw(m);
-  cudaError_t e;
-  if (curn_dw(m, fp64)) {
+  const int mode = curn_dw_mode(m, fp64);
+  cudaError_t e = cudaSuccess;
+  if (mode == 1) {
+    const size_t smdw = curn_fwd_smem_dw(m);
     e = cudaFuncSetAttribute(k_curn_forward_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smdw);
     if (e != cudaSuccess) return e;
     k_curn_forward_dw<<<dim3(m.npsr, B), kCTdw, smdw, st>>>(m, x, s.sk, s.skd, s.srho, s.a64, s.curnW, s.curnAhat,
                                                             s.curnLd, s.stat, m.cw ? s.curnG0 : nullptr, B);
+  } else if (mode > 1) {
+    e = mode == 2 ? launch_fwd_dwc<2>(m, s, B, x, st)
+                  : (mode == 4 ? launch_fwd_dwc<4>(m, s, B, x, st) : launch_fwd_dwc<8>(m, s, B, x, st));
+    if (e != cudaSuccess) return e;
   } else {
     const bool tri = fwd_smem(m, true) <= kCurnSmemMax;
     const size_t sm = fwd_smem(m, tri);
@@ -670,14 +859,16 @@ cudaError_t launch_curn_forward(const DevModel& m, const Scratch& s, int B, cons
 
 cudaError_t launch_curn_adjoint(const DevModel& m, const Scratch& s, int B, const float* x, float* grad, int fp64,
                                 cudaStream_t st) {
-  if (curn_dw(m, fp64)) {
+  if (curn_dw_mode(m, fp64)) {  // Y' in shared memory while it fits, else read from the W slot
     const size_t P = m.P, nseg = std::max<size_t>(1, std::min<size_t>(4, kCTdw / P));
-    const size_t sm = (P * (P + 1) / 2 + 3 * P + 4 * nseg * P) * sizeof(float2) + P * sizeof(double);
+    const size_t rest = (3 * P + 4 * nseg * P) * sizeof(float2) + P * sizeof(double);
+    const bool ysm = P * (P + 1) / 2 * sizeof(float2) + rest <= kDwSmemMax;
+    const size_t sm = (ysm ? P * (P + 1) / 2 * sizeof(float2) : 0) + rest;
     cudaError_t e = cudaFuncSetAttribute(k_curn_adjoint_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k_curn_adjoint_dw<<<dim3(m.npsr, B), kCTdw, sm, st>>>(
         m, x, s.ghat, reinterpret_cast<const float2*>(s.curnW), s.curnV, s.curnAhat, s.sk, s.skd, s.srho, grad,
-        s.dlnk, s.dlnkd, s.dlnrc, m.cw ? s.curnV2 : nullptr, B);
+        s.dlnk, s.dlnkd, s.dlnrc, m.cw ? s.curnV2 : nullptr, B, ysm ? 1 : 0);
     return cudaGetLastError();
   }
   const bool tri = adj_smem(m, true) <= kCurnSmemMax;

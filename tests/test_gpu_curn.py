@@ -110,8 +110,9 @@ def test_curn_paper_config_nodm():
 
 
 def test_curn_ng15_global_factor():
-    """67 pulsars with 100 DM bins (P = 260: the factor lives in the global inverse
-    buffer), 16 chains, two sampled against the oracle."""
+    """67 pulsars with 100 DM bins (P = 260: the double-word factor over a cluster of two
+    CTAs; FP64 mode keeps it in the global inverse buffer), 16 chains, two sampled
+    against the oracle."""
     arr = synth.make_array("ng15")
     orc = O.Oracle(arr, transform="curn")
     X = synth.make_points(arr, 16, seed=64)
@@ -123,6 +124,28 @@ def test_curn_ng15_global_factor():
     lo = np.array([orc.logp(x) for x in Xd])
     go = np.array([orc.grad(x) for x in Xd])
     _check("fp32", lp[idx], g[idx], lo, go, "curn ng15")
+
+
+@pytest.mark.parametrize("n_dm", [110, 160, 235])
+@pytest.mark.parametrize("prec", ["fp32", "gram"])
+def test_curn_cluster_factor_matches_oracle(n_dm, prec):
+    """P = 240, 340, 490: above one CTA's shared memory the double-word factorisation runs over
+    a thread-block cluster of 2, 4 and 8 CTAs (interleaved row pairs); 4 chains against the
+    oracle, the 340 case also tempered."""
+    kw = dict(npsr=3, ntoa=[600, 900, 1300], m=[3, 6, 8], n_gwb=6, n_rn=10, n_dm=n_dm, seed=71, nbackend=2)
+    arr = synth.small_array(**kw)
+    orc = O.Oracle(arr, transform="curn")
+    X = synth.make_points(arr, 4, seed=72)
+    beta = np.array([1.0, 0.6, 0.2, 0.0]) if n_dm == 160 else np.ones(4)
+    eng = _engine(arr, prec)
+    if n_dm == 160:
+        eng.set_beta(torch.tensor(beta, device="cuda"))
+    lp, g, st = _eval(eng, X)
+    assert np.all(st == 0)
+    Xd = X.astype(np.float64)
+    lo = np.array([orc.logp(x, beta=b) for x, b in zip(Xd, beta)])
+    go = np.array([orc.grad(x, beta=b) for x, b in zip(Xd, beta)])
+    _check(prec, lp, g, lo, go, f"curn cluster P={20 + 2 * n_dm}")
 
 
 def test_curn_hmc_trajectory_and_rejections():
