@@ -235,11 +235,11 @@ def curn_factor_mode(P):
     prow = P * (P + 2) // 2 if P % 2 == 0 else (P + 1) ** 2 // 2
     if stage + prow * 8 <= lim:
         return 1
-    npairs = (P + 1) // 2
+    npairs, cstage = (P + 1) // 2, (10 * (P // 2 + 1) + 8) * 16
     for C in (2, 4, 8):
         part = max(4 * M * (k + 1) + 2 * C * M * (M - 1)
                    for k in range(C) for M in [(npairs - k + C - 1) // C if npairs > k else 0])
-        if stage + 2 * P * 8 + part * 8 <= lim:
+        if cstage + 2 * P * 8 + part * 8 <= lim:
             return C
     return 0
 

@@ -175,8 +175,8 @@ int pta_set_beta(pta_ctx* ctx, int n, const double* beta, void* stream);
  *     keeps the layout of pta_layout: the entry of coefficient (I, p) sits where the
  *     prior-whitened transform keeps it.  Each evaluation factorises one P x P matrix
  *     per (pulsar, chain), about P^3/3 multiply-adds (double-word outside PTA_PREC_FP64 and
- *     PTA_CHOL_FP64, in one CTA or, for P >= 236, over a cluster of 2 to 8 CTAs; FP64 for
- *     P >= 612), and keeps B N_p P (P + 1) / 2 doubles of inverse factors between the value
+ *     PTA_CHOL_FP64, in one CTA or, for P >= 234, over a cluster of 2 to 8 CTAs; FP64 for
+ *     P >= 584), and keeps B N_p P (P + 1) / 2 doubles of inverse factors between the value
  *     and the gradient (PTA_ENOMEM from the evaluation if they do not fit).
  * With the continuous-wave signal h(theta) the mean is abar_I = beta Sigma_I F_I^T N~_I^-1
  * (dt_I - h_I) (Eq. decenter_det_PTA) and the CW gradient includes its dependence on theta;

@@ -361,9 +361,9 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NT, 1024 / NT)
   __shared__ double red[NT / 32];
   __shared__ double s_ld;
   const int k = cl_rank(), I = blockIdx.x / C, b = blockIdx.y, tid = threadIdx.x, nt = blockDim.x, P = m.P;
-  const int nh = P / 2 + 1, lane = tid & 31, wp = tid >> 5, nw = nt >> 5;
+  const int lane = tid & 31, wp = tid >> 5, nw = nt >> 5;
   const int nrow = 2 * cpairs<C>(P, k);  // this CTA's rows 2 (k + C m) + h, m < nrow / 2, h = 0, 1
-  float2* part = reinterpret_cast<float2*>(smq + 6 * nh);  // [2P] column sums over this CTA's rows
+  float2* part = reinterpret_cast<float2*>(smq + cstage_f4(P));  // [2P] column sums over this CTA's rows
   float2* T = part + 2 * P;                                 // this CTA's row pairs of A', then of L'^-1
   const size_t o = (size_t)I * B + b;
   const double bt = m.beta ? m.beta[b] : 1.0;
@@ -800,7 +800,7 @@ template <int C>
 static size_t curn_fwd_smem_dwc(const DevModel& m) {
   int mx = 0;
   for (int k = 0; k < C; ++k) mx = std::max(mx, cpart<C>(m.P, k));
-  return 6 * (size_t)(m.P / 2 + 1) * sizeof(float4) + 2 * (size_t)m.P * sizeof(float2) + (size_t)mx * sizeof(float2);
+  return (size_t)cstage_f4(m.P) * sizeof(float4) + 2 * (size_t)m.P * sizeof(float2) + (size_t)mx * sizeof(float2);
 }
 constexpr size_t kDwSmemMax = 226 * 1024;  // of the 227 KB a CTA may opt into, 1 KB for static shared memory
 static int curn_dw_mode(const DevModel& m, int fp64) {

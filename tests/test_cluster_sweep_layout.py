@@ -1,15 +1,14 @@
 """Index arithmetic of the cluster LDL^T sweep (csrc/dw_ldl_cluster.cuh), restated on the host.
 
-The CURN factorisation for P >= 236 spreads one packed triangle over the C CTAs of a
+The CURN factorisation for P >= 234 spreads one packed triangle over the C CTAs of a
 thread-block cluster: row pair r lives in CTA r mod C at offset 4m(k+1) + 2Cm(m-1) (its m-th
 pair), and pass B of each step enumerates a CTA's tiles by a float square-root decode of a flat
 index.  These tests run the same index formulas in Python (float64 arithmetic in place of
 double words) and check that every tile of every step is visited exactly once by exactly one
 CTA, that every access stays inside the CTA's part, that the padding layout matches the
-kernel's 16-byte pair accesses, and that the sweep produces D and L^-1 of A = L D L^T.  The
-float32 decode is checked exhaustively up to the largest order the cluster path takes."""
-import math
-
+kernel's 16-byte pair accesses, that the next pivot block every CTA factors from the staged
+entries equals the owner's, and that the sweep produces D and L^-1 of A = L D L^T.  The float32
+decode is checked exhaustively up to the largest order the cluster path takes."""
 import numpy as np
 import pytest
 
@@ -56,20 +55,24 @@ def sweep(A, C):
         if not i & 1:
             T[k][at(k, b + i + 1)] = 0.0
     stage = {nm: [np.full((nh, 2), np.nan) for _ in range(C)] for nm in ("plE", "plO", "uuE", "uuO", "xrE", "xrO")}
-    pv = [None] * C
+    pb = [[None] * 4 for _ in range(C)]  # the next pivot block's rows before the update, and their l pairs
 
-    def pivot(a00, a10, a11, two, k, bj, bj1, j):
-        T[k][at(k, bj + j)] = a00
-        r0, r1, l10 = 1.0 / a00, 0.0, 0.0
+    def pivot(a00, a10, a11, two):
+        r0, r1, l10, d1 = 1.0 / a00, 0.0, 0.0, 0.0
         if two:
             l10 = a10 * r0
             d1 = a11 - l10 * a10
-            T[k][at(k, bj1 + j + 1)] = d1
             r1 = 1.0 / d1
-        for q in range(C):
-            pv[q] = (r0, r1, a10, l10)
+        return (a00, d1), (r0, r1, a10, l10)
 
-    pivot(T[0][0], T[0][2] if n > 1 else 0, T[0][3] if n > 1 else 0, n > 1, 0, 0, 2, 0)
+    def upd(v, p, qa, qb):
+        return (v[0] - (p[0] * qa[0] + p[1] * qa[1]), v[1] - (p[0] * qb[0] + p[1] * qb[1]))
+
+    d, pv0 = pivot(T[0][0], T[0][2] if n > 1 else 0, T[0][3] if n > 1 else 0, n > 1)
+    T[0][0] = d[0]
+    if n > 1:
+        T[0][3] = d[1]
+    pv = [pv0] * C
     for j in range(0, n - 1, 2):
         s2, R0 = n - j - 2, (j + 2) >> 1
         pvs = list(pv)
@@ -90,6 +93,9 @@ def sweep(A, C):
                     stage["plO" if e & 1 else "plE"][k][e >> 1] = (l0, w * r1)
                     for q in range(C):
                         stage["uuO" if e & 1 else "uuE"][q][e >> 1] = (a0, w)
+                        if e < 2:
+                            pb[q][e] = (T[k][at(k, b + j + 2)], T[k][at(k, b + j + 3)])
+                            pb[q][2 + e] = (l0, w * r1)
                 else:
                     c, rj, rj1 = t - 2 * nr, crow(j, C), crow(j + 1, C)
                     xj, x1 = 0.0, 1.0
@@ -135,8 +141,18 @@ def sweep(A, C):
                     e1 = T[k][at(k, b + c0 + 1)] - (p[0] * q1[0] + p[1] * q1[1])
                     T[k][b + c0], T[k][b + c0 + 1] = e0, e1
                     v.append((e0, e1))
-                if s == 0 and I == 0:
-                    pivot(v[0][0], v[1][0], v[1][1], i0 + 1 < n, k, b0, b1, j + 2)
+                if s == 0 and I == 0:  # the owner's pivots go to its diagonal
+                    dd, own = pivot(v[0][0], v[1][0], v[1][1], i0 + 1 < n)
+                    T[k][at(k, b0 + j + 2)] = dd[0]
+                    if i0 + 1 < n:
+                        T[k][at(k, b1 + j + 3)] = dd[1]
+        if s2 > 0:  # every CTA factors the next pivot block from its staging
+            two = s2 > 1
+            for k in range(C):
+                w0 = upd(pb[k][0], pb[k][2], stage["uuE"][k][0], stage["uuO"][k][0])
+                w1 = upd(pb[k][1], pb[k][3], stage["uuE"][k][0], stage["uuO"][k][0]) if two else w0
+                _, pv[k] = pivot(w0[0], w1[0], w1[1], two)
+                assert pv[k] == own, (j, k)
         nT = (s2 + 1) >> 1
         want = [("T", I, L) for I in range(nT) for L in range(I + 1)] + [("X", I, c) for I in range(nT) for c in range(R0)]
         assert sorted(seen) == sorted(want), j
@@ -164,7 +180,7 @@ def test_cluster_sweep_covers_and_factors(n, C):
 def test_cluster_parts_tile_the_triangle():
     """the parts hold every padded row exactly once, and sum to the one-CTA padded triangle"""
     for C in (2, 4, 8):
-        for n in range(1, 613):
+        for n in range(1, 585):
             npairs = (n + 1) >> 1
             total = sum(cpart(n, k, C) for k in range(C))
             assert total == sum(4 * (r + 1) for r in range(npairs))
@@ -174,7 +190,7 @@ def test_cluster_parts_tile_the_triangle():
                 assert offs == [sum(4 * (q + 1) for q in pairs[:m]) for m in range(len(pairs))]
 
 
-@pytest.mark.parametrize("C,P", [(2, 236), (2, 260), (2, 322), (4, 324), (4, 446), (8, 448), (8, 610)])
+@pytest.mark.parametrize("C,P", [(2, 234), (2, 260), (2, 314), (4, 316), (4, 430), (8, 432), (8, 582)])
 def test_cluster_tile_decode_exact(C, P):
     """the float32 square-root decode with its +-1 correction gives every step's (row, tile)"""
     npairs = (P + 1) >> 1
