@@ -5,6 +5,8 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pta_internal.cuh"
 
 using namespace pta;
@@ -740,7 +742,12 @@ int ensure_f64(pta_ctx* c) {
 }  // namespace
 
 namespace {
-// Record an event pair around one stage when profiling is on.
+// NVTX range names of the stages (host-side ranges around each stage's launches, always
+// emitted: without a tool attached a push or pop is one test of a null pointer); ncu's
+// --nvtx --nvtx-include "pta:toa/" selects one stage's kernels
+const char* const kStageRange[5] = {"pta:prior_forward", "pta:toa", "pta:epilogue", "pta:adjoint",
+                                              "pta:final"};
+// An NVTX range around one stage, and an event pair around it when profiling is on.
 struct StageTimer {
   pta_ctx* c;
   cudaStream_t st;
@@ -748,12 +755,14 @@ struct StageTimer {
   cudaEvent_t e0 = nullptr;
   int stage = -1;
   void begin(int s) {
+    nvtxRangePushA(kStageRange[s]);
     if (!on) return;
     stage = s;
     cudaEventCreate(&e0);
     cudaEventRecord(e0, st);
   }
   void end(int launches) {
+    nvtxRangePop();
     if (!on) return;
     cudaEvent_t e1;
     cudaEventCreate(&e1);
