@@ -58,21 +58,24 @@ DW_PEAK_TFLOPS = 148 * 128 * 2.032e9 * 2 / DW_OPS_PER_FMA / 1e12
 # kernel from one ncu capture, valid only while the kernel's sources are the ones
 # profiled (sha256 of each file); see profiles/.
 CAPTURED_TRAFFIC = {
-    "k_chol_forward_dw": {"bytes": (7.334400 + 78.897408) * 1e6, "profile": "profiles/k_chol_forward_dw_ng15_b256.md",
-                          "sources": {"k_prior.cu": "02616a4da228d5d294640eafa07e27328a860d9816f9b67ec941cbee7bd7b7da",
-                                      "dw_ldl.cuh": "155831b5eef5337ca1824aaf19e7d3675c28ed743237428e1118db0b9da9d752",
+    "k_chol_forward_dw": {"bytes": (7.477248 + 78.906112) * 1e6, "profile": "profiles/k_chol_forward_dw_ng15_b256.md",
+                          "sources": {"k_prior.cu": "577a257f2b1635253165b9e54b638f14c8155b1975415154e5661089bec34220",
+                                      "dw_ldl.cuh": "f0f4f50e696915f9891833b063ccc90b6bd9e024447d1020ad7d16f07c3dd3af",
                                       "dwarith.cuh": "487efa32b981977af53e8f51e037f947a3a1373050868a1543ad1ac2869bdae0",
+                                      "pta_check.cuh": "8922e66311c1eaef8cef83b01d22f538ca1c01ce3714480bf04d301dd04618a6",
                                       "pta_internal.cuh":
-                                          "8337b7312037cce44ff7ff89544a4f04a46a83b602f19d37180c0e446bd3507c"}},
-    "k_f16_res": {"bytes": (743.145984 + 286.228480) * 1e6, "profile": "profiles/k_f16_res_ng15_b256.md",
-                  "sources": {"k_toa_f16.cu": "008e254fef26fd727a0cea74fdfd2114bc9073072fcbd7727849f4bdb7b11bd3",
+                                          "77ac6b320ff664cb6fc0ede00f32a73d8b1e294df681d41d324ca9dc63c03f45"}},
+    "k_f16_res": {"bytes": (743.047168 + 286.591488) * 1e6, "profile": "profiles/k_f16_res_ng15_b256.md",
+                  "sources": {"k_toa_f16.cu": "0ee63d4252e783834f58afda7beab9780ef47efe3837d7b726ec5fa22d7eb71c",
                               "dwarith.cuh": "487efa32b981977af53e8f51e037f947a3a1373050868a1543ad1ac2869bdae0",
-                              "pta_internal.cuh": "8337b7312037cce44ff7ff89544a4f04a46a83b602f19d37180c0e446bd3507c",
+                              "pta_check.cuh": "8922e66311c1eaef8cef83b01d22f538ca1c01ce3714480bf04d301dd04618a6",
+                              "pta_internal.cuh": "77ac6b320ff664cb6fc0ede00f32a73d8b1e294df681d41d324ca9dc63c03f45",
                               "tc_ptx.cuh": "3c9784327356c5b1fdfbf233ac793b19bb50883f641ee44cceddaaed2465521c"}},
-    "k_f16_ftw": {"bytes": (835.932160 + 39.319808) * 1e6, "profile": "profiles/k_f16_ftw_ng15_b256.md",
-                  "sources": {"k_toa_f16.cu": "008e254fef26fd727a0cea74fdfd2114bc9073072fcbd7727849f4bdb7b11bd3",
+    "k_f16_ftw": {"bytes": (835.902208 + 39.038464) * 1e6, "profile": "profiles/k_f16_ftw_ng15_b256.md",
+                  "sources": {"k_toa_f16.cu": "0ee63d4252e783834f58afda7beab9780ef47efe3837d7b726ec5fa22d7eb71c",
                               "dwarith.cuh": "487efa32b981977af53e8f51e037f947a3a1373050868a1543ad1ac2869bdae0",
-                              "pta_internal.cuh": "8337b7312037cce44ff7ff89544a4f04a46a83b602f19d37180c0e446bd3507c",
+                              "pta_check.cuh": "8922e66311c1eaef8cef83b01d22f538ca1c01ce3714480bf04d301dd04618a6",
+                              "pta_internal.cuh": "77ac6b320ff664cb6fc0ede00f32a73d8b1e294df681d41d324ca9dc63c03f45",
                               "tc_ptx.cuh": "3c9784327356c5b1fdfbf233ac793b19bb50883f641ee44cceddaaed2465521c"}},
 }
 

@@ -38,6 +38,8 @@ extern "C" {
 #define PTA_ECUDA (-3)    /* a CUDA runtime call failed */
 #define PTA_ENOMEM (-4)   /* device or host allocation failed */
 #define PTA_ETIMEOUT (-5) /* a bounded device wait gave up */
+#define PTA_ECHECK (-6)   /* check build (libptahmc_check.so) only: an index check failed; the
+                            site, value and limit are in pta_last_error */
 
 /* Precision of the TOA-length contractions F a, F^T w, M^T w (Sec. "Single
  * precision").  The log-det, the timing-model solve and the final sums are FP64 in

@@ -1,16 +1,16 @@
 """ctypes declarations of the C ABI in include/ptahmc.h (argument marshalling only).
 
-Importing this module loads the in-tree libptahmc.so and raises ImportError if it
-is missing: there is no CPU fallback."""
+Importing this module loads the in-tree libptahmc.so (its check build libptahmc_check.so
+when PTA_CHECK_BUILD=1) and raises ImportError if it is missing: there is no CPU fallback."""
 from __future__ import annotations
 
 import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libptahmc.so")
+LIB_PATH = os.path.join(HERE, "libptahmc_check.so" if os.environ.get("PTA_CHECK_BUILD") == "1" else "libptahmc.so")
 
-PTA_OK, PTA_EINVAL, PTA_ESTATE, PTA_ECUDA, PTA_ENOMEM, PTA_ETIMEOUT = 0, -1, -2, -3, -4, -5
+PTA_OK, PTA_EINVAL, PTA_ESTATE, PTA_ECUDA, PTA_ENOMEM, PTA_ETIMEOUT, PTA_ECHECK = 0, -1, -2, -3, -4, -5, -6
 PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2, "tf32": 3, "bf16x3": 4, "gram": 5, "f16split": 6}
 TRANSFORM = {"prior": 0, "curn": 1}
 CHOLESKY = {"dw": 0, "fp64": 1}

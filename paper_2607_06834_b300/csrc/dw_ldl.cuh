@@ -16,6 +16,7 @@
 // tile's upper entry is the even row's padding).  Two barriers per two columns.
 #pragma once
 #include "dwarith.cuh"
+#include "pta_check.cuh"
 
 namespace pta {
 
@@ -63,17 +64,19 @@ __device__ __forceinline__ void tri_decode_f(int e, int& i, int& j) {
 // L^-1's in the next pass A), and r0 = 1/d0, r1 = 1/d1, the unscaled a10, l10 and the
 // pivots' square roots at true scale (sqrt(d) usc) to pv for the step that uses them;
 // with Lg the step's entries of L D^(1/2) on and next to the diagonal are emitted.  A
-// pivot that is not positive marks the factorisation bad and continues with 1.
+// pivot that is not positive marks the factorisation bad and continues with 1.  nT, nL:
+// the triangle's and Lg's element counts for the check build's index checks (record chk).
 __device__ __forceinline__ void dw_pivot_pair(float2 a00, float2 a10, float2 a11, bool two, float2* T, int j,
-                                               float2* pv, int* s_bad, float2* Lg, float usc) {
+                                               float2* pv, int* s_bad, float2* Lg, float usc, int nT = 0,
+                                               int nL = 0, long long* chk = nullptr) {
   int bad = !(a00.x > 0.0f);
   if (bad) a00 = make_float2(1.0f, 0.0f);
   const float2 r0 = dw_recip(a00);
   float2 sq0 = dw_sqrt(a00);
   sq0 = make_float2(sq0.x * usc, sq0.y * usc);
-  T[prow(j) + j] = a00;
+  if (PTA_IN(chk, prow(j) + j, nT, kChkSweepT)) T[prow(j) + j] = a00;
   const int tj = j * (j + 1) / 2;
-  if (Lg) Lg[tj + j] = sq0;
+  if (Lg && PTA_IN(chk, tj + j, nL, kChkSweepLg)) Lg[tj + j] = sq0;
   if (two) {
     const float2 l10 = dw_mul(a10, r0);
     float2 d1 = dw_fms(a11, l10, a10);
@@ -83,8 +86,8 @@ __device__ __forceinline__ void dw_pivot_pair(float2 a00, float2 a10, float2 a11
     }
     float2 sq1 = dw_sqrt(d1);
     sq1 = make_float2(sq1.x * usc, sq1.y * usc);
-    T[prow(j + 1) + j + 1] = d1;
-    if (Lg) {
+    if (PTA_IN(chk, prow(j + 1) + j + 1, nT, kChkSweepT)) T[prow(j + 1) + j + 1] = d1;
+    if (Lg && PTA_IN(chk, tj + 2 * j + 2, nL, kChkSweepLg)) {
       Lg[tj + 2 * j + 1] = dw_mul(l10, sq0);  // (j+1, j)
       Lg[tj + 2 * j + 2] = sq1;           // (j+1, j+1)
     }
@@ -111,16 +114,21 @@ __device__ __forceinline__ void dw_pivot_pair(float2 a00, float2 a10, float2 a11
 // packed-lower index -> (row << 8) | column for the ((np-1)/2 + 1) ((np-1)/2 + 2) / 2 tiles
 // of the largest trailing triangle, or nullptr to decode by a square root.  Called by every
 // thread of the block after a barrier that follows the fill of T; returns after a barrier.
+// chk: the check build's index-check record (bounds: prow(np) triangle elements, nh staging
+// entries per array, np (np + 1) / 2 elements of Lg).
 __device__ __forceinline__ void dw_ldl_sweep(int np, float2* T, float4* stage, float2* pv, int* s_bad,
-                                           const unsigned short* trimap, float2* Lg, float usc) {
+                                           const unsigned short* trimap, float2* Lg, float usc,
+                                           long long* chk = nullptr) {
   const int tid = threadIdx.x, nt = blockDim.x, nh = np / 2 + 1;
+  const int nTri = prow(np), nL = np * (np + 1) / 2;
   float4* plE = stage;     // [nh] (l_ij, l_i,j+1) of rows j+2+e, e even (index e/2)
   float4* plO = plE + nh;  // e odd
   float4* uuE = plO + nh;  // [nh] unscaled (u_j, u_j+1) of columns j+2+f, f even
   float4* uuO = uuE + nh;  // f odd
   float4* xrE = uuO + nh;  // [nh] (X_jc, X_j+1,c), c even
   float4* xrO = xrE + nh;  // c odd
-  if (tid == 0) dw_pivot_pair(T[0], np > 1 ? T[2] : T[0], np > 1 ? T[3] : T[0], np > 1, T, 0, pv, s_bad, Lg, usc);
+  if (tid == 0)
+    dw_pivot_pair(T[0], np > 1 ? T[2] : T[0], np > 1 ? T[3] : T[0], np > 1, T, 0, pv, s_bad, Lg, usc, nTri, nL, chk);
   __syncthreads();
   for (int j = 0; j + 1 < np; j += 2) {
     const float2 r0 = pv[0], r1 = pv[1], a10 = pv[2], l10 = pv[3], sq0 = pv[4], sq1 = pv[5];
@@ -130,23 +138,27 @@ __device__ __forceinline__ void dw_ldl_sweep(int np, float2* T, float4* stage, f
       if (e < s2) {
         const int i = j + 2 + e;
         float4* ap = reinterpret_cast<float4*>(T + prow(i) + j);
-        const float4 a = *ap;
+        const bool ok = PTA_IN(chk, prow(i) + j + 1, nTri, kChkSweepT) && PTA_IN(chk, e >> 1, nh, kChkSweepStage);
+        const float4 a = ok ? *ap : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         const float2 a0 = make_float2(a.x, a.y);
         const float2 l0 = dw_mul(a0, r0);
         const float2 w = dw_fms(make_float2(a.z, a.w), l0, a10);
         const float2 l1 = dw_mul(w, r1);
         const float4 pl = make_float4(l0.x, l0.y, l1.x, l1.y);
-        *ap = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // L^-1's entries (i, j), (i, j+1) start at 0
-        if (Lg) {
-          const int ti = i * (i + 1) / 2 + j;
-          Lg[ti] = dw_mul(l0, sq0);
-          Lg[ti + 1] = dw_mul(l1, sq1);
+        if (ok) {
+          *ap = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // L^-1's entries (i, j), (i, j+1) start at 0
+          if (Lg && PTA_IN(chk, i * (i + 1) / 2 + j + 1, nL, kChkSweepLg)) {
+            const int ti = i * (i + 1) / 2 + j;
+            Lg[ti] = dw_mul(l0, sq0);
+            Lg[ti + 1] = dw_mul(l1, sq1);
+          }
+          (e & 1 ? plO : plE)[e >> 1] = pl;
+          (e & 1 ? uuO : uuE)[e >> 1] = make_float4(a0.x, a0.y, w.x, w.y);
         }
-        (e & 1 ? plO : plE)[e >> 1] = pl;
-        (e & 1 ? uuO : uuE)[e >> 1] = make_float4(a0.x, a0.y, w.x, w.y);
       } else {
         const int c = e - s2;  // 0 .. j+1: row j+1 of L^-1 and the staged rows j, j+1
         float2 xj = make_float2(0.0f, 0.0f), x1 = make_float2(1.0f, 0.0f);
+        if (!PTA_IN(chk, rj1 + c, nTri, kChkSweepT) || !PTA_IN(chk, c >> 1, nh, kChkSweepStage)) continue;
         if (c < j) {
           xj = T[rj + c];
           x1 = dw_fms(T[rj1 + c], l10, xj);
@@ -177,6 +189,9 @@ __device__ __forceinline__ void dw_ldl_sweep(int np, float2* T, float4* stage, f
           tri_decode_f(t, I, L);
         }
         const int i0 = j + 2 + 2 * I, c0 = j + 2 + 2 * L;
+        if (!PTA_IN(chk, I, nh, kChkSweepStage) || !PTA_IN(chk, L, nh, kChkSweepStage) ||
+            !PTA_IN(chk, (2 * I + 1 < s2 ? (i0 + 2) * (i0 + 2) / 2 : i0 * (i0 + 2) / 2) + c0 + 1, nTri, kChkSweepT))
+          continue;
         const float4 p0 = plE[I], p1 = plO[I], q0 = uuE[L], q1 = uuO[L];
         float4* r0p = reinterpret_cast<float4*>(T + i0 * (i0 + 2) / 2 + c0);
         float4 v0 = *r0p;
@@ -192,13 +207,16 @@ __device__ __forceinline__ void dw_ldl_sweep(int np, float2* T, float4* stage, f
         }
         if (t == 0)
           dw_pivot_pair(make_float2(v0.x, v0.y), make_float2(v1.x, v1.y), make_float2(v1.z, v1.w), row1, T, j + 2,
-                         pv, s_bad, Lg, usc);
+                         pv, s_bad, Lg, usc, nTri, nL, chk);
       } else {
         const int e = t - cntT;
         int q = (int)(((float)e + 0.5f) * rw);
         q -= (q * W > e);
         q += ((q + 1) * W <= e);
         const int cc = e - q * W, i0 = j + 2 + 2 * q, c0 = 2 * cc;
+        if (!PTA_IN(chk, q, nh, kChkSweepStage) || !PTA_IN(chk, cc, nh, kChkSweepStage) ||
+            !PTA_IN(chk, (2 * q + 1 < s2 ? (i0 + 2) * (i0 + 2) / 2 : i0 * (i0 + 2) / 2) + c0 + 1, nTri, kChkSweepT))
+          continue;
         const float4 p0 = plE[q], p1 = plO[q], q0 = xrE[cc], q1 = xrO[cc];
         float4* r0p = reinterpret_cast<float4*>(T + i0 * (i0 + 2) / 2 + c0);
         float4 v0 = *r0p;

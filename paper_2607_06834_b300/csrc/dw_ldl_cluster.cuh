@@ -12,6 +12,7 @@
 #include <stdint.h>
 
 #include "dw_ldl.cuh"
+#include "pta_check.cuh"
 
 namespace pta {
 
@@ -114,10 +115,13 @@ __device__ __forceinline__ void dwc_pivot(float2 a00, float2 a10, float2 a11, bo
 // staging that other CTAs write alternates between two sets, so a CTA that runs a step ahead
 // never overwrites what a slower one still reads.  Called by every thread of every CTA of the
 // cluster after the fill of T (it begins with a cluster barrier); returns after a barrier of
-// its own CTA.
+// its own CTA.  chk: the check build's index-check record (bounds: cpart<C>(np, k) elements of
+// T, nh entries per staging array).
 template <int C>
-__device__ __forceinline__ void dwc_ldl_sweep(int np, float2* T, float4* stage, float2* pv, int* s_bad) {
+__device__ __forceinline__ void dwc_ldl_sweep(int np, float2* T, float4* stage, float2* pv, int* s_bad,
+                                              long long* chk = nullptr) {
   const int tid = threadIdx.x, nt = blockDim.x, nh = np / 2 + 1, k = cl_rank(), npairs = (np + 1) >> 1;
+  const int nPart = cpart<C>(np, k);
   float4* plE = stage;     // [nh] (l_ij, l_i,j+1) of this CTA's rows j+2+e, e even (index e/2)
   float4* plO = plE + nh;  // e odd
   float4* pv4 = reinterpret_cast<float4*>(pv);
@@ -152,7 +156,8 @@ __device__ __forceinline__ void dwc_ldl_sweep(int np, float2* T, float4* stage, 
     for (int t = tid; t < nA; t += nt) {
       if (t < 2 * nr) {
         const int i = 2 * (rf + C * (t >> 1)) + (t & 1);
-        if (i < np) {
+        if (i < np && PTA_IN(chk, crow<C>(i) + j + 3, nPart, kChkClusterT) &&
+            PTA_IN(chk, (i - j - 2) >> 1, nh, kChkClusterStage)) {
           const int e = i - j - 2;
           float4* ap = reinterpret_cast<float4*>(T + crow<C>(i) + j);
           const float4 a = *ap;
@@ -172,6 +177,7 @@ __device__ __forceinline__ void dwc_ldl_sweep(int np, float2* T, float4* stage, 
       } else {
         const int c = t - 2 * nr;  // 0 .. j+1
         const int rj = crow<C>(j), rj1 = crow<C>(j + 1);
+        if (!PTA_IN(chk, rj1 + c, nPart, kChkClusterT) || !PTA_IN(chk, c >> 1, nh, kChkClusterStage)) continue;
         float2 xj = make_float2(0.0f, 0.0f), x1 = make_float2(1.0f, 0.0f);
         if (c < j) {
           xj = T[rj + c];
@@ -204,6 +210,9 @@ __device__ __forceinline__ void dwc_ldl_sweep(int np, float2* T, float4* stage, 
       const int r = rf + C * u, I = r - R0, i0 = 2 * r;
       const int b0 = crow<C>(i0), b1 = b0 + 2 * (r + 1);
       const bool row1 = i0 + 1 < np;
+      if (!PTA_IN(chk, I, nh, kChkClusterStage) || !PTA_IN(chk, s <= I ? s : s - I - 1, nh, kChkClusterStage) ||
+          !PTA_IN(chk, (row1 ? b1 : b0) + (s <= I ? j + 2 + 2 * s : 2 * (s - I - 1)) + 1, nPart, kChkClusterT))
+        continue;
       const float4 p0 = plE[I], p1 = plO[I];
       float4 q0, q1;
       int c0;

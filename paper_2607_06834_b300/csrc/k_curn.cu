@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kCTdw)
     if (i == j && !(i & 1)) A[q + 1] = make_float2(0.0f, 0.0f);
   }
   __syncthreads();
-  dw_ldl_sweep(P, A, smq, pv, &s_bad, nullptr, nullptr, 1.0f);
+  dw_ldl_sweep(P, A, smq, pv, &s_bad, nullptr, nullptr, 1.0f, m.chk);
   // 1 / sqrt(d_i) at the true scale, g and z in reversed order (the staging area is free)
   float2* rqw = reinterpret_cast<float2*>(smq);  // [P]
   float2* gpw = rqw + P;                          // [P] g'
@@ -393,7 +393,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NT, 1024 / NT)
   const float sc = __int_as_float((127 - E) << 23);
   for (int rr = wp; rr < nrow; rr += nw) {  // a warp per row
     const int i = 2 * (k + C * (rr >> 1)) + (rr & 1);
-    if (i >= P) continue;
+    if (i >= P || !PTA_IN(m.chk, crow<C>(i) + i + ((i & 1) ? 0 : 1), cpart<C>(P, k), kChkClusterT)) continue;
     float2* row = T + crow<C>(i);
     const float2* Gi = G + i * (i + 1) / 2;
     for (int c = lane; c <= i; c += 32) {
@@ -403,7 +403,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NT, 1024 / NT)
     }
     if (!(i & 1) && lane == 0) row[i + 1] = make_float2(0.0f, 0.0f);
   }
-  dwc_ldl_sweep<C>(P, T, smq, pv, &s_bad);
+  dwc_ldl_sweep<C>(P, T, smq, pv, &s_bad, m.chk);
   float2* rqw = reinterpret_cast<float2*>(smq);  // [P] (this CTA's rows)
   float2* gpw = rqw + P;
   float2* zpw = gpw + P;
@@ -472,6 +472,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NT, 1024 / NT)
     const int i = 2 * (k + C * (rr >> 1)) + (rr & 1);
     if (i >= P) continue;
     const float2* row = T + crow<C>(i);
+    if (!PTA_IN(m.chk, i * (i + 1) / 2 + i, P * (P + 1) / 2, kChkWslot)) continue;
     for (int c = lane; c <= i; c += 32) Wslot[i * (i + 1) / 2 + c] = row[c];
   }
   cl_sync();  // every CTA's column sums and log det part are in place

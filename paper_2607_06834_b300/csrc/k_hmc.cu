@@ -23,6 +23,7 @@ int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* gr
                       cudaStream_t st);
 int pta_prepare_internal(pta_ctx* c, int B);
 int pta_ensure_bounds(pta_ctx* c);
+int pta_check_result(pta_ctx* c, cudaStream_t st);
 
 namespace pta {
 namespace {
@@ -302,5 +303,5 @@ extern "C" int pta_hmc_trajectory(pta_ctx* c, int B, float* x, double* logp, flo
     c->err = std::string("hmc launch: ") + cudaGetErrorString(e);
     return PTA_ECUDA;
   }
-  return PTA_OK;
+  return pta_check_result(c, st);
 }

@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(512, 4)  // 32 registers: 8 CTAs of 256 thread
   float2* Lg = Lpk + ((size_t)b * m.n_chol + k) * ntri;
   float2* Xg = Lipk + ((size_t)b * m.n_chol + k) * ntri;
   const float usc = __int_as_float((127 + E / 2) << 23);  // 2^(E/2): sqrt of the true pivots
-  dw_ldl_sweep(np, T, smq, pv, &s_bad, m.trimap, Lg, usc);
+  dw_ldl_sweep(np, T, smq, pv, &s_bad, m.trimap, Lg, usc, m.chk);
   if (s_bad && tid == 0) atomicOr(&stat[b], 2);
   // 1/sqrt(d_j) at true scale and z (the staging area is free now)
   float2* rqw = reinterpret_cast<float2*>(smq);  // [np]

@@ -446,6 +446,8 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
   const int cb = blockIdx.x, u = blockIdx.y, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int I = m.unit_psr[u], start = m.unit_start[u], len = m.unit_len[u];
   const int KXM = m.x16_kxm, KX = kx_of(m, I), nkc = KX / KCB, ntile = len / TTA, G = ntile * nkc;
+  const bool unit_ok = PTA_IN(m.chk, start - m.toa_off[I], m.n_pad[I] - len + 1, kChkUnit) &&
+                       PTA_ALIGNED(m.chk, start - m.toa_off[I], TTA, kChkUnit);
   const int b0 = cb * NC, nvalid = min(NC, B - b0);
   const size_t csz = 4 * (size_t)KXM * NC * 2;
   constexpr int CSL = 2 * 4 * NC * 16;                              // coefficient slice of one 16-column step
@@ -534,8 +536,15 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
         mbar_expect_tx(&xfull[s], kb * STB);
         for (int h = 0; h < kb; ++h) {
           const int gb = kb * g + h;  // stored block: (tile gb / nkc, column block gb % nkc)
-          bulk_g2s(Xs + s * STG + h * STB, xsrc + (size_t)gb * RES_XSB, RES_XSB, &xfull[s]);
-          bulk_g2s(Xs + s * STG + h * STB + RES_XSB, csrc + (size_t)(gb % nkc) * CSL, CSL, &xfull[s]);
+          if (unit_ok &&
+              PTA_IN(m.chk, (start - m.toa_off[I]) / TTA * nkc + gb, m.n_pad[I] / TTA * nkc, kChkResBasis) &&
+              PTA_IN(m.chk, (size_t)(gb % nkc) * CSL + CSL - 1, csz, kChkResCoef) &&
+              PTA_ALIGNED(m.chk, reinterpret_cast<uintptr_t>(xsrc + (size_t)gb * RES_XSB), 16, kChkBulkAlign) &&
+              PTA_ALIGNED(m.chk, reinterpret_cast<uintptr_t>(csrc + (size_t)(gb % nkc) * CSL), 16, kChkBulkAlign) &&
+              PTA_ALIGNED(m.chk, tc::smem_u32(Xs + s * STG + h * STB), 16, kChkBulkAlign)) {
+            bulk_g2s(Xs + s * STG + h * STB, xsrc + (size_t)gb * RES_XSB, RES_XSB, &xfull[s]);
+            bulk_g2s(Xs + s * STG + h * STB + RES_XSB, csrc + (size_t)(gb % nkc) * CSL, CSL, &xfull[s]);
+          }
         }
       }
       // no copy in flight into this CTA's shared memory at exit (bounded waits)
@@ -839,9 +848,15 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
       if (g >= NSM && !(wait(&wread[s], ((g / NSM) - 1) & 1) && wait(&xfree[s], ((g / NSM) - 1) & 1))) break;
       const int toa = g * KWB, tau = tau0 + toa / TTA, tsub = toa % TTA;
       mbar_expect_tx(&wland[s], FW_WSB);
-      for (int h = 0; h < KWB / 32; ++h) tma_2d(wsm + s * FW_WSB + h * FW_WHB, &tw, start + toa + 32 * h, b0, &wland[s]);
+      for (int h = 0; h < KWB / 32; ++h)
+        if (PTA_ALIGNED(m.chk, start + toa + 32 * h, 4, kChkTmaX) &&
+            PTA_IN(m.chk, start + toa + 32 * h + 31, m.ntoa_pad, kChkTmaRange) &&
+            PTA_IN(m.chk, start + toa + 32 * h - m.toa_off[I], m.n_pad[I], kChkUnit))
+          tma_2d(wsm + s * FW_WSB + h * FW_WHB, &tw, start + toa + 32 * h, b0, &wland[s]);
       mbar_expect_tx(&xfull[s], FW_XST);
-      tma_4d(smem + s * FW_XST, &tx, 8 * tsub, 0, blk0 + tau * nkc, 0, &xfull[s]);
+      if (PTA_ALIGNED(m.chk, 8 * tsub, 8, kChkTmaX) && PTA_IN(m.chk, 8 * tsub + 255, 8 * TTA, kChkTmaRange) &&
+          PTA_IN(m.chk, tau * nkc + q0 / KCB, m.n_pad[I] / TTA * nkc, kChkResBasis))
+        tma_4d(smem + s * FW_XST, &tx, 8 * tsub, 0, blk0 + tau * nkc, 0, &xfull[s]);
     }
     // no copy in flight into this CTA's shared memory at exit (bounded waits)
     for (int h = max(0, g - NSM); h < g; ++h) {

@@ -558,6 +558,13 @@ int pta_finalize(pta_ctx* c, void* stream) {
     if (cudaDeviceGetAttribute(&m.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || m.nsm < 1) m.nsm = 1;
   }
   UP(Gam, Gamma);
+  {  // the index-check record (read only by the check build)
+    long long* rec = nullptr;
+    if (cudaMalloc(&rec, 4 * sizeof(long long)) != cudaSuccess || cudaMemset(rec, 0, 4 * sizeof(long long)) != cudaSuccess)
+      return fail(c, PTA_ENOMEM, "finalize: index-check record");
+    c->dev_allocs.push_back(rec);
+    m.chk = rec;
+  }
   {
     std::vector<float2> gdw((size_t)npsr * (npsr + 1) / 2);
     for (int i = 0, q = 0; i < npsr; ++i)
@@ -876,6 +883,33 @@ int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* gr
   return pta_eval_scratch(c, c->sc, B, x, logp, grad, status, st, profile);
 }
 
+// The check build (nvcc -DPTA_CHECK): after a public call's launches, wait for them and report
+// the first failed index check (PTA_ECHECK with the site, value and limit in pta_last_error),
+// clearing the record.  The release build returns PTA_OK without touching the device.
+int pta_check_result(pta_ctx* c, cudaStream_t st) {
+#ifdef PTA_CHECK
+  long long rec[3] = {0, 0, 0};
+  if (cudaMemcpyAsync(rec, c->dm.chk, sizeof rec, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(c, PTA_ECUDA, "index-check record: read failed");
+  if (rec[0] != 0) {
+    static const char* const names[pta::kChkCount] = {
+        "none", "LDL sweep triangle", "LDL sweep staging", "LDL sweep L D^1/2 output", "cluster sweep triangle part",
+        "cluster sweep staging", "work unit TOA range", "exact-split basis block", "exact-split coefficient slice",
+        "bulk copy alignment", "TMA innermost coordinate alignment", "TMA coordinate range", "CURN inverse factor slot"};
+    const int site = (int)rec[0];
+    cudaMemsetAsync(c->dm.chk, 0, sizeof rec, st);
+    cudaStreamSynchronize(st);
+    return fail(c, PTA_ECHECK, std::string("index check failed: ") + (site > 0 && site < pta::kChkCount ? names[site] : "?") +
+                                   ", value " + std::to_string(rec[1]) + " outside [0, " + std::to_string(rec[2]) + ")");
+  }
+#else
+  (void)c;
+  (void)st;
+#endif
+  return PTA_OK;
+}
+
 int pta_eval_internal(pta_ctx* c, int B, const float* x, double* logp, float* grad, int32_t* status,
                       cudaStream_t st) {
   return pta_eval_scratch(c, c->sc, B, x, logp, grad, status, st, false);
@@ -1174,7 +1208,8 @@ int pta_logp_and_grad(pta_ctx* c, int B, const float* x, double* logp, float* gr
                 "the continuous-wave model runs on the FP32 and exact-split paths (PTA_PREC_FP32, PTA_PREC_F16SPLIT)");
   int rc = pta_prepare_internal(c, B);
   if (rc != PTA_OK) return rc;
-  return pta_eval_internal(c, B, x, logp, grad, status, (cudaStream_t)stream, true);
+  rc = pta_eval_internal(c, B, x, logp, grad, status, (cudaStream_t)stream, true);
+  return rc == PTA_OK ? pta_check_result(c, (cudaStream_t)stream) : rc;
 }
 
 int pta_logp_constant(const pta_ctx* c, double* out) {

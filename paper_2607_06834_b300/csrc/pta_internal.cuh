@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/ptahmc.h"
+#include "pta_check.cuh"
 
 namespace pta {
 
@@ -56,6 +57,7 @@ struct DevModel {
   int nthr;                     // red-noise parameters per pulsar (2, or n_rn when free)
   const double* beta;           // per-chain inverse temperature (App. "tempered likelihoods"); nullptr: 1
   int inject;                   // test hook (pta_debug_inject): 1 = the BF16 kernel withholds one MMA completion
+  long long* chk;               // index-check record of the check build (site, value, limit); unused otherwise
   const float* Gth;
   const float* Gtl;
   const double* g2;

@@ -22,6 +22,7 @@
 
 #include "pta_internal.cuh"
 
+int pta_check_result(pta_ctx* c, cudaStream_t st);
 int pta_eval_scratch(pta_ctx* c, const pta::Scratch& s, int B, const float* x, double* logp, float* grad,
                      int32_t* status, cudaStream_t st, bool profile);
 
@@ -151,5 +152,6 @@ extern "C" int pta_logp_and_grad_noalloc(pta_ctx* c, int B, const float* x, doub
   s.queue = (int*)take(16);
   // Run the same kernel sequence as pta_logp_and_grad on this workspace; the
   // context's own scratch is not touched.
-  return pta_eval_scratch(c, s, B, x, logp, grad, status, (cudaStream_t)stream, false);
+  const int rc = pta_eval_scratch(c, s, B, x, logp, grad, status, (cudaStream_t)stream, false);
+  return rc == PTA_OK ? pta_check_result(c, (cudaStream_t)stream) : rc;
 }

@@ -26,6 +26,22 @@ def test_header_symbols_exported():
     assert set(names) == set(abi.EXPORTED)
 
 
+def test_check_build_exports_and_error_codes():
+    """the check build (libptahmc_check.so) exports the same entry points; the error codes of
+    the binding are the header's"""
+    from paper_2607_06834_b300 import build
+    if not os.path.exists(build.LIB_CHECK):
+        pytest.skip("check build not built")
+    lib = C.CDLL(build.LIB_CHECK)
+    for n in declared_symbols():
+        assert hasattr(lib, n), n
+    hdr = open(os.path.join(ROOT, "include", "ptahmc.h")).read()
+    codes = {k: int(v) for k, v in re.findall(r"#define (PTA_E[A-Z]+|PTA_OK) \(?(-?\d+)\)?", hdr)}
+    for k, v in codes.items():
+        assert getattr(abi, k) == v, k
+    assert codes["PTA_ECHECK"] == -6
+
+
 def _ctx(**kw):
     d = abi.ModelDesc(kw.get("n_gwb", 2), kw.get("n_rn", 2), kw.get("n_dm", 0), 0, 1, 0.0)
     h = C.c_void_p()
