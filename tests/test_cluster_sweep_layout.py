@@ -205,3 +205,22 @@ def test_cluster_tile_decode_exact(C, P):
             u, s = decode(t, n0, C)
             want_u = np.repeat(np.arange(nr), lens)
             assert np.array_equal(u, want_u) and np.array_equal(s, t - start[want_u])
+
+
+def test_curn_kernel_choice_follows_the_shared_memory_rule():
+    """the benchmark's mirror of the library's choice of CURN forward kernel: one CTA while the
+    padded triangle and the staging fit 226 KB, else the smallest cluster (2, 4, 8) whose largest
+    part, the double-buffered staging and the column sums fit, else FP64"""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    lim = 226 * 1024
+    for P in range(2, 700, 2):
+        prow = P * (P + 2) // 2
+        one = 6 * (P // 2 + 1) * 16 + prow * 8 <= lim
+        fits = {C: (10 * (P // 2 + 1) + 8) * 16 + 2 * P * 8 + max(cpart(P, k, C) for k in range(C)) * 8 <= lim
+                for C in (2, 4, 8)}
+        want = 1 if one else next((C for C in (2, 4, 8) if fits[C]), 0)
+        assert bench.curn_factor_mode(P) == want, P
+    assert [bench.curn_factor_mode(P) for P in (232, 234, 314, 316, 430, 432, 582, 584)] == [1, 2, 2, 4, 4, 8, 8, 0]
